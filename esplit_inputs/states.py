@@ -1,0 +1,96 @@
+"""Seeded initial states, laid out as the residual expects: (n_e, n_c, n_p)
+float64 conservative variables [rho, rho V_1..V_d, e], e = p/(gam-1) + rho|V|^2/2
+(Sec. 2.2).
+
+The 2D isentropic vortex follows Sec. 7.3 with two readings of the printed
+formula: the density coefficient is alpha^2 (gam-1) / (16 gam pi^2) (the
+printed "16 gam pi" is a typo; the pi^2 is forced by the radial momentum
+balance of the printed velocity field), and the vortex core sits at
+(x_c + t, y_c) (the printed r^2 uses "+t").  Domain [0, L]^2, centre (L/2, L/2).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def prim_to_cons(rho, V, p, gam=GAMMA):
+    """rho (...), V (d, ...), p (...) -> U (d + 2, ...)."""
+    ke = 0.5 * rho * np.sum(V * V, axis=0)
+    return np.concatenate([rho[None], rho[None] * V, (p / (gam - 1) + ke)[None]], axis=0)
+
+
+def isentropic_vortex_prims(x, y, t=0.0, xc=5.0, yc=5.0, alpha=3.0, gam=GAMMA):
+    dx = x - xc - t
+    dy = y - yc
+    r2 = dx * dx + dy * dy
+    ex = np.exp(1.0 - r2)
+    rho = (1.0 - alpha ** 2 * (gam - 1.0) / (16.0 * gam * np.pi ** 2) * ex * ex) ** (1.0 / (gam - 1.0))
+    p = rho ** gam
+    u = 1.0 - alpha / (2.0 * np.pi) * dy * ex
+    v = alpha / (2.0 * np.pi) * dx * ex
+    return rho, np.stack([u, v]), p
+
+
+def isentropic_vortex(mesh, t=0.0, alpha=3.0, gam=GAMMA):
+    """Vortex of strength alpha centred at the domain centre. Periodic images
+    are left out: on [0, 10]^2 their perturbation is O(e^-24)."""
+    L = mesh.L[0]
+    x, y = mesh.x[:, 0], mesh.x[:, 1]
+    rho, V, p = isentropic_vortex_prims(x, y, t=t, xc=L / 2, yc=L / 2, alpha=alpha, gam=gam)
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))
+
+
+def add_uniform_noise(u, amplitude, seed):
+    """u + amplitude * U(-1, 1), drawn by numpy's PCG64 in C order of u."""
+    rng = np.random.default_rng(seed)
+    return u + amplitude * rng.uniform(-1.0, 1.0, size=u.shape)
+
+
+def random_positive_state(n_e, d, n_p, seed, rho=(0.5, 2.0), vel=(-1.0, 1.0), p=(0.5, 2.0), gam=GAMMA):
+    """Independent random primitive states at every node (well inside the
+    admissible set), returned as conservative variables (n_e, d+2, n_p)."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(*rho, size=(n_e, n_p))
+    V = rng.uniform(*vel, size=(d, n_e, n_p))
+    pr = rng.uniform(*p, size=(n_e, n_p))
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(r, V, pr, gam), 0, 1))
+
+
+def uniform_state(n_e, d, n_p, rho=1.0, V=(0.3, -0.2, 0.1), p=1.0, gam=GAMMA):
+    r = np.full((n_e, n_p), rho)
+    Vv = np.stack([np.full((n_e, n_p), V[i]) for i in range(d)])
+    pr = np.full((n_e, n_p), p)
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(r, Vv, pr, gam), 0, 1))
+
+
+def quadrant_states(mesh, seed, pressure_ratio_max=10.0, gam=GAMMA):
+    """Four piecewise-constant quadrant states on [0, L]^2 (a 2D Riemann-type
+    problem): rho ~ U[0.5, 2], u, v ~ U[-0.5, 0.5], p ~ U[0.2, 2], redrawn
+    until max p / min p <= pressure_ratio_max. A node belongs to the quadrant
+    of its element centroid, so every element is constant."""
+    rng = np.random.default_rng(seed)
+    while True:
+        rho = rng.uniform(0.5, 2.0, 4)
+        vel = rng.uniform(-0.5, 0.5, (2, 4))
+        pr = rng.uniform(0.2, 2.0, 4)
+        if pr.max() / pr.min() <= pressure_ratio_max:
+            break
+    L = mesh.L[0]
+    c = mesh.x.mean(axis=2)
+    q = (c[:, 0] >= L / 2).astype(int) + 2 * (c[:, 1] >= L / 2).astype(int)
+    r = np.repeat(rho[q][:, None], mesh.n_p, 1)
+    V = np.stack([np.repeat(vel[i][q][:, None], mesh.n_p, 1) for i in range(2)])
+    pp = np.repeat(pr[q][:, None], mesh.n_p, 1)
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(r, V, pp, gam), 0, 1))
+
+
+def cfl_timestep(mesh, u, cfl, gam=GAMMA):
+    """Time step of Sec. 7.1: min over elements of CFL * h_min / |lambda|_max,
+    |lambda|_max = max over the element's nodes of |V| + sqrt(gam p / rho)."""
+    rho = u[:, 0]
+    V = u[:, 1:-1] / rho[:, None]
+    p = (gam - 1.0) * (u[:, -1] - 0.5 * rho * np.sum(V * V, axis=1))
+    lam = np.sqrt(np.sum(V * V, axis=1)) + np.sqrt(gam * p / rho)
+    return float(np.min(cfl * mesh.hmin / lam.max(axis=1)))

@@ -1,0 +1,292 @@
+"""Pointwise physics of the oracle (plain PyTorch, float64).
+
+State arrays carry the component index LAST: U (..., n_c) with
+n_c = d + 2, U = [rho, rho V_1..V_d, e] (Sec. 2.2, Eq. (5)).
+
+Pins (tests/test_oracle_physics.py):
+  * W = dS_H/dU by autograd vs the closed form of Eq. (25),
+  * A~_i symmetric (Sec. 2.4) and A~_i W = beta F_i (Eq. (26)),
+  * beta/(beta+1) W^T F_i = V_i S (Eq. (30)), S = beta phi (Eq. (33)),
+  * Sjogreen-Yee flux: consistency, symmetry, Tadmor's condition Eq. (49) on
+    random state pairs (this fixes the reading of the printed Eq. (48)),
+  * exponential average vs brute force in extended precision,
+  * dissipation: X^ S^ X^T = dU/dW at equal states (2D) and A_n X^ = X^ Lambda,
+  * T(W) (Eq. (39)) and W_nc (Eq. (41)) vs the primitive definitions; dT/dW
+    vs the exact derivative of Eq. (39) (the printed Eq. (40) has a sign typo
+    in the momentum entries and a missing alpha in the last entry),
+  * heat-flux-free K~ positive semidefinite (Sec. 5, LDL^T statement).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+DT = torch.float64
+
+
+@dataclass(frozen=True)
+class Params:
+    """Physical and scheme parameters.
+
+    gam   ratio of specific heats (7/5, Sec. 2.2)
+    beta  split parameter; Harten's alpha = -gam - beta (gam - 1) follows from
+          beta = -(gam + alpha)/(gam - 1) (Eq. (16)); beta = 2.5 (Sec. 6.4)
+    R     gas constant (1, Secs. 7.4-7.5); mu dynamic viscosity; Pr Prandtl
+    heat_flux  include the heat flux in the viscous flux
+    """
+
+    gam: float = 1.4
+    beta: float = 2.5
+    R: float = 1.0
+    mu: float = 0.0
+    Pr: float = 0.71
+    heat_flux: bool = True
+
+    @property
+    def alpha(self) -> float:
+        return -self.gam - self.beta * (self.gam - 1.0)
+
+    @property
+    def kappa(self) -> float:
+        # heat conductivity mu c_p / Pr with c_p = gam R / (gam - 1)
+        return self.mu * self.gam * self.R / ((self.gam - 1.0) * self.Pr)
+
+
+def primitives(U, prm: Params):
+    """rho, V (..., d), p from conservative variables (closure of Sec. 2.2)."""
+    rho = U[..., 0]
+    V = U[..., 1:-1] / rho[..., None]
+    p = (prm.gam - 1.0) * (U[..., -1] - 0.5 * rho * (V * V).sum(-1))
+    return rho, V, p
+
+
+def conservative(rho, V, p, prm: Params):
+    e = p / (prm.gam - 1.0) + 0.5 * rho * (V * V).sum(-1)
+    return torch.cat([rho[..., None], rho[..., None] * V, e[..., None]], dim=-1)
+
+
+def harten_entropy(U, prm: Params):
+    """S_H = beta rho (p rho^-gam)^(1/(alpha+gam)), Eq. (16)."""
+    rho, V, p = primitives(U, prm)
+    return prm.beta * rho * (p * rho ** (-prm.gam)) ** (1.0 / (prm.alpha + prm.gam))
+
+
+def entropy_variables(U, prm: Params):
+    """Harten entropy variables, Eq. (25):
+    W = (rho/p)(p rho^-gam)^(1/(alpha+gam)) [-alpha/(gam-1) p/rho - |V|^2/2, V, -1]."""
+    rho, V, p = primitives(U, prm)
+    q = (rho / p) * (p * rho ** (-prm.gam)) ** (1.0 / (prm.alpha + prm.gam))
+    first = -prm.alpha / (prm.gam - 1.0) * p / rho - 0.5 * (V * V).sum(-1)
+    return q[..., None] * torch.cat([first[..., None], V, -torch.ones_like(first)[..., None]], dim=-1)
+
+
+def euler_flux(U, prm: Params):
+    """Inviscid fluxes F^{I(i)} of Eq. (5) for all directions: (..., d, n_c)."""
+    rho, V, p = primitives(U, prm)
+    d = V.shape[-1]
+    e = U[..., -1]
+    out = []
+    for i in range(d):
+        mom = rho[..., None] * V[..., i:i + 1] * V
+        mom = mom + p[..., None] * torch.nn.functional.one_hot(torch.tensor(i), d).to(U)
+        out.append(torch.cat([(rho * V[..., i])[..., None], mom, ((e + p) * V[..., i])[..., None]], -1))
+    return torch.stack(out, dim=-2)
+
+
+def param_vector(U, prm: Params):
+    """Parameter vector z = [(rho/p)(p rho^-gam)^(1/(alpha+gam)), V, p], Eq. (45)."""
+    rho, V, p = primitives(U, prm)
+    z1 = (rho / p) * (p * rho ** (-prm.gam)) ** (1.0 / (prm.alpha + prm.gam))
+    return torch.cat([z1[..., None], V, p[..., None]], dim=-1)
+
+
+def arith_avg(a, b):
+    """{u} = (u_k + u_v)/2, Eq. (46)."""
+    return 0.5 * (a + b)
+
+
+def exp_avg(a, b, r):
+    """Exponential average {u^(r-1)}_e = (u_k^r - u_v^r) / (r (u_k - u_v)), Eq. (47).
+
+    Evaluated as u_k^(r-1) g(eps), eps = u_v/u_k - 1,
+    g(eps) = ((1+eps)^r - 1)/(r eps) = expm1(r log1p(eps)) / (r eps), which is
+    the same quotient without cancellation; g(0) = 1 (limit u_v -> u_k).  The
+    eps == 0 branch keeps the first Taylor term so that autograd returns the
+    correct derivative g'(0) = (r-1)/2 at coincident states."""
+    eps = b / a - 1.0
+    zero = eps == 0
+    safe = torch.where(zero, torch.ones_like(eps), eps)
+    g = torch.expm1(r * torch.log1p(safe)) / (r * safe)
+    g = torch.where(zero, 1.0 + 0.5 * (r - 1.0) * eps, g)
+    return a ** (r - 1.0) * g
+
+
+def sy_flux(Uk, Uv, prm: Params):
+    """Sjogreen-Yee two-point flux F*_i(U_k, U_v), Eq. (48), all directions:
+    returns (..., d, n_c).
+
+    Reading of the printed formula (the one that satisfies Tadmor's condition,
+    Eq. (49), to round-off): {z_1 z_(i+1)} is the arithmetic mean of the
+    product; the averages {z_1^(-gam/alpha)} and {z_nc^(-(gam-1)/alpha)} that
+    carry no subscript e are arithmetic means of the powers; {.}_e terms are
+    the exponential averages of Eq. (47) with r - 1 equal to the printed
+    exponent."""
+    g, a = prm.gam, prm.alpha
+    zk, zv = param_vector(Uk, prm), param_vector(Uv, prm)
+    d = Uk.shape[-1] - 2
+    z1k, z1v, znk, znv = zk[..., 0], zv[..., 0], zk[..., -1], zv[..., -1]
+    Vk, Vv = zk[..., 1:-1], zv[..., 1:-1]
+    den = arith_avg(z1k ** (-g / a), z1v ** (-g / a)) * exp_avg(znk, znv, (1.0 - g - a) / a + 1.0)
+    Vavg = arith_avg(Vk, Vv)
+    ke = (Vavg * Vavg).sum(-1) - 0.5 * arith_avg((Vk * Vk).sum(-1), (Vv * Vv).sum(-1))
+    enth = (g / (g - 1.0)) * arith_avg(znk ** (-(g - 1.0) / a), znv ** (-(g - 1.0) / a)) \
+        * exp_avg(z1k, z1v, -(g + a) / a + 1.0)
+    pavg = arith_avg(znk, znv)
+    out = []
+    for i in range(d):
+        F1 = arith_avg(z1k * Vk[..., i], z1v * Vv[..., i]) / den
+        mom = F1[..., None] * Vavg
+        mom = mom + pavg[..., None] * torch.nn.functional.one_hot(torch.tensor(i), d).to(Uk)
+        Fe = F1 * (enth + ke)
+        out.append(torch.cat([F1[..., None], mom, Fe[..., None]], -1))
+    return torch.stack(out, dim=-2)
+
+
+def _jacobian(fn, U):
+    """Pointwise Jacobian d fn(U) / dU for a batch of states (..., n_c)."""
+    shp = U.shape
+    flat = U.reshape(-1, shp[-1])
+    J = torch.func.vmap(torch.func.jacrev(fn))(flat)
+    return J.reshape(*shp[:-1], *J.shape[1:])
+
+
+def dW_dU(U, prm: Params):
+    return _jacobian(lambda x: entropy_variables(x, prm), U)
+
+
+def dU_dW(U, prm: Params):
+    """A~_0 = dU/dW = (dW/dU)^-1, Eq. (19)."""
+    return torch.linalg.inv(dW_dU(U, prm))
+
+
+def symmetrized_flux_jacobians(U, prm: Params):
+    """A~_i = A_i A~_0 with A_i = dF^{I(i)}/dU (Eq. (19)); returns (..., d, n_c, n_c)."""
+    A = _jacobian(lambda x: euler_flux(x, prm), U)        # (..., d, nc, nc)
+    return A @ dU_dW(U, prm)[..., None, :, :]
+
+
+# ----------------------------------------------------------------------------
+# Matrix interface dissipation ingredients, Sec. 4.5, Eqs. (69), (73)-(80)
+# ----------------------------------------------------------------------------
+
+def dissipation_factors(Uk, Uv, n, prm: Params):
+    """X^ (..., n_c, n_c; columns are the eigenvectors of Eq. (80)), the
+    eigenvalues Lambda_n (..., n_c) of Eq. (79) (signed) and the diagonal of
+    S^ (..., n_c) of Eqs. (76)-(78), at the intermediate state of Eqs.
+    (73)-(75) between U_k and U_v, for unit normal n (..., d).  3D as printed;
+    2D by deleting the fourth row and column."""
+    g, a = prm.gam, prm.alpha
+    zk, zv = param_vector(Uk, prm), param_vector(Uv, prm)
+    d = Uk.shape[-1] - 2
+    z1k, z1v, znk, znv = zk[..., 0], zv[..., 0], zk[..., -1], zv[..., -1]
+    A1 = arith_avg(z1k ** (-g / a), z1v ** (-g / a))
+    E1 = exp_avg(znk, znv, (1.0 - g - a) / a + 1.0)
+    E2 = exp_avg(z1k, z1v, -(g + a) / a + 1.0)
+    z1a = arith_avg(z1k, z1v)
+    rho_h = z1a / (A1 * E1)
+    V_h = arith_avg(z1k[..., None] * zk[..., 1:-1], z1v[..., None] * zv[..., 1:-1]) / z1a[..., None]
+    p_h = arith_avg(znk, znv)
+    theta = rho_h / (p_h * A1 * E1)
+    eta = 1.0 / (z1a * E2 * E1)
+    a_h = torch.sqrt(g * p_h / rho_h)
+    H_h = a_h ** 2 / (g - 1.0) + 0.5 * (V_h * V_h).sum(-1)
+    vn = (V_h * n).sum(-1)
+    one = torch.ones_like(vn)
+    zero = torch.zeros_like(vn)
+    if d == 2:
+        n1, n2 = n[..., 0], n[..., 1]
+        V1, V2 = V_h[..., 0], V_h[..., 1]
+        cols = [
+            torch.stack([one, V1 - a_h * n1, V2 - a_h * n2, H_h - a_h * vn], -1),
+            torch.stack([one, V1, V2, 0.5 * (V_h * V_h).sum(-1)], -1),
+            torch.stack([zero, n2, -n1, V1 * n2 - V2 * n1], -1),
+            torch.stack([one, V1 + a_h * n1, V2 + a_h * n2, H_h + a_h * vn], -1),
+        ]
+        lam = [vn - a_h, vn, vn, vn + a_h]
+        sc = [theta / (2 * g), (g - 1) * (g + a) * theta / (g * a), eta, theta / (2 * g)]
+    else:
+        n1, n2, n3 = n[..., 0], n[..., 1], n[..., 2]
+        V1, V2, V3 = V_h[..., 0], V_h[..., 1], V_h[..., 2]
+        cols = [
+            torch.stack([one, V1 - a_h * n1, V2 - a_h * n2, V3 - a_h * n3, H_h - a_h * vn], -1),
+            torch.stack([one, V1, V2, V3, 0.5 * (V_h * V_h).sum(-1)], -1),
+            torch.stack([zero, n2, -n1, zero, V1 * n2 - V2 * n1], -1),
+            torch.stack([zero, -n3, zero, n1, V3 * n1 - V1 * n3], -1),
+            torch.stack([one, V1 + a_h * n1, V2 + a_h * n2, V3 + a_h * n3, H_h + a_h * vn], -1),
+        ]
+        lam = [vn - a_h, vn, vn, vn, vn + a_h]
+        sc = [theta / (2 * g), (g - 1) * (g + a) * theta / (g * a), eta, eta, theta / (2 * g)]
+    return torch.stack(cols, -1), torch.stack(lam, -1), torch.stack(sc, -1)
+
+
+def dissipation_matrix(Uk, Uv, n, prm: Params):
+    """X^ |Lambda_n| S^ X^T of Eq. (69) (..., n_c, n_c)."""
+    X, lam, sc = dissipation_factors(Uk, Uv, n, prm)
+    return (X * (lam.abs() * sc)[..., None, :]) @ X.transpose(-1, -2)
+
+
+# ----------------------------------------------------------------------------
+# Viscous fluxes, Eq. (5), written in terms of the entropy-variable gradient
+# ----------------------------------------------------------------------------
+
+def temperature(U, prm: Params):
+    rho, V, p = primitives(U, prm)
+    return p / (rho * prm.R)
+
+
+def viscous_flux_from_prim_grads(U, dV, dT, prm: Params):
+    """F^{V(i)} of Eq. (5) from velocity gradients dV (..., d, d) with
+    dV[..., j, k] = dV_k/dx_j and temperature gradient dT (..., d); returns
+    (..., d, n_c)."""
+    rho, V, p = primitives(U, prm)
+    d = V.shape[-1]
+    div = torch.diagonal(dV, dim1=-2, dim2=-1).sum(-1)
+    out = []
+    for i in range(d):
+        # tau_{x_i x_k} = mu (dV_i/dx_k + dV_k/dx_i - 2/3 delta_ik div V)
+        tau = prm.mu * (dV[..., :, i] + dV[..., i, :])
+        tau = tau - prm.mu * (2.0 / 3.0) * div[..., None] * torch.nn.functional.one_hot(torch.tensor(i), d).to(U)
+        energy = (V * tau).sum(-1)
+        if prm.heat_flux:
+            energy = energy + prm.kappa * dT[..., i]
+        out.append(torch.cat([torch.zeros_like(energy)[..., None], tau, energy[..., None]], -1))
+    return torch.stack(out, dim=-2)
+
+
+def viscous_flux_from_w_grads(U, gW, prm: Params):
+    """Sum_j K~_ij dW/dx_j: the viscous flux of Eq. (5) with the primitive
+    gradients obtained from the entropy-variable gradients gW (..., d, n_c)
+    through dV/dW and dT/dW (both dq/dU (dW/dU)^-1 by autograd)."""
+    d = U.shape[-1] - 2
+    Ainv = dU_dW(U, prm)                                         # dU/dW
+    JV = _jacobian(lambda x: primitives(x, prm)[1], U) @ Ainv    # (..., d, nc)
+    JT = _jacobian(lambda x: temperature(x, prm)[..., None], U) @ Ainv  # (..., 1, nc)
+    dV = torch.einsum("...kc,...jc->...jk", JV, gW)              # dV_k/dx_j
+    dT = torch.einsum("...c,...jc->...j", JT[..., 0, :], gW)
+    return viscous_flux_from_prim_grads(U, dV, dT, prm)
+
+
+def viscous_K(U, prm: Params):
+    """K~_ij (..., d, d, n_c, n_c) by probing the linear map dW/dx_j -> F^V_i
+    on unit vectors (exact; the map is linear in the gradient)."""
+    d = U.shape[-1] - 2
+    nc = d + 2
+    K = torch.zeros(*U.shape[:-1], d, d, nc, nc, dtype=U.dtype)
+    for j in range(d):
+        for c in range(nc):
+            gW = torch.zeros(*U.shape[:-1], d, nc, dtype=U.dtype)
+            gW[..., j, c] = 1.0
+            Fv = viscous_flux_from_w_grads(U, gW, prm)          # (..., d, nc)
+            K[..., :, j, :, c] = Fv
+    return K

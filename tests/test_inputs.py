@@ -1,0 +1,129 @@
+"""Pins of the seeded inputs: SBP operators (Def. 1, Sec. 2.1), curved
+periodic meshes (Assumption 1) and the vortex initial state (Sec. 7.3)."""
+import numpy as np
+import pytest
+
+from esplit_inputs import tri_operator, periodic_tri_mesh, states
+from esplit_inputs.sbp import (vandermonde, tri_monomial_integral, solve_tri_quadrature,
+                               _TRI_RULES, monomial_basis)
+
+PS = [1, 2, 3, 4]
+
+
+@pytest.mark.parametrize("p", PS)
+def test_sbp_property_and_accuracy(p):
+    op = tri_operator(p)
+    assert op.n_p == {1: 7, 2: 12, 3: 18, 4: 27}[p]
+    assert np.all(op.H > 0)
+    for j in range(2):
+        # Q + Q^T = E (SBP property)
+        assert np.abs(op.Q[j] + op.Q[j].T - np.diag(op.E[j])).max() < 1e-14
+    V, dV = vandermonde(op.xi, p, np.array([1 / 3, 1 / 3]))
+    for j in range(2):
+        # D exact on P^p (Def. 1, item 1)
+        assert np.abs(op.D[j] @ V - dV[j]).max() < 1e-11
+
+
+@pytest.mark.parametrize("p", PS)
+def test_volume_quadrature_degree(p):
+    op = tri_operator(p)
+    q = op.volume_degree
+    assert q >= 2 * p - 1
+    for i in range(q + 1):
+        for j in range(q + 1 - i):
+            got = np.sum(op.H * op.xi[:, 0] ** i * op.xi[:, 1] ** j)
+            assert abs(got - tri_monomial_integral(i, j)) < 1e-15
+    # interior nodes strictly inside
+    inner = op.xi[3 * (p + 1):]
+    assert np.all(inner > 0) and np.all(inner.sum(1) < 1)
+
+
+@pytest.mark.parametrize("p", PS)
+def test_E_is_boundary_integral(p):
+    """p^T E_xj q = int_dT P Q n_j = int_T d(PQ)/dxi_j for P, Q in P^p (Def. 1, item 3)."""
+    op = tri_operator(p)
+    basis = monomial_basis(p, 2)
+    for j in range(2):
+        for a in basis:
+            for b in basis:
+                e = (a[0] + b[0], a[1] + b[1])
+                val = np.sum(op.E[j] * op.xi[:, 0] ** e[0] * op.xi[:, 1] ** e[1])
+                if j == 0:
+                    ex = e[0] * tri_monomial_integral(e[0] - 1, e[1]) if e[0] > 0 else 0.0
+                else:
+                    ex = e[1] * tri_monomial_integral(e[0], e[1] - 1) if e[1] > 0 else 0.0
+                assert abs(val - ex) < 1e-14
+
+
+def test_tabulated_rule_rederived():
+    """p = 2 (4 equations, 4 unknowns) is re-derived from the moment equations."""
+    x = solve_tri_quadrature(2, 4, ["S21"], tries=20)
+    assert x is not None
+    assert np.allclose(x, _TRI_RULES[2]["x"], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", PS)
+def test_mesh_pairing_and_normals(p):
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 4, 10.0, 0.05)
+    fn = op.facet_nodes.reshape(-1)
+    pe = m.pair[..., 0].reshape(m.n_e, -1)
+    ps = m.pair[..., 1].reshape(m.n_e, -1)
+    xs = m.x[:, :, fn].transpose(0, 2, 1)           # (e, slot, 2)
+    xo = xs[pe, ps]
+    dx = xs - xo
+    dx -= 10.0 * np.round(dx / 10.0)
+    assert np.abs(dx).max() < 1e-13                 # coincident facet nodes (mod L)
+    nu = m.nu.reshape(m.n_e, -1, 2)
+    assert np.abs(nu + nu[pe, ps]).max() < 1e-13    # nu_k = -nu_v
+    # pairing is an involution
+    assert np.all(pe[pe, ps] == np.arange(m.n_e)[:, None])
+    assert np.all(ps[pe, ps] == np.arange(nu.shape[1])[None, :])
+    assert np.all(m.J > 0)
+    assert abs(np.sum(m.J * op.H[None]) - 100.0) < 1e-11
+
+
+@pytest.mark.parametrize("p", PS)
+def test_discrete_metric_identity(p):
+    """sum_j D_xi_j Lam_ij = 0 at every node (Assumption 1)."""
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 3, 10.0, 0.05)
+    for i in range(2):
+        s = sum(np.einsum("mk,ek->em", op.D[j], m.Lam[:, i, j]) for j in range(2))
+        assert np.abs(s).max() < 1e-12
+
+
+def test_affine_mesh_has_constant_metrics():
+    op = tri_operator(2)
+    m = periodic_tri_mesh(op, 3, 10.0, 0.0)
+    assert np.ptp(m.Lam, axis=-1).max() < 1e-13
+
+
+def test_vortex_solves_euler():
+    """The vortex reading (pi^2 coefficient, core at x_c + t) satisfies
+    dU/dt + div F = 0 (central differences, h = 1e-4)."""
+    g = 1.4
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(3.0, 7.0, size=(50, 2))
+    h = 1e-4
+
+    def U(x, y, t):
+        rho, V, p = states.isentropic_vortex_prims(np.array(x), np.array(y), t=t)
+        return states.prim_to_cons(rho, V, p)
+
+    def F(x, y, t, i):
+        u = U(x, y, t)
+        rho = u[0]
+        V = u[1:3] / rho
+        p = (g - 1) * (u[3] - 0.5 * rho * (V * V).sum(0))
+        return np.stack([rho * V[i], rho * V[i] * V[0] + p * (i == 0), rho * V[i] * V[1] + p * (i == 1),
+                         (u[3] + p) * V[i]])
+
+    x, y = pts[:, 0], pts[:, 1]
+    dUdt = (U(x, y, h) - U(x, y, -h)) / (2 * h)
+    div = (F(x + h, y, 0, 0) - F(x - h, y, 0, 0)) / (2 * h) + (F(x, y + h, 0, 1) - F(x, y - h, 0, 1)) / (2 * h)
+    assert np.abs(dUdt + div).max() < 1e-7
+    # the printed 16 gam pi coefficient would not
+    rho_bad = (1 - 9 * 0.4 / (16 * 1.4 * np.pi) * np.exp(2 * (1 - ((x - 5) ** 2 + (y - 5) ** 2)))) ** 2.5
+    rho_ok = U(x, y, 0)[0]
+    assert np.abs(rho_bad - rho_ok).max() > 1e-2

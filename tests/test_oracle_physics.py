@@ -1,0 +1,225 @@
+"""Pins of oracle/physics.py against identities the paper states (Secs. 2-5)."""
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.physics import (Params, primitives, conservative, harten_entropy, entropy_variables,
+                            euler_flux, sy_flux, exp_avg, symmetrized_flux_jacobians, dU_dW,
+                            dissipation_matrix, dissipation_factors, viscous_K, temperature, _jacobian)
+
+P = Params()
+DT = torch.float64
+
+
+def rand_states(n, d, seed, lo=0.3):
+    g = torch.Generator().manual_seed(seed)
+    rho = lo + 2 * torch.rand(n, generator=g, dtype=DT)
+    V = 2 * torch.rand(n, d, generator=g, dtype=DT) - 1
+    p = lo + 2 * torch.rand(n, generator=g, dtype=DT)
+    return conservative(rho, V, p, P)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_entropy_variables_are_gradient(d):
+    """W^T = dS_H/dU (Eq. (17)) with S_H of Eq. (16) vs the closed form Eq. (25)."""
+    U = rand_states(64, d, 1).requires_grad_(True)
+    S = harten_entropy(U, P).sum()
+    (g,) = torch.autograd.grad(S, U)
+    W = entropy_variables(U.detach(), P)
+    assert torch.allclose(g, W, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_symmetrized_jacobians(d):
+    """A~_i symmetric (Sec. 2.4) and A~_i W = beta F_i (Eq. (26))."""
+    U = rand_states(32, d, 2)
+    At = symmetrized_flux_jacobians(U, P)
+    assert (At - At.transpose(-1, -2)).abs().max() < 1e-12 * At.abs().max()
+    W = entropy_variables(U, P)
+    F = euler_flux(U, P)
+    AW = torch.einsum("nicd,nd->nic", At, W)
+    assert (AW - P.beta * F).abs().max() < 1e-12 * F.abs().max()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_potential_identities(d):
+    """beta/(beta+1) W^T F_i = V_i S (Eq. (30)); S = beta phi, phi = W^T U - S (Eqs. (22), (33))."""
+    U = rand_states(64, d, 3)
+    W = entropy_variables(U, P)
+    S = harten_entropy(U, P)
+    F = euler_flux(U, P)
+    rho, V, p = primitives(U, P)
+    lhs = P.beta / (P.beta + 1) * torch.einsum("nc,nic->ni", W, F)
+    assert torch.allclose(lhs, V * S[:, None], rtol=1e-12, atol=1e-13)
+    phi = (W * U).sum(-1) - S
+    assert torch.allclose(S, P.beta * phi, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_sy_flux_consistency_symmetry(d):
+    Uk, Uv = rand_states(200, d, 4), rand_states(200, d, 5)
+    assert torch.allclose(sy_flux(Uk, Uk, P), euler_flux(Uk, P), rtol=1e-13, atol=1e-13)
+    assert torch.allclose(sy_flux(Uk, Uv, P), sy_flux(Uv, Uk, P), rtol=1e-14, atol=1e-14)
+    # near-coincident states: continuity into the consistent flux
+    Un = Uk * (1 + 1e-9)
+    assert torch.allclose(sy_flux(Uk, Un, P), euler_flux(Uk, P), rtol=1e-7, atol=1e-8)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_sy_flux_tadmor(d):
+    """Tadmor's condition, Eq. (49): (W'' - W')^T F*_i = psi_i'' - psi_i',
+    psi_i = W^T F_i - V_i S (Eq. (23)), on 10^4 random state pairs."""
+    Ua, Ub = rand_states(10000, d, 6), rand_states(10000, d, 7)
+    Fs = sy_flux(Ua, Ub, P)
+    Wa, Wb = entropy_variables(Ua, P), entropy_variables(Ub, P)
+
+    def psi(U):
+        W = entropy_variables(U, P)
+        rho, V, p = primitives(U, P)
+        return torch.einsum("nc,nic->ni", W, euler_flux(U, P)) - V * harten_entropy(U, P)[:, None]
+
+    lhs = torch.einsum("nc,nic->ni", Wb - Wa, Fs)
+    rhs = psi(Ub) - psi(Ua)
+    scale = (torch.einsum("nc,nic->ni", Wb.abs() + Wa.abs(), Fs.abs()))
+    assert ((lhs - rhs).abs() / scale).max() < 1e-13
+
+
+def test_exp_avg_extended_precision():
+    getcontext().prec = 60
+    rng = np.random.default_rng(8)
+    for r in [1.0 / 6.0, 7.0 / 12.0, -0.5, 2.5]:
+        a = rng.uniform(0.2, 3.0, 300)
+        eps = 10.0 ** rng.uniform(-15, 0, 300) * rng.choice([-0.9, 0.9], 300)
+        b = a * (1 + eps)
+        got = exp_avg(torch.tensor(a), torch.tensor(b), r).numpy()
+        for ai, bi, gi in zip(a, b, got):
+            A, B, R = Decimal(float(ai)), Decimal(float(bi)), Decimal(r)
+            ex = (A ** R - B ** R) / (R * (A - B))
+            assert abs(Decimal(float(gi)) - ex) / abs(ex) < Decimal(8e-16)
+    # coincident states: the limit a^(r-1)
+    a = torch.tensor([0.7, 1.3])
+    assert torch.allclose(exp_avg(a, a, 0.3), a ** (-0.7), rtol=1e-15)
+
+
+def _nhat(n, d, seed):
+    g = torch.Generator().manual_seed(seed)
+    v = torch.randn(n, d, generator=g, dtype=DT)
+    return v / torch.linalg.norm(v, dim=-1, keepdim=True)
+
+
+def test_dissipation_scaling_2d():
+    """Barth scaling: X^ S^ X^T = dU/dW at coincident states (Sec. 4.5, 2D)."""
+    U = rand_states(200, 2, 9)
+    n = _nhat(200, 2, 10)
+    X, lam, sc = dissipation_factors(U, U, n, P)
+    A0 = dU_dW(U, P)
+    got = X @ torch.diag_embed(sc) @ X.transpose(-1, -2)
+    assert ((got - A0).abs().amax((-1, -2)) / A0.abs().amax((-1, -2))).max() < 1e-12
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dissipation_eigenvectors(d):
+    """A_n X^ = X^ Lambda_n (Eqs. (79)-(80)) at coincident states, n_1 != 0."""
+    U = rand_states(100, d, 16)
+    n = _nhat(100, d, 17)
+    X, lam, sc = dissipation_factors(U, U, n, P)
+    for k in range(100):
+        nk = n[k]
+        Ak = torch.func.jacrev(lambda x: torch.einsum("ic,i->c", euler_flux(x, P), nk))(U[k])
+        assert (Ak @ X[k] - X[k] * lam[k]).abs().max() < 1e-12 * (1 + Ak.abs().max())
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_dissipation_symmetric_psd_and_flip(d):
+    Uk, Uv = rand_states(100, d, 11), rand_states(100, d, 12)
+    n = _nhat(100, d, 13)
+    D = dissipation_matrix(Uk, Uv, n, P)
+    assert (D - D.transpose(-1, -2)).abs().max() < 1e-13 * D.abs().max()
+    assert torch.linalg.eigvalsh(D).min() > -1e-12 * D.abs().max()
+    assert torch.allclose(D, dissipation_matrix(Uk, Uv, -n, P), rtol=1e-12, atol=1e-12)
+    assert torch.allclose(D, dissipation_matrix(Uv, Uk, n, P), rtol=1e-12, atol=1e-12)
+
+
+def test_temperature_closed_forms():
+    """T(W) of Eq. (39) and W_nc of Eq. (41) (R = 1), and dT/dW.
+
+    Eq. (40) as printed has two typos: differentiating Eq. (39) gives
+    dT/dW_i = +(gam-1) V_i / (alpha R W_nc) (printed with a minus sign) and
+    dT/dW_nc = -T/W_nc + (gam-1)|V|^2 / (2 alpha R W_nc) (printed without
+    alpha).  The exact derivative of Eq. (39) is the reading used."""
+    U = rand_states(40, 3, 14)
+    W = entropy_variables(U, P)
+    rho, V, p = primitives(U, P)
+    g, a, R = P.gam, P.alpha, P.R
+    Wn = W[:, -1]
+    T = (g - 1) * (2 * W[:, 0] * Wn - (W[:, 1:-1] ** 2).sum(-1)) / (2 * a * R * Wn ** 2)
+    assert torch.allclose(T, temperature(U, P), rtol=1e-12)
+    assert torch.allclose(Wn, -p ** ((1 - a - g) / (a + g)) * rho ** (a / (a + g)), rtol=1e-13)
+    dTdW = (_jacobian(lambda x: temperature(x, P)[..., None], U) @ dU_dW(U, P))[:, 0]
+    ex = torch.cat([((g - 1) / (a * R * Wn))[:, None], (g - 1) * V / (a * R * Wn[:, None]),
+                    (-T / Wn + (g - 1) * (V * V).sum(-1) / (2 * a * R * Wn))[:, None]], -1)
+    assert torch.allclose(dTdW, ex, rtol=1e-10, atol=1e-12)
+    printed = torch.cat([((g - 1) / (a * R * Wn))[:, None], -(g - 1) * V / (a * R * Wn[:, None]),
+                         (-T / Wn + (g - 1) * (V * V).sum(-1) / (2 * R * Wn))[:, None]], -1)
+    assert not torch.allclose(dTdW, printed, rtol=1e-6)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_viscous_tensor_psd_without_heat_flux(d):
+    """K~ symmetric positive semidefinite without heat flux (Sec. 5); the heat
+    flux breaks the symmetry (Sec. 3, Eq. (38))."""
+    U = rand_states(10, d, 15)
+    nc = d + 2
+    for heat in [False, True]:
+        prm = Params(mu=0.1, heat_flux=heat)
+        K = viscous_K(U, prm)  # (n, d, d, nc, nc)
+        Kb = K.permute(0, 1, 3, 2, 4).reshape(10, d * nc, d * nc)
+        asym = (Kb - Kb.transpose(1, 2)).abs().max() / Kb.abs().max()
+        if heat:
+            assert asym > 1e-3
+        else:
+            assert asym < 1e-12
+            assert torch.linalg.eigvalsh(Kb).min() > -1e-12 * Kb.abs().max()
+            # rank of K~ equals the number of nonzero pivots of the LDL^T
+            # statement of Sec. 5 (3D: pivots 4/3 delta and four delta -> 5; 2D: 3)
+            ev = torch.linalg.eigvalsh(Kb)
+            rank = (ev > 1e-10 * ev.amax(-1, keepdim=True)).sum(-1)
+            assert torch.all(rank == {2: 3, 3: 5}[d])
+
+
+def test_viscous_flux_special_cases():
+    """Plane shear V = (s y, 0): tau_xy = mu s, tau_xx = 0; pure temperature
+    gradient dT/dx: energy flux kappa dT/dx (Eq. (5)); and the flux from the
+    entropy-variable gradient equals the flux from primitive gradients of a
+    smooth field (chain rule through dU/dW)."""
+    from oracle.physics import viscous_flux_from_prim_grads, viscous_flux_from_w_grads
+    prm = Params(mu=0.3)
+    U = rand_states(5, 2, 18)
+    s = 0.7
+    dV = torch.zeros(5, 2, 2, dtype=DT)
+    dV[:, 1, 0] = s                      # dV_1/dx_2
+    F = viscous_flux_from_prim_grads(U, dV, torch.zeros(5, 2, dtype=DT), prm)
+    assert torch.allclose(F[:, 0, 2], torch.full((5,), prm.mu * s, dtype=DT))   # tau_xy in x-flux
+    assert torch.allclose(F[:, 0, 1], torch.zeros(5, dtype=DT))                   # tau_xx
+    dT = torch.zeros(5, 2, dtype=DT)
+    dT[:, 0] = 2.0
+    F = viscous_flux_from_prim_grads(U, torch.zeros(5, 2, 2, dtype=DT), dT, prm)
+    assert torch.allclose(F[:, 0, 3], torch.full((5,), 2.0 * prm.kappa, dtype=DT))
+    # smooth field x -> U(x): gradients by autograd in x
+    x0 = torch.tensor([0.3, -0.2], dtype=DT)
+
+    def Ufield(x):
+        rho = 1.0 + 0.2 * torch.sin(x[0]) * torch.cos(x[1])
+        V = torch.stack([0.3 + 0.1 * x[1] ** 2, -0.2 + 0.1 * torch.sin(x[0] + x[1])])
+        p = 1.0 + 0.1 * torch.cos(2 * x[0] - x[1])
+        return conservative(rho, V, p, prm)
+
+    Ux = Ufield(x0)
+    gW = torch.func.jacrev(lambda x: entropy_variables(Ufield(x), prm))(x0).T       # (d, nc)
+    dVx = torch.func.jacrev(lambda x: primitives(Ufield(x), prm)[1])(x0).T          # [j, k] = dV_k/dx_j
+    dTx = torch.func.jacrev(lambda x: temperature(Ufield(x), prm))(x0)
+    Fa = viscous_flux_from_w_grads(Ux[None], gW[None], prm)[0]
+    Fb = viscous_flux_from_prim_grads(Ux[None], dVx[None], dTx[None], prm)[0]
+    assert torch.allclose(Fa, Fb, rtol=1e-12, atol=1e-13)
