@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Throughput of the entropy-split SBP-SAT solver on one GB300.
+
+Workload (default): 2D isentropic vortex + 1e-3 uniform noise (seed 2) on the
+periodic [0,10]^2 square, 128 x 128 quads cut into 32,768 curved triangles
+(sinusoidal warp, amplitude 0.05), degree p = 3 diagonal-E SBP operator
+(18 nodes), entropy-split volume term + EC SATs + matrix interface
+dissipation, float64.  A step is one relaxation RK4 step (four residual
+evaluations, the stage entropy productions, the relaxation root solve and the
+update).  The metric counts node-DOF residual evaluations per second:
+4 * n_e * n_p per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl esplit|reference]
+
+Prints one JSON line on rank 0.  N > 1 runs independent replicas (the
+solver does not shard), launched by torch.distributed.run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "DOF-residual evals/s vs Hadamard form, FP64 & FP32, % roofline; 1 GB300"
+UNIT = "DOF-residual evals/s"
+FP64_PEAK_NOMINAL = 1.25e12            # recipe table: GB300 FP64 1.25 TFLOP/s
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="esplit", choices=["esplit", "reference"])
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--N", type=int, default=128)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-sweep", action="store_true", help="skip the residual-only sweep over p / scheme / precision")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def workload(p, N):
+    from esplit_inputs import tri_operator, periodic_tri_mesh, states
+    op = tri_operator(p)
+    mesh = periodic_tri_mesh(op, N, 10.0, 0.05)
+    u0 = states.add_uniform_noise(states.isentropic_vortex(mesh), 1e-3, 2)
+    dt = states.cfl_timestep(mesh, u0, 0.1)
+    return op, mesh, u0, dt
+
+
+def workload_name(p, N, precision):
+    return (f"2D isentropic vortex + 1e-3 noise, {N}x{N} quads -> {2 * N * N} curved triangles (warp 0.05), "
+            f"p={p} diagonal-E SBP, entropy split + EC SAT + matrix dissipation, {precision}, relaxation RK4 step")
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic work per launch (stated in the design doc)
+# ---------------------------------------------------------------------------------------------
+def algorithmic_flops(group, n_e, n_p, d, n_pairs):
+    nc = d + 2
+    if group == "split_volume":
+        contraction = 2 * d * 2 * n_p * n_p * nc          # 2d applications of n_p x n_p to n_p x nc
+        pointwise = n_p * (30 + 43 * d)                    # primitives, W, fluxes, A~_i D_i w, products
+        return n_e * (contraction + pointwise)
+    if group == "hadamard_volume":
+        pairs = n_p * (n_p - 1) // 2
+        return n_e * pairs * (60 + 2 * d)
+    if group == "face":
+        return n_pairs * 400
+    return None
+
+
+def algorithmic_bytes(group, n_e, n_p, d, n_pairs):
+    nc = d + 2
+    if group == "split_volume":
+        return n_e * (8 * (2 * d * n_p * n_p) + 8 * n_p * (2 * nc + 1) + 8 * nc * (3 * (n_p // 2)))
+    if group == "face":
+        return n_pairs * (2 * 8 * nc + 2 * 8 * nc + 8 * d + 8 + 16)
+    return None
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_setup(gpus, backend):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(op, mesh, u0, budget_s=12.0):
+    """The FP64 oracle (as it stands) on the host cores: full-mesh residual
+    evaluations (split + EC SAT + dissipation) until the time budget is spent."""
+    from oracle import residual as R
+    from oracle.physics import Params as OP
+    R.residual(u0, op, mesh, OP(), dissipation=True, elems=np.arange(64))  # warm the vmap path
+    n, t0 = 0, time.perf_counter()
+    while True:
+        R.residual(u0, op, mesh, OP(), dissipation=True)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 8:
+            break
+    return {"value": n * mesh.n_e * op.n_p / el, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n} full-mesh residual evaluations ({mesh.n_e} elements, p={op.p}, split + EC SAT + "
+                      f"dissipation, FP64) in {el:.1f} s; RK stage combination and relaxation root solve excluded"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import residual as R
+    from oracle.physics import Params as OP
+    op, mesh, u0, dt = workload(args.p, args.N)
+    R.residual(u0, op, mesh, OP(), dissipation=True, elems=np.arange(64))
+    for _ in range(args.warmup):
+        R.residual(u0, op, mesh, OP(), dissipation=True)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        R.residual(u0, op, mesh, OP(), dissipation=True)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * mesh.n_e * op.n_p / tot
+    cores = torch.get_num_threads()
+    sample = (f"one full-mesh oracle residual per step ({mesh.n_e} elements, p={args.p}, split + EC SAT + "
+              f"dissipation, FP64; RK stages and root solve excluded)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.p, args.N, "fp64"), "n_e": mesh.n_e, "p": args.p,
+                       "n_p": op.n_p},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def residual_sweep(es, device, flush):
+    """Residual-only throughput (no RK / root solve) of the split and Hadamard
+    forms, FP64 and FP32-bulk, p = 1..4, on the same 32,768-triangle mesh."""
+    out = {}
+    stream = torch.cuda.current_stream(device)
+    for p in (1, 2, 3, 4):
+        op, mesh, u0, dt = workload(p, 128)
+        s = es.Solver(op, mesh, es.Params(dissipation=True), device=device)
+        ud = s.to_device(u0)
+        r = s.empty()
+        for scheme in ("split", "hadamard"):
+            for prec in ("fp64", "fp32"):
+                s.set_params(es.Params(dissipation=True, scheme=scheme, precision=prec))
+                for _ in range(3):
+                    s.residual(ud, r)
+                ts = []
+                for k in range(10):
+                    flush.fill_(float(k))
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    s.residual(ud, r)
+                    b.record(stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                ms = statistics.median(ts)
+                out[f"p{p}_{scheme}_{prec}"] = {"ms": ms, "dof_per_s": mesh.n_e * op.n_p / (ms * 1e-3)}
+        s.close()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_setup(args.gpus, "nccl")
+    torch.cuda.set_device(local)
+    device = local
+    import paper_2305_07181_gb300 as es
+    op, mesh, u0, dt = workload(args.p, args.N)
+    solver = es.Solver(op, mesh, es.Params(dissipation=True, precision=args.precision), device=device)
+    stream = torch.cuda.current_stream(device)
+    u = solver.to_device(u0)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{device}")  # 256 MB > L2
+    n_p, n_e, d = op.n_p, mesh.n_e, op.d
+    dof = n_e * n_p
+    for _ in range(args.warmup):
+        solver.rrk_step(u, dt)
+    torch.cuda.synchronize()
+    # ---------------- timed region (device state, per-step CUDA events, L2 flushed between steps)
+    solver.profile(True)
+    solver.profile_read()
+    launches0 = solver.launch_count()
+    step_ms = []
+    gs = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(device) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g, _ = solver.rrk_step(u, dt)
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            gs.append(g)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier(ws)
+    launches = solver.launch_count() - launches0
+    prof = solver.profile_read()
+    solver.profile(False)
+    tot_s = max_over_ranks(sum(step_ms) * 1e-3, ws, device)
+    value = ws * args.steps * 4 * dof / tot_s
+
+    # ---------------- dominant kernel roofline (live event timing of the timed region)
+    groups = {g: v for g, v in prof.items() if v[1] > 0}
+    dom = max(groups, key=lambda g: groups[g][0])
+    dom_ms = groups[dom][0] / groups[dom][1]
+    per_launch_units = n_e if dom in ("split_volume", "hadamard_volume") else solver_pairs(mesh, op)
+    fl = algorithmic_flops(dom, n_e, n_p, d, solver_pairs(mesh, op))
+    roofline = None
+    if fl is not None:
+        achieved = fl / (dom_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_NOMINAL / 1e12 if args.precision == "fp64" else None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (achieved / peak) if peak else None, "traffic": None, "kernel": dom,
+                    "avg_launch_ms": dom_ms, "launches": groups[dom][1], "units_per_launch": per_launch_units,
+                    "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (152 SMs x 4 FLOP/clk x "
+                                   "2.07 GHz); FP64 pipe, not the bf16 tensor peak"}
+    # ---------------- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    u_host = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
+    u_host.copy_(torch.as_tensor(u0))
+    uh = u_host.numpy()
+    for _ in range(2):
+        solver.rrk_step_host(uh, dt)
+    e2e_tot = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        solver.rrk_step_host(uh, dt)          # H2D copy, step, D2H copy, stream sync
+        e2e_tot += time.perf_counter() - t_a
+    e2e_tot = max_over_ranks(e2e_tot, ws, device)
+    nbytes = u0.size * 8
+    e2e = {"value": ws * args.steps * 4 * dof / e2e_tot, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+    extras = {"kernel_ms_timed_region": {g: {"ms_total": v[0], "launches": v[1]} for g, v in groups.items()},
+              "g_range": [min(gs), max(gs)], "wall_s_timed": t_wall, "dt": dt}
+    if rank == 0 and not args.no_sweep:
+        extras["residual_sweep"] = residual_sweep(es, device, flush)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(op, mesh, u0)
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.p, args.N, args.precision), "n_e": n_e, "p": args.p,
+                       "n_p": n_p, "dof": dof, "residuals_per_step": 4, "dt": dt,
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "extras": extras}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def solver_pairs(mesh, op):
+    return mesh.n_e * op.n_fac * op.n_f // 2
+
+
+if __name__ == "__main__":
+    sys.exit(main())

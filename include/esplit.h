@@ -1,0 +1,183 @@
+/*
+ * esplit -- entropy-split SBP-SAT residual of the Euler / compressible
+ * Navier-Stokes equations on curved periodic simplex meshes, for one GB300
+ * (sm_103a).  Plain C ABI: host or device pointers and sizes only.
+ *
+ * Method: Worku & Zingg, "Entropy-split multidimensional summation-by-parts
+ * discretization of the Euler and compressible Navier-Stokes equations".
+ * Equation numbers below are the paper's.
+ *
+ * Conventions shared by every call
+ *   d      spatial dimension (2 or 3), n_c = d + 2 components
+ *   state  u: float64 conservative variables [rho, rho V_1..V_d, e],
+ *          layout [n_e][n_c][n_p] (element-major, node fastest)
+ *   all pointers named *_dev are device pointers owned by the caller;
+ *   *_host pointers are host pointers owned by the caller; the library copies
+ *   what it keeps.  Calls taking a stream enqueue work on that stream
+ *   (cudaStream_t passed as void*, NULL = legacy default stream) and return
+ *   before it finishes unless stated otherwise.
+ *   Every call returns ESPLIT_OK (0) or a negative code; the message of the
+ *   last failure is available from esplit_last_error().
+ */
+#ifndef ESPLIT_H
+#define ESPLIT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESPLIT_OK 0
+#define ESPLIT_ERR_ARG (-1)          /* bad argument (null, size, range)             */
+#define ESPLIT_ERR_CUDA (-2)         /* a CUDA call failed                            */
+#define ESPLIT_ERR_MESH (-3)         /* mesh rejected (pairing not an involution,
+                                        J <= 0, normals of paired nodes not opposite) */
+#define ESPLIT_ERR_NONPHYSICAL (-4)  /* rho <= 0, p <= 0 or a non-finite value seen   */
+#define ESPLIT_ERR_RRK_NO_ROOT (-5)  /* relaxation parameter not bracketed            */
+#define ESPLIT_ERR_UNSUPPORTED (-6)  /* operator size / dimension not compiled in     */
+#define ESPLIT_ERR_STATE (-7)        /* call order (e.g. residual before mesh upload) */
+
+#define ESPLIT_FP64 0       /* everything in float64                               */
+#define ESPLIT_FP32_BULK 1  /* fluxes and operator contractions in float32; metric
+                               terms, entropy-rate products and the relaxation root
+                               solve stay float64                                   */
+
+#define ESPLIT_SCHEME_SPLIT 0     /* entropy split, Eq. (100)                       */
+#define ESPLIT_SCHEME_HADAMARD 1  /* Sjogreen-Yee Hadamard form, Eq. (99)            */
+#define ESPLIT_SCHEME_HYBRID 2    /* per-element choice (Thm. 4), flags below        */
+
+typedef struct esplit_ctx esplit_ctx;
+
+typedef struct esplit_params {
+  double gam;      /* ratio of specific heats (Sec. 2.2), default 1.4                */
+  double beta;     /* split parameter (Sec. 6.4), alpha = -gam - beta (gam - 1)      */
+  double R;        /* gas constant                                                   */
+  double mu;       /* dynamic viscosity (constant)                                   */
+  double Pr;       /* Prandtl number                                                 */
+  int dissipation; /* 1: add the matrix interface dissipation of Eq. (69)            */
+  int viscous;     /* 1: add Eqs. (83)-(85) with Baumann-Oden SATs, Eq. (96)         */
+  int heat_flux;   /* 1: include the heat flux in the viscous flux                   */
+  int scheme;      /* ESPLIT_SCHEME_*                                                */
+  int precision;   /* ESPLIT_FP64 or ESPLIT_FP32_BULK                                */
+} esplit_params;
+
+typedef struct esplit_stepinfo {
+  double g;            /* relaxation parameter gamma_n of Eq. (97)                  */
+  double estimate;     /* dt sum_i b_i w_i^T H r_i                                  */
+  double S_before;     /* 1^T H s(u_n)                                              */
+  double S_after;      /* 1^T H s(u_{n+1})                                          */
+  int iterations;      /* root-solve evaluations of f                               */
+  int status;          /* ESPLIT_OK or the step's error code                        */
+} esplit_stepinfo;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int esplit_version(void);
+
+/* Create a context on CUDA device `device` for dimension `dim` (2 or 3).
+ * The context owns every device copy it makes (operators, mesh, scratch).
+ * Defaults: gam 1.4, beta 2.5, R 1, mu 0, Pr 0.71, split scheme, FP64,
+ * no dissipation, no viscous terms, heat flux on. */
+int esplit_create(esplit_ctx** out, int dim, int device);
+void esplit_destroy(esplit_ctx* ctx);
+
+/* Reference diagonal-E SBP operator (Def. 1; diagonal H and E, Sec. 2.1).
+ *   H_ref        [n_p]               diagonal norm (quadrature weights), > 0
+ *   Q_ref        [d][n_p][n_p]       Q_xi_j, row-major
+ *   facet_nodes  [n_fac][n_f]        volume node of each facet slot; every
+ *                                    facet node belongs to exactly one slot
+ *   facet_w      [n_fac][n_f]        facet quadrature weights (unused by the
+ *                                    residual; kept for diagnostics)
+ *   ref_normals  [n_fac][d]          outward unit normals of reference facets
+ * Host pointers, copied.  Supported (d, n_p): (2, 7), (2, 12), (2, 18),
+ * (2, 27); others -> ESPLIT_ERR_UNSUPPORTED. */
+int esplit_upload_operator(esplit_ctx* ctx, int n_p, int n_fac, int n_f, const double* H_ref,
+                           const double* Q_ref, const int* facet_nodes, const double* facet_w,
+                           const double* ref_normals);
+
+/* Curved periodic mesh (every facet interior, Sec. 2.1 conforming meshes).
+ *   J      [n_e][n_p]               mapping Jacobian at the nodes, > 0
+ *   Lambda [n_e][d][d][n_p]         Lambda_ij = J dxi_j/dx_i at the nodes
+ *   nu     [n_e][n_fac][n_f][d]     scaled outward normal b n at facet slots
+ *                                   (the diagonal of E_x_i, Eq. (2))
+ *   pair   [n_e][n_fac][n_f][2]     (neighbour element, neighbour flat slot)
+ *   hmin   [n_e]                    smallest node distance (may be NULL)
+ * Host pointers, copied.  Validation: pair is an involution, nu of paired
+ * slots are opposite (relative 1e-10), J > 0; else ESPLIT_ERR_MESH.  The
+ * per-element physical operators Q_x_i = 1/2 sum_j (Lam_ij Q_xi_j -
+ * Q_xi_j^T Lam_ij) + 1/2 E_x_i are formed on the device here. */
+int esplit_upload_mesh(esplit_ctx* ctx, int n_e, const double* J, const double* Lambda,
+                       const double* nu, const int* pair, const double* hmin);
+
+/* Parameters (host struct, copied).  Changing beta re-forms the stored
+ * split operators. */
+int esplit_set_params(esplit_ctx* ctx, const esplit_params* params);
+int esplit_get_params(esplit_ctx* ctx, esplit_params* params);
+
+/* Hybrid flags for ESPLIT_SCHEME_HYBRID (Thm. 4): flags_host[n_e], 0 = entropy
+ * split volume term, 1 = Hadamard volume term.  Host pointer, copied. */
+int esplit_set_hybrid_flags(esplit_ctx* ctx, const unsigned char* flags_host, int n_e);
+
+/* Semi-discrete residual du/dt of Eq. (100) (split), Eq. (99) (Hadamard) or
+ * the hybrid, with the EC SATs of Eq. (43) and, per the parameters, the
+ * dissipation of Eq. (69) and the viscous terms of Eqs. (83)-(85).
+ *   u_dev    [n_e][n_c][n_p] float64, device, read only
+ *   dudt_dev [n_e][n_c][n_p] float64, device, written
+ * Asynchronous on `stream`.  A non-physical node (rho <= 0, p <= 0,
+ * non-finite) sets the context status ESPLIT_ERR_NONPHYSICAL, read with
+ * esplit_get_status(). */
+int esplit_residual(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void* stream);
+
+/* Same with host buffers: copies u_host to the device, evaluates, copies the
+ * residual back, and synchronises `stream` before returning. */
+int esplit_residual_host(esplit_ctx* ctx, const double* u_host, double* dudt_host, void* stream);
+
+/* 1^T H s(u) with Harten's entropy, Eq. (16), in float64 (synchronises). */
+int esplit_entropy(esplit_ctx* ctx, const double* u_dev, double* S_total, void* stream);
+
+/* sum_k w_k^T H_k dudt_k (the rate of Thm. 2), float64 (synchronises). */
+int esplit_entropy_rate(esplit_ctx* ctx, const double* u_dev, const double* dudt_dev,
+                        double* rate, void* stream);
+
+/* One relaxation RK4 step, Sec. 6.1, Eqs. (97)-(98): classical RK4 stages,
+ * relaxation parameter g by a bracketed Newton iteration on the device to
+ * round-off, u <- u + g dt sum_i b_i r_i.  u_dev is updated in place (left
+ * untouched on failure).  Synchronises `stream` at the end; g and the step
+ * summary are returned through g_out / info (either may be NULL). */
+int esplit_rrk_step(esplit_ctx* ctx, double* u_dev, double dt, double* g_out, esplit_stepinfo* info,
+                    void* stream);
+
+/* Same step with a host state: copies u_host (pinned or pageable) to the
+ * device, steps, copies the new state back, and synchronises `stream`. */
+int esplit_rrk_step_host(esplit_ctx* ctx, double* u_host, double dt, double* g_out, esplit_stepinfo* info,
+                         void* stream);
+
+/* Reverse mode of the residual: grad_dev = (d dudt / d u)^T cot_dev.
+ *   u_dev, cot_dev, grad_dev: [n_e][n_c][n_p] float64 device buffers. */
+int esplit_residual_vjp(esplit_ctx* ctx, const double* u_dev, const double* cot_dev,
+                        double* grad_dev, void* stream);
+
+/* Sticky status of asynchronous work (synchronises the context's last
+ * stream): ESPLIT_OK or ESPLIT_ERR_NONPHYSICAL; reading clears it. */
+int esplit_get_status(esplit_ctx* ctx);
+
+/* Message of the last failure on this context (static storage of ctx). */
+const char* esplit_last_error(esplit_ctx* ctx);
+
+/* Number of kernels this context has launched so far (for accounting). */
+long long esplit_launch_count(esplit_ctx* ctx);
+
+/* Kernel timing: when enabled, every kernel launch of the context is
+ * bracketed by CUDA events on its own stream.  Groups:
+ *   0 facet kernel (EC SAT + dissipation)   1 entropy-split volume kernel
+ *   2 Hadamard volume kernel                3 entropy functionals + reductions
+ *   4 relaxation root solve                 5 RK stage / update kernels
+ * esplit_profile_read synchronises, fills ms[g] (total milliseconds) and
+ * count[g] (launches) for g < n_groups, and resets the accumulators. */
+#define ESPLIT_PROFILE_GROUPS 6
+int esplit_profile_enable(esplit_ctx* ctx, int on);
+int esplit_profile_read(esplit_ctx* ctx, double* ms, long long* count, int n_groups);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESPLIT_H */

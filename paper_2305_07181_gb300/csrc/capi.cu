@@ -1,0 +1,510 @@
+// C ABI of the library (declared in include/esplit.h): context, uploads,
+// validation, and the host side of the residual, entropy functionals and
+// relaxation RK4 step.  All arithmetic of the method runs in kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using esplit::RefTables;
+
+namespace {
+
+constexpr double kNuTol = 1e-10;
+
+int fail(esplit_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(c, ESPLIT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dalloc(esplit_ctx* c, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) return ESPLIT_OK;
+  CK(cudaMalloc((void**)p, count * sizeof(T)));
+  return ESPLIT_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool supported(int dim, int n_p) {
+  if (dim == 2) return n_p == 7 || n_p == 12 || n_p == 18 || n_p == 27;
+  return false;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_ready(esplit_ctx* c) {
+  if (!c) return ESPLIT_ERR_ARG;
+  if (!c->have_op || !c->have_mesh) return fail(c, ESPLIT_ERR_STATE, "operator and mesh must be uploaded first");
+  return ESPLIT_OK;
+}
+
+int ensure_partial(esplit_ctx* c) {
+  size_t need = 2 * ((size_t)c->n_e * c->n_p / 256 + (size_t)c->n_e + 64);
+  if (c->partial_cap >= need) return ESPLIT_OK;
+  int rc = dalloc(c, &c->b.partial, need);
+  if (rc) return rc;
+  c->partial_cap = need;
+  return ESPLIT_OK;
+}
+
+int rebuild_ops(esplit_ctx* c, cudaStream_t s) {
+  if (!c->have_op || !c->have_mesh) return ESPLIT_OK;
+  if (esplit::launch_build_ops(c, s)) return fail(c, ESPLIT_ERR_CUDA, "build_ops launch failed");
+  CK(cudaStreamSynchronize(s));
+  c->ops_beta = c->prm.beta;
+  c->ops_beta_valid = true;
+  return ESPLIT_OK;
+}
+
+int read_status(esplit_ctx* c, cudaStream_t s, bool clear) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->b.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (clear && h) CK(cudaMemsetAsync(c->b.status, 0, sizeof(int), s));
+  return h ? ESPLIT_ERR_NONPHYSICAL : ESPLIT_OK;
+}
+
+}  // namespace
+
+namespace esplit {
+
+ProfScope::ProfScope(esplit_ctx* c_, int g_, cudaStream_t s_) : c(c_), g(g_), s(s_) {
+  if (!c->prof) return;
+  for (cudaEvent_t* ev : {&a, &b}) {
+    if (!c->pool.empty()) {
+      *ev = c->pool.back();
+      c->pool.pop_back();
+    } else if (cudaEventCreate(ev) != cudaSuccess) {
+      *ev = nullptr;
+    }
+  }
+  if (a) cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+  if (!c->prof || !a || !b) return;
+  cudaEventRecord(b, s);
+  c->recs.push_back(ProfRec{g, a, b});
+}
+
+}  // namespace esplit
+
+extern "C" {
+
+int esplit_version(void) { return 100; }
+
+int esplit_create(esplit_ctx** out, int dim, int device) {
+  if (!out) return ESPLIT_ERR_ARG;
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return ESPLIT_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return ESPLIT_ERR_CUDA;
+  if (device < 0 || device >= ndev) return ESPLIT_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return ESPLIT_ERR_CUDA;
+  esplit_ctx* c = new esplit_ctx();
+  c->dim = dim;
+  c->n_c = dim + 2;
+  c->device = device;
+  c->prm.gam = 1.4;
+  c->prm.beta = 2.5;
+  c->prm.R = 1.0;
+  c->prm.mu = 0.0;
+  c->prm.Pr = 0.71;
+  c->prm.dissipation = 0;
+  c->prm.viscous = 0;
+  c->prm.heat_flux = 1;
+  c->prm.scheme = ESPLIT_SCHEME_SPLIT;
+  c->prm.precision = ESPLIT_FP64;
+  if (cudaMalloc((void**)&c->b.status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->b.root, sizeof(esplit::RootState)) != cudaSuccess ||
+      cudaMalloc((void**)&c->b.scal, 64 * sizeof(double)) != cudaSuccess) {
+    esplit_destroy(c);
+    return ESPLIT_ERR_CUDA;
+  }
+  cudaMemset(c->b.status, 0, sizeof(int));
+  cudaMemset(c->b.scal, 0, 64 * sizeof(double));
+  *out = c;
+  return ESPLIT_OK;
+}
+
+void esplit_destroy(esplit_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  esplit::Buffers& b = c->b;
+  void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,
+                b.list_split, b.list_had, b.sat, b.partial, b.scal, b.root, b.status, b.stage_u,
+                b.stage_r, b.dacc, b.host_u, b.host_r};
+  for (void* p : ps) dfree(p);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int esplit_upload_operator(esplit_ctx* c, int n_p, int n_fac, int n_f, const double* H_ref, const double* Q_ref,
+                           const int* facet_nodes, const double* facet_w, const double* ref_normals) {
+  if (!c) return ESPLIT_ERR_ARG;
+  if (!H_ref || !Q_ref || !facet_nodes) return fail(c, ESPLIT_ERR_ARG, "null operator array");
+  if (n_p <= 0 || n_fac <= 0 || n_f <= 0) return fail(c, ESPLIT_ERR_ARG, "operator sizes must be positive");
+  if (!supported(c->dim, n_p))
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size n_p=" + std::to_string(n_p) + " not compiled in");
+  int n_slot = n_fac * n_f;
+  if (n_slot > esplit::MAX_SLOT || n_p > esplit::MAX_NP) return fail(c, ESPLIT_ERR_UNSUPPORTED, "too many nodes");
+  cudaSetDevice(c->device);
+  RefTables t{};
+  t.n_p = n_p;
+  t.n_fac = n_fac;
+  t.n_f = n_f;
+  t.n_slot = n_slot;
+  for (int m = 0; m < esplit::MAX_NP; ++m) t.node_slot[m] = -1;
+  for (int s = 0; s < n_slot; ++s) {
+    int m = facet_nodes[s];
+    if (m < 0 || m >= n_p) return fail(c, ESPLIT_ERR_ARG, "facet node index out of range");
+    if (t.node_slot[m] >= 0) return fail(c, ESPLIT_ERR_ARG, "a volume node belongs to two facet slots");
+    t.node_slot[m] = s;
+    t.slot_node[s] = m;
+  }
+  for (int m = 0; m < n_p; ++m) {
+    if (!(H_ref[m] > 0.0)) return fail(c, ESPLIT_ERR_ARG, "H_ref must be positive");
+    t.H[m] = H_ref[m];
+  }
+  (void)facet_w;
+  (void)ref_normals;
+  int rc = dalloc(c, &c->b.Qref, (size_t)c->dim * n_p * n_p);
+  if (rc) return rc;
+  CK(cudaMemcpy(c->b.Qref, Q_ref, sizeof(double) * c->dim * n_p * n_p, cudaMemcpyHostToDevice));
+  if (esplit::set_ref_tables(t)) return fail(c, ESPLIT_ERR_CUDA, "constant-table upload failed");
+  c->ref = t;
+  c->n_p = n_p;
+  c->n_fac = n_fac;
+  c->n_f = n_f;
+  c->n_slot = n_slot;
+  c->have_op = true;
+  c->have_mesh = false;  // a new operator invalidates the mesh-derived data
+  return ESPLIT_OK;
+}
+
+int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* Lambda, const double* nu,
+                       const int* pair, const double* hmin) {
+  if (!c) return ESPLIT_ERR_ARG;
+  if (!c->have_op) return fail(c, ESPLIT_ERR_STATE, "upload the operator before the mesh");
+  if (n_e <= 0 || !J || !Lambda || !nu || !pair) return fail(c, ESPLIT_ERR_ARG, "bad mesh arguments");
+  (void)hmin;
+  cudaSetDevice(c->device);
+  const int d = c->dim, NP = c->n_p, NS = c->n_slot;
+  // --- host validation
+  for (size_t i = 0; i < (size_t)n_e * NP; ++i)
+    if (!(J[i] > 0.0)) return fail(c, ESPLIT_ERR_MESH, "J must be positive at every node");
+  std::vector<int2> fpairs;
+  fpairs.reserve((size_t)n_e * NS / 2);
+  for (int k = 0; k < n_e; ++k) {
+    for (int s = 0; s < NS; ++s) {
+      size_t a = (size_t)k * NS + s;
+      int v = pair[2 * a], s2 = pair[2 * a + 1];
+      if (v < 0 || v >= n_e || s2 < 0 || s2 >= NS) return fail(c, ESPLIT_ERR_MESH, "pair index out of range");
+      size_t b2 = (size_t)v * NS + s2;
+      if (pair[2 * b2] != k || pair[2 * b2 + 1] != s) return fail(c, ESPLIT_ERR_MESH, "pairing is not an involution");
+      if (b2 == a) return fail(c, ESPLIT_ERR_MESH, "facet slot paired with itself");
+      double sc = 0.0, df = 0.0;
+      for (int i = 0; i < d; ++i) {
+        sc = std::max(sc, std::fabs(nu[a * d + i]));
+        df = std::max(df, std::fabs(nu[a * d + i] + nu[b2 * d + i]));
+      }
+      if (!(sc > 0.0) || df > kNuTol * sc) return fail(c, ESPLIT_ERR_MESH, "normals of paired slots are not opposite");
+      if (a < b2) fpairs.push_back(make_int2((int)a, (int)b2));
+    }
+  }
+  c->n_e = n_e;
+  c->n_pairs = (int)fpairs.size();
+  int rc;
+  if ((rc = dalloc(c, &c->b.J, (size_t)n_e * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.nu, (size_t)n_e * NS * d))) return rc;
+  if ((rc = dalloc(c, &c->b.pair, (size_t)n_e * NS * 2))) return rc;
+  if ((rc = dalloc(c, &c->b.Lam, (size_t)n_e * d * d * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.face_pairs, fpairs.size()))) return rc;
+  if ((rc = dalloc(c, &c->b.ops64, (size_t)n_e * 2 * d * NP * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.ops32, (size_t)n_e * 2 * d * NP * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
+  c->partial_cap = 0;
+  if ((rc = ensure_partial(c))) return rc;
+  CK(cudaMemcpy(c->b.J, J, sizeof(double) * n_e * NP, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->b.nu, nu, sizeof(double) * n_e * NS * d, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->b.pair, pair, sizeof(int) * n_e * NS * 2, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->b.Lam, Lambda, sizeof(double) * n_e * d * d * NP, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->b.face_pairs, fpairs.data(), sizeof(int2) * fpairs.size(), cudaMemcpyHostToDevice));
+  // RRK / host-path scratch is (re)allocated lazily
+  dalloc(c, &c->b.stage_u, 0);
+  dalloc(c, &c->b.stage_r, 0);
+  dalloc(c, &c->b.dacc, 0);
+  dalloc(c, &c->b.host_u, 0);
+  dalloc(c, &c->b.host_r, 0);
+  c->flags.assign(n_e, 0);
+  c->n_split = n_e;
+  c->n_had = 0;
+  c->have_mesh = true;
+  return rebuild_ops(c, 0);
+}
+
+int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
+  if (!c || !p) return ESPLIT_ERR_ARG;
+  if (!(p->gam > 1.0)) return fail(c, ESPLIT_ERR_ARG, "gam must exceed 1");
+  double alpha = -p->gam - p->beta * (p->gam - 1.0);
+  if (!(alpha < -p->gam || alpha > 0.0)) return fail(c, ESPLIT_ERR_ARG, "beta must give alpha < -gam or alpha > 0");
+  if (!(p->R > 0.0) || p->mu < 0.0 || !(p->Pr > 0.0)) return fail(c, ESPLIT_ERR_ARG, "R, Pr must be > 0, mu >= 0");
+  if (p->scheme < 0 || p->scheme > 2) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
+  if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK) return fail(c, ESPLIT_ERR_ARG, "unknown precision");
+  if (p->viscous) return fail(c, ESPLIT_ERR_UNSUPPORTED, "viscous terms are not built in this version");
+  cudaSetDevice(c->device);
+  bool beta_changed = p->beta != c->prm.beta;
+  c->prm = *p;
+  if (beta_changed && c->have_mesh) return rebuild_ops(c, 0);
+  return ESPLIT_OK;
+}
+
+int esplit_get_params(esplit_ctx* c, esplit_params* p) {
+  if (!c || !p) return ESPLIT_ERR_ARG;
+  *p = c->prm;
+  return ESPLIT_OK;
+}
+
+int esplit_set_hybrid_flags(esplit_ctx* c, const unsigned char* flags, int n_e) {
+  if (!c || !flags) return ESPLIT_ERR_ARG;
+  if (!c->have_mesh) return fail(c, ESPLIT_ERR_STATE, "upload the mesh before the hybrid flags");
+  if (n_e != c->n_e) return fail(c, ESPLIT_ERR_ARG, "flags length must equal n_e");
+  cudaSetDevice(c->device);
+  std::vector<int> ls, lh;
+  for (int e = 0; e < n_e; ++e) {
+    if (flags[e] > 1) return fail(c, ESPLIT_ERR_ARG, "hybrid flags must be 0 or 1");
+    (flags[e] ? lh : ls).push_back(e);
+  }
+  c->flags.assign(flags, flags + n_e);
+  int rc;
+  if ((rc = dalloc(c, &c->b.list_split, std::max<size_t>(ls.size(), 1)))) return rc;
+  if ((rc = dalloc(c, &c->b.list_had, std::max<size_t>(lh.size(), 1)))) return rc;
+  if (!ls.empty()) CK(cudaMemcpy(c->b.list_split, ls.data(), sizeof(int) * ls.size(), cudaMemcpyHostToDevice));
+  if (!lh.empty()) CK(cudaMemcpy(c->b.list_had, lh.data(), sizeof(int) * lh.size(), cudaMemcpyHostToDevice));
+  c->n_split = (int)ls.size();
+  c->n_had = (int)lh.size();
+  return ESPLIT_OK;
+}
+
+static int residual_impl(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* npart) {
+  if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
+    return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
+  int rc = esplit::launch_residual(c, u, r, s, prod, npart);
+  if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
+  if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString(cudaGetLastError()));
+  c->last_stream = s;
+  return ESPLIT_OK;
+}
+
+int esplit_residual(esplit_ctx* c, const double* u, double* r, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !r) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
+  if (u == r) return fail(c, ESPLIT_ERR_ARG, "u and dudt must not alias");
+  cudaSetDevice(c->device);
+  return residual_impl(c, u, r, as_stream(stream), nullptr, nullptr);
+}
+
+int esplit_residual_host(esplit_ctx* c, const double* u, double* r, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !r) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
+  cudaSetDevice(c->device);
+  size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  if (!c->b.host_u) {
+    if ((rc = dalloc(c, &c->b.host_u, n))) return rc;
+    if ((rc = dalloc(c, &c->b.host_r, n))) return rc;
+  }
+  cudaStream_t s = as_stream(stream);
+  CK(cudaMemcpyAsync(c->b.host_u, u, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  if ((rc = residual_impl(c, c->b.host_u, c->b.host_r, s, nullptr, nullptr))) return rc;
+  CK(cudaMemcpyAsync(r, c->b.host_r, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return ESPLIT_OK;
+}
+
+int esplit_entropy(esplit_ctx* c, const double* u, double* S_total, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !S_total) return fail(c, ESPLIT_ERR_ARG, "null pointer");
+  cudaSetDevice(c->device);
+  cudaStream_t s = as_stream(stream);
+  int np = 0;
+  if (esplit::launch_entropy(c, u, s, &np)) return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
+  if (esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal + 8, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
+  double h[2];
+  CK(cudaMemcpyAsync(h, c->b.scal + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *S_total = h[0];
+  return ESPLIT_OK;
+}
+
+int esplit_entropy_rate(esplit_ctx* c, const double* u, const double* r, double* rate, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !r || !rate) return fail(c, ESPLIT_ERR_ARG, "null pointer");
+  cudaSetDevice(c->device);
+  cudaStream_t s = as_stream(stream);
+  int np = 0;
+  if (esplit::launch_entropy_rate(c, u, r, s, &np)) return fail(c, ESPLIT_ERR_CUDA, "entropy-rate launch");
+  if (esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal + 10, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
+  double h[2];
+  CK(cudaMemcpyAsync(h, c->b.scal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *rate = h[0];
+  return ESPLIT_OK;
+}
+
+int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_stepinfo* info, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ESPLIT_ERR_ARG, "dt must be positive and finite");
+  cudaSetDevice(c->device);
+  cudaStream_t s = as_stream(stream);
+  size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  if (!c->b.stage_u) {
+    if ((rc = dalloc(c, &c->b.stage_u, n))) return rc;
+    if ((rc = dalloc(c, &c->b.stage_r, n))) return rc;
+    if ((rc = dalloc(c, &c->b.dacc, n))) return rc;
+  }
+  static const double A[4] = {0.0, 0.5, 0.5, 1.0};
+  static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  int np = 0;
+  // S0 and sum H |s| of u_n -> scal[0..1]
+  if (esplit::launch_entropy(c, u, s, &np) || esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal, s))
+    return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
+  for (int i = 0; i < 4; ++i) {
+    const double* Ui = (i == 0) ? u : c->b.stage_u;
+    if ((rc = residual_impl(c, Ui, c->b.stage_r, s, c->b.partial, &np))) return rc;
+    if (esplit::launch_reduce(c, c->b.partial, np, 1, c->b.scal + 2 + i, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
+    double a_next = (i < 3) ? A[i + 1] * dt : 0.0;
+    if (esplit::launch_stage(c, u, c->b.stage_r, a_next, B[i] * dt, i == 0, (i < 3) ? c->b.stage_u : nullptr,
+                             c->b.dacc, n, s))
+      return fail(c, ESPLIT_ERR_CUDA, "stage launch");
+  }
+  if (esplit::launch_root_start(c, dt, s)) return fail(c, ESPLIT_ERR_CUDA, "root init");
+  esplit::RootState st{};
+  for (int it = 0; it < esplit::ROOT_EVALS_MAX; ++it) {
+    if (esplit::launch_root_eval(c, u, c->b.dacc, s, &np) || esplit::launch_root_update(c, np, s))
+      return fail(c, ESPLIT_ERR_CUDA, "root launch");
+    if ((it + 1) % esplit::ROOT_CHECK_EVERY == 0) {
+      CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (st.done) break;
+    }
+  }
+  if (esplit::launch_root_apply(c, u, c->b.dacc, n, s)) return fail(c, ESPLIT_ERR_CUDA, "apply launch");
+  CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int phys = read_status(c, s, true);
+  c->last_stream = s;
+  int status = phys ? phys : st.status;
+  if (g_out) *g_out = st.g;
+  if (info) {
+    info->g = st.g;
+    info->estimate = st.est;
+    info->S_before = st.S0;
+    info->iterations = st.iters;
+    info->status = status;
+    double Sa = 0.0;
+    if (status == ESPLIT_OK && esplit_entropy(c, u, &Sa, stream) == ESPLIT_OK) info->S_after = Sa;
+    else info->S_after = st.S0;
+  }
+  if (status == ESPLIT_ERR_NONPHYSICAL) return fail(c, status, "non-physical state during the step");
+  if (status == ESPLIT_ERR_RRK_NO_ROOT) return fail(c, status, "relaxation parameter could not be bracketed");
+  return ESPLIT_OK;
+}
+
+int esplit_rrk_step_host(esplit_ctx* c, double* u_host, double dt, double* g_out, esplit_stepinfo* info,
+                         void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u_host) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
+  cudaSetDevice(c->device);
+  size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  if (!c->b.host_u) {
+    if ((rc = dalloc(c, &c->b.host_u, n))) return rc;
+    if ((rc = dalloc(c, &c->b.host_r, n))) return rc;
+  }
+  cudaStream_t s = as_stream(stream);
+  CK(cudaMemcpyAsync(c->b.host_u, u_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  rc = esplit_rrk_step(c, c->b.host_u, dt, g_out, info, stream);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(u_host, c->b.host_u, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return ESPLIT_OK;
+}
+
+int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  (void)u;
+  (void)cot;
+  (void)grad;
+  (void)stream;
+  return fail(c, ESPLIT_ERR_UNSUPPORTED, "residual VJP is not built in this version");
+}
+
+int esplit_get_status(esplit_ctx* c) {
+  if (!c) return ESPLIT_ERR_ARG;
+  cudaSetDevice(c->device);
+  return read_status(c, c->last_stream, true);
+}
+
+const char* esplit_last_error(esplit_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+long long esplit_launch_count(esplit_ctx* c) { return c ? c->launches : -1; }
+
+int esplit_profile_enable(esplit_ctx* c, int on) {
+  if (!c) return ESPLIT_ERR_ARG;
+  c->prof = on != 0;
+  return ESPLIT_OK;
+}
+
+int esplit_profile_read(esplit_ctx* c, double* ms, long long* count, int n_groups) {
+  if (!c || n_groups < 0) return ESPLIT_ERR_ARG;
+  cudaSetDevice(c->device);
+  std::vector<double> acc(ESPLIT_PROFILE_GROUPS, 0.0);
+  std::vector<long long> cnt(ESPLIT_PROFILE_GROUPS, 0);
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    CK(cudaEventSynchronize(r.b));
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    acc[r.group] += t;
+    cnt[r.group] += 1;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  for (int g = 0; g < n_groups && g < ESPLIT_PROFILE_GROUPS; ++g) {
+    if (ms) ms[g] = acc[g];
+    if (count) count[g] = cnt[g];
+  }
+  return ESPLIT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Library-internal declarations: the context and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/esplit.h"
+
+namespace esplit {
+
+constexpr int MAX_NP = 32;
+constexpr int MAX_SLOT = 64;
+
+// Reference-operator tables every kernel reads (constant memory).
+struct RefTables {
+  int n_p, n_fac, n_f, n_slot;
+  int slot_node[MAX_SLOT];  // volume node of facet slot
+  int node_slot[MAX_NP];    // facet slot of volume node, -1 for interior nodes
+  double H[MAX_NP];         // reference norm
+};
+
+// Device-resident state of the relaxation root solve (Eq. (97)).
+struct RootState {
+  double S0, Sabs, est;      // 1^T H s(u_n), 1^T H |s(u_n)|, dt sum b_i e_i
+  double g, lo, hi, flo, fhi;
+  double f_last, df_last;
+  int phase, done, iters, status;
+};
+
+struct Buffers {
+  // operators
+  double* Qref = nullptr;      // [d][n_p][n_p]
+  // mesh
+  double* J = nullptr;         // [n_e][n_p]
+  double* nu = nullptr;        // [n_e][n_slot][d]
+  int* pair = nullptr;         // [n_e][n_slot][2]
+  double* Lam = nullptr;       // [n_e][d][d][n_p]
+  int2* face_pairs = nullptr;  // [n_pairs] (k*n_slot+s, v*n_slot+s') with owner k
+  // per-element split/derivative operators, transposed ([k][n][m]):
+  //   k <  d: M_i^T, M_i = H^-1 (Q_x_i/(beta+1) + Q_x_i^T)
+  //   k >= d: D_i^T, D_i = H^-1 Q_x_i
+  double* ops64 = nullptr;     // [n_e][2d][n_p][n_p]
+  float* ops32 = nullptr;      // same, float
+  // element lists for the hybrid scheme
+  int* list_split = nullptr;
+  int* list_had = nullptr;
+  // scratch
+  double* sat = nullptr;       // [n_e][n_c][n_slot] facet contributions
+  double* partial = nullptr;   // block partial sums
+  double* scal = nullptr;      // small device scalars
+  RootState* root = nullptr;
+  int* status = nullptr;       // sticky error flag
+  // RRK work arrays [n_e][n_c][n_p]
+  double* stage_u = nullptr;
+  double* stage_r = nullptr;
+  double* dacc = nullptr;
+  double* host_u = nullptr;    // device copies for the host-buffer entry point
+  double* host_r = nullptr;
+};
+
+}  // namespace esplit
+
+namespace esplit {
+struct ProfRec {
+  int group;
+  cudaEvent_t a, b;
+};
+}  // namespace esplit
+
+struct esplit_ctx {
+  int dim = 2, device = 0, n_c = 4;
+  int n_p = 0, n_fac = 0, n_f = 0, n_slot = 0;
+  int n_e = 0, n_pairs = 0;
+  int n_split = 0, n_had = 0;
+  bool have_op = false, have_mesh = false, ops_beta_valid = false;
+  double ops_beta = 0.0;
+  esplit_params prm{};
+  esplit::RefTables ref{};
+  esplit::Buffers b;
+  size_t partial_cap = 0;
+  std::vector<unsigned char> flags;
+  std::string err;
+  long long launches = 0;
+  cudaStream_t last_stream = nullptr;
+  bool prof = false;
+  std::vector<esplit::ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace esplit {
+
+// Brackets one kernel launch with CUDA events on its stream when the
+// context's profiling is enabled (groups listed in include/esplit.h).
+enum ProfGroup { PG_FACE = 0, PG_SPLIT = 1, PG_HAD = 2, PG_ENTROPY = 3, PG_ROOT = 4, PG_STAGE = 5 };
+struct ProfScope {
+  esplit_ctx* c;
+  int g;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(esplit_ctx* c_, int g_, cudaStream_t s_);
+  ~ProfScope();
+};
+
+// launchers (kernels.cu)
+int launch_build_ops(esplit_ctx* c, cudaStream_t s);
+int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod_partial,
+                    int* n_partial);
+int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial);
+int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial);
+int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s);
+int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, double* out, size_t n, cudaStream_t s);
+int launch_stage(esplit_ctx* c, const double* un, const double* r, double a_dt, double b_dt, int first,
+                 double* u_next, double* dacc, size_t n, cudaStream_t s);
+int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s);
+constexpr int ROOT_CHECK_EVERY = 4;
+constexpr int ROOT_EVALS_MAX = 40;
+int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s, int* n_partial);
+int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s);
+int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
+int set_ref_tables(const RefTables& t);
+
+}  // namespace esplit

@@ -1,0 +1,788 @@
+// CUDA kernels of the entropy-split residual, its Hadamard-form counterpart,
+// the entropy functionals and the relaxation RK4 root solve (sm_103a).
+//
+// Data layout in HBM (float64 unless noted):
+//   u, r          [n_e][n_c][n_p]      element-major, node fastest
+//   J             [n_e][n_p]
+//   nu            [n_e][n_slot][d]     scaled outward normals at facet slots
+//   face_pairs    int2 [n_pairs]       (k*n_slot+s, v*n_slot+s'), one per
+//                                      coincident facet-node pair
+//   ops64/ops32   [n_e][2d][n_p][n_p]  per-element operators, transposed:
+//                 k < d: M_i^T with M_i = H^-1 (Q_x_i/(beta+1) + Q_x_i^T)
+//                 k >= d: D_i^T with D_i = H^-1 Q_x_i
+//   sat           [n_e][n_c][n_slot]   facet (SAT + dissipation) contributions
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <type_traits>
+
+#include "internal.h"
+#include "phys.cuh"
+
+namespace esplit {
+
+__constant__ RefTables c_ref;
+
+int set_ref_tables(const RefTables& t) {
+  return cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables)) == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// block reduction helpers (deterministic: fixed shuffle tree + fixed warp order)
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void block_sum(double (&v)[W], double* out_row) {
+  __shared__ double red[32][W];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      double x = lane < nw ? red[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) out_row[k] = x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-element operators (run once per mesh upload / beta change)
+// Q_x_i = 1/2 sum_j (Lam_ij Q_xi_j - Q_xi_j^T Lam_ij) + 1/2 E_x_i
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void build_ops_kernel(const double* __restrict__ Qref, const double* __restrict__ Lam,
+                                 const double* __restrict__ J, const double* __restrict__ nu, int n_e,
+                                 double inv_bp1, double* __restrict__ ops64, float* __restrict__ ops32) {
+  const int NP = c_ref.n_p, NS = c_ref.n_slot;
+  size_t per = (size_t)2 * D * NP * NP;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per * (size_t)n_e) return;
+  int e = (int)(idx / per);
+  int rem = (int)(idx - (size_t)e * per);
+  int k = rem / (NP * NP);
+  int nm = rem - k * NP * NP;
+  int n = nm / NP, m = nm - n * NP;  // stored entry (k, n, m) = matrix[m][n]
+  int i = k % D;
+  auto Qx = [&](int a, int b) -> double {
+    double s = 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double* L = Lam + (((size_t)e * D + i) * D + j) * NP;
+      s += L[a] * Qref[((size_t)j * NP + a) * NP + b] - Qref[((size_t)j * NP + b) * NP + a] * L[b];
+    }
+    s *= 0.5;
+    if (a == b) {
+      int sl = c_ref.node_slot[a];
+      if (sl >= 0) s += 0.5 * nu[((size_t)e * NS + sl) * D + i];
+    }
+    return s;
+  };
+  double Hm = c_ref.H[m] * J[(size_t)e * NP + m];
+  double val;
+  if (k < D)
+    val = (Qx(m, n) * inv_bp1 + Qx(n, m)) / Hm;
+  else
+    val = Qx(m, n) / Hm;
+  ops64[idx] = val;
+  ops32[idx] = (float)val;
+}
+
+int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
+  size_t total = (size_t)c->n_e * 2 * c->dim * c->n_p * c->n_p;
+  int bs = 256;
+  unsigned nb = (unsigned)((total + bs - 1) / bs);
+  double inv_bp1 = 1.0 / (c->prm.beta + 1.0);
+  if (c->dim == 2)
+    build_ops_kernel<2><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
+                                          c->b.ops32);
+  else
+    build_ops_kernel<3><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
+                                          c->b.ops32);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// facet kernel: one thread per coincident facet-node pair (k, m) ~ (v, n).
+//   G = sum_i nu_i F*_i(u_km, u_vn) + |nu|/2 X|L|SX^T (w_km - w_vn)
+//   sat_k,m = -G / H_k,m ;  sat_v,n = +G / H_v,n       (Eqs. (43), (69))
+// ---------------------------------------------------------------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u, const int2* __restrict__ fp,
+                                                   int n_pairs, const double* __restrict__ nu,
+                                                   const double* __restrict__ J, double* __restrict__ sat,
+                                                   Phys<T> c, int dissipation, int* __restrict__ status) {
+  constexpr int NC = D + 2;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_pairs) return;
+  const int NP = c_ref.n_p, NS = c_ref.n_slot;
+  int2 pr = __ldg(&fp[t]);
+  int k = pr.x / NS, s = pr.x - k * NS;
+  int v = pr.y / NS, s2 = pr.y - v * NS;
+  int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
+  T uk[NC], uv[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    uk[q] = (T)__ldg(&u[((size_t)k * NC + q) * NP + m]);
+    uv[q] = (T)__ldg(&u[((size_t)v * NC + q) * NP + n]);
+  }
+  Node<T, D> nk, nv;
+  bool ok = node_from_u<T, D>(uk, c, nk);
+  ok = node_from_u<T, D>(uv, c, nv) && ok;
+  if (!ok) atomicOr(status, 1);
+  ZNode<T, D> zk, zv;
+  znode<T, D>(nk, c, zk);
+  znode<T, D>(nv, c, zv);
+  PairAvg<T, D> a;
+  pair_avg<T, D>(zk, zv, c, a);
+  T nuv[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) nuv[i] = (T)__ldg(&nu[((size_t)k * NS + s) * D + i]);
+  T G[NC];
+  sy_flux_dir<T, D>(a, c, nuv, G);
+  if (dissipation) {
+    T b2 = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+    T b = t_sqrt(b2);
+    T nh[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+    T dw[NC], out[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
+    diss_apply<T, D>(a, c, nh, dw, out);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) G[q] += T(0.5) * b * out[q];
+  }
+  double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
+  double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    sat[((size_t)k * NC + q) * NS + s] = -(double)G[q] * ihk;
+    sat[((size_t)v * NC + q) * NS + s2] = (double)G[q] * ihv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// entropy-split volume kernel (Eq. (100)): EB elements per block, one thread
+// per node.  r = sum_i M_i f_i - 1/(beta+1) sum_i A~_i (D_i w) + sat
+// Optional: block partial of sum H w^T r (entropy production, float64).
+// ---------------------------------------------------------------------------
+template <typename T, int D, int NP, int EB>
+__global__ void __launch_bounds__(EB * NP) split_volume_kernel(
+    const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
+    const double* __restrict__ J, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
+    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  __shared__ T sf[EB][D][NC][NP];
+  __shared__ T sw[EB][NC][NP];
+  const int NS = c_ref.n_slot;
+  int el = threadIdx.x / NP;
+  int m = threadIdx.x - el * NP;
+  int li = blockIdx.x * EB + el;
+  bool active = (el < EB) && (li < n_list);
+  int e = active ? (list ? list[li] : li) : 0;
+  Node<T, D> nd;
+  T uu[NC];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) uu[q] = (T)__ldg(&u[((size_t)e * NC + q) * NP + m]);
+    if (!node_from_u<T, D>(uu, c, nd)) atomicOr(status, 1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T F[NC];
+      euler_flux<T, D>(nd, i, F);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sf[el][i][q][m] = F[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sw[el][q][m] = nd.W[q];
+  }
+  __syncthreads();
+  double hw = 0.0;
+  if (active) {
+    T acc[NC], g[D][NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) g[i][q] = T(0);
+    const T* op = ops + (size_t)e * (2 * D * NP * NP);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll 4
+      for (int n = 0; n < NP; ++n) {
+        T mt = __ldg(&op[(i * NP + n) * NP + m]);
+        T dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          acc[q] += mt * sf[el][i][q][n];
+          g[i][q] += dt * sw[el][q][n];
+        }
+      }
+    }
+    T nonc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) nonc[q] = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T dF[NC];
+      dflux_dw<T, D>(nd, c, i, g[i], dF);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
+    }
+    int sl = c_ref.node_slot[m];
+    double res[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      res[q] = (double)(acc[q] - c.inv_bp1 * nonc[q]);
+      if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
+      r[((size_t)e * NC + q) * NP + m] = res[q];
+    }
+    if (prod) {
+      double Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
+      if constexpr (sizeof(T) == sizeof(double)) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) hw += (double)nd.W[q] * res[q];
+      } else {
+        double u64[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) u64[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
+        Node<double, D> n64;
+        node_from_u<double, D>(u64, c64, n64);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) hw += n64.W[q] * res[q];
+      }
+      hw *= Hm;
+    }
+  }
+  if (prod) {
+    double v[1] = {hw};
+    block_sum<1>(v, prod + blockIdx.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Hadamard-form volume kernel (Eq. (99)), Sjogreen-Yee flux, each unordered
+// node pair evaluated once: thread m takes pairs (m, m+k mod NP),
+// k = 1..NP/2 (k = NP/2 only for m < NP/2 when NP is even), and hands the
+// partner's share through shared memory (no atomics).
+//   G = sum_i S_i[m][n] F*_i(u_m, u_n),  S_i[m][n] = H_m D_i[m][n]
+//   r_m -= 2 G / H_m,  r_n += 2 G / H_n
+// ---------------------------------------------------------------------------
+template <typename T, int D, int NP, int EB>
+__global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
+    const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
+    const double* __restrict__ J, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
+    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  constexpr int K = NP / 2;
+  constexpr int NZ = D + 5;  // q, V[D], p, P1, P2, v2
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sz = reinterpret_cast<T*>(smem_raw);           // [EB][NZ][NP]
+  T* sg = sz + EB * NZ * NP;                         // [EB][NP][K][NC]
+  T* sH = sg + EB * NP * K * NC;                     // [EB][NP]
+  const int NS = c_ref.n_slot;
+  int el = threadIdx.x / NP;
+  int m = threadIdx.x - el * NP;
+  int li = blockIdx.x * EB + el;
+  bool active = (el < EB) && (li < n_list);
+  int e = active ? (list ? list[li] : li) : 0;
+  Node<T, D> nd;
+  if (active) {
+    T uu[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) uu[q] = (T)__ldg(&u[((size_t)e * NC + q) * NP + m]);
+    if (!node_from_u<T, D>(uu, c, nd)) atomicOr(status, 1);
+    ZNode<T, D> z;
+    znode<T, D>(nd, c, z);
+    T* zz = sz + el * NZ * NP;
+    zz[0 * NP + m] = z.q;
+#pragma unroll
+    for (int i = 0; i < D; ++i) zz[(1 + i) * NP + m] = z.V[i];
+    zz[(D + 1) * NP + m] = z.p;
+    zz[(D + 2) * NP + m] = z.P1;
+    zz[(D + 3) * NP + m] = z.P2;
+    zz[(D + 4) * NP + m] = z.v2;
+    sH[el * NP + m] = (T)(c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]));
+  }
+  __syncthreads();
+  T acc[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) acc[q] = T(0);
+  if (active) {
+    const T* zz = sz + el * NZ * NP;
+    ZNode<T, D> zm;
+    zm.q = zz[m];
+#pragma unroll
+    for (int i = 0; i < D; ++i) zm.V[i] = zz[(1 + i) * NP + m];
+    zm.p = zz[(D + 1) * NP + m];
+    zm.P1 = zz[(D + 2) * NP + m];
+    zm.P2 = zz[(D + 3) * NP + m];
+    zm.v2 = zz[(D + 4) * NP + m];
+    T Hm = sH[el * NP + m];
+    const T* op = ops + (size_t)e * (2 * D * NP * NP);
+    T* gout = sg + ((size_t)el * NP + m) * K * NC;
+    for (int k = 1; k <= K; ++k) {
+      if ((NP % 2 == 0) && k == K && m >= K) break;
+      int n = m + k;
+      if (n >= NP) n -= NP;
+      ZNode<T, D> zn;
+      zn.q = zz[n];
+#pragma unroll
+      for (int i = 0; i < D; ++i) zn.V[i] = zz[(1 + i) * NP + n];
+      zn.p = zz[(D + 1) * NP + n];
+      zn.P1 = zz[(D + 2) * NP + n];
+      zn.P2 = zz[(D + 3) * NP + n];
+      zn.v2 = zz[(D + 4) * NP + n];
+      PairAvg<T, D> a;
+      pair_avg<T, D>(zm, zn, c, a);
+      T Smn[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) Smn[i] = Hm * __ldg(&op[((D + i) * NP + n) * NP + m]);
+      T G[NC];
+      sy_flux_dir<T, D>(a, c, Smn, G);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        acc[q] -= T(2) * G[q] / Hm;
+        gout[(k - 1) * NC + q] = T(2) * G[q];
+      }
+    }
+  }
+  __syncthreads();
+  double hw = 0.0;
+  if (active) {
+    T Hm = sH[el * NP + m];
+    for (int k = 1; k <= K; ++k) {
+      int src = m - k;
+      if (src < 0) src += NP;
+      if ((NP % 2 == 0) && k == K && src >= K) continue;
+      const T* gin = sg + ((size_t)el * NP + src) * K * NC + (k - 1) * NC;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) acc[q] += gin[q] / Hm;
+    }
+    int sl = c_ref.node_slot[m];
+    double res[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      res[q] = (double)acc[q];
+      if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
+      r[((size_t)e * NC + q) * NP + m] = res[q];
+    }
+    if (prod) {
+      double u64[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) u64[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
+      Node<double, D> n64;
+      node_from_u<double, D>(u64, c64, n64);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) hw += n64.W[q] * res[q];
+      hw *= c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
+    }
+  }
+  if (prod) {
+    double v[1] = {hw};
+    block_sum<1>(v, prod + blockIdx.x);
+  }
+}
+
+template <int NP>
+struct VolCfg {
+  static constexpr int EB_SPLIT = (256 / NP) > 0 ? (256 / NP) : 1;
+  static constexpr int EB_HAD = (128 / NP) > 0 ? (128 / NP) : 1;
+};
+
+template <typename T, int D, int NP>
+static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+  const Phys<T> ph = make_phys<T>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  const Phys<double> ph64 = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  const T* ops = std::is_same<T, double>::value ? (const T*)c->b.ops64 : (const T*)c->b.ops32;
+  // facet terms first: they fill the sat buffer the volume kernels add
+  {
+    int bs = 128;
+    int nb = (c->n_pairs + bs - 1) / bs;
+    ProfScope ps(c, PG_FACE, s);
+    face_kernel<T, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.sat, ph,
+                                        c->prm.dissipation, c->b.status);
+    c->launches++;
+  }
+  int np_used = 0;
+  int scheme = c->prm.scheme;
+  int n_split = scheme == ESPLIT_SCHEME_SPLIT ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_split : 0);
+  int n_had = scheme == ESPLIT_SCHEME_HADAMARD ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_had : 0);
+  const int* lsplit = scheme == ESPLIT_SCHEME_HYBRID ? c->b.list_split : nullptr;
+  const int* lhad = scheme == ESPLIT_SCHEME_HYBRID ? c->b.list_had : nullptr;
+  if (n_split > 0) {
+    constexpr int EB = VolCfg<NP>::EB_SPLIT;
+    int nb = (n_split + EB - 1) / EB;
+    ProfScope ps(c, PG_SPLIT, s);
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.J, c->b.sat, lsplit, n_split, ph,
+                                                             ph64, c->b.status, prod ? prod + np_used : nullptr);
+    c->launches++;
+    np_used += nb;
+  }
+  if (n_had > 0) {
+    constexpr int EB = VolCfg<NP>::EB_HAD;
+    constexpr int K = NP / 2;
+    size_t smem = sizeof(T) * ((size_t)EB * (D + 5) * NP + (size_t)EB * NP * K * (D + 2) + (size_t)EB * NP);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      attr_set = true;
+    }
+    int nb = (n_had + EB - 1) / EB;
+    ProfScope ps(c, PG_HAD, s);
+    hadamard_volume_kernel<T, D, NP, EB><<<nb, EB * NP, smem, s>>>(
+        u, r, ops, c->b.J, c->b.sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
+    c->launches++;
+    np_used += nb;
+  }
+  if (n_partial) *n_partial = np_used;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T>
+static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+  if (c->dim == 2) {
+    switch (c->n_p) {
+      case 7: return residual_np<T, 2, 7>(c, u, r, s, prod, n_partial);
+      case 12: return residual_np<T, 2, 12>(c, u, r, s, prod, n_partial);
+      case 18: return residual_np<T, 2, 18>(c, u, r, s, prod, n_partial);
+      case 27: return residual_np<T, 2, 27>(c, u, r, s, prod, n_partial);
+    }
+  }
+  return -2;
+}
+
+int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+  if (c->prm.precision == ESPLIT_FP32_BULK) return residual_t<float>(c, u, r, s, prod, n_partial);
+  return residual_t<double>(c, u, r, s, prod, n_partial);
+}
+
+// ---------------------------------------------------------------------------
+// entropy functionals, one thread per node
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) entropy_kernel(const double* __restrict__ u, const double* __restrict__ J,
+                                                      size_t n_nodes, Phys<double> c, double* __restrict__ part) {
+  constexpr int NC = D + 2;
+  const int NP = c_ref.n_p;
+  size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (g < n_nodes) {
+    size_t e = g / NP;
+    int m = (int)(g - e * NP);
+    double uu[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) uu[q] = __ldg(&u[(e * NC + q) * NP + m]);
+    Node<double, D> nd;
+    node_from_u<double, D>(uu, c, nd);
+    double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
+    double sH = c.beta * nd.q * nd.p;  // S_H = beta rho (p rho^-gam)^(1/(alpha+gam)) = beta q p
+    v[0] = H * sH;
+    v[1] = H * fabs(sH);
+  }
+  block_sum<2>(v, part + 2 * blockIdx.x);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) entropy_rate_kernel(const double* __restrict__ u,
+                                                           const double* __restrict__ r,
+                                                           const double* __restrict__ J, size_t n_nodes,
+                                                           Phys<double> c, double* __restrict__ part) {
+  constexpr int NC = D + 2;
+  const int NP = c_ref.n_p;
+  size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (g < n_nodes) {
+    size_t e = g / NP;
+    int m = (int)(g - e * NP);
+    double uu[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) uu[q] = __ldg(&u[(e * NC + q) * NP + m]);
+    Node<double, D> nd;
+    node_from_u<double, D>(uu, c, nd);
+    double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
+    double wr = 0.0, w2 = 0.0, r2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      double rq = __ldg(&r[(e * NC + q) * NP + m]);
+      wr += nd.W[q] * rq;
+      w2 += nd.W[q] * nd.W[q];
+      r2 += rq * rq;
+    }
+    v[0] = H * wr;
+    v[1] = H * sqrt(w2 * r2);
+  }
+  block_sum<2>(v, part + 2 * blockIdx.x);
+}
+
+int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial) {
+  size_t n = (size_t)c->n_e * c->n_p;
+  int nb = (int)((n + 255) / 256);
+  Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  ProfScope ps(c, PG_ENTROPY, s);
+  if (c->dim == 2)
+    entropy_kernel<2><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial);
+  else
+    entropy_kernel<3><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial);
+  c->launches++;
+  *n_partial = nb;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial) {
+  size_t n = (size_t)c->n_e * c->n_p;
+  int nb = (int)((n + 255) / 256);
+  Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  ProfScope ps(c, PG_ENTROPY, s);
+  if (c->dim == 2)
+    entropy_rate_kernel<2><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, c->b.partial);
+  else
+    entropy_rate_kernel<3><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, c->b.partial);
+  c->launches++;
+  *n_partial = nb;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// fixed-order reduction of `n` rows of `width` partials into out[width]
+__global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* __restrict__ part, int n, int width,
+                                                               double* __restrict__ out) {
+  for (int k = 0; k < width; ++k) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += part[(size_t)i * width + k];
+    block_sum<1>(v, out + k);
+    __syncthreads();
+  }
+}
+
+int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s) {
+  ProfScope ps(c, PG_ENTROPY, s);
+  reduce_partials_kernel<<<1, 1024, 0, s>>>(partial, n_partial, width, out);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// RK4 stage combination: u_next = u_n + a_dt r ; dacc (=|+=) b_dt r
+// ---------------------------------------------------------------------------
+__global__ void stage_kernel(const double* __restrict__ un, const double* __restrict__ r, double a_dt, double b_dt,
+                             int first, double* __restrict__ u_next, double* __restrict__ dacc, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) {
+    double ri = r[i];
+    if (u_next) u_next[i] = un[i] + a_dt * ri;
+    dacc[i] = first ? b_dt * ri : dacc[i] + b_dt * ri;
+  }
+}
+
+static unsigned grid_for(size_t n) {
+  size_t nb = (n + 255) / 256;
+  size_t cap = 152 * 16;
+  return (unsigned)(nb < cap ? nb : cap);
+}
+
+int launch_stage(esplit_ctx* c, const double* un, const double* r, double a_dt, double b_dt, int first,
+                 double* u_next, double* dacc, size_t n, cudaStream_t s) {
+  ProfScope ps(c, PG_STAGE, s);
+  stage_kernel<<<grid_for(n), 256, 0, s>>>(un, r, a_dt, b_dt, first, u_next, dacc, n);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+__global__ void axpy_kernel(const double* __restrict__ x, double a, const double* __restrict__ y,
+                            double* __restrict__ out, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) out[i] = x[i] + a * y[i];
+}
+
+int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, double* out, size_t n, cudaStream_t s) {
+  ProfScope ps(c, PG_STAGE, s);
+  axpy_kernel<<<grid_for(n), 256, 0, s>>>(x, a, y, out, n);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// relaxation root solve of Eq. (97) on the device
+//   f(g) = 1^T H s(u_n + g d) - S0 - g est,  f'(g) = 1^T H w(u_n + g d) . d - est
+// Newton from g = 1, safeguarded by the bracket [lo, hi] (f(lo) < 0 < f(hi));
+// bisection whenever the Newton point leaves the bracket or f' <= 0.
+// Termination: |f| <= 8 eps 1^T H |s|, |step| <= 4 eps g, or 40 evaluations.
+// No positive root (hi shrinking below 2^-10 or g beyond 4) -> status -5.
+// ---------------------------------------------------------------------------
+constexpr int ROOT_MAX_EVALS = 40;
+
+__global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
+  // scal[0..1] = S0, Sabs ; scal[2..5] = stage productions e_1..e_4
+  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  st->S0 = scal[0];
+  st->Sabs = scal[1];
+  double est = 0.0;
+  for (int i = 0; i < 4; ++i) est += b[i] * scal[2 + i];
+  st->est = dt * est;
+  st->g = 1.0;
+  st->lo = 0.0;
+  st->hi = -1.0;  // unset
+  st->flo = 0.0;
+  st->fhi = 0.0;
+  st->phase = 0;
+  st->done = 0;
+  st->iters = 0;
+  st->status = 0;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict__ un, const double* __restrict__ d,
+                                                        const double* __restrict__ J, size_t n_nodes,
+                                                        Phys<double> c, const RootState* __restrict__ st,
+                                                        double* __restrict__ part) {
+  if (st->done) return;
+  constexpr int NC = D + 2;
+  const int NP = c_ref.n_p;
+  double g = st->g;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (t < n_nodes) {
+    size_t e = t / NP;
+    int m = (int)(t - e * NP);
+    double uu[NC], dd[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      size_t ix = (e * NC + q) * NP + m;
+      dd[q] = __ldg(&d[ix]);
+      uu[q] = __ldg(&un[ix]) + g * dd[q];
+    }
+    Node<double, D> nd;
+    node_from_u<double, D>(uu, c, nd);
+    double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
+    double wd = 0.0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) wd += nd.W[q] * dd[q];
+    v[0] = H * c.beta * nd.q * nd.p;
+    v[1] = H * wd;
+  }
+  block_sum<2>(v, part + 2 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) root_update_kernel(const double* __restrict__ part, int n,
+                                                           RootState* st) {
+  if (st->done) return;
+  __shared__ double tot[2];
+  for (int k = 0; k < 2; ++k) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += part[(size_t)i * 2 + k];
+    block_sum<1>(v, tot + k);
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double eps = 2.220446049250313e-16;
+  double g = st->g;
+  double f = tot[0] - st->S0 - g * st->est;
+  double df = tot[1] - st->est;
+  st->iters += 1;
+  st->f_last = f;
+  st->df_last = df;
+  if (fabs(f) <= 8.0 * eps * st->Sabs) {
+    st->done = 1;
+    return;
+  }
+  if (f < 0.0) {
+    st->lo = g;
+    st->flo = f;
+  } else {
+    st->hi = g;
+    st->fhi = f;
+  }
+  bool have_hi = st->hi > 0.0;
+  double gn;
+  if (df > 0.0)
+    gn = g - f / df;
+  else
+    gn = have_hi ? 0.5 * (st->lo + st->hi) : 2.0 * g;
+  if (gn <= st->lo || (have_hi && gn >= st->hi)) gn = have_hi ? 0.5 * (st->lo + st->hi) : 2.0 * fmax(g, st->lo);
+  if (have_hi && st->hi < 0.0009765625 && st->lo == 0.0) {
+    st->status = ESPLIT_ERR_RRK_NO_ROOT;
+    st->done = 1;
+    return;
+  }
+  if (gn > 4.0) {
+    st->status = ESPLIT_ERR_RRK_NO_ROOT;
+    st->done = 1;
+    return;
+  }
+  if (fabs(gn - g) <= 4.0 * eps * fabs(g) || (have_hi && st->hi - st->lo <= 4.0 * eps * st->hi)) {
+    st->g = gn;
+    st->done = 1;
+    return;
+  }
+  if (st->iters >= ROOT_MAX_EVALS) {
+    if (!have_hi || st->lo == 0.0) st->status = ESPLIT_ERR_RRK_NO_ROOT;
+    st->g = gn;
+    st->done = 1;
+    return;
+  }
+  st->g = gn;
+}
+
+int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s, int* n_partial) {
+  size_t n = (size_t)c->n_e * c->n_p;
+  int nb = (int)((n + 255) / 256);
+  Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  ProfScope ps(c, PG_ROOT, s);
+  if (c->dim == 2)
+    root_eval_kernel<2><<<nb, 256, 0, s>>>(un, d, c->b.J, n, ph, c->b.root, c->b.partial);
+  else
+    root_eval_kernel<3><<<nb, 256, 0, s>>>(un, d, c->b.J, n, ph, c->b.root, c->b.partial);
+  c->launches++;
+  *n_partial = nb;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s) {
+  ProfScope ps(c, PG_ROOT, s);
+  root_update_kernel<<<1, 1024, 0, s>>>(c->b.partial, n_partial, c->b.root);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+__global__ void root_apply_kernel(double* __restrict__ un, const double* __restrict__ d, size_t n,
+                                  const RootState* __restrict__ st, const int* __restrict__ status) {
+  if (st->status != 0 || *status != 0) return;
+  double g = st->g;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) un[i] += g * d[i];
+}
+
+int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s) {
+  ProfScope ps(c, PG_STAGE, s);
+  root_apply_kernel<<<grid_for(n), 256, 0, s>>>(un, d, n, c->b.root, c->b.status);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
+  ProfScope ps(c, PG_ROOT, s);
+  root_init_kernel<<<1, 1, 0, s>>>(c->b.root, c->b.scal, dt);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace esplit

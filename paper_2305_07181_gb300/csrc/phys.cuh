@@ -1,0 +1,325 @@
+// Pointwise physics of the entropy-split scheme, device side, templated on the
+// arithmetic type T (double for the FP64 path, float for the FP32-bulk path)
+// and the dimension D (n_c = D + 2 components).
+//
+// Paper: Worku & Zingg, entropy-split multidimensional SBP (Secs. 2-4).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace esplit {
+
+// Constants derived from (gam, beta) on the host, Sec. 2.4 / Eq. (16):
+// alpha = -gam - beta (gam - 1).
+template <typename T>
+struct Phys {
+  T gam, alpha, beta;
+  T gm1, inv_gm1;      // gam - 1, 1/(gam - 1)
+  T a_q, b_q;          // q = rho^a_q p^b_q = (rho/p)(p rho^-gam)^(1/(alpha+gam)), Eq. (41)
+  T w1c;               // -alpha/(gam-1): W_1 = q (w1c p/rho - |V|^2/2), Eq. (25)
+  T inv_w1c;           // -(gam-1)/alpha
+  T inv_apb;           // 1/(a_q + b_q) = (alpha+gam)/(1-gam)
+  T r1, r2;            // -gam/alpha and (1-gam)/alpha: the powers of z_1 and z_nc
+                       // appearing in Eq. (48) (arithmetic and exponential means)
+  T inv_bp1;           // 1/(beta+1)
+  T gam_gm1;           // gam/(gam-1)
+  T s_ac, s_en;        // S^ entries: 1/(2 gam), (gam-1)(gam+alpha)/(gam alpha), Eq. (76)
+  T mu, kappa, R;      // viscosity, conductivity mu gam R/((gam-1) Pr), gas constant
+};
+
+template <typename T>
+__host__ inline Phys<T> make_phys(double gam, double beta, double R, double mu, double Pr) {
+  Phys<T> c;
+  double alpha = -gam - beta * (gam - 1.0);
+  c.gam = (T)gam;
+  c.alpha = (T)alpha;
+  c.beta = (T)beta;
+  c.gm1 = (T)(gam - 1.0);
+  c.inv_gm1 = (T)(1.0 / (gam - 1.0));
+  c.a_q = (T)(alpha / (alpha + gam));
+  c.b_q = (T)((1.0 - alpha - gam) / (alpha + gam));
+  c.w1c = (T)(-alpha / (gam - 1.0));
+  c.inv_w1c = (T)(-(gam - 1.0) / alpha);
+  c.inv_apb = (T)((alpha + gam) / (1.0 - gam));
+  c.r1 = (T)(-gam / alpha);
+  c.r2 = (T)((1.0 - gam) / alpha);
+  c.inv_bp1 = (T)(1.0 / (beta + 1.0));
+  c.gam_gm1 = (T)(gam / (gam - 1.0));
+  c.s_ac = (T)(1.0 / (2.0 * gam));
+  c.s_en = (T)((gam - 1.0) * (gam + alpha) / (gam * alpha));
+  c.mu = (T)mu;
+  c.kappa = (T)(mu * gam * R / ((gam - 1.0) * Pr));
+  c.R = (T)R;
+  return c;
+}
+
+__device__ __forceinline__ double t_log(double x) { return log(x); }
+__device__ __forceinline__ float t_log(float x) { return logf(x); }
+__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+__device__ __forceinline__ float t_exp(float x) { return expf(x); }
+__device__ __forceinline__ double t_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float t_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double t_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float t_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double t_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
+
+// Nodal state: primitives, q = z_1 of Eq. (45) (= -W_nc), Harten entropy
+// variables W of Eq. (25).
+template <typename T, int D>
+struct Node {
+  T rho, V[D], p, e, q, v2;
+  T W[D + 2];
+};
+
+// Returns false for a non-physical state (rho <= 0, p <= 0 or NaN).
+template <typename T, int D>
+__device__ __forceinline__ bool node_from_u(const T* u, const Phys<T>& c, Node<T, D>& n) {
+  n.rho = u[0];
+  T ir = T(1) / n.rho;
+  n.v2 = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    n.V[i] = u[1 + i] * ir;
+    n.v2 += n.V[i] * n.V[i];
+  }
+  n.e = u[D + 1];
+  n.p = c.gm1 * (n.e - T(0.5) * n.rho * n.v2);
+  bool ok = (n.rho > T(0)) && (n.p > T(0)) && isfinite(n.e);
+  n.q = t_exp(c.a_q * t_log(n.rho) + c.b_q * t_log(n.p));
+  n.W[0] = n.q * (c.w1c * n.p * ir - T(0.5) * n.v2);
+#pragma unroll
+  for (int i = 0; i < D; ++i) n.W[1 + i] = n.q * n.V[i];
+  n.W[D + 1] = -n.q;
+  return ok;
+}
+
+// Euler flux F^{I(i)} of Eq. (5).
+template <typename T, int D>
+__device__ __forceinline__ void euler_flux(const Node<T, D>& n, int i, T* F) {
+  T m = n.rho * n.V[i];
+  F[0] = m;
+#pragma unroll
+  for (int j = 0; j < D; ++j) F[1 + j] = m * n.V[j] + (j == i ? n.p : T(0));
+  F[D + 1] = (n.e + n.p) * n.V[i];
+}
+
+// dF^{I(i)} = A~_i v (Eq. (19)): the change of F_i(U(W)) for a change v of
+// the entropy variables, by the chain rule through (q, V, theta = p/rho, rho):
+//   q = -W_nc, V = W_(1..d)/q, W_1/q = w1c theta - |V|^2/2,
+//   q = rho^(a_q + b_q) theta^b_q.
+template <typename T, int D>
+__device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const Phys<T>& c, int i, const T* v, T* dF) {
+  T iq = T(1) / n.q;
+  T dq = -v[D + 1];
+  T dV[D];
+  T vdv = T(0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    dV[j] = (v[1 + j] - dq * n.V[j]) * iq;
+    vdv += n.V[j] * dV[j];
+  }
+  T ir = T(1) / n.rho;
+  T theta = n.p * ir;
+  T w0q = c.w1c * theta - T(0.5) * n.v2;
+  T dtheta = c.inv_w1c * ((v[0] - dq * w0q) * iq + vdv);
+  T drho = n.rho * c.inv_apb * (dq * iq - c.b_q * dtheta / theta);
+  T dp = drho * theta + n.rho * dtheta;
+  T dm = drho * n.V[i] + n.rho * dV[i];
+  dF[0] = dm;
+  T rvi = n.rho * n.V[i];
+#pragma unroll
+  for (int j = 0; j < D; ++j) dF[1 + j] = dm * n.V[j] + rvi * dV[j] + (j == i ? dp : T(0));
+  T de = dp * c.inv_gm1 + T(0.5) * drho * n.v2 + n.rho * vdv;
+  dF[D + 1] = (de + dp) * n.V[i] + (n.e + n.p) * dV[i];
+}
+
+// Powers of the parameter vector used by the two-point flux and the
+// dissipation: P1 = z_1^r1 = q^r1, P2 = z_nc^r2 = p^r2.
+template <typename T, int D>
+__device__ __forceinline__ void z_powers(const Node<T, D>& n, const Phys<T>& c, T& P1, T& P2) {
+  T lq = c.a_q * t_log(n.rho) + c.b_q * t_log(n.p);
+  P1 = t_exp(c.r1 * lq);
+  P2 = t_exp(c.r2 * t_log(n.p));
+}
+
+// Exponential average of Eq. (47), {u^(r-1)}_e = (a^r - b^r)/(r (a - b)),
+// given ar = a^r and br = b^r.  For |b/a - 1| >= EPS_SWITCH the quotient is
+// used directly; below it the equivalent form a^(r-1) g(eps),
+// g(eps) = ((1+eps)^r - 1)/(r eps) = sum_k c_k eps^k with c_0 = 1,
+// c_k = c_(k-1) (r - k)/(k + 1), summed to NTERMS terms.
+template <typename T>
+struct ExpAvgCfg;
+template <>
+struct ExpAvgCfg<double> {
+  static constexpr double EPS_SWITCH = 0.05;
+  static constexpr int NTERMS = 16;
+};
+template <>
+struct ExpAvgCfg<float> {
+  static constexpr float EPS_SWITCH = 0.25f;
+  static constexpr int NTERMS = 14;
+};
+
+template <typename T>
+__device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, T r) {
+  T ia = T(1) / a;
+  T eps = (b - a) * ia;
+  if (t_abs(eps) >= ExpAvgCfg<T>::EPS_SWITCH) {
+    return (ar - br) / (r * (a - b));
+  }
+  T ck = T(1), sum = T(1), ep = T(1);
+#pragma unroll
+  for (int k = 1; k < ExpAvgCfg<T>::NTERMS; ++k) {
+    ck = ck * (r - T(k)) / T(k + 1);
+    ep *= eps;
+    sum += ck * ep;
+  }
+  return ar * ia * sum;
+}
+
+// Everything the two-point flux needs at one node.
+template <typename T, int D>
+struct ZNode {
+  T q, V[D], p, P1, P2, v2;
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void znode(const Node<T, D>& n, const Phys<T>& c, ZNode<T, D>& z) {
+  z.q = n.q;
+  z.p = n.p;
+  z.v2 = n.v2;
+#pragma unroll
+  for (int i = 0; i < D; ++i) z.V[i] = n.V[i];
+  z_powers<T, D>(n, c, z.P1, z.P2);
+}
+
+// Pair averages shared by the Sjogreen-Yee flux (Eq. (48)) and the
+// intermediate state of the dissipation (Eqs. (73)-(78)).
+template <typename T, int D>
+struct PairAvg {
+  T A1;       // {z_1^(-gam/alpha)}            arithmetic
+  T E1;       // {z_nc^((1-gam-alpha)/alpha)}_e exponential
+  T A2;       // {z_nc^(-(gam-1)/alpha)}       arithmetic
+  T E2;       // {z_1^(-(gam+alpha)/alpha)}_e  exponential
+  T z1a;      // {z_1}
+  T qV[D];    // {z_1 z_(i+1)}
+  T Va[D];    // {V}
+  T pa;       // {p}
+  T ke;       // sum {V_j}^2 - 1/2 {sum V_j^2}
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void pair_avg(const ZNode<T, D>& k, const ZNode<T, D>& v, const Phys<T>& c,
+                                         PairAvg<T, D>& a) {
+  a.A1 = T(0.5) * (k.P1 + v.P1);
+  a.E1 = exp_avg<T>(k.p, v.p, k.P2, v.P2, c.r2);
+  a.A2 = T(0.5) * (k.P2 + v.P2);
+  a.E2 = exp_avg<T>(k.q, v.q, k.P1, v.P1, c.r1);
+  a.z1a = T(0.5) * (k.q + v.q);
+  a.ke = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    a.qV[i] = T(0.5) * (k.q * k.V[i] + v.q * v.V[i]);
+    a.Va[i] = T(0.5) * (k.V[i] + v.V[i]);
+    a.ke += a.Va[i] * a.Va[i];
+  }
+  a.ke -= T(0.25) * (k.v2 + v.v2);
+  a.pa = T(0.5) * (k.p + v.p);
+}
+
+// sum_i nu_i F*_i(U_k, U_v) (Eq. (48)) for a direction vector nu.
+template <typename T, int D>
+__device__ __forceinline__ void sy_flux_dir(const PairAvg<T, D>& a, const Phys<T>& c, const T* nu, T* F) {
+  T inv_den = T(1) / (a.A1 * a.E1);
+  T mn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) mn += nu[i] * a.qV[i];
+  mn *= inv_den;
+  F[0] = mn;
+#pragma unroll
+  for (int j = 0; j < D; ++j) F[1 + j] = mn * a.Va[j] + nu[j] * a.pa;
+  F[D + 1] = mn * (c.gam_gm1 * a.A2 * a.E2 + a.ke);
+}
+
+// X^ |Lambda_n| S^ X^T dw of Eq. (69) at the intermediate state (Eqs.
+// (73)-(80)); n is a unit normal.  3D eigenvectors as printed, 2D by
+// deleting the fourth row and column.
+template <typename T, int D>
+__device__ __forceinline__ void diss_apply(const PairAvg<T, D>& a, const Phys<T>& c, const T* n, const T* dw,
+                                           T* out) {
+  T rho_h = a.z1a / (a.A1 * a.E1);
+  T iz = T(1) / a.z1a;
+  T Vh[D];
+  T vh2 = T(0), vn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Vh[i] = a.qV[i] * iz;
+    vh2 += Vh[i] * Vh[i];
+    vn += Vh[i] * n[i];
+  }
+  T p_h = a.pa;
+  T theta = rho_h / (p_h * a.A1 * a.E1);
+  T eta = T(1) / (a.z1a * a.E2 * a.E1);
+  T ah = t_sqrt(c.gam * p_h / rho_h);
+  T Hh = ah * ah * c.inv_gm1 + T(0.5) * vh2;
+  constexpr int NC = D + 2;
+  // columns of X^
+  T X[NC][NC];  // X[row][col]
+  X[0][0] = T(1);
+  X[0][1] = T(1);
+  X[0][NC - 1] = T(1);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    X[1 + i][0] = Vh[i] - ah * n[i];
+    X[1 + i][1] = Vh[i];
+    X[1 + i][NC - 1] = Vh[i] + ah * n[i];
+  }
+  X[NC - 1][0] = Hh - ah * vn;
+  X[NC - 1][1] = T(0.5) * vh2;
+  X[NC - 1][NC - 1] = Hh + ah * vn;
+  if constexpr (D == 2) {
+    X[0][2] = T(0);
+    X[1][2] = n[1];
+    X[2][2] = -n[0];
+    X[3][2] = Vh[0] * n[1] - Vh[1] * n[0];
+  } else {
+    X[0][2] = T(0);
+    X[1][2] = n[1];
+    X[2][2] = -n[0];
+    X[3][2] = T(0);
+    X[4][2] = Vh[0] * n[1] - Vh[1] * n[0];
+    X[0][3] = T(0);
+    X[1][3] = -n[2];
+    X[2][3] = T(0);
+    X[3][3] = n[0];
+    X[4][3] = Vh[2] * n[0] - Vh[0] * n[2];
+  }
+  T s_ac = c.s_ac * theta;
+  T lam_s[NC];
+  lam_s[0] = t_abs(vn - ah) * s_ac;
+  lam_s[1] = t_abs(vn) * c.s_en * theta;
+#pragma unroll
+  for (int k = 2; k < NC - 1; ++k) lam_s[k] = t_abs(vn) * eta;
+  lam_s[NC - 1] = t_abs(vn + ah) * s_ac;
+  T y[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < NC; ++r) s += X[r][k] * dw[r];
+    y[k] = s * lam_s[k];
+  }
+#pragma unroll
+  for (int r = 0; r < NC; ++r) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) s += X[r][k] * y[k];
+    out[r] = s;
+  }
+}
+
+}  // namespace esplit

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA residual, entropy functionals and relaxation RK4 step
+through the C ABI against the FP64 CPU oracle on identical seeded inputs.
+
+Tolerances
+  FP64 residual: max-norm relative error per component <= 1e-12
+  FP32-bulk residual: <= FP32_BOUND (stated bound, see FP32_BOUND below)
+  entropy functionals: <= 1e-12 relative
+  relaxation parameter: <= 1e-10 absolute (g is defined only to about
+  eps |S| / |f'(g)|; both sides stop at that noise floor)
+"""
+import numpy as np
+import pytest
+import torch
+
+from esplit_inputs import tri_operator, periodic_tri_mesh, states
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_BOUND = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_07181_gb300 as es
+    return es
+
+
+def _oracle():
+    from oracle import residual as R, diagnostics as Dg, rrk
+    from oracle.physics import Params as OP
+    return R, Dg, rrk, OP
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.abs(a - b).max(axis=(0, 2))
+    den = np.abs(b).max(axis=(0, 2))
+    return float((num / den).max())
+
+
+CASES = [("split", False), ("split", True), ("hadamard", False), ("hadamard", True), ("hybrid", True)]
+
+
+def _mesh(p, N=5, amp=0.05):
+    op = tri_operator(p)
+    return op, periodic_tri_mesh(op, N, 10.0, amp)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("scheme,diss", CASES)
+def test_residual_fp64_parity(lib, p, scheme, diss):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(p)  # 50 elements: several blocks and a ragged tail for every n_p
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=10 + p)
+    flags = np.random.default_rng(p).integers(0, 2, m.n_e).astype(np.uint8)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=diss))
+    if scheme == "hybrid":
+        s.set_hybrid_flags(flags)
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=diss, hybrid_flags=flags).numpy()
+    assert rel_err(r, ro) <= FP64_TOL
+    assert s.status() == 0
+    s.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("scheme", ["split", "hadamard"])
+def test_residual_fp32_bulk_bound(lib, p, scheme):
+    """FP32-bulk against the FP64 oracle on the config-2 state kind (vortex +
+    1e-3 noise), with dissipation."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(p, N=8)
+    u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32"))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True).numpy()
+    err = rel_err(r, ro)
+    print(f"fp32 p={p} {scheme} rel err {err:.3e}")
+    assert err <= FP32_BOUND
+    s.close()
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_entropy_functionals(lib, p):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(p)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=3)
+    s = lib.Solver(op, m, lib.Params(dissipation=True))
+    ud = s.to_device(u)
+    r = s.residual(ud)
+    S = s.entropy(ud)
+    So = float(Dg.entropy_total(u, op, m, OP()))
+    assert abs(S - So) <= 1e-13 * abs(So)
+    rate = s.entropy_rate(ud, r)
+    rate_o = float(Dg.entropy_rate(u, r.cpu().numpy(), op, m, OP()))
+    scale = float(Dg.entropy_rate_scale(u, r.cpu().numpy(), op, m, OP()))
+    assert abs(rate - rate_o) <= 1e-13 * scale
+    s.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("scheme", ["split", "hadamard", "hybrid"])
+def test_gpu_entropy_conservation(lib, p, scheme):
+    """Thms. 2 and 4 hold for the GPU residual itself (any state)."""
+    op, m = _mesh(p)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=20 + p)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme))
+    if scheme == "hybrid":
+        s.set_hybrid_flags(np.random.default_rng(9).integers(0, 2, m.n_e))
+    ud = s.to_device(u)
+    r = s.residual(ud)
+    R, Dg, rrk, OP = _oracle()
+    scale = float(Dg.entropy_rate_scale(u, r.cpu().numpy(), op, m, OP()))
+    assert abs(s.entropy_rate(ud, r)) <= 1e-13 * scale
+    s.close()
+
+
+def test_hybrid_extremes_match_pure_schemes(lib):
+    op, m = _mesh(3)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=5)
+    s = lib.Solver(op, m, lib.Params(scheme="hybrid", dissipation=True))
+    ud = s.to_device(u)
+    s.set_hybrid_flags(np.zeros(m.n_e))
+    r0 = s.residual(ud).cpu().numpy()
+    s.set_hybrid_flags(np.ones(m.n_e))
+    r1 = s.residual(ud).cpu().numpy()
+    s.set_params(lib.Params(scheme="split", dissipation=True))
+    rs = s.residual(ud).cpu().numpy()
+    s.set_params(lib.Params(scheme="hadamard", dissipation=True))
+    rh = s.residual(ud).cpu().numpy()
+    assert np.array_equal(r0, rs)
+    assert np.array_equal(r1, rh)
+    s.close()
+
+
+def test_host_entry_matches_device(lib):
+    op, m = _mesh(2)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=6)
+    s = lib.Solver(op, m, lib.Params(dissipation=True))
+    r_dev = s.residual(s.to_device(u)).cpu().numpy()
+    r_host = s.residual_host(np.ascontiguousarray(u))
+    assert np.array_equal(r_dev, r_host)
+    s.close()
+
+
+def test_two_element_mesh(lib):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(1, N=1)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=7)
+    s = lib.Solver(op, m, lib.Params(dissipation=True))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), dissipation=True).numpy()
+    assert rel_err(r, ro) <= FP64_TOL
+    s.close()
+
+
+def test_freestream_gpu(lib):
+    for p in [1, 2, 3, 4]:
+        op, m = _mesh(p)
+        u = states.uniform_state(m.n_e, 2, op.n_p)
+        for scheme in ["split", "hadamard"]:
+            s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True))
+            r = s.residual(s.to_device(u)).cpu().numpy()
+            assert np.abs(r).max() < 1e-12
+            s.close()
+
+
+def test_nonphysical_state_reports_error(lib):
+    op, m = _mesh(2)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=8)
+    u[3, 0, 5] = -1.0  # negative density at one node
+    s = lib.Solver(op, m, lib.Params())
+    s.residual(s.to_device(u))
+    assert s.status() == lib.capi.ESPLIT_ERR_NONPHYSICAL
+    assert s.status() == 0  # reading clears the sticky flag
+    s.close()
+
+
+def test_bad_inputs_rejected(lib):
+    op, m = _mesh(2)
+    bad = periodic_tri_mesh(op, 5, 10.0, 0.05)
+    bad.pair = bad.pair.copy()
+    bad.pair[0, 0, 0, 1] = (bad.pair[0, 0, 0, 1] + 1) % 9
+    with pytest.raises(lib.EsplitError) as ei:
+        lib.Solver(op, bad)
+    assert ei.value.code == lib.capi.ESPLIT_ERR_MESH
+    bad2 = periodic_tri_mesh(op, 5, 10.0, 0.05)
+    bad2.J = bad2.J.copy()
+    bad2.J[2, 3] = -1.0
+    with pytest.raises(lib.EsplitError) as ei:
+        lib.Solver(op, bad2)
+    assert ei.value.code == lib.capi.ESPLIT_ERR_MESH
+    s = lib.Solver(op, m)
+    with pytest.raises(lib.EsplitError) as ei:
+        s.set_params(lib.Params(beta=-0.5))
+    assert ei.value.code == lib.capi.ESPLIT_ERR_ARG
+    s.close()
+
+
+def test_rrk_config1_parity(lib):
+    """Config 1: 8x8 quads -> 128 curved triangles (amplitude 0.05), p = 2,
+    vortex, EC split, relaxation RK4 for 20 steps at CFL 0.1: per-step g and
+    the final state against the oracle; entropy conserved to round-off."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(2, N=8)
+    u0 = states.isentropic_vortex(m)
+    dt = states.cfl_timestep(m, u0, 0.1)
+    s = lib.Solver(op, m, lib.Params())
+    ud = s.to_device(u0)
+    uo = torch.as_tensor(u0)
+    rhs = lambda x: R.residual(x, op, m, OP())
+    S0 = s.entropy(ud)
+    for step in range(20):
+        g, info = s.rrk_step(ud, dt)
+        uo, io = rrk.rrk4_step(uo, dt, rhs, op, m, OP())
+        assert abs(g - io.g) <= 1e-10, (step, g, io.g)
+        assert abs(info.S_after - S0) <= 1e-14 * abs(S0) * (step + 1)
+    assert rel_err(ud.cpu().numpy(), uo.numpy()) <= 1e-11
+    s.close()
+
+
+def test_rrk_dissipative_parity(lib):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(3, N=6)
+    u0 = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
+    dt = states.cfl_timestep(m, u0, 0.1)
+    s = lib.Solver(op, m, lib.Params(dissipation=True))
+    ud = s.to_device(u0)
+    rhs = lambda x: R.residual(x, op, m, OP(), dissipation=True)
+    g, info = s.rrk_step(ud, dt)
+    uo, io = rrk.rrk4_step(torch.as_tensor(u0), dt, rhs, op, m, OP())
+    assert abs(g - io.g) <= 1e-10
+    assert info.estimate < 0
+    assert abs(info.estimate - io.estimate) <= 1e-12 * abs(io.estimate) + 1e-16 * abs(io.S_before)
+    assert rel_err(ud.cpu().numpy(), uo.numpy()) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_full_size_config2_sampled(lib, p):
+    """Config 2 at full size (128 x 128 quads -> 32,768 curved triangles,
+    vortex + 1e-3 noise, seed 2): the GPU residual in the bench's launch
+    configuration, checked on sampled elements the oracle evaluates one by
+    one, for the split and Hadamard forms with dissipation."""
+    R, Dg, rrk, OP = _oracle()
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 128, 10.0, 0.05)
+    u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
+    sample = np.random.default_rng(40 + p).choice(m.n_e, 48, replace=False)
+    sample = np.concatenate([sample, [0, m.n_e - 1]])
+    for scheme in ["split", "hadamard"]:
+        s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True))
+        r = s.residual(s.to_device(u)).cpu().numpy()
+        ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True, elems=sample).numpy()
+        assert rel_err(r[sample], ro) <= FP64_TOL
+        s.close()
