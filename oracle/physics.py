@@ -72,6 +72,29 @@ def harten_entropy(U, prm: Params):
     return prm.beta * rho * (p * rho ** (-prm.gam)) ** (1.0 / (prm.alpha + prm.gam))
 
 
+def harten_entropy_change(U, dU, prm: Params):
+    """s(U + dU) - s(U) for Harten's entropy, Eq. (16), evaluated without
+    cancellation (both states positive).
+
+    With s = beta rho^A p^B, A = alpha/(alpha+gam), B = 1/(alpha+gam):
+        s(U + dU) - s(U) = s(U) expm1(A log1p(drho/rho) + B log1p(dp/p)),
+    where the pressure change follows exactly from the closure of Sec. 2.2:
+        dp = (gam-1) (de - [(2 m.dm + |dm|^2) rho - |m|^2 drho] / (2 rho (rho + drho))),
+    m = rho V.  Every quantity is a small difference computed directly, so the
+    result carries relative (not absolute) round-off.  Used for the relaxation
+    function of Eq. (97), whose root is defined by such differences."""
+    g, a = prm.gam, prm.alpha
+    A = a / (a + g)
+    B = 1.0 / (a + g)
+    rho, m, E = U[..., 0], U[..., 1:-1], U[..., -1]
+    drho, dm, dE = dU[..., 0], dU[..., 1:-1], dU[..., -1]
+    p = (g - 1.0) * (E - 0.5 * (m * m).sum(-1) / rho)
+    dke = ((2.0 * (m * dm).sum(-1) + (dm * dm).sum(-1)) * rho - (m * m).sum(-1) * drho) / (2.0 * rho * (rho + drho))
+    dp = (g - 1.0) * (dE - dke)
+    s = prm.beta * rho ** A * p ** B
+    return s * torch.expm1(A * torch.log1p(drho / rho) + B * torch.log1p(dp / p))
+
+
 def entropy_variables(U, prm: Params):
     """Harten entropy variables, Eq. (25):
     W = (rho/p)(p rho^-gam)^(1/(alpha+gam)) [-alpha/(gam-1) p/rho - |V|^2/2, V, -1]."""

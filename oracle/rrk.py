@@ -10,6 +10,12 @@ by bisection to machine precision, and u_{n+1} = u_n + g_n d.
 
 Readings (the paper is silent on these details):
   * the equality form of Eq. (97) is used for every scheme (relaxation RK);
+  * f is evaluated as sum_k 1^T H_k [s(u_n + g d) - s(u_n)] - g est with the
+    per-node entropy change computed without cancellation
+    (physics.harten_entropy_change): the difference of the two global sums
+    in Eq. (97) loses all but a few digits (|f| ~ 1e-13 |S| near the root),
+    which would leave g undefined beyond ~1e-9; bisection "to machine
+    precision" needs f itself to relative precision;
   * g = 0 is always a root; f is convex in g (S_H is convex), so the root
     wanted is the other one, near 1.  Bracket [0.5, 1.5]; while f(lo) >= 0
     halve lo (down to 2^-10); while f(hi) <= 0 double hi (up to 4); no
@@ -32,7 +38,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from .physics import Params, harten_entropy, entropy_variables
+from .physics import Params, harten_entropy, harten_entropy_change, entropy_variables
 
 DT = torch.float64
 RK4_A = (0.0, 0.5, 0.5, 1.0)
@@ -64,11 +70,11 @@ def _S_total(u, Hn, prm):
 def relaxation_gamma(u_n, d, estimate, ref, mesh, prm: Params = Params(), max_iter=200):
     """Bisection root of f(g) of Eq. (97) (equality form). Returns (g, iterations)."""
     Hn = _H(ref, mesh)
-    S0 = _S_total(u_n, Hn, prm)
     floor = 64.0 * np.finfo(float).eps * float((Hn * harten_entropy(u_n.transpose(1, 2), prm).abs()).sum())
+    Ut, dt_ = u_n.transpose(1, 2), d.transpose(1, 2)
 
     def f(g):
-        return _S_total(u_n + g * d, Hn, prm) - S0 - g * estimate
+        return float((Hn * harten_entropy_change(Ut, g * dt_, prm)).sum()) - g * estimate
 
     lo, hi = 0.5, 1.5
     flo, fhi = f(lo), f(hi)

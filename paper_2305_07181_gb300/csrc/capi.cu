@@ -58,7 +58,7 @@ int check_ready(esplit_ctx* c) {
 }
 
 int ensure_partial(esplit_ctx* c) {
-  size_t need = 2 * ((size_t)c->n_e * c->n_p / 256 + (size_t)c->n_e + 64);
+  size_t need = 6 * ((size_t)c->n_e * c->n_p / 256 + 1) + 2 * ((size_t)c->n_e + 64);
   if (c->partial_cap >= need) return ESPLIT_OK;
   int rc = dalloc(c, &c->b.partial, need);
   if (rc) return rc;

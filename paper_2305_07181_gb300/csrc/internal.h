@@ -24,7 +24,7 @@ struct RefTables {
 // Device-resident state of the relaxation root solve (Eq. (97)).
 struct RootState {
   double S0, Sabs, est;      // 1^T H s(u_n), 1^T H |s(u_n)|, dt sum b_i e_i
-  double g, lo, hi, flo, fhi;
+  double g, ga, gb, lo, hi, flo, fhi;  // ga, gb: next evaluation points (gb < 0: one point)
   double f_last, df_last;
   int phase, done, iters, status;
 };

@@ -178,15 +178,26 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 // ---------------------------------------------------------------------------
 // entropy-split volume kernel (Eq. (100)): EB elements per block, one thread
 // per node.  r = sum_i M_i f_i - 1/(beta+1) sum_i A~_i (D_i w) + sat
+//
+// Node states, fluxes and entropy variables are always formed in float64.
+// The contractions act on values relative to the element's node 0,
+//   M_i f_i = M_i (f_i - f_i,0) + f_i,0 E_x_i/H,   D_i w = D_i (w - w_0),
+// (M_i 1 = H^-1 E_x_i 1 and D_i 1 = 0 for the SBP operators of Def. 1), so the
+// operator entries (~1/(h H_ref)) multiply only the variation inside the
+// element; with T = float this is what keeps the float32 contraction within
+// the stated bound, with T = double it removes most of the cancellation.
 // Optional: block partial of sum H w^T r (entropy production, float64).
 // ---------------------------------------------------------------------------
 template <typename T, int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
-    const double* __restrict__ J, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
-    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
+    const double* __restrict__ J, const double* __restrict__ nu, const double* __restrict__ sat,
+    const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64, int* __restrict__ status,
+    double* __restrict__ prod) {
   constexpr int NC = D + 2;
-  __shared__ T sf[EB][D][NC][NP];
+  __shared__ double rf[EB][D][NC][NP];  // raw fluxes
+  __shared__ double rw[EB][NC][NP];     // raw entropy variables
+  __shared__ T sf[EB][D][NC][NP];       // relative to node 0
   __shared__ T sw[EB][NC][NP];
   const int NS = c_ref.n_slot;
   int el = threadIdx.x / NP;
@@ -194,21 +205,34 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
   int li = blockIdx.x * EB + el;
   bool active = (el < EB) && (li < n_list);
   int e = active ? (list ? list[li] : li) : 0;
-  Node<T, D> nd;
-  T uu[NC];
+  Node<double, D> nd;
   if (active) {
+    double uu[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) uu[q] = (T)__ldg(&u[((size_t)e * NC + q) * NP + m]);
-    if (!node_from_u<T, D>(uu, c, nd)) atomicOr(status, 1);
+    for (int q = 0; q < NC; ++q) uu[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
+    if (!node_from_u<double, D>(uu, c64, nd)) atomicOr(status, 1);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      T F[NC];
-      euler_flux<T, D>(nd, i, F);
+      double F[NC];
+      euler_flux<double, D>(nd, i, F);
 #pragma unroll
-      for (int q = 0; q < NC; ++q) sf[el][i][q][m] = F[q];
+      for (int q = 0; q < NC; ++q) rf[el][i][q][m] = F[q];
     }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) sw[el][q][m] = nd.W[q];
+    for (int q = 0; q < NC; ++q) rw[el][q][m] = nd.W[q];
+  }
+  __syncthreads();
+  double f0[D][NC];
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f0[i][q] = rf[el][i][q][0];
+        sf[el][i][q][m] = (T)(rf[el][i][q][m] - f0[i][q]);
+      }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sw[el][q][m] = (T)(rw[el][q][m] - rw[el][q][0]);
   }
   __syncthreads();
   double hw = 0.0;
@@ -234,38 +258,48 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
         }
       }
     }
+    Node<T, D> nt;
+    nt.rho = (T)nd.rho;
+    nt.p = (T)nd.p;
+    nt.e = (T)nd.e;
+    nt.q = (T)nd.q;
+    nt.v2 = (T)nd.v2;
+#pragma unroll
+    for (int i = 0; i < D; ++i) nt.V[i] = (T)nd.V[i];
     T nonc[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) nonc[q] = T(0);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       T dF[NC];
-      dflux_dw<T, D>(nd, c, i, g[i], dF);
+      dflux_dw<T, D>(nt, c, i, g[i], dF);
 #pragma unroll
       for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
     }
     int sl = c_ref.node_slot[m];
+    double Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
+    double back[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) back[q] = 0.0;
+    if (sl >= 0) {
+      double ih = 1.0 / Hm;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double ei = __ldg(&nu[((size_t)e * NS + sl) * D + i]) * ih;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) back[q] += f0[i][q] * ei;
+      }
+    }
     double res[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      res[q] = (double)(acc[q] - c.inv_bp1 * nonc[q]);
+      res[q] = ((double)acc[q] + back[q]) - (double)(c.inv_bp1 * nonc[q]);
       if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
       r[((size_t)e * NC + q) * NP + m] = res[q];
     }
     if (prod) {
-      double Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
-      if constexpr (sizeof(T) == sizeof(double)) {
 #pragma unroll
-        for (int q = 0; q < NC; ++q) hw += (double)nd.W[q] * res[q];
-      } else {
-        double u64[NC];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) u64[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
-        Node<double, D> n64;
-        node_from_u<double, D>(u64, c64, n64);
-#pragma unroll
-        for (int q = 0; q < NC; ++q) hw += n64.W[q] * res[q];
-      }
+      for (int q = 0; q < NC; ++q) hw += nd.W[q] * res[q];
       hw *= Hm;
     }
   }
@@ -429,8 +463,8 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.J, c->b.sat, lsplit, n_split, ph,
-                                                             ph64, c->b.status, prod ? prod + np_used : nullptr);
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.J, c->b.nu, c->b.sat, lsplit, n_split,
+                                                             ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
   }
@@ -621,16 +655,17 @@ int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, doubl
 
 // ---------------------------------------------------------------------------
 // relaxation root solve of Eq. (97) on the device
-//   f(g) = 1^T H s(u_n + g d) - S0 - g est,  f'(g) = 1^T H w(u_n + g d) . d - est
-// Newton from g = 1, safeguarded by the bracket [lo, hi] (f(lo) < 0 < f(hi));
-// bisection whenever the Newton point leaves the bracket or f' <= 0.
-// Termination: |f| <= 8 eps 1^T H |s|, |step| <= 4 eps g, or 40 evaluations.
-// No positive root (hi shrinking below 2^-10 or g beyond 4) -> status -5.
+//   f(g) = sum H [s(u_n + g d) - s(u_n)] - g est,   f'(g) = sum H w(u_n + g d).d - est
+// with the per-node entropy change evaluated without cancellation:
+//   s(U+dU) - s(U) = s(U) expm1(A log1p(drho/rho) + B log1p(dp/p)),
+//   A = alpha/(alpha+gam), B = 1/(alpha+gam), dp from the closure exactly.
+// Pass 0 evaluates g = 0.5 and 1.5 together (bracket and round-off floor rule);
+// then a safeguarded Newton iteration from the quadratic model through
+// (0, 0), (lo, f_lo), (hi, f_hi).  Stops at |step| <= 4 eps g, |f| at its own
+// round-off level, or ROOT_EVALS_MAX evaluations; no bracket -> status -5.
 // ---------------------------------------------------------------------------
-constexpr int ROOT_MAX_EVALS = 40;
-
 __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
-  // scal[0..1] = S0, Sabs ; scal[2..5] = stage productions e_1..e_4
+  // scal[0..1] = S0, sum H |s| ; scal[2..5] = stage productions e_1..e_4
   const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   st->S0 = scal[0];
   st->Sabs = scal[1];
@@ -638,14 +673,44 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
   for (int i = 0; i < 4; ++i) est += b[i] * scal[2 + i];
   st->est = dt * est;
   st->g = 1.0;
-  st->lo = 0.0;
-  st->hi = -1.0;  // unset
+  st->ga = 0.5;
+  st->gb = 1.5;
+  st->lo = 0.5;
+  st->hi = 1.5;
   st->flo = 0.0;
   st->fhi = 0.0;
   st->phase = 0;
   st->done = 0;
   st->iters = 0;
   st->status = 0;
+}
+
+template <int D>
+__device__ __forceinline__ void entropy_change_and_slope(const double* u, const double* dd, double g, double s0,
+                                                         const Phys<double>& c, double& ds, double& wd) {
+  constexpr int NC = D + 2;
+  double rho = u[0], E = u[NC - 1];
+  double drho = g * dd[0], dE = g * dd[NC - 1];
+  double mm = 0.0, mdm = 0.0, dmdm = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double m = u[1 + i], dm = g * dd[1 + i];
+    mm += m * m;
+    mdm += m * dm;
+    dmdm += dm * dm;
+  }
+  double p = c.gm1 * (E - 0.5 * mm / rho);
+  double dke = ((2.0 * mdm + dmdm) * rho - mm * drho) / (2.0 * rho * (rho + drho));
+  double dp = c.gm1 * (dE - dke);
+  ds = s0 * expm1(c.a_q * log1p(drho / rho) + (c.b_q + 1.0) * log1p(dp / p));
+  double u1[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) u1[q] = u[q] + g * dd[q];
+  Node<double, D> n1;
+  node_from_u<double, D>(u1, c, n1);
+  wd = 0.0;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) wd += n1.W[q] * dd[q];
 }
 
 template <int D>
@@ -656,9 +721,9 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
   if (st->done) return;
   constexpr int NC = D + 2;
   const int NP = c_ref.n_p;
-  double g = st->g;
+  const double ga = st->ga, gb = st->gb;
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double v[2] = {0.0, 0.0};
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   if (t < n_nodes) {
     size_t e = t / NP;
     int m = (int)(t - e * NP);
@@ -667,42 +732,112 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
     for (int q = 0; q < NC; ++q) {
       size_t ix = (e * NC + q) * NP + m;
       dd[q] = __ldg(&d[ix]);
-      uu[q] = __ldg(&un[ix]) + g * dd[q];
+      uu[q] = __ldg(&un[ix]);
     }
-    Node<double, D> nd;
-    node_from_u<double, D>(uu, c, nd);
+    Node<double, D> n0;
+    node_from_u<double, D>(uu, c, n0);
+    double s0 = c.beta * n0.q * n0.p;
     double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
-    double wd = 0.0;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) wd += nd.W[q] * dd[q];
-    v[0] = H * c.beta * nd.q * nd.p;
+    double ds, wd;
+    entropy_change_and_slope<D>(uu, dd, ga, s0, c, ds, wd);
+    v[0] = H * ds;
     v[1] = H * wd;
+    v[2] = H * fabs(ds);
+    if (gb > 0.0) {
+      entropy_change_and_slope<D>(uu, dd, gb, s0, c, ds, wd);
+      v[3] = H * ds;
+      v[4] = H * wd;
+      v[5] = H * fabs(ds);
+    }
   }
-  block_sum<2>(v, part + 2 * blockIdx.x);
+  block_sum<6>(v, part + 6 * blockIdx.x);
 }
 
 __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restrict__ part, int n,
                                                            RootState* st) {
   if (st->done) return;
-  __shared__ double tot[2];
-  for (int k = 0; k < 2; ++k) {
+  __shared__ double tot[6];
+  for (int k = 0; k < 6; ++k) {
     double v[1] = {0.0};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += part[(size_t)i * 2 + k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += part[(size_t)i * 6 + k];
     block_sum<1>(v, tot + k);
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
   const double eps = 2.220446049250313e-16;
-  double g = st->g;
-  double f = tot[0] - st->S0 - g * st->est;
-  double df = tot[1] - st->est;
+  const double est = st->est;
   st->iters += 1;
-  st->f_last = f;
-  st->df_last = df;
-  if (fabs(f) <= 8.0 * eps * st->Sabs) {
-    st->done = 1;
+  if (st->phase == 0) {
+    double flo = tot[0] - 0.5 * est, fhi = tot[3] - 1.5 * est;
+    double floor = 64.0 * eps * st->Sabs;
+    st->flo = flo;
+    st->fhi = fhi;
+    if (fabs(flo) <= floor && fabs(fhi) <= floor) {
+      st->g = 1.0;
+      st->done = 1;
+      return;
+    }
+    if (flo >= 0.0) {
+      st->phase = 1;
+      st->ga = 0.25;
+      st->gb = -1.0;
+      return;
+    }
+    if (fhi <= 0.0) {
+      st->phase = 2;
+      st->ga = 3.0;
+      st->gb = -1.0;
+      return;
+    }
+  } else if (st->phase == 1) {  // shrink lo by halves (bracket [2^-10, 1.5])
+    double f = tot[0] - st->ga * est;
+    if (f >= 0.0) {
+      double ng = 0.5 * st->ga;
+      if (ng < 0.0009765625) {
+        st->status = ESPLIT_ERR_RRK_NO_ROOT;
+        st->done = 1;
+        return;
+      }
+      st->ga = ng;
+      return;
+    }
+    st->lo = st->ga;
+    st->flo = f;
+  } else if (st->phase == 2) {  // grow hi by doubling (up to 4)
+    double f = tot[0] - st->ga * est;
+    if (f <= 0.0) {
+      double ng = 2.0 * st->ga;
+      if (ng > 4.0) {
+        st->status = ESPLIT_ERR_RRK_NO_ROOT;
+        st->done = 1;
+        return;
+      }
+      st->lo = st->ga;
+      st->flo = f;
+      st->ga = ng;
+      return;
+    }
+    st->hi = st->ga;
+    st->fhi = f;
+  }
+  if (st->phase <= 2) {
+    // quadratic model f ~ c g (g - g*) through (0,0), (lo, flo), (hi, fhi)
+    double lo = st->lo, hi = st->hi;
+    double cq = (st->fhi / hi - st->flo / lo) / (hi - lo);
+    double g0 = cq > 0.0 ? lo - (st->flo / lo) / cq : 0.5 * (lo + hi);
+    if (!(g0 > lo && g0 < hi)) g0 = 0.5 * (lo + hi);
+    st->phase = 3;
+    st->ga = g0;
+    st->gb = -1.0;
+    st->g = g0;
     return;
   }
+  // Newton phase
+  double g = st->ga;
+  double f = tot[0] - g * est;
+  double df = tot[1] - est;
+  st->f_last = f;
+  st->df_last = df;
   if (f < 0.0) {
     st->lo = g;
     st->flo = f;
@@ -710,35 +845,20 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
     st->hi = g;
     st->fhi = f;
   }
-  bool have_hi = st->hi > 0.0;
-  double gn;
-  if (df > 0.0)
-    gn = g - f / df;
-  else
-    gn = have_hi ? 0.5 * (st->lo + st->hi) : 2.0 * g;
-  if (gn <= st->lo || (have_hi && gn >= st->hi)) gn = have_hi ? 0.5 * (st->lo + st->hi) : 2.0 * fmax(g, st->lo);
-  if (have_hi && st->hi < 0.0009765625 && st->lo == 0.0) {
-    st->status = ESPLIT_ERR_RRK_NO_ROOT;
+  st->g = g;
+  if (fabs(f) <= 4.0 * eps * (tot[2] + fabs(g * est))) {
     st->done = 1;
     return;
   }
-  if (gn > 4.0) {
-    st->status = ESPLIT_ERR_RRK_NO_ROOT;
-    st->done = 1;
-    return;
-  }
-  if (fabs(gn - g) <= 4.0 * eps * fabs(g) || (have_hi && st->hi - st->lo <= 4.0 * eps * st->hi)) {
+  double gn = (df > 0.0) ? g - f / df : 0.5 * (st->lo + st->hi);
+  if (!(gn > st->lo && gn < st->hi)) gn = 0.5 * (st->lo + st->hi);
+  if (fabs(gn - g) <= 4.0 * eps * fabs(g) || st->hi - st->lo <= 4.0 * eps * st->hi ||
+      st->iters >= ROOT_EVALS_MAX) {
     st->g = gn;
     st->done = 1;
     return;
   }
-  if (st->iters >= ROOT_MAX_EVALS) {
-    if (!have_hi || st->lo == 0.0) st->status = ESPLIT_ERR_RRK_NO_ROOT;
-    st->g = gn;
-    st->done = 1;
-    return;
-  }
-  st->g = gn;
+  st->ga = gn;
 }
 
 int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s, int* n_partial) {

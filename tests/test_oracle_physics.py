@@ -223,3 +223,41 @@ def test_viscous_flux_special_cases():
     Fa = viscous_flux_from_w_grads(Ux[None], gW[None], prm)[0]
     Fb = viscous_flux_from_prim_grads(Ux[None], dVx[None], dTx[None], prm)[0]
     assert torch.allclose(Fa, Fb, rtol=1e-12, atol=1e-13)
+
+
+def test_entropy_change_extended_precision():
+    """s(U+dU) - s(U) without cancellation (used by Eq. (97)) against the
+    plain difference of Eq. (16) evaluated in 60-digit decimal arithmetic."""
+    from oracle.physics import harten_entropy_change
+    getcontext().prec = 60
+    U = rand_states(200, 2, 21)
+    g = torch.Generator().manual_seed(22)
+    scale = 10.0 ** (-torch.randint(1, 12, (200, 1), generator=g).double())
+    dU = (2 * torch.rand(200, 4, generator=g, dtype=DT) - 1) * scale * U.abs()
+    got = harten_entropy_change(U, dU, P).numpy()
+    gam, a, beta = Decimal(P.gam), Decimal(P.alpha), Decimal(P.beta)
+    A, B = a / (a + gam), Decimal(1) / (a + gam)
+
+    def sdec(u):
+        rho, m1, m2, E = [Decimal(float(x)) for x in u]
+        p = (gam - 1) * (E - (m1 * m1 + m2 * m2) / (2 * rho))
+        return beta * rho ** A * p ** B
+
+    eps = np.finfo(float).eps
+    A_, B_ = float(A), float(B)
+    for k in range(200):
+        u0 = U[k].numpy()
+        du = dU[k].numpy()
+        u1 = [Decimal(float(x)) + Decimal(float(y)) for x, y in zip(u0, du)]
+        ex = sdec([float(x) for x in u0])
+        rho, m1, m2, E = u1
+        p1 = (gam - 1) * (E - (m1 * m1 + m2 * m2) / (2 * rho))
+        diff = beta * rho ** A * p1 ** B - ex
+        # forward-error scale of the formula: |s| times the sizes of the small
+        # relative changes it combines (not |s| itself, as a plain difference)
+        r0, m, E0 = u0[0], u0[1:3], u0[3]
+        p0 = (P.gam - 1) * (E0 - 0.5 * (m @ m) / r0)
+        dke = (abs(2 * m @ du[1:3]) + du[1:3] @ du[1:3]) / (2 * r0) + (m @ m) * abs(du[0]) / (2 * r0 * r0)
+        scale = abs(float(ex)) * (abs(A_) * abs(du[0]) / r0 + abs(B_) * (P.gam - 1) * (abs(du[3]) + dke) / p0)
+        assert abs(Decimal(float(got[k])) - diff) <= Decimal(64 * eps * scale) + Decimal(1e-300)
+        assert abs(Decimal(float(got[k])) - diff) <= Decimal(1e-9) * abs(diff) + Decimal(64 * eps * scale)
