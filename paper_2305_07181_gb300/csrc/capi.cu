@@ -151,8 +151,8 @@ void esplit_destroy(esplit_ctx* c) {
   cudaSetDevice(c->device);
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,
-                b.list_split, b.list_had, b.sat, b.partial, b.scal, b.root, b.status, b.stage_u,
-                b.stage_r, b.dacc, b.host_u, b.host_r};
+                b.list_split, b.list_had, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
+                b.stage_r, b.dacc, b.node_cache, b.host_u, b.host_r};
   for (void* p : ps) dfree(p);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
@@ -245,6 +245,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.face_pairs, fpairs.size()))) return rc;
   if ((rc = dalloc(c, &c->b.ops64, (size_t)n_e * 2 * d * NP * NP))) return rc;
   if ((rc = dalloc(c, &c->b.ops32, (size_t)n_e * 2 * d * NP * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.rows, (size_t)n_e * 2 * d * NP))) return rc;
   if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
   c->partial_cap = 0;
   if ((rc = ensure_partial(c))) return rc;
@@ -257,6 +258,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   dalloc(c, &c->b.stage_u, 0);
   dalloc(c, &c->b.stage_r, 0);
   dalloc(c, &c->b.dacc, 0);
+  dalloc(c, &c->b.node_cache, 0);
   dalloc(c, &c->b.host_u, 0);
   dalloc(c, &c->b.host_r, 0);
   c->flags.assign(n_e, 0);
@@ -390,12 +392,14 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     if ((rc = dalloc(c, &c->b.stage_u, n))) return rc;
     if ((rc = dalloc(c, &c->b.stage_r, n))) return rc;
     if ((rc = dalloc(c, &c->b.dacc, n))) return rc;
+    if ((rc = dalloc(c, &c->b.node_cache, 4 * (size_t)c->n_e * c->n_p))) return rc;
   }
   static const double A[4] = {0.0, 0.5, 0.5, 1.0};
   static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   int np = 0;
   // S0 and sum H |s| of u_n -> scal[0..1]
-  if (esplit::launch_entropy(c, u, s, &np) || esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal, s))
+  if (esplit::launch_entropy(c, u, s, &np, c->b.node_cache) ||
+      esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal, s))
     return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
   for (int i = 0; i < 4; ++i) {
     const double* Ui = (i == 0) ? u : c->b.stage_u;
@@ -430,9 +434,8 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     info->S_before = st.S0;
     info->iterations = st.iters;
     info->status = status;
-    double Sa = 0.0;
-    if (status == ESPLIT_OK && esplit_entropy(c, u, &Sa, stream) == ESPLIT_OK) info->S_after = Sa;
-    else info->S_after = st.S0;
+    // entropy change at the last evaluated g (within 4 eps g of the returned g)
+    info->S_after = st.S0 + (st.phase == 3 ? st.dS_last : 0.0);
   }
   if (status == ESPLIT_ERR_NONPHYSICAL) return fail(c, status, "non-physical state during the step");
   if (status == ESPLIT_ERR_RRK_NO_ROOT) return fail(c, status, "relaxation parameter could not be bracketed");

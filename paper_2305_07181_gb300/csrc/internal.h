@@ -25,7 +25,7 @@ struct RefTables {
 struct RootState {
   double S0, Sabs, est;      // 1^T H s(u_n), 1^T H |s(u_n)|, dt sum b_i e_i
   double g, ga, gb, lo, hi, flo, fhi;  // ga, gb: next evaluation points (gb < 0: one point)
-  double f_last, df_last;
+  double f_last, df_last, dS_last;
   int phase, done, iters, status;
 };
 
@@ -43,6 +43,7 @@ struct Buffers {
   //   k >= d: D_i^T, D_i = H^-1 Q_x_i
   double* ops64 = nullptr;     // [n_e][2d][n_p][n_p]
   float* ops32 = nullptr;      // same, float
+  double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
   // element lists for the hybrid scheme
   int* list_split = nullptr;
   int* list_had = nullptr;
@@ -56,6 +57,7 @@ struct Buffers {
   double* stage_u = nullptr;
   double* stage_r = nullptr;
   double* dacc = nullptr;
+  double* node_cache = nullptr;  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
   double* host_u = nullptr;    // device copies for the host-buffer entry point
   double* host_r = nullptr;
 };
@@ -107,7 +109,7 @@ struct ProfScope {
 int launch_build_ops(esplit_ctx* c, cudaStream_t s);
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod_partial,
                     int* n_partial);
-int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial);
+int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache = nullptr);
 int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial);
 int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s);
 int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, double* out, size_t n, cudaStream_t s);

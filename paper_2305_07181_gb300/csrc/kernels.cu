@@ -98,6 +98,20 @@ __global__ void build_ops_kernel(const double* __restrict__ Qref, const double* 
   ops32[idx] = (float)val;
 }
 
+// row sums M_i 1 and D_i 1 of the stored float64 operators, summed in node
+// order: rows[e][k][m] = sum_n ops64[e][k][n][m]
+__global__ void build_rows_kernel(const double* __restrict__ ops64, int n_e, int two_d, double* __restrict__ rows) {
+  const int NP = c_ref.n_p;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n_e * two_d * NP) return;
+  size_t ek = idx / NP;
+  int m = (int)(idx - ek * NP);
+  const double* op = ops64 + ek * NP * NP;
+  double s = 0.0;
+  for (int n = 0; n < NP; ++n) s += op[(size_t)n * NP + m];
+  rows[idx] = s;
+}
+
 int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   size_t total = (size_t)c->n_e * 2 * c->dim * c->n_p * c->n_p;
   int bs = 256;
@@ -109,7 +123,9 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   else
     build_ops_kernel<3><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
                                           c->b.ops32);
-  c->launches++;
+  size_t nr = (size_t)c->n_e * 2 * c->dim * c->n_p;
+  build_rows_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(c->b.ops64, c->n_e, 2 * c->dim, c->b.rows);
+  c->launches += 2;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -144,6 +160,7 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
   ZNode<T, D> zk, zv;
   znode<T, D>(nk, c, zk);
   znode<T, D>(nv, c, zv);
+  znode_recips<T, D>(zk);
   PairAvg<T, D> a;
   pair_avg<T, D>(zk, zv, c, a);
   T nuv[D];
@@ -191,7 +208,7 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 template <typename T, int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
-    const double* __restrict__ J, const double* __restrict__ nu, const double* __restrict__ sat,
+    const double* __restrict__ rows, const double* __restrict__ J, const double* __restrict__ sat,
     const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64, int* __restrict__ status,
     double* __restrict__ prod) {
   constexpr int NC = D + 2;
@@ -222,17 +239,44 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     for (int q = 0; q < NC; ++q) rw[el][q][m] = nd.W[q];
   }
   __syncthreads();
-  double f0[D][NC];
+  // reference values c: node 0 (float64 path) or the float32 element mean
+  // (float32 path, smaller variations); any c is exact once the row sums of
+  // the stored operators are added back: M f = M (f - c) + c (M 1).
+  double f0[D][NC], w0[NC];
   if (active) {
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        f0[i][q] = rf[el][i][q][0];
-        sf[el][i][q][m] = (T)(rf[el][i][q][m] - f0[i][q]);
+        if constexpr (sizeof(T) == sizeof(double)) {
+          f0[i][q] = rf[el][i][q][0];
+        } else {
+          float s = 0.f;
+#pragma unroll
+          for (int n = 0; n < NP; ++n) s += (float)rf[el][i][q][n];
+          f0[i][q] = (double)(s * (1.f / NP));
+        }
       }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) sw[el][q][m] = (T)(rw[el][q][m] - rw[el][q][0]);
+    for (int q = 0; q < NC; ++q) {
+      if constexpr (sizeof(T) == sizeof(double)) {
+        w0[q] = rw[el][q][0];
+      } else {
+        float s = 0.f;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) s += (float)rw[el][q][n];
+        w0[q] = (double)(s * (1.f / NP));
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sf[el][i][q][m] = (T)(rf[el][i][q][m] - f0[i][q]);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sw[el][q][m] = (T)(rw[el][q][m] - w0[q]);
   }
   __syncthreads();
   double hw = 0.0;
@@ -258,6 +302,21 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
         }
       }
     }
+    // add back the reference values through the stored operators' row sums
+    const double* rs = rows + (size_t)e * (2 * D * NP);
+    double back[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) back[q] = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double rm = __ldg(&rs[i * NP + m]);
+      double rd = __ldg(&rs[(D + i) * NP + m]);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        back[q] += f0[i][q] * rm;
+        g[i][q] = (T)((double)g[i][q] + w0[q] * rd);
+      }
+    }
     Node<T, D> nt;
     nt.rho = (T)nd.rho;
     nt.p = (T)nd.p;
@@ -266,30 +325,19 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     nt.v2 = (T)nd.v2;
 #pragma unroll
     for (int i = 0; i < D; ++i) nt.V[i] = (T)nd.V[i];
+    const JvpPrep<T> jp = jvp_prep<T, D>(nt);
     T nonc[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) nonc[q] = T(0);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       T dF[NC];
-      dflux_dw<T, D>(nt, c, i, g[i], dF);
+      dflux_dw<T, D>(nt, jp, c, i, g[i], dF);
 #pragma unroll
       for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
     }
     int sl = c_ref.node_slot[m];
     double Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
-    double back[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) back[q] = 0.0;
-    if (sl >= 0) {
-      double ih = 1.0 / Hm;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        double ei = __ldg(&nu[((size_t)e * NS + sl) * D + i]) * ih;
-#pragma unroll
-        for (int q = 0; q < NC; ++q) back[q] += f0[i][q] * ei;
-      }
-    }
     double res[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
@@ -324,7 +372,7 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   constexpr int K = NP / 2;
-  constexpr int NZ = D + 5;  // q, V[D], p, P1, P2, v2
+  constexpr int NZ = D + 7;  // q, V[D], p, P1, P2, v2, 1/q, 1/p
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sz = reinterpret_cast<T*>(smem_raw);           // [EB][NZ][NP]
   T* sg = sz + EB * NZ * NP;                         // [EB][NP][K][NC]
@@ -343,6 +391,7 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     if (!node_from_u<T, D>(uu, c, nd)) atomicOr(status, 1);
     ZNode<T, D> z;
     znode<T, D>(nd, c, z);
+    znode_recips<T, D>(z);
     T* zz = sz + el * NZ * NP;
     zz[0 * NP + m] = z.q;
 #pragma unroll
@@ -351,7 +400,9 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     zz[(D + 2) * NP + m] = z.P1;
     zz[(D + 3) * NP + m] = z.P2;
     zz[(D + 4) * NP + m] = z.v2;
-    sH[el * NP + m] = (T)(c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]));
+    zz[(D + 5) * NP + m] = z.iq;
+    zz[(D + 6) * NP + m] = z.ip;
+    sH[el * NP + m] = (T)(1.0 / (c_ref.H[m] * __ldg(&J[(size_t)e * NP + m])));  // 1/H
   }
   __syncthreads();
   T acc[NC];
@@ -367,7 +418,10 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     zm.P1 = zz[(D + 2) * NP + m];
     zm.P2 = zz[(D + 3) * NP + m];
     zm.v2 = zz[(D + 4) * NP + m];
-    T Hm = sH[el * NP + m];
+    zm.iq = zz[(D + 5) * NP + m];
+    zm.ip = zz[(D + 6) * NP + m];
+    T iHm = sH[el * NP + m];
+    T Hm = T(1) / iHm;
     const T* op = ops + (size_t)e * (2 * D * NP * NP);
     T* gout = sg + ((size_t)el * NP + m) * K * NC;
     for (int k = 1; k <= K; ++k) {
@@ -391,7 +445,7 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
       sy_flux_dir<T, D>(a, c, Smn, G);
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        acc[q] -= T(2) * G[q] / Hm;
+        acc[q] -= T(2) * G[q] * iHm;
         gout[(k - 1) * NC + q] = T(2) * G[q];
       }
     }
@@ -399,14 +453,14 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
   __syncthreads();
   double hw = 0.0;
   if (active) {
-    T Hm = sH[el * NP + m];
+    T iHm = sH[el * NP + m];
     for (int k = 1; k <= K; ++k) {
       int src = m - k;
       if (src < 0) src += NP;
       if ((NP % 2 == 0) && k == K && src >= K) continue;
       const T* gin = sg + ((size_t)el * NP + src) * K * NC + (k - 1) * NC;
 #pragma unroll
-      for (int q = 0; q < NC; ++q) acc[q] += gin[q] / Hm;
+      for (int q = 0; q < NC; ++q) acc[q] += gin[q] * iHm;
     }
     int sl = c_ref.node_slot[m];
     double res[NC];
@@ -449,8 +503,10 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     int bs = 128;
     int nb = (c->n_pairs + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
-    face_kernel<T, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.sat, ph,
-                                        c->prm.dissipation, c->b.status);
+    // facet terms are O(1/h) and cancel against the volume's boundary part:
+    // they stay float64 in both precision modes
+    face_kernel<double, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.sat, ph64,
+                                             c->prm.dissipation, c->b.status);
     c->launches++;
   }
   int np_used = 0;
@@ -463,15 +519,16 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.J, c->b.nu, c->b.sat, lsplit, n_split,
-                                                             ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.rows, c->b.J, c->b.sat, lsplit,
+                                                             n_split, ph, ph64, c->b.status,
+                                                             prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
   }
   if (n_had > 0) {
     constexpr int EB = VolCfg<NP>::EB_HAD;
     constexpr int K = NP / 2;
-    size_t smem = sizeof(T) * ((size_t)EB * (D + 5) * NP + (size_t)EB * NP * K * (D + 2) + (size_t)EB * NP);
+    size_t smem = sizeof(T) * ((size_t)EB * (D + 7) * NP + (size_t)EB * NP * K * (D + 2) + (size_t)EB * NP);
     static bool attr_set = false;
     if (!attr_set) {
       cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -512,7 +569,8 @@ int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, d
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(256) entropy_kernel(const double* __restrict__ u, const double* __restrict__ J,
-                                                      size_t n_nodes, Phys<double> c, double* __restrict__ part) {
+                                                      size_t n_nodes, Phys<double> c, double* __restrict__ part,
+                                                      double* __restrict__ cache) {
   constexpr int NC = D + 2;
   const int NP = c_ref.n_p;
   size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -529,6 +587,12 @@ __global__ void __launch_bounds__(256) entropy_kernel(const double* __restrict__
     double sH = c.beta * nd.q * nd.p;  // S_H = beta rho (p rho^-gam)^(1/(alpha+gam)) = beta q p
     v[0] = H * sH;
     v[1] = H * fabs(sH);
+    if (cache) {  // per-node values the relaxation passes reuse: s, 1/rho, 1/p, log q
+      cache[g] = sH;
+      cache[n_nodes + g] = 1.0 / nd.rho;
+      cache[2 * n_nodes + g] = 1.0 / nd.p;
+      cache[3 * n_nodes + g] = nd.lnq;
+    }
   }
   block_sum<2>(v, part + 2 * blockIdx.x);
 }
@@ -565,15 +629,15 @@ __global__ void __launch_bounds__(256) entropy_rate_kernel(const double* __restr
   block_sum<2>(v, part + 2 * blockIdx.x);
 }
 
-int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial) {
+int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache) {
   size_t n = (size_t)c->n_e * c->n_p;
   int nb = (int)((n + 255) / 256);
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ENTROPY, s);
   if (c->dim == 2)
-    entropy_kernel<2><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial);
+    entropy_kernel<2><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial, cache);
   else
-    entropy_kernel<3><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial);
+    entropy_kernel<3><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial, cache);
   c->launches++;
   *n_partial = nb;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -685,11 +749,14 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
   st->status = 0;
 }
 
+// Entropy change s(u + g d) - s(u) and slope w(u + g d) . d at one node,
+// from the cached s(u), 1/rho, 1/p, log q of u.
 template <int D>
 __device__ __forceinline__ void entropy_change_and_slope(const double* u, const double* dd, double g, double s0,
-                                                         const Phys<double>& c, double& ds, double& wd) {
+                                                         double ir, double ip, double lnq, const Phys<double>& c,
+                                                         double& ds, double& wd) {
   constexpr int NC = D + 2;
-  double rho = u[0], E = u[NC - 1];
+  double rho = u[0];
   double drho = g * dd[0], dE = g * dd[NC - 1];
   double mm = 0.0, mdm = 0.0, dmdm = 0.0;
 #pragma unroll
@@ -699,23 +766,29 @@ __device__ __forceinline__ void entropy_change_and_slope(const double* u, const 
     mdm += m * dm;
     dmdm += dm * dm;
   }
-  double p = c.gm1 * (E - 0.5 * mm / rho);
-  double dke = ((2.0 * mdm + dmdm) * rho - mm * drho) / (2.0 * rho * (rho + drho));
+  double ir1 = 1.0 / (rho + drho);  // 1/rho'
+  double dke = 0.5 * ((2.0 * mdm + dmdm) - mm * drho * ir) * ir1;
   double dp = c.gm1 * (dE - dke);
-  ds = s0 * expm1(c.a_q * log1p(drho / rho) + (c.b_q + 1.0) * log1p(dp / p));
-  double u1[NC];
+  double l1 = log1p(drho * ir), l2 = log1p(dp * ip);
+  ds = s0 * expm1(c.a_q * l1 + (c.b_q + 1.0) * l2);
+  // entropy variables at u' = u + g d (Eq. (25)) from log q' = log q + a_q l1 + b_q l2
+  double q1 = exp(lnq + c.a_q * l1 + c.b_q * l2);
+  double p1 = c.gm1 * (u[NC - 1] - 0.5 * mm * ir) + dp;
+  double v2 = 0.0, vd = 0.0;
 #pragma unroll
-  for (int q = 0; q < NC; ++q) u1[q] = u[q] + g * dd[q];
-  Node<double, D> n1;
-  node_from_u<double, D>(u1, c, n1);
-  wd = 0.0;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) wd += n1.W[q] * dd[q];
+  for (int i = 0; i < D; ++i) {
+    double V = (u[1 + i] + g * dd[1 + i]) * ir1;
+    v2 += V * V;
+    vd += V * dd[1 + i];
+  }
+  double W0 = q1 * (c.w1c * p1 * ir1 - 0.5 * v2);
+  wd = W0 * dd[0] + q1 * vd - q1 * dd[NC - 1];
 }
 
 template <int D>
 __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict__ un, const double* __restrict__ d,
-                                                        const double* __restrict__ J, size_t n_nodes,
+                                                        const double* __restrict__ J,
+                                                        const double* __restrict__ cache, size_t n_nodes,
                                                         Phys<double> c, const RootState* __restrict__ st,
                                                         double* __restrict__ part) {
   if (st->done) return;
@@ -734,17 +807,16 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
       dd[q] = __ldg(&d[ix]);
       uu[q] = __ldg(&un[ix]);
     }
-    Node<double, D> n0;
-    node_from_u<double, D>(uu, c, n0);
-    double s0 = c.beta * n0.q * n0.p;
+    double s0 = __ldg(&cache[t]), ir = __ldg(&cache[n_nodes + t]);
+    double ip = __ldg(&cache[2 * n_nodes + t]), lnq = __ldg(&cache[3 * n_nodes + t]);
     double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
     double ds, wd;
-    entropy_change_and_slope<D>(uu, dd, ga, s0, c, ds, wd);
+    entropy_change_and_slope<D>(uu, dd, ga, s0, ir, ip, lnq, c, ds, wd);
     v[0] = H * ds;
     v[1] = H * wd;
     v[2] = H * fabs(ds);
     if (gb > 0.0) {
-      entropy_change_and_slope<D>(uu, dd, gb, s0, c, ds, wd);
+      entropy_change_and_slope<D>(uu, dd, gb, s0, ir, ip, lnq, c, ds, wd);
       v[3] = H * ds;
       v[4] = H * wd;
       v[5] = H * fabs(ds);
@@ -835,6 +907,7 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
   // Newton phase
   double g = st->ga;
   double f = tot[0] - g * est;
+  st->dS_last = tot[0];
   double df = tot[1] - est;
   st->f_last = f;
   st->df_last = df;
@@ -867,9 +940,9 @@ int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStrea
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ROOT, s);
   if (c->dim == 2)
-    root_eval_kernel<2><<<nb, 256, 0, s>>>(un, d, c->b.J, n, ph, c->b.root, c->b.partial);
+    root_eval_kernel<2><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
   else
-    root_eval_kernel<3><<<nb, 256, 0, s>>>(un, d, c->b.J, n, ph, c->b.root, c->b.partial);
+    root_eval_kernel<3><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
   c->launches++;
   *n_partial = nb;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

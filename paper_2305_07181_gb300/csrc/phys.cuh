@@ -26,6 +26,9 @@ struct Phys {
   T gam_gm1;           // gam/(gam-1)
   T s_ac, s_en;        // S^ entries: 1/(2 gam), (gam-1)(gam+alpha)/(gam alpha), Eq. (76)
   T mu, kappa, R;      // viscosity, conductivity mu gam R/((gam-1) Pr), gas constant
+  // Taylor coefficients of g(eps) = ((1+eps)^r - 1)/(r eps) for r = r1, r2
+  // (c_0 = 1, c_k = c_(k-1) (r - k)/(k + 1)), used by exp_avg
+  T ser1[16], ser2[16];
 };
 
 template <typename T>
@@ -51,6 +54,16 @@ __host__ inline Phys<T> make_phys(double gam, double beta, double R, double mu, 
   c.mu = (T)mu;
   c.kappa = (T)(mu * gam * R / ((gam - 1.0) * Pr));
   c.R = (T)R;
+  double r1 = -gam / alpha, r2 = (1.0 - gam) / alpha;
+  double a1 = 1.0, a2 = 1.0;
+  for (int k = 0; k < 16; ++k) {
+    if (k > 0) {
+      a1 *= (r1 - k) / (k + 1);
+      a2 *= (r2 - k) / (k + 1);
+    }
+    c.ser1[k] = (T)a1;
+    c.ser2[k] = (T)a2;
+  }
   return c;
 }
 
@@ -72,6 +85,7 @@ __device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
 template <typename T, int D>
 struct Node {
   T rho, V[D], p, e, q, v2;
+  T lnq, lnp;  // log q, log p (reused by the parameter-vector powers)
   T W[D + 2];
 };
 
@@ -89,7 +103,9 @@ __device__ __forceinline__ bool node_from_u(const T* u, const Phys<T>& c, Node<T
   n.e = u[D + 1];
   n.p = c.gm1 * (n.e - T(0.5) * n.rho * n.v2);
   bool ok = (n.rho > T(0)) && (n.p > T(0)) && isfinite(n.e);
-  n.q = t_exp(c.a_q * t_log(n.rho) + c.b_q * t_log(n.p));
+  n.lnp = t_log(n.p);
+  n.lnq = c.a_q * t_log(n.rho) + c.b_q * n.lnp;
+  n.q = t_exp(n.lnq);
   n.W[0] = n.q * (c.w1c * n.p * ir - T(0.5) * n.v2);
 #pragma unroll
   for (int i = 0; i < D; ++i) n.W[1 + i] = n.q * n.V[i];
@@ -111,9 +127,26 @@ __device__ __forceinline__ void euler_flux(const Node<T, D>& n, int i, T* F) {
 // the entropy variables, by the chain rule through (q, V, theta = p/rho, rho):
 //   q = -W_nc, V = W_(1..d)/q, W_1/q = w1c theta - |V|^2/2,
 //   q = rho^(a_q + b_q) theta^b_q.
+// reciprocals shared by the d directions of dflux_dw
+template <typename T>
+struct JvpPrep {
+  T iq, ir, theta, itheta;
+};
+
 template <typename T, int D>
-__device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const Phys<T>& c, int i, const T* v, T* dF) {
-  T iq = T(1) / n.q;
+__device__ __forceinline__ JvpPrep<T> jvp_prep(const Node<T, D>& n) {
+  JvpPrep<T> j;
+  j.iq = T(1) / n.q;
+  j.ir = T(1) / n.rho;
+  j.theta = n.p * j.ir;
+  j.itheta = n.rho / n.p;
+  return j;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& jp, const Phys<T>& c, int i,
+                                         const T* v, T* dF) {
+  T iq = jp.iq;
   T dq = -v[D + 1];
   T dV[D];
   T vdv = T(0);
@@ -122,11 +155,10 @@ __device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const Phys<T>& c, 
     dV[j] = (v[1 + j] - dq * n.V[j]) * iq;
     vdv += n.V[j] * dV[j];
   }
-  T ir = T(1) / n.rho;
-  T theta = n.p * ir;
+  T theta = jp.theta;
   T w0q = c.w1c * theta - T(0.5) * n.v2;
   T dtheta = c.inv_w1c * ((v[0] - dq * w0q) * iq + vdv);
-  T drho = n.rho * c.inv_apb * (dq * iq - c.b_q * dtheta / theta);
+  T drho = n.rho * c.inv_apb * (dq * iq - c.b_q * dtheta * jp.itheta);
   T dp = drho * theta + n.rho * dtheta;
   T dm = drho * n.V[i] + n.rho * dV[i];
   dF[0] = dm;
@@ -141,9 +173,8 @@ __device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const Phys<T>& c, 
 // dissipation: P1 = z_1^r1 = q^r1, P2 = z_nc^r2 = p^r2.
 template <typename T, int D>
 __device__ __forceinline__ void z_powers(const Node<T, D>& n, const Phys<T>& c, T& P1, T& P2) {
-  T lq = c.a_q * t_log(n.rho) + c.b_q * t_log(n.p);
-  P1 = t_exp(c.r1 * lq);
-  P2 = t_exp(c.r2 * t_log(n.p));
+  P1 = t_exp(c.r1 * n.lnq);
+  P2 = t_exp(c.r2 * n.lnp);
 }
 
 // Exponential average of Eq. (47), {u^(r-1)}_e = (a^r - b^r)/(r (a - b)),
@@ -165,19 +196,14 @@ struct ExpAvgCfg<float> {
 };
 
 template <typename T>
-__device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, T r) {
-  T ia = T(1) / a;
+__device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, T r, T ia, const T* coef) {
   T eps = (b - a) * ia;
   if (t_abs(eps) >= ExpAvgCfg<T>::EPS_SWITCH) {
     return (ar - br) / (r * (a - b));
   }
-  T ck = T(1), sum = T(1), ep = T(1);
+  T sum = coef[ExpAvgCfg<T>::NTERMS - 1];
 #pragma unroll
-  for (int k = 1; k < ExpAvgCfg<T>::NTERMS; ++k) {
-    ck = ck * (r - T(k)) / T(k + 1);
-    ep *= eps;
-    sum += ck * ep;
-  }
+  for (int k = ExpAvgCfg<T>::NTERMS - 2; k >= 0; --k) sum = sum * eps + coef[k];  // Horner
   return ar * ia * sum;
 }
 
@@ -185,6 +211,7 @@ __device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, T r) {
 template <typename T, int D>
 struct ZNode {
   T q, V[D], p, P1, P2, v2;
+  T iq, ip;  // 1/q, 1/p (used by the exponential averages)
 };
 
 template <typename T, int D>
@@ -195,6 +222,15 @@ __device__ __forceinline__ void znode(const Node<T, D>& n, const Phys<T>& c, ZNo
 #pragma unroll
   for (int i = 0; i < D; ++i) z.V[i] = n.V[i];
   z_powers<T, D>(n, c, z.P1, z.P2);
+  z.iq = T(0);
+  z.ip = T(0);
+}
+
+// the reciprocals the exponential averages of a pair need (side k only)
+template <typename T, int D>
+__device__ __forceinline__ void znode_recips(ZNode<T, D>& z) {
+  z.iq = T(1) / z.q;
+  z.ip = T(1) / z.p;
 }
 
 // Pair averages shared by the Sjogreen-Yee flux (Eq. (48)) and the
@@ -216,9 +252,9 @@ template <typename T, int D>
 __device__ __forceinline__ void pair_avg(const ZNode<T, D>& k, const ZNode<T, D>& v, const Phys<T>& c,
                                          PairAvg<T, D>& a) {
   a.A1 = T(0.5) * (k.P1 + v.P1);
-  a.E1 = exp_avg<T>(k.p, v.p, k.P2, v.P2, c.r2);
+  a.E1 = exp_avg<T>(k.p, v.p, k.P2, v.P2, c.r2, k.ip, c.ser2);
   a.A2 = T(0.5) * (k.P2 + v.P2);
-  a.E2 = exp_avg<T>(k.q, v.q, k.P1, v.P1, c.r1);
+  a.E2 = exp_avg<T>(k.q, v.q, k.P1, v.P1, c.r1, k.iq, c.ser1);
   a.z1a = T(0.5) * (k.q + v.q);
   a.ke = T(0);
 #pragma unroll
