@@ -465,11 +465,18 @@ int esplit_rrk_step_host(esplit_ctx* c, double* u_host, double dt, double* g_out
 int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, void* stream) {
   int rc = check_ready(c);
   if (rc) return rc;
-  (void)u;
-  (void)cot;
-  (void)grad;
-  (void)stream;
-  return fail(c, ESPLIT_ERR_UNSUPPORTED, "residual VJP is not built in this version");
+  if (!u || !cot || !grad) return fail(c, ESPLIT_ERR_ARG, "null pointer");
+  if (grad == u || grad == cot) return fail(c, ESPLIT_ERR_ARG, "grad must not alias u or cot");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the residual VJP is built for the entropy-split scheme");
+  if (c->prm.viscous) return fail(c, ESPLIT_ERR_UNSUPPORTED, "viscous VJP not built");
+  cudaSetDevice(c->device);
+  cudaStream_t s = as_stream(stream);
+  rc = esplit::launch_residual_vjp(c, u, cot, grad, s);
+  if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
+  if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("vjp launch: ") + cudaGetErrorString(cudaGetLastError()));
+  c->last_stream = s;
+  return ESPLIT_OK;
 }
 
 int esplit_get_status(esplit_ctx* c) {

@@ -979,3 +979,5 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 }
 
 }  // namespace esplit
+
+#include "vjp.cuh"

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "dual.cuh"
+
 namespace esplit {
 
 // Constants derived from (gam, beta) on the host, Sec. 2.4 / Eq. (16):
@@ -79,6 +81,8 @@ __device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
 __device__ __forceinline__ double t_log1p(double x) { return log1p(x); }
 __device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ bool t_isfinite(double x) { return ::isfinite(x); }
+__device__ __forceinline__ bool t_isfinite(float x) { return ::isfinite(x); }
 
 // Nodal state: primitives, q = z_1 of Eq. (45) (= -W_nc), Harten entropy
 // variables W of Eq. (25).
@@ -90,8 +94,8 @@ struct Node {
 };
 
 // Returns false for a non-physical state (rho <= 0, p <= 0 or NaN).
-template <typename T, int D>
-__device__ __forceinline__ bool node_from_u(const T* u, const Phys<T>& c, Node<T, D>& n) {
+template <typename T, int D, typename C>
+__device__ __forceinline__ bool node_from_u(const T* u, const C& c, Node<T, D>& n) {
   n.rho = u[0];
   T ir = T(1) / n.rho;
   n.v2 = T(0);
@@ -102,7 +106,7 @@ __device__ __forceinline__ bool node_from_u(const T* u, const Phys<T>& c, Node<T
   }
   n.e = u[D + 1];
   n.p = c.gm1 * (n.e - T(0.5) * n.rho * n.v2);
-  bool ok = (n.rho > T(0)) && (n.p > T(0)) && isfinite(n.e);
+  bool ok = (n.rho > T(0)) && (n.p > T(0)) && t_isfinite(n.e);
   n.lnp = t_log(n.p);
   n.lnq = c.a_q * t_log(n.rho) + c.b_q * n.lnp;
   n.q = t_exp(n.lnq);
@@ -143,8 +147,8 @@ __device__ __forceinline__ JvpPrep<T> jvp_prep(const Node<T, D>& n) {
   return j;
 }
 
-template <typename T, int D>
-__device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& jp, const Phys<T>& c, int i,
+template <typename T, int D, typename C>
+__device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& jp, const C& c, int i,
                                          const T* v, T* dF) {
   T iq = jp.iq;
   T dq = -v[D + 1];
@@ -171,8 +175,8 @@ __device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& 
 
 // Powers of the parameter vector used by the two-point flux and the
 // dissipation: P1 = z_1^r1 = q^r1, P2 = z_nc^r2 = p^r2.
-template <typename T, int D>
-__device__ __forceinline__ void z_powers(const Node<T, D>& n, const Phys<T>& c, T& P1, T& P2) {
+template <typename T, int D, typename C>
+__device__ __forceinline__ void z_powers(const Node<T, D>& n, const C& c, T& P1, T& P2) {
   P1 = t_exp(c.r1 * n.lnq);
   P2 = t_exp(c.r2 * n.lnp);
 }
@@ -195,8 +199,11 @@ struct ExpAvgCfg<float> {
   static constexpr int NTERMS = 14;
 };
 
-template <typename T>
-__device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, T r, T ia, const T* coef) {
+template <int N>
+struct ExpAvgCfg<Dual<N>> : ExpAvgCfg<double> {};
+
+template <typename T, typename S>
+__device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, S r, T ia, const S* coef) {
   T eps = (b - a) * ia;
   if (t_abs(eps) >= ExpAvgCfg<T>::EPS_SWITCH) {
     return (ar - br) / (r * (a - b));
@@ -214,8 +221,8 @@ struct ZNode {
   T iq, ip;  // 1/q, 1/p (used by the exponential averages)
 };
 
-template <typename T, int D>
-__device__ __forceinline__ void znode(const Node<T, D>& n, const Phys<T>& c, ZNode<T, D>& z) {
+template <typename T, int D, typename C>
+__device__ __forceinline__ void znode(const Node<T, D>& n, const C& c, ZNode<T, D>& z) {
   z.q = n.q;
   z.p = n.p;
   z.v2 = n.v2;
@@ -248,8 +255,8 @@ struct PairAvg {
   T ke;       // sum {V_j}^2 - 1/2 {sum V_j^2}
 };
 
-template <typename T, int D>
-__device__ __forceinline__ void pair_avg(const ZNode<T, D>& k, const ZNode<T, D>& v, const Phys<T>& c,
+template <typename T, int D, typename C>
+__device__ __forceinline__ void pair_avg(const ZNode<T, D>& k, const ZNode<T, D>& v, const C& c,
                                          PairAvg<T, D>& a) {
   a.A1 = T(0.5) * (k.P1 + v.P1);
   a.E1 = exp_avg<T>(k.p, v.p, k.P2, v.P2, c.r2, k.ip, c.ser2);
@@ -268,8 +275,8 @@ __device__ __forceinline__ void pair_avg(const ZNode<T, D>& k, const ZNode<T, D>
 }
 
 // sum_i nu_i F*_i(U_k, U_v) (Eq. (48)) for a direction vector nu.
-template <typename T, int D>
-__device__ __forceinline__ void sy_flux_dir(const PairAvg<T, D>& a, const Phys<T>& c, const T* nu, T* F) {
+template <typename T, int D, typename C>
+__device__ __forceinline__ void sy_flux_dir(const PairAvg<T, D>& a, const C& c, const T* nu, T* F) {
   T inv_den = T(1) / (a.A1 * a.E1);
   T mn = T(0);
 #pragma unroll
@@ -284,8 +291,8 @@ __device__ __forceinline__ void sy_flux_dir(const PairAvg<T, D>& a, const Phys<T
 // X^ |Lambda_n| S^ X^T dw of Eq. (69) at the intermediate state (Eqs.
 // (73)-(80)); n is a unit normal.  3D eigenvectors as printed, 2D by
 // deleting the fourth row and column.
-template <typename T, int D>
-__device__ __forceinline__ void diss_apply(const PairAvg<T, D>& a, const Phys<T>& c, const T* n, const T* dw,
+template <typename T, int D, typename C>
+__device__ __forceinline__ void diss_apply(const PairAvg<T, D>& a, const C& c, const T* n, const T* dw,
                                            T* out) {
   T rho_h = a.z1a / (a.A1 * a.E1);
   T iz = T(1) / a.z1a;

@@ -1,0 +1,241 @@
+// Reverse mode (vector-Jacobian product) of the entropy-split residual with
+// EC SATs and matrix interface dissipation: grad = (d dudt / d u)^T cot.
+//
+// The residual of element k at node m is
+//   r_m = sum_i (M_i f_i)_m - 1/(beta+1) sum_i A~_i(u_m) (D_i w)_m + sat_m,
+// with f_i, w pointwise in u and sat_m = -G(u_km, u_vn)/H_km for the facet
+// node pair (k, m) ~ (v, n) (and +G/H_vn on the other side).  Its transpose:
+//   gbar_i   = -1/(beta+1) A~_i(u_m) cot_m          (A~_i symmetric, Sec. 2.4)
+//   fbar_i   = M_i^T cot,   wbar = sum_i D_i^T gbar_i           (per element)
+//   grad_m   = sum_i (df_i/du)^T fbar_i + (dw/du)^T wbar
+//              - 1/(beta+1) d/du [cot_m . sum_i A~_i(u) g_i]|_(g_i = (D_i w)_m)
+//              + facet part (dG/du)^T (-cot_km/H_km + cot_vn/H_vn).
+// The pointwise Jacobians are exact, from the same physics templates run on
+// forward-mode dual numbers (dual.cuh); the contractions are transposed
+// applications of the stored per-element operators.  Float64 throughout.
+// Included by kernels.cu (one device translation unit: the constant-memory
+// operator tables are shared).
+#pragma once
+
+namespace esplit {
+
+// facet pairs: each thread writes the facet part of grad at its two slots
+template <int D>
+__global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__ u, const double* __restrict__ cot,
+                                                      const int2* __restrict__ fp, int n_pairs,
+                                                      const double* __restrict__ nu, const double* __restrict__ J,
+                                                      double* __restrict__ gsat, Phys<double> c, int dissipation) {
+  constexpr int NC = D + 2;
+  constexpr int N2 = 2 * NC;
+  using T = Dual<N2>;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_pairs) return;
+  const int NP = c_ref.n_p, NS = c_ref.n_slot;
+  int2 pr = __ldg(&fp[t]);
+  int k = pr.x / NS, s = pr.x - k * NS;
+  int v = pr.y / NS, s2 = pr.y - v * NS;
+  int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
+  T uk[NC], uv[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    uk[q] = T(__ldg(&u[((size_t)k * NC + q) * NP + m]));
+    uv[q] = T(__ldg(&u[((size_t)v * NC + q) * NP + n]));
+    uk[q].d[q] = 1.0;
+    uv[q].d[NC + q] = 1.0;
+  }
+  Node<T, D> nk, nv;
+  node_from_u<T, D>(uk, c, nk);
+  node_from_u<T, D>(uv, c, nv);
+  ZNode<T, D> zk, zv;
+  znode<T, D>(nk, c, zk);
+  znode<T, D>(nv, c, zv);
+  znode_recips<T, D>(zk);
+  PairAvg<T, D> a;
+  pair_avg<T, D>(zk, zv, c, a);
+  double nud[D];
+  T nuv[D];
+  double b2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    nud[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
+    nuv[i] = T(nud[i]);
+    b2 += nud[i] * nud[i];
+  }
+  T G[NC];
+  sy_flux_dir<T, D>(a, c, nuv, G);
+  if (dissipation) {
+    double b = sqrt(b2);
+    T nh[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = T(nud[i] / b);
+    T dw[NC], out[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
+    diss_apply<T, D>(a, c, nh, dw, out);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) G[q] += (0.5 * b) * out[q];
+  }
+  double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
+  double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+  double gb[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+    gb[q] = -__ldg(&cot[((size_t)k * NC + q) * NP + m]) * ihk + __ldg(&cot[((size_t)v * NC + q) * NP + n]) * ihv;
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) {
+    double gk = 0.0, gv = 0.0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      gk += gb[q] * G[q].d[cc];
+      gv += gb[q] * G[q].d[NC + cc];
+    }
+    gsat[((size_t)k * NC + cc) * NS + s] = gk;
+    gsat[((size_t)v * NC + cc) * NS + s2] = gv;
+  }
+}
+
+template <int D, int NP, int EB>
+__global__ void __launch_bounds__(EB * NP) split_vjp_kernel(const double* __restrict__ u,
+                                                            const double* __restrict__ cot,
+                                                            const double* __restrict__ ops,
+                                                            const double* __restrict__ gsat, int n_e,
+                                                            double* __restrict__ grad, Phys<double> c) {
+  constexpr int NC = D + 2;
+  using TD = Dual<NC>;
+  __shared__ double sw[EB][NC][NP];
+  __shared__ double sv[EB][NC][NP];
+  __shared__ double sgb[EB][D][NC][NP];
+  const int NS = c_ref.n_slot;
+  int el = threadIdx.x / NP;
+  int m = threadIdx.x - el * NP;
+  int e = blockIdx.x * EB + el;
+  bool active = e < n_e;
+  Node<double, D> nd;
+  double uu[NC], vv[NC];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      uu[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
+      vv[q] = __ldg(&cot[((size_t)e * NC + q) * NP + m]);
+      sv[el][q][m] = vv[q];
+    }
+    node_from_u<double, D>(uu, c, nd);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sw[el][q][m] = nd.W[q];
+  }
+  __syncthreads();
+  const double* op = ops + (size_t)(active ? e : 0) * (2 * D * NP * NP);
+  double g[D][NC];
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) g[i][q] = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+      for (int n = 0; n < NP; ++n) {
+        double dt = __ldg(&op[((D + i) * NP + n) * NP + m]);  // D_i[m][n]
+#pragma unroll
+        for (int q = 0; q < NC; ++q) g[i][q] += dt * sw[el][q][n];
+      }
+    const JvpPrep<double> jp = jvp_prep<double, D>(nd);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double a[NC];
+      dflux_dw<double, D>(nd, jp, c, i, vv, a);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sgb[el][i][q][m] = -c.inv_bp1 * a[q];
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  double fb[D][NC], wb[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) wb[q] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) fb[i][q] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    for (int n = 0; n < NP; ++n) {
+      double mt = __ldg(&op[(i * NP + m) * NP + n]);        // M_i[n][m]
+      double dt = __ldg(&op[((D + i) * NP + m) * NP + n]);  // D_i[n][m]
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        fb[i][q] += mt * sv[el][q][n];
+        wb[q] += dt * sgb[el][i][q][n];
+      }
+    }
+  // exact pointwise Jacobians at u_m by dual numbers
+  TD ud[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    ud[q] = TD(uu[q]);
+    ud[q].d[q] = 1.0;
+  }
+  Node<TD, D> ndd;
+  node_from_u<TD, D>(ud, c, ndd);
+  const JvpPrep<TD> jpd = jvp_prep<TD, D>(ndd);
+  double gr[NC];
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) gr[cc] = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    TD F[NC];
+    euler_flux<TD, D>(ndd, i, F);
+    TD gi[NC], dF[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) gi[q] = TD(g[i][q]);
+    dflux_dw<TD, D>(ndd, jpd, c, i, gi, dF);
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) gr[cc] += fb[i][q] * F[q].d[cc] - c.inv_bp1 * vv[q] * dF[q].d[cc];
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) gr[cc] += wb[q] * ndd.W[q].d[cc];
+  int sl = c_ref.node_slot[m];
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) {
+    if (sl >= 0) gr[cc] += __ldg(&gsat[((size_t)e * NC + cc) * NS + sl]);
+    grad[((size_t)e * NC + cc) * NP + m] = gr[cc];
+  }
+}
+
+template <int D, int NP>
+static int vjp_np(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s) {
+  const Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  {
+    int bs = 64;
+    int nb = (c->n_pairs + bs - 1) / bs;
+    ProfScope ps(c, PG_FACE, s);
+    face_vjp_kernel<D><<<nb, bs, 0, s>>>(u, cot, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.sat, ph,
+                                         c->prm.dissipation);
+    c->launches++;
+  }
+  {
+    constexpr int EB = (128 / NP) > 0 ? (128 / NP) : 1;
+    int nb = (c->n_e + EB - 1) / EB;
+    ProfScope ps(c, PG_SPLIT, s);
+    split_vjp_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, cot, c->b.ops64, c->b.sat, c->n_e, grad, ph);
+    c->launches++;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s) {
+  if (c->dim == 2) {
+    switch (c->n_p) {
+      case 7: return vjp_np<2, 7>(c, u, cot, grad, s);
+      case 12: return vjp_np<2, 12>(c, u, cot, grad, s);
+      case 18: return vjp_np<2, 18>(c, u, cot, grad, s);
+      case 27: return vjp_np<2, 27>(c, u, cot, grad, s);
+    }
+  }
+  return -2;
+}
+
+}  // namespace esplit
