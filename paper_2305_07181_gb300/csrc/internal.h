@@ -123,5 +123,4 @@ int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s);
 int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
 int set_ref_tables(const RefTables& t);
 int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);
-
 }  // namespace esplit

@@ -196,15 +196,28 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 // entropy-split volume kernel (Eq. (100)): EB elements per block, one thread
 // per node.  r = sum_i M_i f_i - 1/(beta+1) sum_i A~_i (D_i w) + sat
 //
-// Node states, fluxes and entropy variables are always formed in float64.
-// The contractions act on values relative to the element's node 0,
-//   M_i f_i = M_i (f_i - f_i,0) + f_i,0 E_x_i/H,   D_i w = D_i (w - w_0),
-// (M_i 1 = H^-1 E_x_i 1 and D_i 1 = 0 for the SBP operators of Def. 1), so the
-// operator entries (~1/(h H_ref)) multiply only the variation inside the
-// element; with T = float this is what keeps the float32 contraction within
-// the stated bound, with T = double it removes most of the cancellation.
+// Node states, fluxes, entropy variables and the A~_i products are float64 in
+// both precision modes.  T = double: plain float64 contractions.  T = float
+// (FP32-bulk): the contractions act in float32 on the variation inside the
+// element, relative to its node 0, and the node-0 values come back through
+// the float64 row sums of the stored operators,
+//   M_i f_i = M_i (f_i - f_i,0) + f_i,0 (M_i 1),  D_i w = D_i (w - w_0) + w_0 (D_i 1),
+// so the operator entries (~1/(h H_ref)) multiply only small variations.
 // Optional: block partial of sum H w^T r (entropy production, float64).
 // ---------------------------------------------------------------------------
+template <typename T, int D, int NP, int EB>
+struct SplitSmem {
+  double rf[EB][D][D + 2][NP];  // fluxes
+  double rw[EB][D + 2][NP];     // entropy variables
+  T sf[EB][D][D + 2][NP];       // float32 variations (FP32-bulk only)
+  T sw[EB][D + 2][NP];
+};
+template <int D, int NP, int EB>
+struct SplitSmem<double, D, NP, EB> {
+  double rf[EB][D][D + 2][NP];
+  double rw[EB][D + 2][NP];
+};
+
 template <typename T, int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
@@ -212,10 +225,8 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64, int* __restrict__ status,
     double* __restrict__ prod) {
   constexpr int NC = D + 2;
-  __shared__ double rf[EB][D][NC][NP];  // raw fluxes
-  __shared__ double rw[EB][NC][NP];     // raw entropy variables
-  __shared__ T sf[EB][D][NC][NP];       // relative to node 0
-  __shared__ T sw[EB][NC][NP];
+  constexpr bool F64 = sizeof(T) == sizeof(double);
+  __shared__ SplitSmem<T, D, NP, EB> sm;
   const int NS = c_ref.n_slot;
   int el = threadIdx.x / NP;
   int m = threadIdx.x - el * NP;
@@ -233,52 +244,30 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       double F[NC];
       euler_flux<double, D>(nd, i, F);
 #pragma unroll
-      for (int q = 0; q < NC; ++q) rf[el][i][q][m] = F[q];
+      for (int q = 0; q < NC; ++q) sm.rf[el][i][q][m] = F[q];
     }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) rw[el][q][m] = nd.W[q];
+    for (int q = 0; q < NC; ++q) sm.rw[el][q][m] = nd.W[q];
   }
   __syncthreads();
-  // reference values c: node 0 (float64 path) or the float32 element mean
-  // (float32 path, smaller variations); any c is exact once the row sums of
-  // the stored operators are added back: M f = M (f - c) + c (M 1).
   double f0[D][NC], w0[NC];
-  if (active) {
+  if constexpr (!F64) {
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          f0[i][q] = sm.rf[el][i][q][0];
+          sm.sf[el][i][q][m] = (T)(sm.rf[el][i][q][m] - f0[i][q]);
+        }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        if constexpr (sizeof(T) == sizeof(double)) {
-          f0[i][q] = rf[el][i][q][0];
-        } else {
-          float s = 0.f;
-#pragma unroll
-          for (int n = 0; n < NP; ++n) s += (float)rf[el][i][q][n];
-          f0[i][q] = (double)(s * (1.f / NP));
-        }
-      }
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      if constexpr (sizeof(T) == sizeof(double)) {
-        w0[q] = rw[el][q][0];
-      } else {
-        float s = 0.f;
-#pragma unroll
-        for (int n = 0; n < NP; ++n) s += (float)rw[el][q][n];
-        w0[q] = (double)(s * (1.f / NP));
+        w0[q] = sm.rw[el][q][0];
+        sm.sw[el][q][m] = (T)(sm.rw[el][q][m] - w0[q]);
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
-  if (active) {
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int q = 0; q < NC; ++q) sf[el][i][q][m] = (T)(rf[el][i][q][m] - f0[i][q]);
-#pragma unroll
-    for (int q = 0; q < NC; ++q) sw[el][q][m] = (T)(rw[el][q][m] - w0[q]);
-  }
-  __syncthreads();
   double hw = 0.0;
   if (active) {
     T acc[NC], g[D][NC];
@@ -297,42 +286,45 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
         T dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          acc[q] += mt * sf[el][i][q][n];
-          g[i][q] += dt * sw[el][q][n];
+          if constexpr (F64) {
+            acc[q] += mt * sm.rf[el][i][q][n];
+            g[i][q] += dt * sm.rw[el][q][n];
+          } else {
+            acc[q] += mt * sm.sf[el][i][q][n];
+            g[i][q] += dt * sm.sw[el][q][n];
+          }
         }
       }
     }
-    // add back the reference values through the stored operators' row sums
-    const double* rs = rows + (size_t)e * (2 * D * NP);
-    double back[NC];
+    double accd[NC], gd[D][NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) back[q] = 0.0;
+    for (int q = 0; q < NC; ++q) accd[q] = (double)acc[q];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      double rm = __ldg(&rs[i * NP + m]);
-      double rd = __ldg(&rs[(D + i) * NP + m]);
+    for (int i = 0; i < D; ++i)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        back[q] += f0[i][q] * rm;
-        g[i][q] = (T)((double)g[i][q] + w0[q] * rd);
+      for (int q = 0; q < NC; ++q) gd[i][q] = (double)g[i][q];
+    if constexpr (!F64) {
+      // add back the node-0 values through the stored operators' row sums
+      const double* rs = rows + (size_t)e * (2 * D * NP);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double rm = __ldg(&rs[i * NP + m]);
+        double rd = __ldg(&rs[(D + i) * NP + m]);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          accd[q] += f0[i][q] * rm;
+          gd[i][q] += w0[q] * rd;
+        }
       }
     }
-    Node<T, D> nt;
-    nt.rho = (T)nd.rho;
-    nt.p = (T)nd.p;
-    nt.e = (T)nd.e;
-    nt.q = (T)nd.q;
-    nt.v2 = (T)nd.v2;
+    const JvpPrep<double> jp = jvp_prep<double, D>(nd);
+    double nonc[NC];
 #pragma unroll
-    for (int i = 0; i < D; ++i) nt.V[i] = (T)nd.V[i];
-    const JvpPrep<T> jp = jvp_prep<T, D>(nt);
-    T nonc[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) nonc[q] = T(0);
+    for (int q = 0; q < NC; ++q) nonc[q] = 0.0;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      T dF[NC];
-      dflux_dw<T, D>(nt, jp, c, i, g[i], dF);
+      double dF[NC];
+      dflux_dw<double, D>(nd, jp, c64, i, gd[i], dF);
 #pragma unroll
       for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
     }
@@ -341,7 +333,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     double res[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      res[q] = ((double)acc[q] + back[q]) - (double)(c.inv_bp1 * nonc[q]);
+      res[q] = accd[q] - c64.inv_bp1 * nonc[q];
       if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
       r[((size_t)e * NC + q) * NP + m] = res[q];
     }
@@ -494,7 +486,8 @@ struct VolCfg {
 };
 
 template <typename T, int D, int NP>
-static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial,
+                       double* sat) {
   const Phys<T> ph = make_phys<T>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   const Phys<double> ph64 = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   const T* ops = std::is_same<T, double>::value ? (const T*)c->b.ops64 : (const T*)c->b.ops32;
@@ -505,7 +498,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     ProfScope ps(c, PG_FACE, s);
     // facet terms are O(1/h) and cancel against the volume's boundary part:
     // they stay float64 in both precision modes
-    face_kernel<double, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.sat, ph64,
+    face_kernel<double, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
                                              c->prm.dissipation, c->b.status);
     c->launches++;
   }
@@ -519,7 +512,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.rows, c->b.J, c->b.sat, lsplit,
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.rows, c->b.J, sat, lsplit,
                                                              n_split, ph, ph64, c->b.status,
                                                              prod ? prod + np_used : nullptr);
     c->launches++;
@@ -538,7 +531,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     int nb = (n_had + EB - 1) / EB;
     ProfScope ps(c, PG_HAD, s);
     hadamard_volume_kernel<T, D, NP, EB><<<nb, EB * NP, smem, s>>>(
-        u, r, ops, c->b.J, c->b.sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
+        u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
   }
@@ -547,21 +540,22 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
 }
 
 template <typename T>
-static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial,
+                      double* sat) {
   if (c->dim == 2) {
     switch (c->n_p) {
-      case 7: return residual_np<T, 2, 7>(c, u, r, s, prod, n_partial);
-      case 12: return residual_np<T, 2, 12>(c, u, r, s, prod, n_partial);
-      case 18: return residual_np<T, 2, 18>(c, u, r, s, prod, n_partial);
-      case 27: return residual_np<T, 2, 27>(c, u, r, s, prod, n_partial);
+      case 7: return residual_np<T, 2, 7>(c, u, r, s, prod, n_partial, sat);
+      case 12: return residual_np<T, 2, 12>(c, u, r, s, prod, n_partial, sat);
+      case 18: return residual_np<T, 2, 18>(c, u, r, s, prod, n_partial, sat);
+      case 27: return residual_np<T, 2, 27>(c, u, r, s, prod, n_partial, sat);
     }
   }
   return -2;
 }
 
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
-  if (c->prm.precision == ESPLIT_FP32_BULK) return residual_t<float>(c, u, r, s, prod, n_partial);
-  return residual_t<double>(c, u, r, s, prod, n_partial);
+  if (c->prm.precision == ESPLIT_FP32_BULK) return residual_t<float>(c, u, r, s, prod, n_partial, c->b.sat);
+  return residual_t<double>(c, u, r, s, prod, n_partial, c->b.sat);
 }
 
 // ---------------------------------------------------------------------------

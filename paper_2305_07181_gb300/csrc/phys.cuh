@@ -90,6 +90,7 @@ template <typename T, int D>
 struct Node {
   T rho, V[D], p, e, q, v2;
   T lnq, lnp;  // log q, log p (reused by the parameter-vector powers)
+  T ir;        // 1/rho
   T W[D + 2];
 };
 
@@ -98,6 +99,7 @@ template <typename T, int D, typename C>
 __device__ __forceinline__ bool node_from_u(const T* u, const C& c, Node<T, D>& n) {
   n.rho = u[0];
   T ir = T(1) / n.rho;
+  n.ir = ir;
   n.v2 = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -141,7 +143,7 @@ template <typename T, int D>
 __device__ __forceinline__ JvpPrep<T> jvp_prep(const Node<T, D>& n) {
   JvpPrep<T> j;
   j.iq = T(1) / n.q;
-  j.ir = T(1) / n.rho;
+  j.ir = n.ir;
   j.theta = n.p * j.ir;
   j.itheta = n.rho / n.p;
   return j;

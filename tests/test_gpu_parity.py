@@ -249,7 +249,7 @@ def summand_scale(u, op, m, elems, scheme, prm):
     |nu||F*|/H + |nu|/(2H) |X|L|SX^T||dw|.  FP64 rounding of either side is a
     few eps times this, whatever the result's own size."""
     from oracle.physics import (euler_flux, entropy_variables, symmetrized_flux_jacobians, sy_flux,
-                                dissipation_matrix)
+                                dissipation_matrix, dW_dU)
     from oracle.operators import physical_operators
     el = torch.as_tensor(elems)
     ops = physical_operators(op, m, el)
@@ -263,7 +263,9 @@ def summand_scale(u, op, m, elems, scheme, prm):
         w = entropy_variables(U, prm).abs()
         Dw = torch.einsum("nimk,nkc->nimc", ops["D"].abs(), w)
         At = symmetrized_flux_jacobians(U, prm).abs()
-        sc = sc + torch.einsum("nmicd,nimd->nmc", At, Dw) / (prm.beta + 1)
+        # the oracle forms A~_i with (dW/dU)^-1: its rounding carries cond(dW/dU) (~115 here)
+        kappa = torch.linalg.cond(dW_dU(U, prm))
+        sc = sc + kappa[..., None] * torch.einsum("nmicd,nimd->nmc", At, Dw) / (prm.beta + 1)
     else:
         n_, npp, nc = U.shape
         F2 = 2 * sy_flux(U[:, :, None, :].expand(n_, npp, npp, nc), U[:, None, :, :].expand(n_, npp, npp, nc),
@@ -292,7 +294,8 @@ def test_full_size_config2_sampled(lib, p):
     Here the residual is ~1e3-1e4 times smaller than the terms it is summed
     from (the noise is 1e-3 and the operator entries ~1/(h H_ref)), and the
     FP64 oracle's own rounding is ~eps times those terms (checked against
-    extended precision).  The bound is therefore
+    extended precision), times cond(dW/dU) for the A~_i term, which the oracle
+    forms through a matrix inverse.  The bound is therefore
     |r_gpu - r_oracle| <= 1e-12 max|r| + 16 eps (summand scale),
     and the plain max-norm relative error is reported."""
     R, Dg, rrk, OP = _oracle()
