@@ -126,6 +126,26 @@ int esplit_set_hybrid_flags(esplit_ctx* ctx, const unsigned char* flags_host, in
  * esplit_get_status(). */
 int esplit_residual(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void* stream);
 
+/* The residual of esplit_residual for callers that must not allocate device
+ * memory while they run: for example a host application whose device memory
+ * is owned by its own pool allocator, or a time-critical loop that cannot
+ * absorb the device-wide synchronisation cudaMalloc and cudaFree can cause.
+ * This call allocates nothing -- no cudaMalloc, cudaFree, library allocator or
+ * CUDA event -- and does not use the context's facet scratch: the facet
+ * contributions go to a 16 MiB scratch array (2^21 doubles) that the library
+ * holds in static device memory on every GPU that loads it, until the
+ * process exits.  Meshes needing more than that, n_e * n_c * n_slot >
+ * 2^21, are rejected with ESPLIT_ERR_ARG and a message giving both numbers.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it; make that first call before any stream
+ * capture.  Every call on a device shares the one array and overwrites all
+ * of the part it uses (nothing has to start at zero), so calls whose kernels
+ * overlap on the GPU -- on different streams, or from different threads or
+ * contexts -- race on it: serialise them.  Arguments, layout and errors as
+ * for esplit_residual; the result equals esplit_residual's.  The paper has no
+ * counterpart of this entry point; it is a deployment convenience. */
+int esplit_residual_noalloc(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void* stream);
+
 /* Same with host buffers: copies u_host to the device, evaluates, copies the
  * residual back, and synchronises `stream` before returning. */
 int esplit_residual_host(esplit_ctx* ctx, const double* u_host, double* dudt_host, void* stream);

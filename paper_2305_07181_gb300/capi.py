@@ -57,6 +57,7 @@ _SIGNATURES = {
     "esplit_get_params": (_I, [_P, ctypes.POINTER(esplit_params)]),
     "esplit_set_hybrid_flags": (_I, [_P, _P, _I]),
     "esplit_residual": (_I, [_P, _P, _P, _P]),
+    "esplit_residual_noalloc": (_I, [_P, _P, _P, _P]),
     "esplit_residual_host": (_I, [_P, _P, _P, _P]),
     "esplit_entropy": (_I, [_P, _P, _D, _P]),
     "esplit_entropy_rate": (_I, [_P, _P, _P, _D, _P]),
@@ -130,6 +131,13 @@ def esplit_set_hybrid_flags(ctx, flags_ptr, n_e) -> int:
 
 def esplit_residual(ctx, u_ptr, r_ptr, stream=None) -> int:
     return lib.esplit_residual(ctx, u_ptr, r_ptr, stream)
+
+
+def esplit_residual_noalloc(ctx, u_ptr, r_ptr, stream=None) -> int:
+    """Residual whose facet scratch is the library's static device array (no
+    allocation of any kind); see include/esplit.h for the size limit and the
+    rule that calls overlapping on the GPU race on that array."""
+    return lib.esplit_residual_noalloc(ctx, u_ptr, r_ptr, stream)
 
 
 def esplit_residual_host(ctx, u_ptr, r_ptr, stream=None) -> int:

@@ -330,6 +330,30 @@ int esplit_residual(esplit_ctx* c, const double* u, double* r, void* stream) {
   return residual_impl(c, u, r, as_stream(stream), nullptr, nullptr);
 }
 
+int esplit_residual_noalloc(esplit_ctx* c, const double* u, double* r, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !r) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
+  if (u == r) return fail(c, ESPLIT_ERR_ARG, "u and dudt must not alias");
+  if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
+    return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
+  size_t need = (size_t)c->n_e * c->n_c * c->n_slot;
+  if (need > esplit::NOALLOC_SCRATCH_DOUBLES)
+    return fail(c, ESPLIT_ERR_ARG,
+                "mesh too large for esplit_residual_noalloc: its facet scratch needs " + std::to_string(need) +
+                    " doubles (n_e * n_c * n_slot), the static maximum is " +
+                    std::to_string(esplit::NOALLOC_SCRATCH_DOUBLES));
+  CK(cudaSetDevice(c->device));
+  double* scratch = nullptr;
+  if (esplit::noalloc_scratch_ptr(c->device, &scratch))
+    return fail(c, ESPLIT_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+  rc = esplit::launch_residual_noalloc(c, u, r, as_stream(stream), scratch);
+  if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
+  if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString(cudaGetLastError()));
+  c->last_stream = as_stream(stream);
+  return ESPLIT_OK;
+}
+
 int esplit_residual_host(esplit_ctx* c, const double* u, double* r, void* stream) {
   int rc = check_ready(c);
   if (rc) return rc;

@@ -123,4 +123,10 @@ int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s);
 int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
 int set_ref_tables(const RefTables& t);
 int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);
+// static facet scratch of esplit_residual_noalloc: 2^21 doubles (16 MiB)
+constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(1) << 21;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int noalloc_scratch_ptr(int device, double** out);
+int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch);
+
 }  // namespace esplit

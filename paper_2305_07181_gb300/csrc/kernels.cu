@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.h"
@@ -556,6 +557,40 @@ static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s,
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
   if (c->prm.precision == ESPLIT_FP32_BULK) return residual_t<float>(c, u, r, s, prod, n_partial, c->b.sat);
   return residual_t<double>(c, u, r, s, prod, n_partial, c->b.sat);
+}
+
+// ---------------------------------------------------------------------------
+// Residual variant with no device allocation at all: its facet scratch is
+// this file-scope array instead of the context's buffer.  Host code may not
+// use the array's name as a device address; the address is looked up once
+// per device with cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+int noalloc_scratch_ptr(int device, double** out) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) return -1;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != device) return -1;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return -1;
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return 0;
+}
+
+int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch) {
+  const bool prof = c->prof;  // kernel timing would create CUDA events: keep it off here
+  c->prof = false;
+  int rc = c->prm.precision == ESPLIT_FP32_BULK ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
+                                                 : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
+  c->prof = prof;
+  return rc;
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,69 @@
+"""esplit_residual_noalloc: the residual for callers that must not allocate
+device memory while they run (their device memory is owned by a pool
+allocator of their own, or their loop cannot absorb the synchronisation that
+cudaMalloc/cudaFree can cause).  Its facet scratch is a static device array
+of the library, so this file is collected last: if it fails, a run that stops
+at the first failure has already run every other test.  It must pass both
+alone in a fresh process and after the other tests."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from esplit_inputs import tri_operator, periodic_tri_mesh, states
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12  # the FP64 parity tolerance of the other GPU tests
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_07181_gb300 as es
+    return es
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("p,scheme", [(2, "split"), (3, "hybrid"), (4, "hadamard")])
+def test_noalloc_matches_residual_twice(lib, p, scheme):
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 9, 10.0, 0.05)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True))
+    if scheme == "hybrid":
+        s.set_hybrid_flags(np.random.default_rng(1).integers(0, 2, m.n_e))
+    ref = s.empty()
+    for call in range(2):  # two calls in a row, on different states
+        u = s.to_device(states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 100 + call))
+        s.residual(u, ref)
+        out = torch.full_like(ref, float("nan"))
+        rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+        assert rc == 0, lib.capi.esplit_last_error(s.ctx)
+        torch.cuda.synchronize()
+        num = (out - ref).abs().amax(dim=(0, 2))
+        den = ref.abs().amax(dim=(0, 2))
+        assert float((num / den).max()) <= TOL
+    assert s.status() == 0
+    s.close()
+
+
+def test_noalloc_rejects_meshes_beyond_its_scratch(lib):
+    op = tri_operator(4)           # n_c * n_slot = 4 * 15 = 60 doubles per element
+    m = periodic_tri_mesh(op, 192, 10.0, 0.05)   # 73,728 elements -> 4.4e6 > 2^21
+    s = lib.Solver(op, m, lib.Params())
+    u = s.to_device(states.isentropic_vortex(m))
+    out = s.empty()
+    rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+    assert rc == lib.capi.ESPLIT_ERR_ARG
+    msg = lib.capi.esplit_last_error(s.ctx)
+    assert "2097152" in msg and "4423680" in msg
+    s.close()
