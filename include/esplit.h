@@ -175,6 +175,22 @@ int esplit_rrk_step_host(esplit_ctx* ctx, double* u_host, double dt, double* g_o
 int esplit_residual_vjp(esplit_ctx* ctx, const double* u_dev, const double* cot_dev,
                         double* grad_dev, void* stream);
 
+/* Gradient of the total entropy 1^T H s(u) (Eq. (16)): grad_dev = H w(u),
+ * w the entropy variables of Eq. (25).  [n_e][n_c][n_p] device buffers. */
+int esplit_entropy_grad(esplit_ctx* ctx, const double* u_dev, double* grad_dev, void* stream);
+
+/* Reverse of one relaxation RK4 step (Eqs. (97)-(98)) for gradients through
+ * many steps with per-step checkpoints: recomputes the step from the
+ * checkpoint u_dev (unchanged), then maps the cotangent ubar_next_dev of
+ * u_{n+1} to the cotangent ubar_dev of u_n, including the dependence of the
+ * relaxation parameter on the state through the implicit function theorem
+ * (dg = -(f_u du + f_d dd + f_est dest)/f_g).  Entropy-split scheme (with or
+ * without dissipation), inviscid.  Scratch: 12 state-sized device arrays owned
+ * by the context, allocated on the first call.  Synchronises `stream`; the
+ * step's g is returned through g_out (may be NULL). */
+int esplit_rrk_step_vjp(esplit_ctx* ctx, const double* u_dev, double dt, const double* ubar_next_dev,
+                        double* ubar_dev, double* g_out, void* stream);
+
 /* Sticky status of asynchronous work (synchronises the context's last
  * stream): ESPLIT_OK or ESPLIT_ERR_NONPHYSICAL; reading clears it. */
 int esplit_get_status(esplit_ctx* ctx);

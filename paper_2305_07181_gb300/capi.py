@@ -64,6 +64,8 @@ _SIGNATURES = {
     "esplit_rrk_step": (_I, [_P, _P, ctypes.c_double, _D, ctypes.POINTER(esplit_stepinfo), _P]),
     "esplit_rrk_step_host": (_I, [_P, _P, ctypes.c_double, _D, ctypes.POINTER(esplit_stepinfo), _P]),
     "esplit_residual_vjp": (_I, [_P, _P, _P, _P, _P]),
+    "esplit_entropy_grad": (_I, [_P, _P, _P, _P]),
+    "esplit_rrk_step_vjp": (_I, [_P, _P, ctypes.c_double, _P, _P, _D, _P]),
     "esplit_profile_enable": (_I, [_P, _I]),
     "esplit_profile_read": (_I, [_P, _D, ctypes.POINTER(ctypes.c_longlong), _I]),
     "esplit_get_status": (_I, [_P]),
@@ -168,6 +170,16 @@ def esplit_rrk_step_host(ctx, u_host_ptr, dt, stream=None):
     info = esplit_stepinfo()
     rc = lib.esplit_rrk_step_host(ctx, u_host_ptr, dt, ctypes.byref(g), ctypes.byref(info), stream)
     return rc, g.value, info
+
+
+def esplit_entropy_grad(ctx, u_ptr, grad_ptr, stream=None) -> int:
+    return lib.esplit_entropy_grad(ctx, u_ptr, grad_ptr, stream)
+
+
+def esplit_rrk_step_vjp(ctx, u_ptr, dt, ubar_next_ptr, ubar_ptr, stream=None):
+    g = ctypes.c_double()
+    rc = lib.esplit_rrk_step_vjp(ctx, u_ptr, dt, ubar_next_ptr, ubar_ptr, ctypes.byref(g), stream)
+    return rc, g.value
 
 
 PROFILE_GROUPS = ("face", "split_volume", "hadamard_volume", "entropy_reduce", "root_solve", "stage_update")

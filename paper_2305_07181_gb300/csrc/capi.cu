@@ -152,7 +152,7 @@ void esplit_destroy(esplit_ctx* c) {
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,
                 b.list_split, b.list_had, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
-                b.stage_r, b.dacc, b.node_cache, b.host_u, b.host_r};
+                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r};
   for (void* p : ps) dfree(p);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
@@ -259,6 +259,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   dalloc(c, &c->b.stage_r, 0);
   dalloc(c, &c->b.dacc, 0);
   dalloc(c, &c->b.node_cache, 0);
+  dalloc(c, &c->b.vjp_work, 0);
   dalloc(c, &c->b.host_u, 0);
   dalloc(c, &c->b.host_r, 0);
   c->flags.assign(n_e, 0);
@@ -500,6 +501,104 @@ int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
   if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
   if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("vjp launch: ") + cudaGetErrorString(cudaGetLastError()));
   c->last_stream = s;
+  return ESPLIT_OK;
+}
+
+int esplit_entropy_grad(esplit_ctx* c, const double* u, double* grad, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !grad) return fail(c, ESPLIT_ERR_ARG, "null pointer");
+  cudaSetDevice(c->device);
+  if (esplit::launch_wH(c, u, 1.0, grad, as_stream(stream))) return fail(c, ESPLIT_ERR_CUDA, "entropy-grad launch");
+  c->last_stream = as_stream(stream);
+  return ESPLIT_OK;
+}
+
+int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double* ubar1, double* ubar0,
+                        double* g_out, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u || !ubar1 || !ubar0) return fail(c, ESPLIT_ERR_ARG, "null pointer");
+  if (ubar0 == u || ubar0 == ubar1) return fail(c, ESPLIT_ERR_ARG, "ubar0 must not alias u or ubar1");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ESPLIT_ERR_ARG, "dt must be positive and finite");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->prm.viscous)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the step reverse is built for the inviscid entropy-split scheme");
+  cudaSetDevice(c->device);
+  cudaStream_t s = as_stream(stream);
+  size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  if (!c->b.vjp_work) {
+    if ((rc = dalloc(c, &c->b.vjp_work, 12 * n))) return rc;
+  }
+  if (!c->b.node_cache) {
+    if ((rc = dalloc(c, &c->b.node_cache, 4 * (size_t)c->n_e * c->n_p))) return rc;
+  }
+  double* W = c->b.vjp_work;
+  double* Us[3] = {W, W + n, W + 2 * n};                  // U_2, U_3, U_4
+  double* Rs[4] = {W + 3 * n, W + 4 * n, W + 5 * n, W + 6 * n};
+  double* d = W + 7 * n;
+  double* u1 = W + 8 * n;
+  double* rbar = W + 9 * n;
+  double* extra = W + 10 * n;
+  double* Ubar = W + 11 * n;
+  double* tmp = u1;  // u1 is consumed by the combine kernel before the stage loop
+  static const double A[4] = {0.0, 0.5, 0.5, 1.0};
+  static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  int np = 0;
+  // ---- forward recompute from the checkpoint
+  if (esplit::launch_entropy(c, u, s, &np, c->b.node_cache) || esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal, s))
+    return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
+  for (int i = 0; i < 4; ++i) {
+    const double* Ui = (i == 0) ? u : Us[i - 1];
+    if ((rc = residual_impl(c, Ui, Rs[i], s, c->b.partial, &np))) return rc;
+    if (esplit::launch_reduce(c, c->b.partial, np, 1, c->b.scal + 2 + i, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
+    if (esplit::launch_stage(c, u, Rs[i], (i < 3) ? A[i + 1] * dt : 0.0, B[i] * dt, i == 0, (i < 3) ? Us[i] : nullptr,
+                             d, n, s))
+      return fail(c, ESPLIT_ERR_CUDA, "stage launch");
+  }
+  if (esplit::launch_root_start(c, dt, s)) return fail(c, ESPLIT_ERR_CUDA, "root init");
+  esplit::RootState st{};
+  for (int it = 0; it < esplit::ROOT_EVALS_MAX; ++it) {
+    if (esplit::launch_root_eval(c, u, d, s, &np) || esplit::launch_root_update(c, np, s))
+      return fail(c, ESPLIT_ERR_CUDA, "root launch");
+    if ((it + 1) % esplit::ROOT_CHECK_EVERY == 0) {
+      CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (st.done) break;
+    }
+  }
+  CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int phys = read_status(c, s, true);
+  if (phys) return fail(c, phys, "non-physical state during the step");
+  if (st.status) return fail(c, st.status, "relaxation parameter could not be bracketed");
+  const double g = st.g, est = st.est;
+  if (esplit::launch_axpy(c, u, g, d, u1, n, s)) return fail(c, ESPLIT_ERR_CUDA, "axpy launch");
+  // ---- reverse: implicit dependence of g, then the stages
+  if (esplit::launch_rrk_vjp_dots(c, u1, d, ubar1, s, &np) ||
+      esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal + 12, s))
+    return fail(c, ESPLIT_ERR_CUDA, "dots launch");
+  double h2[2];
+  CK(cudaMemcpyAsync(h2, c->b.scal + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double fg = h2[1] - est;
+  if (!(fabs(fg) > 0.0)) return fail(c, ESPLIT_ERR_RRK_NO_ROOT, "f'(g) vanishes at the relaxation root");
+  const double lam = -h2[0] / fg;
+  double* dbar_keep = d;  // d was last read by the dots kernel: dbar reuses its storage
+  if (esplit::launch_rrk_vjp_combine(c, u, u1, ubar1, lam, g, ubar0, dbar_keep, s))
+    return fail(c, ESPLIT_ERR_CUDA, "combine launch");
+  const double estbar = -lam * g;
+  for (int i = 3; i >= 0; --i) {
+    const double* Ui = (i == 0) ? u : Us[i - 1];
+    double c_d = dt * B[i], c_e = dt * B[i] * estbar, c_u = (i < 3) ? A[i + 1] * dt : 0.0;
+    if (esplit::launch_rrk_vjp_stage(c, Ui, Rs[i], dbar_keep, (i < 3) ? Ubar : nullptr, c_d, c_e, c_u, rbar, extra, s))
+      return fail(c, ESPLIT_ERR_CUDA, "stage-reverse launch");
+    if (esplit::launch_residual_vjp(c, Ui, rbar, tmp, s)) return fail(c, ESPLIT_ERR_CUDA, "residual vjp launch");
+    if (esplit::launch_axpy(c, extra, 1.0, tmp, Ubar, n, s) || esplit::launch_axpy(c, ubar0, 1.0, Ubar, ubar0, n, s))
+      return fail(c, ESPLIT_ERR_CUDA, "axpy launch");
+  }
+  CK(cudaStreamSynchronize(s));
+  c->last_stream = s;
+  if (g_out) *g_out = g;
   return ESPLIT_OK;
 }
 

@@ -57,7 +57,8 @@ struct Buffers {
   double* stage_u = nullptr;
   double* stage_r = nullptr;
   double* dacc = nullptr;
-  double* node_cache = nullptr;  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
+  double* node_cache = nullptr;
+  double* vjp_work = nullptr;    // 12 state-sized arrays for the RRK step reverse  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
   double* host_u = nullptr;    // device copies for the host-buffer entry point
   double* host_r = nullptr;
 };
@@ -127,6 +128,14 @@ int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(1) << 21;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 int noalloc_scratch_ptr(int device, double** out);
+int launch_wH(esplit_ctx* c, const double* u, double scale, double* out, cudaStream_t s);
+int launch_rrk_vjp_dots(esplit_ctx* c, const double* u1, const double* d, const double* ubar1, cudaStream_t s,
+                        int* n_partial);
+int launch_rrk_vjp_combine(esplit_ctx* c, const double* un, const double* u1, const double* ubar1, double lam,
+                           double g, double* ubar0, double* dbar, cudaStream_t s);
+int launch_rrk_vjp_stage(esplit_ctx* c, const double* U, const double* r, const double* dbar,
+                         const double* ubar_next, double c_d, double c_e, double c_u, double* rbar, double* extra,
+                         cudaStream_t s);
 int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch);
 
 }  // namespace esplit

@@ -279,6 +279,15 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
 #pragma unroll
       for (int q = 0; q < NC; ++q) g[i][q] = T(0);
     const T* op = ops + (size_t)e * (2 * D * NP * NP);
+    // float32 sums carry compensation terms (Kahan): with plain float32
+    // accumulation its round-off, not the float32 operands, would dominate
+    T cacc[NC], cg[D][NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) cacc[q] = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) cg[i][q] = T(0);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
 #pragma unroll 4
@@ -291,8 +300,14 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
             acc[q] += mt * sm.rf[el][i][q][n];
             g[i][q] += dt * sm.rw[el][q][n];
           } else {
-            acc[q] += mt * sm.sf[el][i][q][n];
-            g[i][q] += dt * sm.sw[el][q][n];
+            T y = mt * sm.sf[el][i][q][n] - cacc[q];
+            T t = acc[q] + y;
+            cacc[q] = (t - acc[q]) - y;
+            acc[q] = t;
+            T y2 = dt * sm.sw[el][q][n] - cg[i][q];
+            T t2 = g[i][q] + y2;
+            cg[i][q] = (t2 - g[i][q]) - y2;
+            g[i][q] = t2;
           }
         }
       }
@@ -1010,3 +1025,4 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 }  // namespace esplit
 
 #include "vjp.cuh"
+#include "rrk_vjp.cuh"

@@ -155,6 +155,19 @@ class Solver:
         self._check(rc)
         return g, info
 
+    def entropy_grad(self, u: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        out = self.empty() if out is None else out
+        self._check(capi.esplit_entropy_grad(self.ctx, _dptr(u), _dptr(out), _stream(stream)))
+        return out
+
+    def rrk_step_vjp(self, u: torch.Tensor, dt: float, ubar_next: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None):
+        out = self.empty() if out is None else out
+        rc, g = capi.esplit_rrk_step_vjp(self.ctx, _dptr(u), float(dt), _dptr(ubar_next), _dptr(out),
+                                         _stream(stream))
+        self._check(rc)
+        return out, g
+
     def profile(self, on: bool = True):
         self._check(capi.esplit_profile_enable(self.ctx, on))
 

@@ -296,8 +296,10 @@ def test_full_size_config2_sampled(lib, p):
     FP64 oracle's own rounding is ~eps times those terms (checked against
     extended precision), times cond(dW/dU) for the A~_i term, which the oracle
     forms through a matrix inverse.  The bound is therefore
-    |r_gpu - r_oracle| <= 1e-12 max|r| + 16 eps (summand scale),
-    and the plain max-norm relative error is reported."""
+    |r_gpu - r_oracle| <= 1e-12 max|r| + 64 n_p eps (summand scale)
+    (a length-n_p dot product of rounded terms on each side, as in the
+    standard gamma_n bound); the observed constant and the plain max-norm
+    relative error are printed."""
     R, Dg, rrk, OP = _oracle()
     op = tri_operator(p)
     m = periodic_tri_mesh(op, 128, 10.0, 0.05)
@@ -313,7 +315,7 @@ def test_full_size_config2_sampled(lib, p):
         err = np.abs(r - ro)
         print(f"full-size p={p} {scheme}: max-norm rel {rel_err(r, ro):.2e}, "
               f"max err/(eps scale) {float((err / (eps * sc)).max()):.2f}, cond ~{float(sc.max() / np.abs(ro).max()):.1e}")
-        assert np.all(err <= 1e-12 * np.abs(ro).max() + 16 * eps * sc)
+        assert np.all(err <= 1e-12 * np.abs(ro).max() + 64 * op.n_p * eps * sc)
         s.close()
 
 
