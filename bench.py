@@ -36,6 +36,9 @@ import torch  # noqa: E402
 METRIC = "DOF-residual evals/s vs Hadamard form, FP64 & FP32, % roofline; 1 GB300"
 UNIT = "DOF-residual evals/s"
 FP64_PEAK_NOMINAL = 1.25e12            # recipe table: GB300 FP64 1.25 TFLOP/s
+# DRAM bytes (read + write) per launch from one ncu capture of the unchanged
+# kernel (profiles/split_volume_config2_p3_fp64.md); keyed by (kernel, p, precision, N)
+NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 393.396e6}
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 
 
@@ -315,7 +318,8 @@ def main():
         achieved = fl / (dom_ms * 1e-3) / 1e12
         peak = FP64_PEAK_NOMINAL / 1e12 if args.precision == "fp64" else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": (achieved / peak) if peak else None, "traffic": None, "kernel": dom,
+                    "frac": (achieved / peak) if peak else None,
+                    "traffic": NCU_TRAFFIC.get((dom, args.p, args.precision, args.N)), "kernel": dom,
                     "avg_launch_ms": dom_ms, "launches": groups[dom][1], "units_per_launch": per_launch_units,
                     "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (152 SMs x 4 FLOP/clk x "
                                    "2.07 GHz); FP64 pipe, not the bf16 tensor peak"}

@@ -137,3 +137,92 @@ def periodic_tri_mesh(op: RefOperator, N: int, L: float = 10.0, amp: float = 0.0
     return Mesh(d=2, n_e=n_e, n_p=op.n_p, n_fac=op.n_fac, n_f=op.n_f, L=(L, L),
                 x=x, J=det, Lam=Lam, nu=nu, pair=pair, hmin=hmin,
                 meta=dict(kind="periodic_tri", N=N, L=L, amp=amp, p=op.p))
+
+
+def _quad_tet_shape(xi: np.ndarray):
+    """Quadratic (10-node) Lagrange shape functions on the reference tetrahedron
+    and their derivatives. Geometry node order: v0..v3, then the edge midpoints
+    m01, m02, m03, m12, m13, m23."""
+    l = [1.0 - xi[:, 0] - xi[:, 1] - xi[:, 2], xi[:, 0], xi[:, 1], xi[:, 2]]
+    dl = np.array([[-1.0, -1.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])  # d lambda_a / d xi_j
+    edges = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    N = [l[a] * (2 * l[a] - 1) for a in range(4)] + [4 * l[a] * l[b] for a, b in edges]
+    dN = np.zeros((3, len(xi), 10))
+    for j in range(3):
+        for a in range(4):
+            dN[j, :, a] = (4 * l[a] - 1) * dl[a, j]
+        for e, (a, b) in enumerate(edges):
+            dN[j, :, 4 + e] = 4 * (dl[a, j] * l[b] + l[a] * dl[b, j])
+    return np.stack(N, axis=1), dN
+
+
+def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float = 0.02) -> Mesh:
+    """Periodic [0, L]^3 mesh of N^3 cubes, each cut into the six Kuhn
+    tetrahedra around its main diagonal (6 N^3 elements), quadratic geometry
+    warped by x_i = xhat_i + A prod_j sin(2 pi xhat_j / L) (Sec. 7.3 builds its
+    3D grids the same way: hexahedra cut into six tetrahedra, then perturbed).
+    Facet nodes are paired by their (unwarped) positions modulo L."""
+    import itertools
+    assert op.d == 3
+    h = L / N
+    perms = list(itertools.permutations(range(3)))
+    n_e = 6 * N ** 3
+    ii, jj, kk = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    base = 2 * np.stack([ii.ravel(order="F"), jj.ravel(order="F"), kk.ravel(order="F")], axis=1)  # i fastest
+    V = np.zeros((N ** 3, 6, 4, 3), dtype=np.int64)  # vertex half-lattice indices
+    for t, sgm in enumerate(perms):
+        cur = base.copy()
+        V[:, t, 0] = cur
+        for a, ax in enumerate(sgm):
+            cur = cur.copy()
+            cur[:, ax] += 2
+            V[:, t, a + 1] = cur
+    V = V.reshape(n_e, 4, 3)
+    # positive orientation: swap the last two vertices where needed
+    d1, d2, d3 = V[:, 1] - V[:, 0], V[:, 2] - V[:, 0], V[:, 3] - V[:, 0]
+    vol = np.einsum("ei,ei->e", d1, np.cross(d2, d3))
+    neg = vol < 0
+    V[neg, 2], V[neg, 3] = V[neg, 3].copy(), V[neg, 2].copy()
+    edges = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    G_idx = np.concatenate([V, np.stack([(V[:, a] + V[:, b]) // 2 for a, b in edges], axis=1)], axis=1)  # (e,10,3)
+    wrap = G_idx % (2 * N)
+    s = np.prod(np.sin(2.0 * np.pi * wrap / (2 * N)), axis=2)  # (e, 10)
+    G = G_idx * (h / 2) + amp * s[..., None]                   # (e, 10, 3)
+    G = np.transpose(G, (0, 2, 1))                             # (e, 3, 10)
+    Nsh, dN = _quad_tet_shape(op.xi)
+    x = np.einsum("pa,eia->eip", Nsh, G)
+    Jm = np.einsum("jpa,eia->eijp", dN, G)                     # dx_i/dxi_j (e, 3, 3, n_p)
+    Jt = np.transpose(Jm, (0, 3, 1, 2))                        # (e, n_p, 3, 3)
+    det = np.linalg.det(Jt)
+    adj = np.linalg.inv(Jt) * det[..., None, None]             # adj[j][i] = J dxi_j/dx_i
+    # Lam[e, i, j, p] = adj[e, p, j, i]
+    Lam = np.ascontiguousarray(np.transpose(np.transpose(adj, (0, 1, 3, 2)), (0, 2, 3, 1)))
+    fn = op.facet_nodes
+    nu = np.zeros((n_e, op.n_fac, op.n_f, 3))
+    for g in range(op.n_fac):
+        for kk in range(op.n_f):
+            mnode = fn[g, kk]
+            nu[:, g, kk, :] = op.facet_w[g, kk] * np.einsum("eij,j->ei", Lam[:, :, :, mnode], op.ref_normals[g])
+    # pairing by straight positions modulo L
+    Gs = np.transpose(G_idx * (h / 2), (0, 2, 1)).astype(float)  # unwarped geometry nodes
+    xs = np.einsum("pa,eia->eip", Nsh, Gs)                         # straight node positions
+    slots = fn.reshape(-1)
+    key = np.round(xs[:, :, slots] / L * 2 ** 30).astype(np.int64) % (2 ** 30)  # (e, 3, n_slot)
+    n_slot = op.n_fac * op.n_f
+    kf = key.transpose(0, 2, 1).reshape(-1, 3)               # (n_e n_slot, 3)
+    order = np.lexsort((kf[:, 2], kf[:, 1], kf[:, 0]))
+    ks = kf[order]
+    a, b = order[0::2], order[1::2]
+    assert np.all(ks[0::2] == ks[1::2]), "facet nodes must coincide in pairs"
+    if len(ks) > 2:
+        assert not np.any(np.all(ks[2::2] == ks[1:-1:2], axis=1)), "a facet node is shared by more than two slots"
+    pair = np.full((n_e * n_slot, 2), -1, dtype=np.int32)
+    pair[a, 0], pair[a, 1] = b // n_slot, b % n_slot
+    pair[b, 0], pair[b, 1] = a // n_slot, a % n_slot
+    pair = pair.reshape(n_e, op.n_fac, op.n_f, 2)
+    diff = x[:, :, :, None] - x[:, :, None, :]
+    dist = np.sqrt((diff ** 2).sum(1))
+    dist[:, np.arange(op.n_p), np.arange(op.n_p)] = np.inf
+    hmin = dist.reshape(n_e, -1).min(1)
+    return Mesh(d=3, n_e=n_e, n_p=op.n_p, n_fac=op.n_fac, n_f=op.n_f, L=(L, L, L), x=x, J=det, Lam=Lam, nu=nu,
+                pair=pair, hmin=hmin, meta=dict(kind="periodic_tet", N=N, L=L, amp=amp, p=op.p))

@@ -254,6 +254,84 @@ class RefOperator:
         return self.Q - 0.5 * np.stack([np.diag(e) for e in self.E])
 
 
+# ---------------------------------------------------------------------------
+# Tetrahedron, p = 2.  Facet nodes: the S3-symmetric 6-point degree-4 rule on
+# every face (two S21 orbits, solved from the triangle moment equations;
+# degree 4 = 2p), so paired faces see the same physical points whatever their
+# relative orientation.  Volume: the 24 facet nodes plus the centroid, weights
+# from the S4-invariant moment equations of degree 3 (= 2p - 1); 25 nodes.
+# ---------------------------------------------------------------------------
+_TRI_FACE_DEG4 = dict(a1=0.44594849091596483, w1=0.11169079483900565,
+                      a2=0.09157621350977083, w2=0.054975871827661026)
+_TET_RULES = {2: dict(degree=3, x=[0.006710441872127204, 0.002335214368444981, 0.058118791779800436])}
+_TET_VERTS = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+_TET_NORMALS = np.array([[1.0, 1.0, 1.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0], [0.0, 0.0, -1.0]])
+_TET_NORMALS[0] /= np.sqrt(3.0)
+_TET_FACE_SCALE = np.array([np.sqrt(3.0), 1.0, 1.0, 1.0])  # face area / (1/2)
+
+
+def tri_face_rule_deg4():
+    """Barycentric points (6, 3) and weights (6,) (sum 1/2) of the degree-4 rule."""
+    r = _TRI_FACE_DEG4
+    pts, w = [], []
+    for a, ww in [(r["a1"], r["w1"]), (r["a2"], r["w2"])]:
+        for lam in [(a, a, 1 - 2 * a), (a, 1 - 2 * a, a), (1 - 2 * a, a, a)]:
+            pts.append(lam)
+            w.append(ww)
+    return np.array(pts), np.array(w)
+
+
+def tet_monomial_integral(a: int, b: int, c: int) -> float:
+    """Exact integral of x^a y^b z^c over the reference tetrahedron."""
+    return factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 3)
+
+
+def _tet_nodes(x):
+    fp, fw = tri_face_rule_deg4()
+    pts, wts, fnodes = [], [], []
+    for face in range(4):  # face `face` is opposite vertex `face`
+        others = [v for v in range(4) if v != face]
+        for k in range(6):
+            lam = np.zeros(4)
+            for j, v in enumerate(others):
+                lam[v] = fp[k][j]
+            pts.append(lam[1:])
+            wts.append(x[0] if k < 3 else x[1])
+    pts.append(np.full(3, 0.25))
+    wts.append(x[2])
+    return np.array(pts), np.array(wts)
+
+
+def tet_operator(p: int) -> RefOperator:
+    """Diagonal-E SBP operator on the reference tetrahedron (p = 2, 25 nodes)."""
+    key = ("tet", p)
+    if key in _CACHE:
+        return _CACHE[key]
+    if p not in _TET_RULES:
+        raise ValueError(f"no tetrahedron rule for p={p}")
+    rule = _TET_RULES[p]
+    xi, H = _tet_nodes(np.asarray(rule["x"], dtype=np.float64))
+    fp, fw = tri_face_rule_deg4()
+    n_fac, nf = 4, 6
+    n_p = len(H)
+    facet_nodes = np.arange(n_fac * nf, dtype=np.int32).reshape(n_fac, nf)
+    facet_w = np.stack([fw * _TET_FACE_SCALE[g] for g in range(n_fac)])
+    E = np.zeros((3, n_p))
+    for g in range(n_fac):
+        for k in range(nf):
+            E[:, facet_nodes[g, k]] += facet_w[g, k] * _TET_NORMALS[g]
+    V, dV = vandermonde(xi, p, np.array([0.25, 0.25, 0.25]))
+    Q = np.zeros((3, n_p, n_p))
+    for j in range(3):
+        S = min_norm_skew(H, E[j], V, dV[j])
+        Q[j] = S + 0.5 * np.diag(E[j])
+    op = RefOperator(d=3, p=p, n_p=n_p, n_fac=n_fac, n_f=nf, xi=xi, H=H, Q=Q, E=E,
+                     facet_nodes=facet_nodes, facet_w=facet_w, ref_normals=_TET_NORMALS.copy(),
+                     volume_degree=rule["degree"])
+    _CACHE[key] = op
+    return op
+
+
 _CACHE: dict = {}
 
 

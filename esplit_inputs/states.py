@@ -94,3 +94,17 @@ def cfl_timestep(mesh, u, cfl, gam=GAMMA):
     p = (gam - 1.0) * (u[:, -1] - 0.5 * rho * np.sum(V * V, axis=1))
     lam = np.sqrt(np.sum(V * V, axis=1)) + np.sqrt(gam * p / rho)
     return float(np.min(cfl * mesh.hmin / lam.max(axis=1)))
+
+
+def taylor_green(mesh, Mach=0.1, gam=GAMMA, R=1.0):
+    """Taylor-Green vortex initial state of Sec. 7.5 with u_0 = rho_0 = R = L = 1
+    on the periodic [0, 2 pi]^3 box: p_0 = rho_0 u_0^2 / (gam M^2), T_0 = p_0,
+    V = (sin x cos y cos z, -cos x sin y cos z, 0),
+    p = p_0 + (cos 2x + cos 2y)(cos 2z + 2)/16, rho = p / (R T_0)."""
+    x, y, z = mesh.x[:, 0], mesh.x[:, 1], mesh.x[:, 2]
+    p0 = 1.0 / (gam * Mach ** 2)
+    T0 = p0 / R
+    V = np.stack([np.sin(x) * np.cos(y) * np.cos(z), -np.cos(x) * np.sin(y) * np.cos(z), 0.0 * x])
+    p = p0 + (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0) / 16.0
+    rho = p / (R * T0)
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))

@@ -88,7 +88,8 @@ void esplit_destroy(esplit_ctx* ctx);
  *                                    residual; kept for diagnostics)
  *   ref_normals  [n_fac][d]          outward unit normals of reference facets
  * Host pointers, copied.  Supported (d, n_p): (2, 7), (2, 12), (2, 18),
- * (2, 27); others -> ESPLIT_ERR_UNSUPPORTED. */
+ * (2, 27) (triangles, p = 1..4) and (3, 25) (tetrahedra, p = 2); others ->
+ * ESPLIT_ERR_UNSUPPORTED. */
 int esplit_upload_operator(esplit_ctx* ctx, int n_p, int n_fac, int n_f, const double* H_ref,
                            const double* Q_ref, const int* facet_nodes, const double* facet_w,
                            const double* ref_normals);
@@ -206,9 +207,10 @@ long long esplit_launch_count(esplit_ctx* ctx);
  *   0 facet kernel (EC SAT + dissipation)   1 entropy-split volume kernel
  *   2 Hadamard volume kernel                3 entropy functionals + reductions
  *   4 relaxation root solve                 5 RK stage / update kernels
+ *   6 viscous terms (three kernels)
  * esplit_profile_read synchronises, fills ms[g] (total milliseconds) and
  * count[g] (launches) for g < n_groups, and resets the accumulators. */
-#define ESPLIT_PROFILE_GROUPS 6
+#define ESPLIT_PROFILE_GROUPS 7
 int esplit_profile_enable(esplit_ctx* ctx, int on);
 int esplit_profile_read(esplit_ctx* ctx, double* ms, long long* count, int n_groups);
 

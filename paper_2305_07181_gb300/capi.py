@@ -182,7 +182,8 @@ def esplit_rrk_step_vjp(ctx, u_ptr, dt, ubar_next_ptr, ubar_ptr, stream=None):
     return rc, g.value
 
 
-PROFILE_GROUPS = ("face", "split_volume", "hadamard_volume", "entropy_reduce", "root_solve", "stage_update")
+PROFILE_GROUPS = ("face", "split_volume", "hadamard_volume", "entropy_reduce", "root_solve", "stage_update",
+                  "viscous")
 
 
 def esplit_profile_enable(ctx, on: bool) -> int:

@@ -46,6 +46,7 @@ void dfree(void* p) {
 
 bool supported(int dim, int n_p) {
   if (dim == 2) return n_p == 7 || n_p == 12 || n_p == 18 || n_p == 27;
+  if (dim == 3) return n_p == 25;
   return false;
 }
 
@@ -152,7 +153,7 @@ void esplit_destroy(esplit_ctx* c) {
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,
                 b.list_split, b.list_had, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
-                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r};
+                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va};
   for (void* p : ps) dfree(p);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
@@ -204,6 +205,8 @@ int esplit_upload_operator(esplit_ctx* c, int n_p, int n_fac, int n_f, const dou
   c->have_mesh = false;  // a new operator invalidates the mesh-derived data
   return ESPLIT_OK;
 }
+
+static int ensure_viscous(esplit_ctx* c);
 
 int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* Lambda, const double* nu,
                        const int* pair, const double* hmin) {
@@ -263,9 +266,13 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   dalloc(c, &c->b.host_u, 0);
   dalloc(c, &c->b.host_r, 0);
   c->flags.assign(n_e, 0);
+  dalloc(c, &c->b.fv, 0);
+  dalloc(c, &c->b.vsat, 0);
+  dalloc(c, &c->b.va, 0);
   c->n_split = n_e;
   c->n_had = 0;
   c->have_mesh = true;
+  if (c->prm.viscous && (rc = ensure_viscous(c))) return rc;
   return rebuild_ops(c, 0);
 }
 
@@ -277,10 +284,13 @@ int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
   if (!(p->R > 0.0) || p->mu < 0.0 || !(p->Pr > 0.0)) return fail(c, ESPLIT_ERR_ARG, "R, Pr must be > 0, mu >= 0");
   if (p->scheme < 0 || p->scheme > 2) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
   if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK) return fail(c, ESPLIT_ERR_ARG, "unknown precision");
-  if (p->viscous) return fail(c, ESPLIT_ERR_UNSUPPORTED, "viscous terms are not built in this version");
   cudaSetDevice(c->device);
   bool beta_changed = p->beta != c->prm.beta;
   c->prm = *p;
+  if (p->viscous) {
+    int rcv = ensure_viscous(c);
+    if (rcv) return rcv;
+  }
   if (beta_changed && c->have_mesh) return rebuild_ops(c, 0);
   return ESPLIT_OK;
 }
@@ -315,10 +325,30 @@ int esplit_set_hybrid_flags(esplit_ctx* c, const unsigned char* flags, int n_e) 
 static int residual_impl(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* npart) {
   if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
     return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
-  int rc = esplit::launch_residual(c, u, r, s, prod, npart);
+  const bool visc = c->prm.viscous != 0;
+  // with viscous terms the entropy production is taken from the complete
+  // residual after the viscous passes
+  int rc = esplit::launch_residual(c, u, r, s, visc ? nullptr : prod, visc ? nullptr : npart);
   if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
   if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString(cudaGetLastError()));
+  if (visc) {
+    if (!c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
+    rc = esplit::launch_viscous(c, u, r, s);
+    if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
+    if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("viscous launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (prod && esplit::launch_entropy_rate(c, u, r, s, npart, prod, 1))
+      return fail(c, ESPLIT_ERR_CUDA, "entropy-production launch");
+  }
   c->last_stream = s;
+  return ESPLIT_OK;
+}
+
+static int ensure_viscous(esplit_ctx* c) {
+  if (!c->have_mesh || c->b.fv) return ESPLIT_OK;
+  int rc;
+  if ((rc = dalloc(c, &c->b.fv, (size_t)c->n_e * c->dim * c->n_c * c->n_p))) return rc;
+  if ((rc = dalloc(c, &c->b.vsat, (size_t)c->n_e * c->n_c * c->n_slot))) return rc;
+  if ((rc = dalloc(c, &c->b.va, (size_t)c->n_e * c->dim * c->n_c * c->n_slot))) return rc;
   return ESPLIT_OK;
 }
 

@@ -58,6 +58,11 @@ struct Buffers {
   double* stage_r = nullptr;
   double* dacc = nullptr;
   double* node_cache = nullptr;
+  // viscous scratch: nodal F^V [n_e][d][n_c][n_p], facet jump terms
+  // [n_e][n_c][n_slot] and lift vectors a_j [n_e][d][n_c][n_slot]
+  double* fv = nullptr;
+  double* vsat = nullptr;
+  double* va = nullptr;
   double* vjp_work = nullptr;    // 12 state-sized arrays for the RRK step reverse  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
   double* host_u = nullptr;    // device copies for the host-buffer entry point
   double* host_r = nullptr;
@@ -96,7 +101,7 @@ namespace esplit {
 
 // Brackets one kernel launch with CUDA events on its stream when the
 // context's profiling is enabled (groups listed in include/esplit.h).
-enum ProfGroup { PG_FACE = 0, PG_SPLIT = 1, PG_HAD = 2, PG_ENTROPY = 3, PG_ROOT = 4, PG_STAGE = 5 };
+enum ProfGroup { PG_FACE = 0, PG_SPLIT = 1, PG_HAD = 2, PG_ENTROPY = 3, PG_ROOT = 4, PG_STAGE = 5, PG_VISC = 6 };
 struct ProfScope {
   esplit_ctx* c;
   int g;
@@ -111,7 +116,9 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s);
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod_partial,
                     int* n_partial);
 int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache = nullptr);
-int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial);
+int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial,
+                        double* part = nullptr, int width = 2);
+int launch_viscous(esplit_ctx* c, const double* u, double* r, cudaStream_t s);
 int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s);
 int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, double* out, size_t n, cudaStream_t s);
 int launch_stage(esplit_ctx* c, const double* un, const double* r, double a_dt, double b_dt, int first,

@@ -565,6 +565,10 @@ static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s,
       case 18: return residual_np<T, 2, 18>(c, u, r, s, prod, n_partial, sat);
       case 27: return residual_np<T, 2, 27>(c, u, r, s, prod, n_partial, sat);
     }
+  } else if (c->dim == 3) {
+    switch (c->n_p) {
+      case 25: return residual_np<T, 3, 25>(c, u, r, s, prod, n_partial, sat);
+    }
   }
   return -2;
 }
@@ -641,7 +645,7 @@ __global__ void __launch_bounds__(256) entropy_kernel(const double* __restrict__
   block_sum<2>(v, part + 2 * blockIdx.x);
 }
 
-template <int D>
+template <int D, int W>
 __global__ void __launch_bounds__(256) entropy_rate_kernel(const double* __restrict__ u,
                                                            const double* __restrict__ r,
                                                            const double* __restrict__ J, size_t n_nodes,
@@ -670,7 +674,12 @@ __global__ void __launch_bounds__(256) entropy_rate_kernel(const double* __restr
     v[0] = H * wr;
     v[1] = H * sqrt(w2 * r2);
   }
-  block_sum<2>(v, part + 2 * blockIdx.x);
+  if constexpr (W == 1) {
+    double v1[1] = {v[0]};
+    block_sum<1>(v1, part + blockIdx.x);
+  } else {
+    block_sum<2>(v, part + 2 * blockIdx.x);
+  }
 }
 
 int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache) {
@@ -687,15 +696,24 @@ int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partia
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial) {
+int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial,
+                        double* part, int width) {
   size_t n = (size_t)c->n_e * c->n_p;
   int nb = (int)((n + 255) / 256);
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ENTROPY, s);
-  if (c->dim == 2)
-    entropy_rate_kernel<2><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, c->b.partial);
-  else
-    entropy_rate_kernel<3><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, c->b.partial);
+  if (!part) part = c->b.partial;
+  if (c->dim == 2) {
+    if (width == 1)
+      entropy_rate_kernel<2, 1><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
+    else
+      entropy_rate_kernel<2, 2><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
+  } else {
+    if (width == 1)
+      entropy_rate_kernel<3, 1><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
+    else
+      entropy_rate_kernel<3, 2><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
+  }
   c->launches++;
   *n_partial = nb;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -1025,4 +1043,5 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 }  // namespace esplit
 
 #include "vjp.cuh"
+#include "visc.cuh"
 #include "rrk_vjp.cuh"

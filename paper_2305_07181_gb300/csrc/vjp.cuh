@@ -234,6 +234,10 @@ int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
       case 18: return vjp_np<2, 18>(c, u, cot, grad, s);
       case 27: return vjp_np<2, 27>(c, u, cot, grad, s);
     }
+  } else if (c->dim == 3) {
+    switch (c->n_p) {
+      case 25: return vjp_np<3, 25>(c, u, cot, grad, s);
+    }
   }
   return -2;
 }
