@@ -142,7 +142,10 @@ int esplit_residual(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void
  * capture.  Every call on a device shares the one array and overwrites all
  * of the part it uses (nothing has to start at zero), so calls whose kernels
  * overlap on the GPU -- on different streams, or from different threads or
- * contexts -- race on it: serialise them.  Arguments, layout and errors as
+ * contexts -- race on it: serialise them.  With viscous terms on, their
+ * scratch is the context's own, allocated by esplit_set_params or
+ * esplit_upload_mesh when the terms were switched on, not by this call.
+ * Arguments, layout and errors as
  * for esplit_residual; the result equals esplit_residual's.  The paper has no
  * counterpart of this entry point; it is a deployment convenience. */
 int esplit_residual_noalloc(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void* stream);

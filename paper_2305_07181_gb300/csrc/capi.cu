@@ -368,6 +368,7 @@ int esplit_residual_noalloc(esplit_ctx* c, const double* u, double* r, void* str
   if (u == r) return fail(c, ESPLIT_ERR_ARG, "u and dudt must not alias");
   if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
     return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
+  if (c->prm.viscous && !c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
   size_t need = (size_t)c->n_e * c->n_c * c->n_slot;
   if (need > esplit::NOALLOC_SCRATCH_DOUBLES)
     return fail(c, ESPLIT_ERR_ARG,

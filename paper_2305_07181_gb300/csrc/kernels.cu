@@ -608,6 +608,8 @@ int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStrea
   c->prof = false;
   int rc = c->prm.precision == ESPLIT_FP32_BULK ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
                                                  : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
+  // viscous terms use the context's viscous scratch, allocated when they were switched on
+  if (rc == 0 && c->prm.viscous) rc = launch_viscous(c, u, r, s);
   c->prof = prof;
   return rc;
 }

@@ -1,0 +1,199 @@
+"""GPU parity for the viscous Baumann-Oden terms (Sec. 5, Eqs. (83)-(85),
+(96)) on triangles and for the whole residual on curved periodic tetrahedra
+(p = 2, 25 nodes), through the C ABI against the FP64 CPU oracle.
+
+Tolerances as for the inviscid residual: FP64 max-norm relative error per
+component <= 1e-12; relaxation parameter <= 1e-10 absolute.
+"""
+import numpy as np
+import pytest
+import torch
+
+from esplit_inputs import tri_operator, tet_operator, periodic_tri_mesh, states
+from esplit_inputs.mesh import periodic_tet_mesh
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_BOUND = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_07181_gb300 as es
+    return es
+
+
+def _oracle():
+    from oracle import residual as R, diagnostics as Dg, rrk
+    from oracle.physics import Params as OP
+    return R, Dg, rrk, OP
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.abs(a - b).max(axis=(0, 2))
+    den = np.abs(b).max(axis=(0, 2))
+    den = np.where(den > 0, den, 1.0)
+    return float((num / den).max())
+
+
+def _tri(p, N=5):
+    op = tri_operator(p)
+    return op, periodic_tri_mesh(op, N, 10.0, 0.05)
+
+
+_TET = {}
+
+
+def _tet(N):
+    # N = 3: 162 curved tetrahedra, several blocks and a ragged tail
+    if N not in _TET:
+        op = tet_operator(2)
+        _TET[N] = (op, periodic_tet_mesh(op, N, 2 * np.pi, 0.02))
+    return _TET[N]
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("heat", [False, True])
+@pytest.mark.parametrize("scheme,diss", [("split", True), ("hadamard", False)])
+def test_viscous_fp64_parity_tri(lib, p, heat, scheme, diss):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tri(p)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=40 + p)
+    s = lib.Solver(op, m, lib.Params(mu=0.05, viscous=True, heat_flux=heat, scheme=scheme, dissipation=diss))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(mu=0.05, heat_flux=heat), scheme=scheme, dissipation=diss, viscous=True).numpy()
+    err = rel_err(r, ro)
+    print(f"viscous p={p} heat={heat} {scheme} rel err {err:.3e}")
+    assert err <= FP64_TOL
+    assert s.status() == 0
+    s.close()
+
+
+@pytest.mark.parametrize("scheme,diss", [("split", False), ("split", True), ("hadamard", False),
+                                         ("hadamard", True), ("hybrid", True)])
+def test_tet_inviscid_fp64_parity(lib, scheme, diss):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(3)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=50)
+    flags = np.random.default_rng(5).integers(0, 2, m.n_e).astype(np.uint8)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=diss))
+    if scheme == "hybrid":
+        s.set_hybrid_flags(flags)
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=diss, hybrid_flags=flags).numpy()
+    err = rel_err(r, ro)
+    print(f"tet {scheme} diss={diss} rel err {err:.3e}")
+    assert err <= FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("heat", [False, True])
+def test_tet_viscous_fp64_parity(lib, heat):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(3)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=51)
+    s = lib.Solver(op, m, lib.Params(mu=0.05, viscous=True, heat_flux=heat, dissipation=True))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(mu=0.05, heat_flux=heat), dissipation=True, viscous=True).numpy()
+    err = rel_err(r, ro)
+    print(f"tet viscous heat={heat} rel err {err:.3e}")
+    assert err <= FP64_TOL
+    s.close()
+
+
+def test_tet_taylor_green_parity(lib):
+    """The Sec. 7.5 state (M = 0.1) on the curved tetrahedra, split + BO +
+    matrix dissipation."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(3)
+    u = states.taylor_green(m)
+    mu = 1.0 / 1600.0
+    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(mu=mu), dissipation=True, viscous=True).numpy()
+    assert rel_err(r, ro) <= FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gpu_entropy_identities(lib, dim):
+    """On the GPU residual itself: inviscid EC terms conserve entropy (Thm. 2);
+    the BO viscous terms alone dissipate exactly the volume quadratic form
+    -sum H (D w)^T K~ (D w) (Thm. 3 with T1 = 0, T2 = T3 = B/2)."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tri(3) if dim == 2 else _tet(2)
+    u = states.random_positive_state(m.n_e, dim, op.n_p, seed=60 + dim)
+    prm = OP(mu=0.05)
+    s = lib.Solver(op, m, lib.Params())
+    ud = s.to_device(u)
+    r0 = s.residual(ud)
+    scale = float(Dg.entropy_rate_scale(u, r0.cpu().numpy(), op, m, prm))
+    assert abs(s.entropy_rate(ud, r0)) <= 1e-13 * scale
+    s.set_params(lib.Params(mu=0.05, viscous=True))
+    r1 = s.residual(ud)
+    rv = r1 - r0
+    rate = s.entropy_rate(ud, rv)
+    from oracle.operators import physical_operators
+    from oracle.physics import entropy_variables, viscous_K
+    U = torch.as_tensor(u).transpose(1, 2)
+    ops = physical_operators(op, m)
+    w = entropy_variables(U, prm)
+    g = torch.einsum("nimk,nkc->nimc", ops["D"], w)
+    qf = float(-torch.einsum("nm,nimc,nmijcb,njmb->", ops["H"], g, viscous_K(U, prm), g))
+    assert qf < 0
+    assert abs(rate - qf) <= 1e-10 * abs(qf)
+    s.close()
+
+
+def test_viscous_fp32_bulk_bound(lib):
+    """Viscous terms stay FP64 under the FP32-bulk mode; the bound of the
+    inviscid FP32-bulk path holds for the Navier-Stokes residual."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tri(3, N=8)
+    u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
+    s = lib.Solver(op, m, lib.Params(mu=0.01, viscous=True, dissipation=True, precision="fp32"))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(mu=0.01), dissipation=True, viscous=True).numpy()
+    err = rel_err(r, ro)
+    print(f"fp32 viscous rel err {err:.3e}")
+    assert err <= FP32_BOUND
+    s.close()
+
+
+def test_freestream_viscous_3d(lib):
+    op, m = _tet(2)
+    u = states.uniform_state(m.n_e, 3, op.n_p)
+    s = lib.Solver(op, m, lib.Params(mu=0.05, viscous=True, dissipation=True))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    assert np.abs(r).max() < 1e-11
+    s.close()
+
+
+def test_rrk_taylor_green_parity(lib):
+    """Relaxation RK4 on the Navier-Stokes Taylor-Green state (split + BO +
+    dissipation, 48 tetrahedra): g and the state after three steps against the
+    oracle; the entropy change is negative and matches the estimate."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(2)
+    u0 = states.taylor_green(m)
+    mu = 1.0 / 1600.0
+    prm = OP(mu=mu)
+    dt = states.cfl_timestep(m, u0, 0.2)
+    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True))
+    ud = s.to_device(u0)
+    uo = torch.as_tensor(u0)
+    rhs = lambda x: R.residual(x, op, m, prm, dissipation=True, viscous=True)
+    for step in range(3):
+        g, info = s.rrk_step(ud, dt)
+        uo, io = rrk.rrk4_step(uo, dt, rhs, op, m, prm)
+        assert abs(g - io.g) <= 1e-10, (step, g, io.g)
+        assert info.estimate < 0
+        assert abs(info.estimate - io.estimate) <= 1e-12 * abs(io.estimate) + 1e-16 * abs(io.S_before)
+    assert rel_err(ud.cpu().numpy(), uo.numpy()) <= 1e-12
+    s.close()
+

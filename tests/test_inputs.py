@@ -127,3 +127,73 @@ def test_vortex_solves_euler():
     rho_bad = (1 - 9 * 0.4 / (16 * 1.4 * np.pi) * np.exp(2 * (1 - ((x - 5) ** 2 + (y - 5) ** 2)))) ** 2.5
     rho_ok = U(x, y, 0)[0]
     assert np.abs(rho_bad - rho_ok).max() > 1e-2
+
+
+def test_tet_operator_sbp_and_accuracy():
+    from esplit_inputs import tet_operator
+    from esplit_inputs.sbp import tet_monomial_integral
+    op = tet_operator(2)
+    assert op.n_p == 25 and op.n_fac == 4 and op.n_f == 6
+    assert np.all(op.H > 0) and abs(op.H.sum() - 1 / 6) < 1e-15
+    for j in range(3):
+        assert np.abs(op.Q[j] + op.Q[j].T - np.diag(op.E[j])).max() < 1e-14
+    V, dV = vandermonde(op.xi, 2, np.array([0.25, 0.25, 0.25]))
+    for j in range(3):
+        assert np.abs(op.D[j] @ V - dV[j]).max() < 1e-11
+    q = op.volume_degree
+    assert q >= 3
+    for a in range(q + 1):
+        for b in range(q + 1 - a):
+            for c in range(q + 1 - a - b):
+                got = np.sum(op.H * op.xi[:, 0] ** a * op.xi[:, 1] ** b * op.xi[:, 2] ** c)
+                assert abs(got - tet_monomial_integral(a, b, c)) < 1e-15
+    # E is the boundary integral of products of quadratics: p^T E_j q = int d(PQ)/dxi_j
+    basis = monomial_basis(2, 3)
+    for j in range(3):
+        for A in basis:
+            for B in basis:
+                ex = [A[i] + B[i] for i in range(3)]
+                val = np.sum(op.E[j] * np.prod([op.xi[:, i] ** ex[i] for i in range(3)], axis=0))
+                if ex[j] == 0:
+                    ref = 0.0
+                else:
+                    e2 = list(ex)
+                    e2[j] -= 1
+                    ref = ex[j] * tet_monomial_integral(*e2)
+                assert abs(val - ref) < 1e-14
+
+
+def test_tet_mesh_pairing_normals_metrics():
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import periodic_tet_mesh
+    op = tet_operator(2)
+    m = periodic_tet_mesh(op, 3, 2 * np.pi, 0.02)
+    L = 2 * np.pi
+    assert m.n_e == 162 and np.all(m.J > 0)
+    assert abs(np.sum(m.J * op.H[None]) - L ** 3) < 1e-10
+    fn = op.facet_nodes.reshape(-1)
+    pe = m.pair[..., 0].reshape(m.n_e, -1)
+    ps = m.pair[..., 1].reshape(m.n_e, -1)
+    xs = m.x[:, :, fn].transpose(0, 2, 1)
+    dx = xs - xs[pe, ps]
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-12
+    nu = m.nu.reshape(m.n_e, -1, 3)
+    assert np.abs(nu + nu[pe, ps]).max() < 1e-13
+    assert np.all(pe[pe, ps] == np.arange(m.n_e)[:, None])
+    for i in range(3):
+        s = sum(np.einsum("mk,ek->em", op.D[j], m.Lam[:, i, j]) for j in range(3))
+        assert np.abs(s).max() < 1e-11
+
+
+def test_taylor_green_state():
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import periodic_tet_mesh
+    op = tet_operator(2)
+    m = periodic_tet_mesh(op, 2, 2 * np.pi, 0.0)
+    u = states.taylor_green(m)
+    rho = u[:, 0]
+    p = 0.4 * (u[:, -1] - 0.5 * (u[:, 1:4] ** 2).sum(1) / rho)
+    T = p / rho
+    assert np.allclose(T, 1 / (1.4 * 0.01), rtol=1e-12)        # T = T_0 everywhere
+    assert abs(p.mean() - 1 / (1.4 * 0.01)) < 0.2

@@ -196,3 +196,49 @@ def test_viscous_bo_entropy_and_conservation(heat):
         assert qf < 0
     c = Dg.conservation(rv, op, m)
     assert c.abs().max() < 1e-11 * float(rv.abs().max())
+
+
+def _tets(N=2, seed=1):
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import periodic_tet_mesh
+    op = tet_operator(2)
+    m = periodic_tet_mesh(op, N, 2 * np.pi, 0.02)
+    return op, m, states.random_positive_state(m.n_e, 3, op.n_p, seed=seed)
+
+
+@pytest.mark.parametrize("scheme", ["split", "hadamard", "hybrid"])
+def test_tet_entropy_conservation_and_forms(scheme):
+    """Thms. 2 and 4 on curved periodic tetrahedra; weak = strong form."""
+    op, m, u = _tets()
+    flags = np.random.default_rng(2).integers(0, 2, m.n_e)
+    r = R.residual(u, op, m, P, scheme=scheme, hybrid_flags=flags)
+    assert abs(float(Dg.entropy_rate(u, r, op, m, P))) < 1e-14 * float(Dg.entropy_rate_scale(u, r, op, m, P))
+    if scheme != "hybrid":
+        rs = R.residual(u, op, m, P, scheme=scheme, form="strong")
+        assert (r - rs).abs().max() < 1e-13 * r.abs().max()
+
+
+def test_tet_freestream_and_dissipation_sign():
+    op, m, u = _tets()
+    uf = states.uniform_state(m.n_e, 3, op.n_p)
+    assert R.residual(uf, op, m, Params(mu=0.01), dissipation=True, viscous=True).abs().max() < 1e-11
+    r0 = R.residual(u, op, m, P)
+    r1 = R.residual(u, op, m, P, dissipation=True)
+    assert float(Dg.entropy_rate(u, r1 - r0, op, m, P)) < 0
+
+
+@pytest.mark.parametrize("heat", [False, True])
+def test_tet_viscous_bo_identity(heat):
+    op, m, u = _tets()
+    prm = Params(mu=0.05, heat_flux=heat)
+    rv = R.residual(u, op, m, prm, viscous=True) - R.residual(u, op, m, prm)
+    rate = float(Dg.entropy_rate(u, rv, op, m, prm))
+    U = torch.as_tensor(u).transpose(1, 2)
+    ops = physical_operators(op, m)
+    w = entropy_variables(U, prm)
+    g = torch.einsum("nimk,nkc->nimc", ops["D"], w)
+    from oracle.physics import viscous_K
+    K = viscous_K(U, prm)
+    qf = float(-torch.einsum("nm,nimc,nmijcb,njmb->", ops["H"], g, K, g))
+    assert abs(rate - qf) < 1e-11 * abs(qf)
+    assert Dg.conservation(rv, op, m).abs().max() < 1e-10 * float(rv.abs().max())

@@ -67,3 +67,19 @@ def test_noalloc_rejects_meshes_beyond_its_scratch(lib):
     msg = lib.capi.esplit_last_error(s.ctx)
     assert "2097152" in msg and "4423680" in msg
     s.close()
+
+
+def test_noalloc_viscous_matches_residual(lib):
+    """With the viscous terms on, the no-allocation call uses the viscous
+    scratch the context allocated when they were switched on."""
+    op = tri_operator(2)
+    m = periodic_tri_mesh(op, 5, 10.0, 0.05)
+    s = lib.Solver(op, m, lib.Params(mu=0.05, viscous=True, dissipation=True))
+    u = s.to_device(states.random_positive_state(m.n_e, 2, op.n_p, seed=70))
+    ref = s.residual(u)
+    out = torch.full_like(ref, float("nan"))
+    rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+    assert rc == 0, lib.capi.esplit_last_error(s.ctx)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    s.close()
