@@ -188,9 +188,28 @@ def dW_dU(U, prm: Params):
     return _jacobian(lambda x: entropy_variables(x, prm), U)
 
 
+def conservative_from_entropy(W, prm: Params):
+    """The inverse of the map of Eq. (25), U(W), in closed form.  With
+    a = -alpha/(gam-1) and q = (rho/p)(p rho^-gam)^(1/(alpha+gam)):
+        q = -W_last,  V = W_mom / q,  T' = p/rho = (W_0/q + |V|^2/2) / a,
+        q T' = (T' rho^(1-gam))^(1/(alpha+gam))
+          =>  rho = ((q T')^(alpha+gam) / T')^(1/(1-gam)),  p = rho T'."""
+    g, al = prm.gam, prm.alpha
+    a = -al / (g - 1.0)
+    q = -W[..., -1]
+    V = W[..., 1:-1] / q[..., None]
+    v2 = (V * V).sum(-1)
+    Tp = (W[..., 0] / q + 0.5 * v2) / a
+    rho = ((q * Tp) ** (al + g) / Tp) ** (1.0 / (1.0 - g))
+    p = rho * Tp
+    return torch.cat([rho[..., None], rho[..., None] * V, (p / (g - 1.0) + 0.5 * rho * v2)[..., None]], dim=-1)
+
+
 def dU_dW(U, prm: Params):
-    """A~_0 = dU/dW = (dW/dU)^-1, Eq. (19)."""
-    return torch.linalg.inv(dW_dU(U, prm))
+    """A~_0 = dU/dW, Eq. (19): the Jacobian of the inverse map U(W) at
+    W = W(U).  (Inverting dW/dU instead would carry its condition number,
+    ~4e5 at Mach 0.1, into the round-off.)"""
+    return _jacobian(lambda w: conservative_from_entropy(w, prm), entropy_variables(U, prm))
 
 
 def symmetrized_flux_jacobians(U, prm: Params):

@@ -1,0 +1,78 @@
+"""Rounding scale of the residual for the FP64 parity bounds.
+
+summand_scale returns, per node and component, the magnitude of the terms
+whose sum is the residual.  FP64 rounding on either side (the GPU path or
+the oracle) is a few eps times this, whatever the size of the result itself;
+where the residual is much smaller than its terms (a state near a constant,
+a low-Mach flow) a plain relative bound on the result is not met by either
+side, and the parity tests bound |r_gpu - r_oracle| by
+1e-12 max|r| + 64 n_p eps (summand scale)
+(a length-n_p dot product of rounded terms on each side, as in the standard
+gamma_n bound).
+"""
+import torch
+
+
+def summand_scale(u, op, m, elems, scheme, prm, dissipation=True, viscous=False):
+    """Terms, for the elements ``elems``:
+      split:     sum_i |M_i||f_i| + |A~_i||D_i||w|/(beta+1)
+      Hadamard:  2 sum_n sum_i |S_i,mn||F*_i(u_m,u_n)|/H_m
+      facets:    |nu||F*|/H + |nu|/(2H) |X|L|SX^T| (|dw| + |w_k| + |w_v|)
+      viscous:   sum_i |D_i| G_i + |nu| (G(k) + G(v))/H
+                 + 1/(2H) sum_j |D_j|^T sum_i |K~_ij||nu_i| (|w_k| + |w_v|)
+                 with G_i = |F^V_i| + sum_j |K~_ij||D_j||w|
+    Both sides form A~_i and the viscous flux from dU/dW written out in closed
+    form (no matrix inverse), so no condition number of dW/dU enters."""
+    from oracle.physics import (euler_flux, entropy_variables, symmetrized_flux_jacobians, sy_flux,
+                                dissipation_matrix, viscous_K, viscous_flux_from_w_grads)
+    from oracle.operators import physical_operators
+    d = op.d
+    el = torch.as_tensor(elems)
+    ops = physical_operators(op, m, el)
+    U_all = torch.as_tensor(u).transpose(1, 2)
+    U = U_all[el]
+    H = ops["H"]
+    w = entropy_variables(U, prm).abs()
+    if scheme == "split":
+        f = euler_flux(U, prm).abs()
+        M = ops["Q"] / (prm.beta + 1) + ops["Q"].transpose(-1, -2)
+        sc = torch.einsum("nimk,nkic->nmc", M.abs(), f) / H[..., None]
+        Dw = torch.einsum("nimk,nkc->nimc", ops["D"].abs(), w)
+        At = symmetrized_flux_jacobians(U, prm).abs()
+        sc = sc + torch.einsum("nmicd,nimd->nmc", At, Dw) / (prm.beta + 1)
+    else:
+        n_, npp, nc = U.shape
+        F2 = 2 * sy_flux(U[:, :, None, :].expand(n_, npp, npp, nc), U[:, None, :, :].expand(n_, npp, npp, nc),
+                         prm).abs()
+        sc = torch.einsum("nimk,nmkic->nmc", ops["S"].abs(), F2) / H[..., None]
+    fn = torch.as_tensor(op.facet_nodes.reshape(-1))
+    pr = torch.as_tensor(m.pair.reshape(m.n_e, -1, 2))[el]
+    Uk, Uv = U[:, fn], U_all[pr[..., 0], fn[pr[..., 1]]]
+    nu = torch.as_tensor(m.nu.reshape(m.n_e, -1, d))[el]
+    b = torch.linalg.norm(nu, dim=-1)
+    wk, wv = entropy_variables(Uk, prm), entropy_variables(Uv, prm)
+    fac = torch.einsum("nsi,nsic->nsc", nu.abs(), sy_flux(Uk, Uv, prm).abs())
+    if dissipation:
+        Dm = dissipation_matrix(Uk, Uv, nu / b[..., None], prm).abs()
+        dws = (wk - wv).abs() + wk.abs() + wv.abs()
+        fac = fac + 0.5 * b[..., None] * torch.einsum("nscd,nsd->nsc", Dm, dws)
+    sc = sc.index_add(1, fn, fac / H[:, fn][..., None])
+    if viscous:
+        ops_all = physical_operators(op, m)
+        Ua = U_all
+        wa = entropy_variables(Ua, prm)
+        gW = torch.einsum("nimk,nkc->nmic", ops_all["D"], wa)
+        Fv = viscous_flux_from_w_grads(Ua, gW, prm).abs()                   # (N, n_p, d, nc)
+        Ka = viscous_K(Ua, prm).abs()                                       # (N, n_p, d, d, nc, nc)
+        Dwa = torch.einsum("nimk,nkc->nmic", ops_all["D"].abs(), wa.abs())  # (N, n_p, d, nc)
+        G = Fv + torch.einsum("nmijcb,nmjb->nmic", Ka, Dwa)
+        Ge = G[el]
+        sc = sc + torch.einsum("nimk,nkic->nmc", ops["D"].abs(), Ge)
+        Gk, Gv = Ge[:, fn], G[pr[..., 0], fn[pr[..., 1]]]
+        sc = sc.index_add(1, fn, torch.einsum("nsi,nsic->nsc", nu.abs(), Gk + Gv) / H[:, fn][..., None])
+        Kk = Ka[el][:, fn]
+        a = torch.einsum("nsijcb,nsi,nsc->nsjb", Kk, nu.abs(), wk.abs() + wv.abs())
+        a_full = torch.zeros(len(el), op.n_p, d, U.shape[-1], dtype=U.dtype).index_add(1, fn, a)
+        lift = torch.einsum("nimk,nmic->nkc", ops["D"].abs(), a_full)
+        sc = sc + 0.5 * lift / H[..., None]
+    return sc.transpose(1, 2).numpy()

@@ -13,6 +13,7 @@ import pytest
 import torch
 
 from esplit_inputs import tri_operator, periodic_tri_mesh, states
+from parity_bounds import summand_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -242,48 +243,6 @@ def test_rrk_dissipative_parity(lib):
     s.close()
 
 
-def summand_scale(u, op, m, elems, scheme, prm):
-    """Per node and component, the magnitude of the terms whose sum is the
-    residual: sum_i |M_i||f_i| + |A~_i||D_i||w|/(beta+1) (split) or
-    2 sum_n sum_i |S_i,mn||F*_i(u_m,u_n)|/H_m (Hadamard), plus the facet terms
-    |nu||F*|/H + |nu|/(2H) |X|L|SX^T||dw|.  FP64 rounding of either side is a
-    few eps times this, whatever the result's own size."""
-    from oracle.physics import (euler_flux, entropy_variables, symmetrized_flux_jacobians, sy_flux,
-                                dissipation_matrix, dW_dU)
-    from oracle.operators import physical_operators
-    el = torch.as_tensor(elems)
-    ops = physical_operators(op, m, el)
-    U_all = torch.as_tensor(u).transpose(1, 2)
-    U = U_all[el]
-    H = ops["H"]
-    if scheme == "split":
-        f = euler_flux(U, prm).abs()
-        M = ops["Q"] / (prm.beta + 1) + ops["Q"].transpose(-1, -2)
-        sc = torch.einsum("nimk,nkic->nmc", M.abs(), f) / H[..., None]
-        w = entropy_variables(U, prm).abs()
-        Dw = torch.einsum("nimk,nkc->nimc", ops["D"].abs(), w)
-        At = symmetrized_flux_jacobians(U, prm).abs()
-        # the oracle forms A~_i with (dW/dU)^-1: its rounding carries cond(dW/dU) (~115 here)
-        kappa = torch.linalg.cond(dW_dU(U, prm))
-        sc = sc + kappa[..., None] * torch.einsum("nmicd,nimd->nmc", At, Dw) / (prm.beta + 1)
-    else:
-        n_, npp, nc = U.shape
-        F2 = 2 * sy_flux(U[:, :, None, :].expand(n_, npp, npp, nc), U[:, None, :, :].expand(n_, npp, npp, nc),
-                         prm).abs()
-        sc = torch.einsum("nimk,nmkic->nmc", ops["S"].abs(), F2) / H[..., None]
-    fn = torch.as_tensor(op.facet_nodes.reshape(-1))
-    pr = torch.as_tensor(m.pair.reshape(m.n_e, -1, 2))[el]
-    Uk, Uv = U[:, fn], U_all[pr[..., 0], fn[pr[..., 1]]]
-    nu = torch.as_tensor(m.nu.reshape(m.n_e, -1, 2))[el]
-    b = torch.linalg.norm(nu, dim=-1)
-    Fs = sy_flux(Uk, Uv, prm).abs()
-    Dm = dissipation_matrix(Uk, Uv, nu / b[..., None], prm).abs()
-    dw = (entropy_variables(Uk, prm) - entropy_variables(Uv, prm)).abs()
-    fac = (torch.einsum("nsi,nsic->nsc", nu.abs(), Fs) + 0.5 * b[..., None] * torch.einsum("nscd,nsd->nsc", Dm, dw))
-    sc = sc.index_add(1, fn, fac / H[:, fn][..., None])
-    return sc.transpose(1, 2).numpy()
-
-
 @pytest.mark.parametrize("p", [2, 3, 4])
 def test_full_size_config2_sampled(lib, p):
     """Config 2 at full size (128 x 128 quads -> 32,768 curved triangles,
@@ -294,8 +253,7 @@ def test_full_size_config2_sampled(lib, p):
     Here the residual is ~1e3-1e4 times smaller than the terms it is summed
     from (the noise is 1e-3 and the operator entries ~1/(h H_ref)), and the
     FP64 oracle's own rounding is ~eps times those terms (checked against
-    extended precision), times cond(dW/dU) for the A~_i term, which the oracle
-    forms through a matrix inverse.  The bound is therefore
+    extended precision).  The bound is therefore
     |r_gpu - r_oracle| <= 1e-12 max|r| + 64 n_p eps (summand scale)
     (a length-n_p dot product of rounded terms on each side, as in the
     standard gamma_n bound); the observed constant and the plain max-norm

@@ -261,3 +261,23 @@ def test_entropy_change_extended_precision():
         scale = abs(float(ex)) * (abs(A_) * abs(du[0]) / r0 + abs(B_) * (P.gam - 1) * (abs(du[3]) + dke) / p0)
         assert abs(Decimal(float(got[k])) - diff) <= Decimal(64 * eps * scale) + Decimal(1e-300)
         assert abs(Decimal(float(got[k])) - diff) <= Decimal(1e-9) * abs(diff) + Decimal(64 * eps * scale)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_inverse_entropy_map(d):
+    """U(W(U)) = U, and dU/dW (Jacobian of the closed-form inverse) times
+    dW/dU (Jacobian of Eq. (25)) is the identity: the two Jacobians come from
+    independent formulas."""
+    from oracle.physics import conservative_from_entropy, dW_dU
+    U = rand_states(300, d, 21)
+    back = conservative_from_entropy(entropy_variables(U, P), P)
+    assert ((back - U).abs() / U.abs().amax(-1, keepdim=True)).max() < 1e-13
+    prod = dU_dW(U, P) @ dW_dU(U, P)
+    I = torch.eye(d + 2, dtype=DT)
+    cond = torch.linalg.cond(dW_dU(U, P))
+    assert ((prod - I).abs().amax((-1, -2)) / cond).max() < 1e-14
+    # a low-Mach state (Mach 0.1, p ~ 71): the inverse map stays accurate
+    # although cond(dW/dU) ~ 4e5
+    Ulm = torch.tensor([[1.0, 0.3, -0.2, 71.43 / 0.4 + 0.065]], dtype=DT)
+    back = conservative_from_entropy(entropy_variables(Ulm, P), P)
+    assert ((back - Ulm).abs() / Ulm.abs()).max() < 1e-13
