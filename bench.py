@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-sweep", action="store_true", help="skip the residual-only sweep over p / scheme / precision")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-tgv", action="store_true", help="skip the 3D Taylor-Green (196,608 tets) measurement")
     return ap.parse_args()
 
 
@@ -261,6 +262,74 @@ def residual_sweep(es, device, flush):
     return out
 
 
+def _timed(fn, stream, flush, n):
+    ts = []
+    for k in range(n):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return ts
+
+
+def taylor_green_run(es, device, flush, steps=5):
+    """Compressible Navier-Stokes Taylor-Green vortex (Re 1600, Ma 0.1, Pr
+    0.71, heat flux on) on [0, 2 pi]^3: 32^3 cubes x 6 = 196,608 curved
+    tetrahedra (warp 0.02), p = 2 (25 nodes); entropy split + EC SATs + BO
+    viscous SATs + matrix dissipation; relaxation RK4 steps in FP64 and in
+    FP32-bulk (entropy, production and root solve in FP64 in both), plus
+    residual-only split vs Hadamard times on the same state."""
+    from esplit_inputs import tet_operator, states
+    from esplit_inputs.mesh import periodic_tet_mesh
+    t0 = time.perf_counter()
+    op = tet_operator(2)
+    mesh = periodic_tet_mesh(op, 32, 2 * np.pi, 0.02)
+    u0 = states.taylor_green(mesh)
+    dt = states.cfl_timestep(mesh, u0, 0.1)
+    host_s = time.perf_counter() - t0
+    mu = 1.0 / 1600.0
+    stream = torch.cuda.current_stream(device)
+    dof = mesh.n_e * op.n_p
+    out = {"workload": "3D Taylor-Green vortex, Re 1600, Ma 0.1, 32^3 x 6 = 196,608 curved tets, p=2 (25 nodes), "
+                       "entropy split + EC SAT + BO viscous SAT + matrix dissipation, relaxation RK4",
+           "n_e": mesh.n_e, "n_p": op.n_p, "dof": dof, "dt": dt, "host_setup_s": host_s}
+    s = es.Solver(op, mesh, es.Params(mu=mu, viscous=True, dissipation=True), device=device)
+    r = s.empty()
+    for prec in ("fp64", "fp32"):
+        s.set_params(es.Params(mu=mu, viscous=True, dissipation=True, precision=prec))
+        u = s.to_device(u0)
+        for _ in range(2):
+            s.rrk_step(u, dt)
+        torch.cuda.synchronize()
+        s.profile(True)
+        s.profile_read()
+        gs, est = [], []
+
+        def step():
+            g, info = s.rrk_step(u, dt)
+            gs.append(g)
+            est.append(info.estimate)
+        ts = _timed(step, stream, flush, steps)
+        prof = s.profile_read()
+        s.profile(False)
+        ms = statistics.median(ts)
+        out[f"rrk_{prec}"] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "dof_residual_per_s": 4 * dof / (ms * 1e-3),
+                              "g_range": [min(gs), max(gs)], "estimate_max": max(est), "status": s.status(),
+                              "kernel_ms": {g: v[0] / steps for g, v in prof.items() if v[1] > 0}}
+        for scheme in ("split", "hadamard"):
+            s.set_params(es.Params(mu=mu, viscous=True, dissipation=True, precision=prec, scheme=scheme))
+            ud = s.to_device(u0)
+            for _ in range(2):
+                s.residual(ud, r)
+            ms = statistics.median(_timed(lambda: s.residual(ud, r), stream, flush, 5))
+            out[f"residual_{scheme}_{prec}"] = {"ms": ms, "dof_per_s": dof / (ms * 1e-3)}
+    s.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -344,6 +413,8 @@ def main():
               "g_range": [min(gs), max(gs)], "wall_s_timed": t_wall, "dt": dt}
     if rank == 0 and not args.no_sweep:
         extras["residual_sweep"] = residual_sweep(es, device, flush)
+    if rank == 0 and not args.no_tgv:
+        extras["taylor_green"] = taylor_green_run(es, device, flush)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(op, mesh, u0)

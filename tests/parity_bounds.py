@@ -58,19 +58,23 @@ def summand_scale(u, op, m, elems, scheme, prm, dissipation=True, viscous=False)
         fac = fac + 0.5 * b[..., None] * torch.einsum("nscd,nsd->nsc", Dm, dws)
     sc = sc.index_add(1, fn, fac / H[:, fn][..., None])
     if viscous:
-        ops_all = physical_operators(op, m)
-        Ua = U_all
-        wa = entropy_variables(Ua, prm)
-        gW = torch.einsum("nimk,nkc->nmic", ops_all["D"], wa)
-        Fv = viscous_flux_from_w_grads(Ua, gW, prm).abs()                   # (N, n_p, d, nc)
-        Ka = viscous_K(Ua, prm).abs()                                       # (N, n_p, d, d, nc, nc)
-        Dwa = torch.einsum("nimk,nkc->nmic", ops_all["D"].abs(), wa.abs())  # (N, n_p, d, nc)
-        G = Fv + torch.einsum("nmijcb,nmjb->nmic", Ka, Dwa)
-        Ge = G[el]
+        # the viscous flux is needed on the elements and their face neighbours
+        need = torch.unique(torch.cat([el, pr[..., 0].reshape(-1)]))
+        loc = torch.full((m.n_e,), -1, dtype=torch.long)
+        loc[need] = torch.arange(len(need))
+        ops_n = physical_operators(op, m, need)
+        Un = U_all[need]
+        wn = entropy_variables(Un, prm)
+        gW = torch.einsum("nimk,nkc->nmic", ops_n["D"], wn)
+        Fv = viscous_flux_from_w_grads(Un, gW, prm).abs()                   # (n, n_p, d, nc)
+        Kn = viscous_K(Un, prm).abs()                                       # (n, n_p, d, d, nc, nc)
+        Dwn = torch.einsum("nimk,nkc->nmic", ops_n["D"].abs(), wn.abs())    # (n, n_p, d, nc)
+        G = Fv + torch.einsum("nmijcb,nmjb->nmic", Kn, Dwn)
+        Ge = G[loc[el]]
         sc = sc + torch.einsum("nimk,nkic->nmc", ops["D"].abs(), Ge)
-        Gk, Gv = Ge[:, fn], G[pr[..., 0], fn[pr[..., 1]]]
+        Gk, Gv = Ge[:, fn], G[loc[pr[..., 0]], fn[pr[..., 1]]]
         sc = sc.index_add(1, fn, torch.einsum("nsi,nsic->nsc", nu.abs(), Gk + Gv) / H[:, fn][..., None])
-        Kk = Ka[el][:, fn]
+        Kk = Kn[loc[el]][:, fn]
         a = torch.einsum("nsijcb,nsi,nsc->nsjb", Kk, nu.abs(), wk.abs() + wv.abs())
         a_full = torch.zeros(len(el), op.n_p, d, U.shape[-1], dtype=U.dtype).index_add(1, fn, a)
         lift = torch.einsum("nimk,nmic->nkc", ops["D"].abs(), a_full)

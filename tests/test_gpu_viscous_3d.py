@@ -208,3 +208,55 @@ def test_rrk_taylor_green_parity(lib):
     assert rel_err(ud.cpu().numpy(), uo.numpy()) <= 1e-12
     s.close()
 
+
+
+_TGV_FULL = {}
+
+
+def _tgv_full():
+    # the 3D Taylor-Green workload at full size: 32^3 cubes x 6 = 196,608 tets
+    if not _TGV_FULL:
+        op = tet_operator(2)
+        m = periodic_tet_mesh(op, 32, 2 * np.pi, 0.02)
+        _TGV_FULL["v"] = (op, m, states.taylor_green(m))
+    return _TGV_FULL["v"]
+
+
+@pytest.mark.parametrize("scheme", ["split", "hadamard"])
+def test_full_size_taylor_green_sampled(lib, scheme):
+    """The Taylor-Green workload at full size (196,608 curved tets, p = 2,
+    split or Hadamard + BO viscous + dissipation, FP64), in the launch
+    configuration the benchmark times, on 40 sampled elements (plus the first
+    and last) that the oracle evaluates one by one; rounding-scale bound as
+    for the small Taylor-Green case."""
+    R, Dg, rrk, OP = _oracle()
+    op, m, u = _tgv_full()
+    mu = 1.0 / 1600.0
+    sample = np.concatenate([np.random.default_rng(80).choice(m.n_e, 40, replace=False), [0, m.n_e - 1]])
+    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True, scheme=scheme))
+    r = s.residual(s.to_device(u)).cpu().numpy()[sample]
+    s.close()
+    ro = R.residual(u, op, m, OP(mu=mu), scheme=scheme, dissipation=True, viscous=True, elems=sample).numpy()
+    sc = summand_scale(u, op, m, sample, scheme, OP(mu=mu), viscous=True)
+    err = np.abs(r - ro)
+    eps = np.finfo(float).eps
+    print(f"TGV full {scheme}: max-norm rel {rel_err(r, ro):.2e}, max err/(eps scale) "
+          f"{float((err / (eps * sc)).max()):.2f}")
+    assert np.all(err <= FP64_TOL * np.abs(ro).max() + 64 * op.n_p * eps * sc)
+
+
+def test_full_size_taylor_green_fp32_bulk(lib):
+    """FP32-bulk on the full-size Taylor-Green workload against the FP64
+    oracle on sampled elements; the bound is the stated FP32-bulk bound
+    relative to each component's max-norm."""
+    R, Dg, rrk, OP = _oracle()
+    op, m, u = _tgv_full()
+    mu = 1.0 / 1600.0
+    sample = np.concatenate([np.random.default_rng(81).choice(m.n_e, 40, replace=False), [0, m.n_e - 1]])
+    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True, precision="fp32"))
+    r = s.residual(s.to_device(u)).cpu().numpy()[sample]
+    s.close()
+    ro = R.residual(u, op, m, OP(mu=mu), dissipation=True, viscous=True, elems=sample).numpy()
+    err = rel_err(r, ro)
+    print(f"TGV full fp32-bulk rel err {err:.3e}")
+    assert err <= FP32_BOUND
