@@ -151,7 +151,7 @@ void esplit_destroy(esplit_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   esplit::Buffers& b = c->b;
-  void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,
+  void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va};
   for (void* p : ps) dfree(p);
@@ -248,6 +248,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.face_pairs, fpairs.size()))) return rc;
   if ((rc = dalloc(c, &c->b.ops64, (size_t)n_e * 2 * d * NP * NP))) return rc;
   if ((rc = dalloc(c, &c->b.ops32, (size_t)n_e * 2 * d * NP * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.ops32lo, (size_t)n_e * 2 * d * NP * NP))) return rc;
   if ((rc = dalloc(c, &c->b.rows, (size_t)n_e * 2 * d * NP))) return rc;
   if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
   c->partial_cap = 0;

@@ -42,7 +42,8 @@ struct Buffers {
   //   k <  d: M_i^T, M_i = H^-1 (Q_x_i/(beta+1) + Q_x_i^T)
   //   k >= d: D_i^T, D_i = H^-1 Q_x_i
   double* ops64 = nullptr;     // [n_e][2d][n_p][n_p]
-  float* ops32 = nullptr;      // same, float
+  float* ops32 = nullptr;      // same, float (nearest)
+  float* ops32lo = nullptr;    // same, float remainder ops64 - ops32 (compensated FP32-bulk contractions)
   double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
   // element lists for the hybrid scheme
   int* list_split = nullptr;
@@ -57,13 +58,13 @@ struct Buffers {
   double* stage_u = nullptr;
   double* stage_r = nullptr;
   double* dacc = nullptr;
-  double* node_cache = nullptr;
+  double* node_cache = nullptr;  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
   // viscous scratch: nodal F^V [n_e][d][n_c][n_p], facet jump terms
   // [n_e][n_c][n_slot] and lift vectors a_j [n_e][d][n_c][n_slot]
   double* fv = nullptr;
   double* vsat = nullptr;
   double* va = nullptr;
-  double* vjp_work = nullptr;    // 12 state-sized arrays for the RRK step reverse  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
+  double* vjp_work = nullptr;    // 12 state-sized arrays for the RRK step reverse
   double* host_u = nullptr;    // device copies for the host-buffer entry point
   double* host_r = nullptr;
 };

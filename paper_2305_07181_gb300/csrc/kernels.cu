@@ -65,7 +65,8 @@ __device__ __forceinline__ void block_sum(double (&v)[W], double* out_row) {
 template <int D>
 __global__ void build_ops_kernel(const double* __restrict__ Qref, const double* __restrict__ Lam,
                                  const double* __restrict__ J, const double* __restrict__ nu, int n_e,
-                                 double inv_bp1, double* __restrict__ ops64, float* __restrict__ ops32) {
+                                 double inv_bp1, double* __restrict__ ops64, float* __restrict__ ops32,
+                                 float* __restrict__ ops32lo) {
   const int NP = c_ref.n_p, NS = c_ref.n_slot;
   size_t per = (size_t)2 * D * NP * NP;
   size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,7 +97,9 @@ __global__ void build_ops_kernel(const double* __restrict__ Qref, const double* 
   else
     val = Qx(m, n) / Hm;
   ops64[idx] = val;
-  ops32[idx] = (float)val;
+  float hi = (float)val;
+  ops32[idx] = hi;
+  ops32lo[idx] = (float)(val - (double)hi);
 }
 
 // row sums M_i 1 and D_i 1 of the stored float64 operators, summed in node
@@ -120,10 +123,10 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   double inv_bp1 = 1.0 / (c->prm.beta + 1.0);
   if (c->dim == 2)
     build_ops_kernel<2><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
-                                          c->b.ops32);
+                                          c->b.ops32, c->b.ops32lo);
   else
     build_ops_kernel<3><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
-                                          c->b.ops32);
+                                          c->b.ops32, c->b.ops32lo);
   size_t nr = (size_t)c->n_e * 2 * c->dim * c->n_p;
   build_rows_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(c->b.ops64, c->n_e, 2 * c->dim, c->b.rows);
   c->launches += 2;
@@ -202,17 +205,40 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 // (FP32-bulk): the contractions act in float32 on the variation inside the
 // element, relative to its node 0, and the node-0 values come back through
 // the float64 row sums of the stored operators,
-//   M_i f_i = M_i (f_i - f_i,0) + f_i,0 (M_i 1),  D_i w = D_i (w - w_0) + w_0 (D_i 1),
-// so the operator entries (~1/(h H_ref)) multiply only small variations.
+//   M_i f_i = M_i (f_i - f_i,0) + f_i,0 (M_i 1),  D_i w = D_i (w - w_0) + w_0 (D_i 1).
+// Operator entries and variations are each held as an unevaluated float32
+// sum hi + lo, and the products are accumulated by the compensated dot
+// product of Ogita, Rump and Oishi (Dot2, SIAM J. Sci. Comput. 26, 2005):
+// the rounding error of every product (exact through fmaf) and of every
+// addition (TwoSum) goes to a second float32 accumulator, together with the
+// cross terms hi*lo.  At low Mach number the energy-flux variation inside an
+// element is ~(E + p)|dV|, hundreds of times the residual, and a plain
+// float32 product would lose that factor.
 // Optional: block partial of sum H w^T r (entropy production, float64).
 // ---------------------------------------------------------------------------
 template <typename T, int D, int NP, int EB>
 struct SplitSmem {
   double rf[EB][D][D + 2][NP];  // fluxes
   double rw[EB][D + 2][NP];     // entropy variables
-  T sf[EB][D][D + 2][NP];       // float32 variations (FP32-bulk only)
+  T sf[EB][D][D + 2][NP];       // float32 variations, hi and lo parts (FP32-bulk only)
   T sw[EB][D + 2][NP];
+  T sfl[EB][D][D + 2][NP];
+  T swl[EB][D + 2][NP];
 };
+
+// acc + cmp += (ah + al) (bh + bl), Dot2 step: exact product error by fmaf,
+// TwoSum for the addition; intrinsics keep the compiler from fusing them.
+__device__ __forceinline__ void dot2_step(float ah, float al, float bh, float bl, float& acc, float& cmp) {
+  float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  float s = __fadd_rn(acc, p);
+  float z = __fsub_rn(s, acc);
+  float t = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p, z));
+  acc = s;
+  cmp = __fadd_rn(cmp, __fadd_rn(t, e));
+}
 template <int D, int NP, int EB>
 struct SplitSmem<double, D, NP, EB> {
   double rf[EB][D][D + 2][NP];
@@ -222,9 +248,9 @@ struct SplitSmem<double, D, NP, EB> {
 template <typename T, int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
-    const double* __restrict__ rows, const double* __restrict__ J, const double* __restrict__ sat,
-    const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64, int* __restrict__ status,
-    double* __restrict__ prod) {
+    const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
+    const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
+    int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -259,12 +285,18 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           f0[i][q] = sm.rf[el][i][q][0];
-          sm.sf[el][i][q][m] = (T)(sm.rf[el][i][q][m] - f0[i][q]);
+          double v = sm.rf[el][i][q][m] - f0[i][q];
+          T hi = (T)v;
+          sm.sf[el][i][q][m] = hi;
+          sm.sfl[el][i][q][m] = (T)(v - (double)hi);
         }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         w0[q] = sm.rw[el][q][0];
-        sm.sw[el][q][m] = (T)(sm.rw[el][q][m] - w0[q]);
+        double v = sm.rw[el][q][m] - w0[q];
+        T hi = (T)v;
+        sm.sw[el][q][m] = hi;
+        sm.swl[el][q][m] = (T)(v - (double)hi);
       }
     }
     __syncthreads();
@@ -279,8 +311,8 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
 #pragma unroll
       for (int q = 0; q < NC; ++q) g[i][q] = T(0);
     const T* op = ops + (size_t)e * (2 * D * NP * NP);
-    // float32 sums carry compensation terms (Kahan): with plain float32
-    // accumulation its round-off, not the float32 operands, would dominate
+    const float* oplo = F64 ? nullptr : opslo + (size_t)e * (2 * D * NP * NP);
+    // float32 sums: second accumulators of the compensated dot products
     T cacc[NC], cg[D][NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) cacc[q] = T(0);
@@ -294,31 +326,30 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       for (int n = 0; n < NP; ++n) {
         T mt = __ldg(&op[(i * NP + n) * NP + m]);
         T dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
+        float mtl = 0.f, dtl = 0.f;
+        if constexpr (!F64) {
+          mtl = __ldg(&oplo[(i * NP + n) * NP + m]);
+          dtl = __ldg(&oplo[((D + i) * NP + n) * NP + m]);
+        }
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           if constexpr (F64) {
             acc[q] += mt * sm.rf[el][i][q][n];
             g[i][q] += dt * sm.rw[el][q][n];
           } else {
-            T y = mt * sm.sf[el][i][q][n] - cacc[q];
-            T t = acc[q] + y;
-            cacc[q] = (t - acc[q]) - y;
-            acc[q] = t;
-            T y2 = dt * sm.sw[el][q][n] - cg[i][q];
-            T t2 = g[i][q] + y2;
-            cg[i][q] = (t2 - g[i][q]) - y2;
-            g[i][q] = t2;
+            dot2_step(mt, mtl, sm.sf[el][i][q][n], sm.sfl[el][i][q][n], acc[q], cacc[q]);
+            dot2_step(dt, dtl, sm.sw[el][q][n], sm.swl[el][q][n], g[i][q], cg[i][q]);
           }
         }
       }
     }
     double accd[NC], gd[D][NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) accd[q] = (double)acc[q];
+    for (int q = 0; q < NC; ++q) accd[q] = F64 ? (double)acc[q] : (double)acc[q] + (double)cacc[q];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) gd[i][q] = (double)g[i][q];
+      for (int q = 0; q < NC; ++q) gd[i][q] = F64 ? (double)g[i][q] : (double)g[i][q] + (double)cg[i][q];
     if constexpr (!F64) {
       // add back the node-0 values through the stored operators' row sums
       const double* rs = rows + (size_t)e * (2 * D * NP);
@@ -528,7 +559,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.rows, c->b.J, sat, lsplit,
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit,
                                                              n_split, ph, ph64, c->b.status,
                                                              prod ? prod + np_used : nullptr);
     c->launches++;
