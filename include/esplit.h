@@ -67,6 +67,7 @@ typedef struct esplit_stepinfo {
   double S_after;      /* 1^T H s(u_{n+1})                                          */
   int iterations;      /* root-solve evaluations of f                               */
   int status;          /* ESPLIT_OK or the step's error code                        */
+  double stage_rate[4]; /* e_i = sum_k w(U_i)^T H r_i of the four stages, Eq. (97)  */
 } esplit_stepinfo;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -149,6 +150,26 @@ int esplit_residual(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void
  * for esplit_residual; the result equals esplit_residual's.  The paper has no
  * counterpart of this entry point; it is a deployment convenience. */
 int esplit_residual_noalloc(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void* stream);
+
+/* Hybrid scheme (Sec. 4.4, Thm. 4): flags for the hybrid scheme computed on
+ * the device from the state u_dev ([n_e][n_c][n_p] float64).  The paper
+ * leaves the choice of troubled elements open; this detector flags element k
+ * when, over the nodes of k and the neighbours' facet nodes coincident with
+ * the facet nodes of k, max p / min p > threshold or a pressure there is not
+ * positive and finite, p = (gam-1)(e - (0.5 |m|^2)/rho) evaluated in that
+ * order in round-to-nearest float64; then every face neighbour of a flagged
+ * element is flagged as well.  The flags replace those of
+ * esplit_set_hybrid_flags and are used by every later residual of the hybrid
+ * scheme (an RRK step keeps them for all four stages: call this before each
+ * step to re-detect).  threshold: finite, >= 1 (ESPLIT_ERR_ARG otherwise).
+ * *n_flagged (may be NULL) receives the number of flagged elements.
+ * Synchronises `stream`. */
+int esplit_detect_hybrid(esplit_ctx* ctx, const double* u_dev, double threshold, int* n_flagged, void* stream);
+
+/* Copies the current hybrid flags (uint8, 0 or 1, [n_e]) to flags_host, from
+ * esplit_set_hybrid_flags or the last esplit_detect_hybrid.  ESPLIT_ERR_STATE
+ * when neither has run since the mesh upload.  Synchronises. */
+int esplit_get_hybrid_flags(esplit_ctx* ctx, unsigned char* flags_host);
 
 /* Same with host buffers: copies u_host to the device, evaluates, copies the
  * residual back, and synchronises `stream` before returning. */

@@ -40,7 +40,8 @@ class esplit_params(ctypes.Structure):
 
 class esplit_stepinfo(ctypes.Structure):
     _fields_ = [("g", ctypes.c_double), ("estimate", ctypes.c_double), ("S_before", ctypes.c_double),
-                ("S_after", ctypes.c_double), ("iterations", ctypes.c_int), ("status", ctypes.c_int)]
+                ("S_after", ctypes.c_double), ("iterations", ctypes.c_int), ("status", ctypes.c_int),
+                ("stage_rate", ctypes.c_double * 4)]
 
 
 _P = ctypes.c_void_p
@@ -56,6 +57,8 @@ _SIGNATURES = {
     "esplit_set_params": (_I, [_P, ctypes.POINTER(esplit_params)]),
     "esplit_get_params": (_I, [_P, ctypes.POINTER(esplit_params)]),
     "esplit_set_hybrid_flags": (_I, [_P, _P, _I]),
+    "esplit_detect_hybrid": (_I, [_P, _P, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _P]),
+    "esplit_get_hybrid_flags": (_I, [_P, _P]),
     "esplit_residual": (_I, [_P, _P, _P, _P]),
     "esplit_residual_noalloc": (_I, [_P, _P, _P, _P]),
     "esplit_residual_host": (_I, [_P, _P, _P, _P]),
@@ -129,6 +132,16 @@ def esplit_get_params(ctx):
 
 def esplit_set_hybrid_flags(ctx, flags_ptr, n_e) -> int:
     return lib.esplit_set_hybrid_flags(ctx, flags_ptr, n_e)
+
+
+def esplit_detect_hybrid(ctx, u_ptr, threshold, stream=None):
+    n = ctypes.c_int()
+    rc = lib.esplit_detect_hybrid(ctx, u_ptr, threshold, ctypes.byref(n), stream)
+    return rc, n.value
+
+
+def esplit_get_hybrid_flags(ctx, flags_ptr) -> int:
+    return lib.esplit_get_hybrid_flags(ctx, flags_ptr)
 
 
 def esplit_residual(ctx, u_ptr, r_ptr, stream=None) -> int:

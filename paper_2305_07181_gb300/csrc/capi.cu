@@ -152,7 +152,7 @@ void esplit_destroy(esplit_ctx* c) {
   cudaSetDevice(c->device);
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
-                b.list_split, b.list_had, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
+                b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va};
   for (void* p : ps) dfree(p);
   for (auto& r : c->recs) {
@@ -207,6 +207,19 @@ int esplit_upload_operator(esplit_ctx* c, int n_p, int n_fac, int n_f, const dou
 }
 
 static int ensure_viscous(esplit_ctx* c);
+
+// hybrid lists and flags, capacity n_e (allocated once per mesh)
+static int ensure_hybrid(esplit_ctx* c) {
+  if (c->b.hcount) return ESPLIT_OK;
+  int rc;
+  size_t n = (size_t)c->n_e;
+  if ((rc = dalloc(c, &c->b.list_split, n))) return rc;
+  if ((rc = dalloc(c, &c->b.list_had, n))) return rc;
+  if ((rc = dalloc(c, &c->b.hflags, n))) return rc;
+  if ((rc = dalloc(c, &c->b.hflag0, n))) return rc;
+  if ((rc = dalloc(c, &c->b.hcount, (n + 1023) / 1024 + 1))) return rc;
+  return ESPLIT_OK;
+}
 
 int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* Lambda, const double* nu,
                        const int* pair, const double* hmin) {
@@ -267,6 +280,11 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   dalloc(c, &c->b.host_u, 0);
   dalloc(c, &c->b.host_r, 0);
   c->flags.assign(n_e, 0);
+  dalloc(c, &c->b.list_split, 0);  // the hybrid scheme needs flags for the new mesh
+  dalloc(c, &c->b.list_had, 0);
+  dalloc(c, &c->b.hflags, 0);
+  dalloc(c, &c->b.hflag0, 0);
+  dalloc(c, &c->b.hcount, 0);
   dalloc(c, &c->b.fv, 0);
   dalloc(c, &c->b.vsat, 0);
   dalloc(c, &c->b.va, 0);
@@ -314,12 +332,42 @@ int esplit_set_hybrid_flags(esplit_ctx* c, const unsigned char* flags, int n_e) 
   }
   c->flags.assign(flags, flags + n_e);
   int rc;
-  if ((rc = dalloc(c, &c->b.list_split, std::max<size_t>(ls.size(), 1)))) return rc;
-  if ((rc = dalloc(c, &c->b.list_had, std::max<size_t>(lh.size(), 1)))) return rc;
+  if ((rc = ensure_hybrid(c))) return rc;
   if (!ls.empty()) CK(cudaMemcpy(c->b.list_split, ls.data(), sizeof(int) * ls.size(), cudaMemcpyHostToDevice));
   if (!lh.empty()) CK(cudaMemcpy(c->b.list_had, lh.data(), sizeof(int) * lh.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->b.hflags, flags, n_e, cudaMemcpyHostToDevice));
   c->n_split = (int)ls.size();
   c->n_had = (int)lh.size();
+  return ESPLIT_OK;
+}
+
+int esplit_detect_hybrid(esplit_ctx* c, const double* u, double threshold, int* n_flagged, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!u) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
+  if (!(threshold >= 1.0) || !std::isfinite(threshold)) return fail(c, ESPLIT_ERR_ARG, "threshold must be finite and >= 1");
+  cudaSetDevice(c->device);
+  if ((rc = ensure_hybrid(c))) return rc;
+  cudaStream_t s = as_stream(stream);
+  if (esplit::launch_detect_hybrid(c, u, threshold, s))
+    return fail(c, ESPLIT_ERR_CUDA, std::string("detector launch: ") + cudaGetErrorString(cudaGetLastError()));
+  int total = 0;
+  CK(cudaMemcpyAsync(&total, c->b.hcount + (c->n_e + 1023) / 1024, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  c->n_had = total;
+  c->n_split = c->n_e - total;
+  c->last_stream = s;
+  if (n_flagged) *n_flagged = total;
+  return ESPLIT_OK;
+}
+
+int esplit_get_hybrid_flags(esplit_ctx* c, unsigned char* flags) {
+  if (!c || !flags) return ESPLIT_ERR_ARG;
+  if (!c->have_mesh) return fail(c, ESPLIT_ERR_STATE, "no mesh uploaded");
+  if (!c->b.hflags) return fail(c, ESPLIT_ERR_STATE, "no hybrid flags set or detected");
+  cudaSetDevice(c->device);
+  CK(cudaStreamSynchronize(c->last_stream));
+  CK(cudaMemcpy(flags, c->b.hflags, c->n_e, cudaMemcpyDeviceToHost));
   return ESPLIT_OK;
 }
 
@@ -479,7 +527,9 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     }
   }
   if (esplit::launch_root_apply(c, u, c->b.dacc, n, s)) return fail(c, ESPLIT_ERR_CUDA, "apply launch");
+  double e_stage[4];
   CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(e_stage, c->b.scal + 2, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int phys = read_status(c, s, true);
   c->last_stream = s;
@@ -493,6 +543,7 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     info->status = status;
     // entropy change at the last evaluated g (within 4 eps g of the returned g)
     info->S_after = st.S0 + (st.phase == 3 ? st.dS_last : 0.0);
+    for (int i = 0; i < 4; ++i) info->stage_rate[i] = e_stage[i];
   }
   if (status == ESPLIT_ERR_NONPHYSICAL) return fail(c, status, "non-physical state during the step");
   if (status == ESPLIT_ERR_RRK_NO_ROOT) return fail(c, status, "relaxation parameter could not be bracketed");

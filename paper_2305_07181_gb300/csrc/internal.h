@@ -45,9 +45,13 @@ struct Buffers {
   float* ops32 = nullptr;      // same, float (nearest)
   float* ops32lo = nullptr;    // same, float remainder ops64 - ops32 (compensated FP32-bulk contractions)
   double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
-  // element lists for the hybrid scheme
+  // element lists for the hybrid scheme (capacity n_e each), the flags they
+  // come from, and the detector's scratch (unwidened flags, block counts + total)
   int* list_split = nullptr;
   int* list_had = nullptr;
+  unsigned char* hflags = nullptr;
+  unsigned char* hflag0 = nullptr;
+  int* hcount = nullptr;
   // scratch
   double* sat = nullptr;       // [n_e][n_c][n_slot] facet contributions
   double* partial = nullptr;   // block partial sums
@@ -145,5 +149,6 @@ int launch_rrk_vjp_stage(esplit_ctx* c, const double* U, const double* r, const 
                          const double* ubar_next, double c_d, double c_e, double c_u, double* rbar, double* extra,
                          cudaStream_t s);
 int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch);
+int launch_detect_hybrid(esplit_ctx* c, const double* u, double threshold, cudaStream_t s);
 
 }  // namespace esplit

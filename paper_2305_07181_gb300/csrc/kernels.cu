@@ -12,6 +12,7 @@
 //                 k >= d: D_i^T with D_i = H^-1 Q_x_i
 //   sat           [n_e][n_c][n_slot]   facet (SAT + dissipation) contributions
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <stdint.h>
 
 #include <cstdio>
@@ -1078,3 +1079,4 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 #include "vjp.cuh"
 #include "visc.cuh"
 #include "rrk_vjp.cuh"
+#include "hybrid.cuh"

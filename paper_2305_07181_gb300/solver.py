@@ -113,6 +113,16 @@ class Solver:
         f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
         self._check(capi.esplit_set_hybrid_flags(self.ctx, _ptr(f), self.n_e))
 
+    def detect_hybrid(self, u: torch.Tensor, threshold: float = 1.1, stream=None) -> int:
+        rc, n = capi.esplit_detect_hybrid(self.ctx, _dptr(u), float(threshold), _stream(stream))
+        self._check(rc)
+        return n
+
+    def hybrid_flags(self) -> np.ndarray:
+        f = np.empty(self.n_e, dtype=np.uint8)
+        self._check(capi.esplit_get_hybrid_flags(self.ctx, _ptr(f)))
+        return f
+
     # -- evaluation ------------------------------------------------------------
     def empty(self):
         return torch.empty(self.shape, dtype=torch.float64, device=f"cuda:{self.device}")
