@@ -38,7 +38,7 @@ UNIT = "DOF-residual evals/s"
 FP64_PEAK_NOMINAL = 1.25e12            # recipe table: GB300 FP64 1.25 TFLOP/s
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged
 # kernel (profiles/split_volume_config2_p3_fp64.md); keyed by (kernel, p, precision, N)
-NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 393.396e6}
+NCU_TRAFFIC = {}
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 
 
@@ -152,7 +152,9 @@ def algorithmic_flops(group, n_e, n_p, d, n_pairs):
 def algorithmic_bytes(group, n_e, n_p, d, n_pairs):
     nc = d + 2
     if group == "split_volume":
-        return n_e * (8 * (2 * d * n_p * n_p) + 8 * n_p * (2 * nc + 1) + 8 * nc * (3 * (n_p // 2)))
+        n_slot = 2 * n_pairs // n_e
+        # D_i operators, u in, r out, J, and at the facet slots nu and the facet contributions
+        return n_e * (8 * d * n_p * n_p + 8 * n_p * (2 * nc + 1) + 8 * n_slot * (nc + d))
     if group == "face":
         return n_pairs * (2 * 8 * nc + 2 * 8 * nc + 8 * d + 8 + 16)
     return None

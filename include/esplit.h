@@ -22,6 +22,8 @@
 #ifndef ESPLIT_H
 #define ESPLIT_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -72,6 +74,13 @@ typedef struct esplit_stepinfo {
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int esplit_version(void);
+
+/* Test aid (no counterpart in the paper): y_dev[i] = f(x_dev[i]) for the
+ * float64 elementary functions the kernels use, fn 0..3 = log, log1p, exp,
+ * expm1 (the library's table-driven versions), fn 4..7 = the same functions
+ * of the CUDA math library.  x_dev, y_dev: n float64 on the current device.
+ * Asynchronous on `stream`; ESPLIT_ERR_ARG for fn outside 0..7. */
+int esplit_math_eval(int fn, const double* x_dev, double* y_dev, size_t n, void* stream);
 
 /* Create a context on CUDA device `device` for dimension `dim` (2 or 3).
  * The context owns every device copy it makes (operators, mesh, scratch).

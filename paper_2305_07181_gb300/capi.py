@@ -50,6 +50,7 @@ _I = ctypes.c_int
 
 _SIGNATURES = {
     "esplit_version": (_I, []),
+    "esplit_math_eval": (_I, [_I, _P, _P, ctypes.c_size_t, _P]),
     "esplit_create": (_I, [ctypes.POINTER(_P), _I, _I]),
     "esplit_destroy": (None, [_P]),
     "esplit_upload_operator": (_I, [_P, _I, _I, _I, _P, _P, _P, _P, _P]),
@@ -226,3 +227,7 @@ def esplit_last_error(ctx) -> str:
 
 def esplit_launch_count(ctx) -> int:
     return lib.esplit_launch_count(ctx)
+
+
+def esplit_math_eval(fn, x_ptr, y_ptr, n, stream=None) -> int:
+    return lib.esplit_math_eval(fn, x_ptr, y_ptr, n, stream)

@@ -113,6 +113,11 @@ extern "C" {
 
 int esplit_version(void) { return 100; }
 
+int esplit_math_eval(int fn, const double* x, double* y, size_t n, void* stream) {
+  if (fn < 0 || fn > 7 || (n > 0 && (!x || !y))) return ESPLIT_ERR_ARG;
+  return esplit::launch_math_eval(fn, x, y, n, (cudaStream_t)stream) ? ESPLIT_ERR_CUDA : ESPLIT_OK;
+}
+
 int esplit_create(esplit_ctx** out, int dim, int device) {
   if (!out) return ESPLIT_ERR_ARG;
   *out = nullptr;

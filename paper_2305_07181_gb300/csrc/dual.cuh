@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "fmath.cuh"
+
 namespace esplit {
 
 template <int N>
@@ -149,11 +151,11 @@ __device__ __forceinline__ Dual<N> chain(const Dual<N>& a, double fv, double dfd
 }
 template <int N>
 __device__ __forceinline__ Dual<N> t_log(const Dual<N>& a) {
-  return chain(a, log(a.v), 1.0 / a.v);
+  return chain(a, fm::log(a.v), 1.0 / a.v);
 }
 template <int N>
 __device__ __forceinline__ Dual<N> t_exp(const Dual<N>& a) {
-  double e = exp(a.v);
+  double e = fm::exp(a.v);
   return chain(a, e, e);
 }
 template <int N>
@@ -168,11 +170,11 @@ __device__ __forceinline__ Dual<N> t_abs(const Dual<N>& a) {
 }
 template <int N>
 __device__ __forceinline__ Dual<N> t_expm1(const Dual<N>& a) {
-  return chain(a, expm1(a.v), exp(a.v));
+  return chain(a, fm::expm1(a.v), fm::exp(a.v));
 }
 template <int N>
 __device__ __forceinline__ Dual<N> t_log1p(const Dual<N>& a) {
-  return chain(a, log1p(a.v), 1.0 / (1.0 + a.v));
+  return chain(a, fm::log1p(a.v), 1.0 / (1.0 + a.v));
 }
 template <int N>
 __device__ __forceinline__ bool t_isfinite(const Dual<N>& a) {

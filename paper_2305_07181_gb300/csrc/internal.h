@@ -150,5 +150,6 @@ int launch_rrk_vjp_stage(esplit_ctx* c, const double* U, const double* r, const 
                          cudaStream_t s);
 int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch);
 int launch_detect_hybrid(esplit_ctx* c, const double* u, double threshold, cudaStream_t s);
+int launch_math_eval(int fn, const double* x, double* y, size_t n, cudaStream_t s);
 
 }  // namespace esplit

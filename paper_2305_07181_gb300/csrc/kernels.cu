@@ -199,14 +199,20 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 
 // ---------------------------------------------------------------------------
 // entropy-split volume kernel (Eq. (100)): EB elements per block, one thread
-// per node.  r = sum_i M_i f_i - 1/(beta+1) sum_i A~_i (D_i w) + sat
+// per node.  With M_i = H^-1 (Q_i/(beta+1) + Q_i^T) and Q_i + Q_i^T = E_i
+// (Def. 1, E_i diagonal), M_i = H^-1 E_i - beta/(beta+1) D_i, so
+//   r = H^-1 sum_i E_i f_i - beta/(beta+1) sum_i D_i f_i
+//       - 1/(beta+1) sum_i A~_i (D_i w) + sat:
+// only the D_i are applied (one operator entry serves the flux and the
+// entropy-variable contraction), and the E_i term is pointwise at the facet
+// nodes (E_i = diag(nu_i) there).
 //
 // Node states, fluxes, entropy variables and the A~_i products are float64 in
 // both precision modes.  T = double: plain float64 contractions.  T = float
 // (FP32-bulk): the contractions act in float32 on the variation inside the
 // element, relative to its node 0, and the node-0 values come back through
 // the float64 row sums of the stored operators,
-//   M_i f_i = M_i (f_i - f_i,0) + f_i,0 (M_i 1),  D_i w = D_i (w - w_0) + w_0 (D_i 1).
+//   D_i f_i = D_i (f_i - f_i,0) + f_i,0 (D_i 1),  D_i w = D_i (w - w_0) + w_0 (D_i 1).
 // Operator entries and variations are each held as an unevaluated float32
 // sum hi + lo, and the products are accumulated by the compensated dot
 // product of Ogita, Rump and Oishi (Dot2, SIAM J. Sci. Comput. 26, 2005):
@@ -250,8 +256,8 @@ template <typename T, int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
-    const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
-    int* __restrict__ status, double* __restrict__ prod) {
+    const double* __restrict__ nu, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
+    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -325,20 +331,16 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     for (int i = 0; i < D; ++i) {
 #pragma unroll 4
       for (int n = 0; n < NP; ++n) {
-        T mt = __ldg(&op[(i * NP + n) * NP + m]);
         T dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
-        float mtl = 0.f, dtl = 0.f;
-        if constexpr (!F64) {
-          mtl = __ldg(&oplo[(i * NP + n) * NP + m]);
-          dtl = __ldg(&oplo[((D + i) * NP + n) * NP + m]);
-        }
+        float dtl = 0.f;
+        if constexpr (!F64) dtl = __ldg(&oplo[((D + i) * NP + n) * NP + m]);
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           if constexpr (F64) {
-            acc[q] += mt * sm.rf[el][i][q][n];
+            acc[q] += dt * sm.rf[el][i][q][n];
             g[i][q] += dt * sm.rw[el][q][n];
           } else {
-            dot2_step(mt, mtl, sm.sf[el][i][q][n], sm.sfl[el][i][q][n], acc[q], cacc[q]);
+            dot2_step(dt, dtl, sm.sf[el][i][q][n], sm.sfl[el][i][q][n], acc[q], cacc[q]);
             dot2_step(dt, dtl, sm.sw[el][q][n], sm.swl[el][q][n], g[i][q], cg[i][q]);
           }
         }
@@ -356,11 +358,10 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       const double* rs = rows + (size_t)e * (2 * D * NP);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        double rm = __ldg(&rs[i * NP + m]);
         double rd = __ldg(&rs[(D + i) * NP + m]);
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          accd[q] += f0[i][q] * rm;
+          accd[q] += f0[i][q] * rd;
           gd[i][q] += w0[q] * rd;
         }
       }
@@ -378,11 +379,26 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     }
     int sl = c_ref.node_slot[m];
     double Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
+    const double kf = c64.beta * c64.inv_bp1;
     double res[NC];
 #pragma unroll
+    for (int q = 0; q < NC; ++q) res[q] = -kf * accd[q] - c64.inv_bp1 * nonc[q];
+    if (sl >= 0) {
+      // H^-1 sum_i E_i f_i at the facet node, and the facet contributions
+      double nv[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) nv[i] = __ldg(&nu[((size_t)e * NS + sl) * D + i]);
+      const double ih = 1.0 / Hm;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        double ef = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) ef += nv[i] * sm.rf[el][i][q][m];
+        res[q] += ef * ih + __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
+      }
+    }
+#pragma unroll
     for (int q = 0; q < NC; ++q) {
-      res[q] = accd[q] - c64.inv_bp1 * nonc[q];
-      if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
       r[((size_t)e * NC + q) * NP + m] = res[q];
     }
     if (prod) {
@@ -560,7 +576,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit,
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, c->b.nu, sat, lsplit,
                                                              n_split, ph, ph64, c->b.status,
                                                              prod ? prod + np_used : nullptr);
     c->launches++;
@@ -819,8 +835,13 @@ int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, doubl
 // with the per-node entropy change evaluated without cancellation:
 //   s(U+dU) - s(U) = s(U) expm1(A log1p(drho/rho) + B log1p(dp/p)),
 //   A = alpha/(alpha+gam), B = 1/(alpha+gam), dp from the closure exactly.
-// Pass 0 evaluates g = 0.5 and 1.5 together (bracket and round-off floor rule);
-// then a safeguarded Newton iteration from the quadratic model through
+// Pass 0 evaluates f and f' at g = 1.  f is convex with f(0) = 0, so Newton
+// from g = 1 approaches the other root monotonically (from above after at
+// most one step): when |f(1)| and |f'(1)| are both at the round-off floor
+// 64 eps sum H|s| the step is a free stream and g = 1; when f'(1) > 0 and the
+// Newton point lies in (0.5, 1.5) the Newton phase starts there.  Otherwise
+// the bracketing path: g = 0.5 and 1.5 together (bracket and floor rule),
+// halving lo / doubling hi, then Newton from the quadratic model through
 // (0, 0), (lo, f_lo), (hi, f_hi).  Stops at |step| <= 4 eps g, |f| at its own
 // round-off level, or ROOT_EVALS_MAX evaluations; no bracket -> status -5.
 // ---------------------------------------------------------------------------
@@ -833,8 +854,8 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
   for (int i = 0; i < 4; ++i) est += b[i] * scal[2 + i];
   st->est = dt * est;
   st->g = 1.0;
-  st->ga = 0.5;
-  st->gb = 1.5;
+  st->ga = 1.0;
+  st->gb = -1.0;
   st->lo = 0.5;
   st->hi = 1.5;
   st->flo = 0.0;
@@ -865,10 +886,10 @@ __device__ __forceinline__ void entropy_change_and_slope(const double* u, const 
   double ir1 = 1.0 / (rho + drho);  // 1/rho'
   double dke = 0.5 * ((2.0 * mdm + dmdm) - mm * drho * ir) * ir1;
   double dp = c.gm1 * (dE - dke);
-  double l1 = log1p(drho * ir), l2 = log1p(dp * ip);
-  ds = s0 * expm1(c.a_q * l1 + (c.b_q + 1.0) * l2);
+  double l1 = fm::log1p(drho * ir), l2 = fm::log1p(dp * ip);
+  ds = s0 * fm::expm1(c.a_q * l1 + (c.b_q + 1.0) * l2);
   // entropy variables at u' = u + g d (Eq. (25)) from log q' = log q + a_q l1 + b_q l2
-  double q1 = exp(lnq + c.a_q * l1 + c.b_q * l2);
+  double q1 = fm::exp(lnq + c.a_q * l1 + c.b_q * l2);
   double p1 = c.gm1 * (u[NC - 1] - 0.5 * mm * ir) + dp;
   double v2 = 0.0, vd = 0.0;
 #pragma unroll
@@ -935,7 +956,37 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
   const double eps = 2.220446049250313e-16;
   const double est = st->est;
   st->iters += 1;
-  if (st->phase == 0) {
+  if (st->phase == 0) {  // f, f' at g = 1
+    double f1 = tot[0] - est, df1 = tot[1] - est;
+    double floor = 64.0 * eps * st->Sabs;
+    if (fabs(f1) <= floor && fabs(df1) <= floor) {
+      st->g = 1.0;
+      st->done = 1;
+      return;
+    }
+    double gn = df1 > 0.0 ? 1.0 - f1 / df1 : -1.0;
+    if (gn > 0.5 && gn < 1.5) {
+      st->phase = 3;
+      st->dS_last = tot[0];
+      st->f_last = f1;
+      st->df_last = df1;
+      if (f1 < 0.0) {
+        st->lo = 1.0;
+        st->flo = f1;
+      } else {
+        st->hi = 1.0;
+        st->fhi = f1;
+      }
+      st->ga = gn;
+      st->g = gn;
+      return;
+    }
+    st->phase = 4;  // bracketing path
+    st->ga = 0.5;
+    st->gb = 1.5;
+    return;
+  }
+  if (st->phase == 4) {
     double flo = tot[0] - 0.5 * est, fhi = tot[3] - 1.5 * est;
     double floor = 64.0 * eps * st->Sabs;
     st->flo = flo;
@@ -988,7 +1039,7 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
     st->hi = st->ga;
     st->fhi = f;
   }
-  if (st->phase <= 2) {
+  if (st->phase != 3) {  // a bracket from phase 4, 1 or 2
     // quadratic model f ~ c g (g - g*) through (0,0), (lo, flo), (hi, fhi)
     double lo = st->lo, hi = st->hi;
     double cq = (st->fhi / hi - st->flo / lo) / (hi - lo);
@@ -1080,3 +1131,32 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 #include "visc.cuh"
 #include "rrk_vjp.cuh"
 #include "hybrid.cuh"
+
+namespace esplit {
+
+// elementwise evaluation of the table-driven functions (fn 0..3: log, log1p,
+// exp, expm1) or of the CUDA library ones (fn 4..7), for their accuracy tests
+__global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* __restrict__ y, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = x[i], out;
+  switch (fn) {
+    case 0: out = fm::log(v); break;
+    case 1: out = fm::log1p(v); break;
+    case 2: out = fm::exp(v); break;
+    case 3: out = fm::expm1(v); break;
+    case 4: out = ::log(v); break;
+    case 5: out = ::log1p(v); break;
+    case 6: out = ::exp(v); break;
+    default: out = ::expm1(v); break;
+  }
+  y[i] = out;
+}
+
+int launch_math_eval(int fn, const double* x, double* y, size_t n, cudaStream_t s) {
+  if (n == 0) return 0;
+  math_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(fn, x, y, n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace esplit

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "dual.cuh"
+#include "fmath.cuh"
 
 namespace esplit {
 
@@ -69,17 +70,17 @@ __host__ inline Phys<T> make_phys(double gam, double beta, double R, double mu, 
   return c;
 }
 
-__device__ __forceinline__ double t_log(double x) { return log(x); }
+__device__ __forceinline__ double t_log(double x) { return fm::log(x); }
 __device__ __forceinline__ float t_log(float x) { return logf(x); }
-__device__ __forceinline__ double t_exp(double x) { return exp(x); }
+__device__ __forceinline__ double t_exp(double x) { return fm::exp(x); }
 __device__ __forceinline__ float t_exp(float x) { return expf(x); }
 __device__ __forceinline__ double t_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float t_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double t_abs(double x) { return fabs(x); }
 __device__ __forceinline__ float t_abs(float x) { return fabsf(x); }
-__device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ double t_expm1(double x) { return fm::expm1(x); }
 __device__ __forceinline__ float t_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ double t_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ double t_log1p(double x) { return fm::log1p(x); }
 __device__ __forceinline__ float t_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ bool t_isfinite(double x) { return ::isfinite(x); }
 __device__ __forceinline__ bool t_isfinite(float x) { return ::isfinite(x); }
