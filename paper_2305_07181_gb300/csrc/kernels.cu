@@ -134,16 +134,36 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// nu . F(u) = sum_i nu_i F^{I(i)}(u), Eq. (5)
+template <int D, typename TN>
+__device__ __forceinline__ void normal_flux(const Node<double, D>& n, const TN* nuv, double* out) {
+  double vn = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) vn += (double)nuv[i] * n.V[i];
+  double mn = n.rho * vn;
+  out[0] = mn;
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[1 + j] = mn * n.V[j] + n.p * (double)nuv[j];
+  out[D + 1] = (n.e + n.p) * vn;
+}
+
 // ---------------------------------------------------------------------------
 // facet kernel: one thread per coincident facet-node pair (k, m) ~ (v, n).
 //   G = sum_i nu_i F*_i(u_km, u_vn) + |nu|/2 X|L|SX^T (w_km - w_vn)
 //   sat_k,m = -G / H_k,m ;  sat_v,n = +G / H_v,n       (Eqs. (43), (69))
+// For a side whose element takes the entropy-split volume term, the facet
+// part of its volume term, H^-1 sum_i E_i f_i = nu . f(u) / H at the node
+// (M_i = H^-1 E_i - beta/(beta+1) D_i, see the split volume kernel), is added
+// here too, next to the two-point flux it cancels against:
+//   ef_mode 0: no side (Hadamard scheme), 1: both sides (split scheme),
+//   2: sides whose hybrid flag is 0.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
 __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u, const int2* __restrict__ fp,
                                                    int n_pairs, const double* __restrict__ nu,
                                                    const double* __restrict__ J, double* __restrict__ sat,
-                                                   Phys<T> c, int dissipation, int* __restrict__ status) {
+                                                   Phys<T> c, int dissipation, int* __restrict__ status,
+                                                   int ef_mode, const unsigned char* __restrict__ hflags) {
   constexpr int NC = D + 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_pairs) return;
@@ -190,10 +210,19 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
   }
   double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
   double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+  double ek[NC], ev[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) ek[q] = ev[q] = 0.0;
+  if (ef_mode != 0) {
+    bool sk = ef_mode == 1 || hflags[k] == 0;
+    bool sv = ef_mode == 1 || hflags[v] == 0;
+    if (sk) normal_flux<D>(nk, nuv, ek);
+    if (sv) normal_flux<D>(nv, nuv, ev);
+  }
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    sat[((size_t)k * NC + q) * NS + s] = -(double)G[q] * ihk;
-    sat[((size_t)v * NC + q) * NS + s2] = (double)G[q] * ihv;
+    sat[((size_t)k * NC + q) * NS + s] = (ek[q] - (double)G[q]) * ihk;
+    sat[((size_t)v * NC + q) * NS + s2] = ((double)G[q] - ev[q]) * ihv;
   }
 }
 
@@ -204,8 +233,9 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 //   r = H^-1 sum_i E_i f_i - beta/(beta+1) sum_i D_i f_i
 //       - 1/(beta+1) sum_i A~_i (D_i w) + sat:
 // only the D_i are applied (one operator entry serves the flux and the
-// entropy-variable contraction), and the E_i term is pointwise at the facet
-// nodes (E_i = diag(nu_i) there).
+// entropy-variable contraction); the E_i term is pointwise at the facet
+// nodes (E_i = diag(nu_i) there) and the facet kernel adds it to the facet
+// contributions.
 //
 // Node states, fluxes, entropy variables and the A~_i products are float64 in
 // both precision modes.  T = double: plain float64 contractions.  T = float
@@ -256,8 +286,8 @@ template <typename T, int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
-    const double* __restrict__ nu, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
-    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
+    const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
+    int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -382,23 +412,10 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double kf = c64.beta * c64.inv_bp1;
     double res[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) res[q] = -kf * accd[q] - c64.inv_bp1 * nonc[q];
-    if (sl >= 0) {
-      // H^-1 sum_i E_i f_i at the facet node, and the facet contributions
-      double nv[D];
-#pragma unroll
-      for (int i = 0; i < D; ++i) nv[i] = __ldg(&nu[((size_t)e * NS + sl) * D + i]);
-      const double ih = 1.0 / Hm;
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        double ef = 0.0;
-#pragma unroll
-        for (int i = 0; i < D; ++i) ef += nv[i] * sm.rf[el][i][q][m];
-        res[q] += ef * ih + __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
-      }
-    }
-#pragma unroll
     for (int q = 0; q < NC; ++q) {
+      // the facet contributions include H^-1 sum_i E_i f_i (added by the facet kernel)
+      res[q] = -kf * accd[q] - c64.inv_bp1 * nonc[q];
+      if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
       r[((size_t)e * NC + q) * NP + m] = res[q];
     }
     if (prod) {
@@ -562,8 +579,9 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     ProfScope ps(c, PG_FACE, s);
     // facet terms are O(1/h) and cancel against the volume's boundary part:
     // they stay float64 in both precision modes
+    const int ef_mode = c->prm.scheme == ESPLIT_SCHEME_SPLIT ? 1 : (c->prm.scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0);
     face_kernel<double, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
-                                             c->prm.dissipation, c->b.status);
+                                             c->prm.dissipation, c->b.status, ef_mode, c->b.hflags);
     c->launches++;
   }
   int np_used = 0;
@@ -576,7 +594,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, c->b.nu, sat, lsplit,
+    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit,
                                                              n_split, ph, ph64, c->b.status,
                                                              prod ? prod + np_used : nullptr);
     c->launches++;
