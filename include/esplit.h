@@ -204,8 +204,12 @@ int esplit_rrk_step(esplit_ctx* ctx, double* u_dev, double dt, double* g_out, es
 int esplit_rrk_step_host(esplit_ctx* ctx, double* u_host, double dt, double* g_out, esplit_stepinfo* info,
                          void* stream);
 
-/* Reverse mode of the residual: grad_dev = (d dudt / d u)^T cot_dev.
- *   u_dev, cot_dev, grad_dev: [n_e][n_c][n_p] float64 device buffers. */
+/* Reverse mode of the residual: grad_dev = (d dudt / d u)^T cot_dev, for the
+ * entropy-split scheme (Eq. (100)) with the EC SATs, the interface
+ * dissipation of Eq. (69) and, when on, the viscous BO terms of Eqs.
+ * (83)-(85), (96); float64 whatever the precision setting.  Other schemes:
+ * ESPLIT_ERR_UNSUPPORTED.  u_dev, cot_dev, grad_dev: [n_e][n_c][n_p]
+ * float64 device buffers; grad_dev must not alias the others. */
 int esplit_residual_vjp(esplit_ctx* ctx, const double* u_dev, const double* cot_dev,
                         double* grad_dev, void* stream);
 
@@ -219,7 +223,7 @@ int esplit_entropy_grad(esplit_ctx* ctx, const double* u_dev, double* grad_dev, 
  * u_{n+1} to the cotangent ubar_dev of u_n, including the dependence of the
  * relaxation parameter on the state through the implicit function theorem
  * (dg = -(f_u du + f_d dd + f_est dest)/f_g).  Entropy-split scheme (with or
- * without dissipation), inviscid.  Scratch: 12 state-sized device arrays owned
+ * without dissipation and viscous terms).  Scratch: 12 state-sized device arrays owned
  * by the context, allocated on the first call.  Synchronises `stream`; the
  * step's g is returned through g_out (may be NULL). */
 int esplit_rrk_step_vjp(esplit_ctx* ctx, const double* u_dev, double dt, const double* ubar_next_dev,

@@ -158,7 +158,7 @@ void esplit_destroy(esplit_ctx* c) {
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
-                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va};
+                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.vfb, b.vfs, b.vus};
   for (void* p : ps) dfree(p);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
@@ -293,6 +293,9 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   dalloc(c, &c->b.fv, 0);
   dalloc(c, &c->b.vsat, 0);
   dalloc(c, &c->b.va, 0);
+  dalloc(c, &c->b.vfb, 0);
+  dalloc(c, &c->b.vfs, 0);
+  dalloc(c, &c->b.vus, 0);
   c->n_split = n_e;
   c->n_had = 0;
   c->have_mesh = true;
@@ -575,6 +578,28 @@ int esplit_rrk_step_host(esplit_ctx* c, double* u_host, double dt, double* g_out
   return ESPLIT_OK;
 }
 
+// (d dudt/du)^T cot: inviscid split terms, then the viscous terms when on
+static int vjp_impl(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s) {
+  int rc = esplit::launch_residual_vjp(c, u, cot, grad, s);
+  if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
+  if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("vjp launch: ") + cudaGetErrorString(cudaGetLastError()));
+  if (c->prm.viscous) {
+    if ((rc = ensure_viscous(c))) return rc;
+    if (!c->b.vfb) {
+      size_t per = (size_t)c->n_e * c->n_c;
+      if ((rc = dalloc(c, &c->b.vfb, per * c->dim * c->n_p))) return rc;
+      if ((rc = dalloc(c, &c->b.vfs, per * c->dim * c->n_slot))) return rc;
+      if ((rc = dalloc(c, &c->b.vus, per * c->n_slot))) return rc;
+    }
+    rc = esplit::launch_viscous_vjp(c, u, cot, grad, s);
+    if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
+    if (rc)
+      return fail(c, ESPLIT_ERR_CUDA, std::string("viscous vjp launch: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  c->last_stream = s;
+  return ESPLIT_OK;
+}
+
 int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, void* stream) {
   int rc = check_ready(c);
   if (rc) return rc;
@@ -582,14 +607,9 @@ int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
   if (grad == u || grad == cot) return fail(c, ESPLIT_ERR_ARG, "grad must not alias u or cot");
   if (c->prm.scheme != ESPLIT_SCHEME_SPLIT)
     return fail(c, ESPLIT_ERR_UNSUPPORTED, "the residual VJP is built for the entropy-split scheme");
-  if (c->prm.viscous) return fail(c, ESPLIT_ERR_UNSUPPORTED, "viscous VJP not built");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
-  rc = esplit::launch_residual_vjp(c, u, cot, grad, s);
-  if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
-  if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("vjp launch: ") + cudaGetErrorString(cudaGetLastError()));
-  c->last_stream = s;
-  return ESPLIT_OK;
+  return vjp_impl(c, u, cot, grad, s);
 }
 
 int esplit_entropy_grad(esplit_ctx* c, const double* u, double* grad, void* stream) {
@@ -609,8 +629,8 @@ int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double*
   if (!u || !ubar1 || !ubar0) return fail(c, ESPLIT_ERR_ARG, "null pointer");
   if (ubar0 == u || ubar0 == ubar1) return fail(c, ESPLIT_ERR_ARG, "ubar0 must not alias u or ubar1");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ESPLIT_ERR_ARG, "dt must be positive and finite");
-  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->prm.viscous)
-    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the step reverse is built for the inviscid entropy-split scheme");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the step reverse is built for the entropy-split scheme");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
   size_t n = (size_t)c->n_e * c->n_c * c->n_p;
@@ -680,7 +700,7 @@ int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double*
     double c_d = dt * B[i], c_e = dt * B[i] * estbar, c_u = (i < 3) ? A[i + 1] * dt : 0.0;
     if (esplit::launch_rrk_vjp_stage(c, Ui, Rs[i], dbar_keep, (i < 3) ? Ubar : nullptr, c_d, c_e, c_u, rbar, extra, s))
       return fail(c, ESPLIT_ERR_CUDA, "stage-reverse launch");
-    if (esplit::launch_residual_vjp(c, Ui, rbar, tmp, s)) return fail(c, ESPLIT_ERR_CUDA, "residual vjp launch");
+    if ((rc = vjp_impl(c, Ui, rbar, tmp, s))) return rc;
     if (esplit::launch_axpy(c, extra, 1.0, tmp, Ubar, n, s) || esplit::launch_axpy(c, ubar0, 1.0, Ubar, ubar0, n, s))
       return fail(c, ESPLIT_ERR_CUDA, "axpy launch");
   }

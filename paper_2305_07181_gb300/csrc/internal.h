@@ -68,6 +68,10 @@ struct Buffers {
   double* fv = nullptr;
   double* vsat = nullptr;
   double* va = nullptr;
+  // viscous reverse-mode scratch: [n_e][d][n_c][n_p], [n_e][d][n_c][n_slot], [n_e][n_c][n_slot]
+  double* vfb = nullptr;
+  double* vfs = nullptr;
+  double* vus = nullptr;
   double* vjp_work = nullptr;    // 12 state-sized arrays for the RRK step reverse
   double* host_u = nullptr;    // device copies for the host-buffer entry point
   double* host_r = nullptr;
@@ -124,6 +128,7 @@ int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partia
 int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial,
                         double* part = nullptr, int width = 2);
 int launch_viscous(esplit_ctx* c, const double* u, double* r, cudaStream_t s);
+int launch_viscous_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);
 int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s);
 int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, double* out, size_t n, cudaStream_t s);
 int launch_stage(esplit_ctx* c, const double* un, const double* r, double a_dt, double b_dt, int first,

@@ -1147,6 +1147,7 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 
 #include "vjp.cuh"
 #include "visc.cuh"
+#include "visc_vjp.cuh"
 #include "rrk_vjp.cuh"
 #include "hybrid.cuh"
 

@@ -66,3 +66,39 @@ def test_entropy_gradient_through_50_steps_closed_form(lib):
     assert err <= 1e-8
     assert abs(s.entropy(uN) - s.entropy(ud)) <= 1e-13 * abs(s.entropy(ud)) * 50
     s.close()
+
+
+def test_step_vjp_viscous_central_differences(lib):
+    """The step reverse with the BO viscous terms (Navier-Stokes, 2D p = 2 and
+    the Taylor-Green state on 48 tetrahedra)."""
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import periodic_tet_mesh
+    cases = []
+    op = tri_operator(2)
+    m = periodic_tri_mesh(op, 4, 10.0, 0.05)
+    cases.append((op, m, states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 17), 0.01))
+    op3 = tet_operator(2)
+    m3 = periodic_tet_mesh(op3, 2, 2 * np.pi, 0.02)
+    cases.append((op3, m3, states.taylor_green(m3), 1.0 / 1600.0))
+    rng = np.random.default_rng(18)
+    for op, m, u0, mu in cases:
+        dt = states.cfl_timestep(m, u0, 0.1)
+        s = lib.Solver(op, m, lib.Params(dissipation=True, viscous=True, mu=mu))
+        u = s.to_device(u0)
+        ubar1 = s.to_device(rng.normal(size=u0.shape))
+        ubar0, g = s.rrk_step_vjp(u, dt, ubar1)
+
+        def phi(x):
+            y = x.clone()
+            s.rrk_step(y, dt)
+            return y
+
+        h = 1e-6
+        for _ in range(4):
+            v = rng.normal(size=u0.shape)
+            v /= np.linalg.norm(v)
+            vd = s.to_device(v)
+            fd = float(((phi(u + h * vd) - phi(u - h * vd)) / (2 * h) * ubar1).sum())
+            ad = float((ubar0 * vd).sum())
+            assert abs(fd - ad) <= 2e-6 * max(1.0, abs(ad)), (fd, ad)
+        s.close()

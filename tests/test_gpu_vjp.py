@@ -89,3 +89,65 @@ def test_vjp_rejects_unsupported_scheme(lib):
         s.residual_vjp(u, u.clone())
     assert ei.value.code == lib.capi.ESPLIT_ERR_UNSUPPORTED
     s.close()
+
+
+def oracle_vjp_visc(u, cot, op, m, prm, diss=True):
+    from oracle import residual as R
+    x = torch.as_tensor(u).clone().requires_grad_(True)
+    r = R.residual(x, op, m, prm, dissipation=diss, viscous=True)
+    (g,) = torch.autograd.grad(r, x, grad_outputs=torch.as_tensor(cot))
+    return g.numpy()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("heat", [False, True])
+def test_viscous_vjp_matches_oracle_adjoint(lib, p, heat):
+    from oracle.physics import Params as OP
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 5, 10.0, 0.05)
+    u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-2, 50 + p)
+    cot = np.random.default_rng(5).normal(size=u.shape)
+    s = lib.Solver(op, m, lib.Params(dissipation=True, viscous=True, mu=0.05, heat_flux=heat))
+    g = s.residual_vjp(s.to_device(u), s.to_device(cot)).cpu().numpy()
+    go = oracle_vjp_visc(u, cot, op, m, OP(mu=0.05, heat_flux=heat))
+    err = np.abs(g - go).max() / np.abs(go).max()
+    print(f"viscous vjp p={p} heat={heat} rel err {err:.2e}")
+    assert err <= 1e-11
+    s.close()
+
+
+def test_viscous_vjp_tetrahedra(lib):
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import periodic_tet_mesh
+    from oracle.physics import Params as OP
+    op = tet_operator(2)
+    m = periodic_tet_mesh(op, 2, 2 * np.pi, 0.02)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=12)
+    cot = np.random.default_rng(6).normal(size=u.shape)
+    s = lib.Solver(op, m, lib.Params(dissipation=True, viscous=True, mu=0.05))
+    g = s.residual_vjp(s.to_device(u), s.to_device(cot)).cpu().numpy()
+    go = oracle_vjp_visc(u, cot, op, m, OP(mu=0.05))
+    err = np.abs(g - go).max() / np.abs(go).max()
+    print(f"viscous vjp tets rel err {err:.2e}")
+    assert err <= 1e-11
+    s.close()
+
+
+def test_viscous_vjp_central_differences(lib):
+    op = tri_operator(3)
+    m = periodic_tri_mesh(op, 6, 10.0, 0.05)
+    u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 14)
+    rng = np.random.default_rng(41)
+    s = lib.Solver(op, m, lib.Params(dissipation=True, viscous=True, mu=0.01))
+    ud = s.to_device(u)
+    cot = s.to_device(rng.normal(size=u.shape))
+    g = s.residual_vjp(ud, cot)
+    h = 1e-6
+    for _ in range(10):
+        d = rng.normal(size=u.shape)
+        d /= np.linalg.norm(d)
+        dd = s.to_device(d)
+        fd = float(((s.residual(ud + h * dd) - s.residual(ud - h * dd)) / (2 * h) * cot).sum())
+        ad = float((g * dd).sum())
+        assert abs(fd - ad) <= 1e-6 * max(1.0, abs(ad))
+    s.close()
