@@ -383,19 +383,14 @@ static int residual_impl(esplit_ctx* c, const double* u, double* r, cudaStream_t
   if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
     return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
   const bool visc = c->prm.viscous != 0;
+  if (visc && !c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
   // with viscous terms the entropy production is taken from the complete
   // residual after the viscous passes
   int rc = esplit::launch_residual(c, u, r, s, visc ? nullptr : prod, visc ? nullptr : npart);
   if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
   if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString(cudaGetLastError()));
-  if (visc) {
-    if (!c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
-    rc = esplit::launch_viscous(c, u, r, s);
-    if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
-    if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("viscous launch: ") + cudaGetErrorString(cudaGetLastError()));
-    if (prod && esplit::launch_entropy_rate(c, u, r, s, npart, prod, 1))
-      return fail(c, ESPLIT_ERR_CUDA, "entropy-production launch");
-  }
+  if (visc && prod && esplit::launch_entropy_rate(c, u, r, s, npart, prod, 1))
+    return fail(c, ESPLIT_ERR_CUDA, "entropy-production launch");
   c->last_stream = s;
   return ESPLIT_OK;
 }

@@ -127,7 +127,6 @@ int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, d
 int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache = nullptr);
 int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial,
                         double* part = nullptr, int width = 2);
-int launch_viscous(esplit_ctx* c, const double* u, double* r, cudaStream_t s);
 int launch_viscous_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);
 int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s);
 int launch_axpy(esplit_ctx* c, const double* x, double a, const double* y, double* out, size_t n, cudaStream_t s);

@@ -21,6 +21,7 @@
 
 #include "internal.h"
 #include "phys.cuh"
+#include "visc_flux.cuh"
 
 namespace esplit {
 
@@ -158,12 +159,13 @@ __device__ __forceinline__ void normal_flux(const Node<double, D>& n, const TN* 
 //   ef_mode 0: no side (Hadamard scheme), 1: both sides (split scheme),
 //   2: sides whose hybrid flag is 0.
 // ---------------------------------------------------------------------------
-template <typename T, int D>
+template <typename T, int D, bool VISC>
 __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u, const int2* __restrict__ fp,
                                                    int n_pairs, const double* __restrict__ nu,
                                                    const double* __restrict__ J, double* __restrict__ sat,
                                                    Phys<T> c, int dissipation, int* __restrict__ status,
-                                                   int ef_mode, const unsigned char* __restrict__ hflags) {
+                                                   int ef_mode, const unsigned char* __restrict__ hflags,
+                                                   int visc_heat, double* __restrict__ ah) {
   constexpr int NC = D + 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_pairs) return;
@@ -218,6 +220,23 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
     bool sv = ef_mode == 1 || hflags[v] == 0;
     if (sk) normal_flux<D>(nk, nuv, ek);
     if (sv) normal_flux<D>(nv, nuv, ev);
+  }
+  if (VISC) {
+    // BO lift vectors of both sides, a = K~(u)^T (nu (w_k - w_v)), divided by H
+    double b[D][NC], ak[D][NC], av[D][NC];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) b[i][q] = nuv[i] * (nk.W[q] - nv.W[q]);
+    visc_flux_transpose<double, D>(nk, c, visc_heat, b, ak);
+    visc_flux_transpose<double, D>(nv, c, visc_heat, b, av);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        ah[(((size_t)k * D + i) * NC + q) * NS + s] = ak[i][q] * ihk;
+        ah[(((size_t)v * D + i) * NC + q) * NS + s2] = av[i][q] * ihv;
+      }
   }
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
@@ -282,12 +301,13 @@ struct SplitSmem<double, D, NP, EB> {
   double rw[EB][D + 2][NP];
 };
 
-template <typename T, int D, int NP, int EB>
+template <typename T, int D, int NP, int EB, bool VISC>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
-    int* __restrict__ status, double* __restrict__ prod) {
+    int* __restrict__ status, double* __restrict__ prod, int visc_heat, const double* __restrict__ nu,
+    const double* __restrict__ ah, double* __restrict__ fvs) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -339,6 +359,9 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     __syncthreads();
   }
   double hw = 0.0;
+  const int sl = c_ref.node_slot[m];
+  const T* op = ops + (size_t)e * (2 * D * NP * NP);
+  double res[NC], Fp[D][NC], Hm = 0.0;
   if (active) {
     T acc[NC], g[D][NC];
 #pragma unroll
@@ -347,7 +370,6 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     for (int i = 0; i < D; ++i)
 #pragma unroll
       for (int q = 0; q < NC; ++q) g[i][q] = T(0);
-    const T* op = ops + (size_t)e * (2 * D * NP * NP);
     const float* oplo = F64 ? nullptr : opslo + (size_t)e * (2 * D * NP * NP);
     // float32 sums: second accumulators of the compensated dot products
     T cacc[NC], cg[D][NC];
@@ -407,17 +429,72 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
 #pragma unroll
       for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
     }
-    int sl = c_ref.node_slot[m];
-    double Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
+    Hm = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
     const double kf = c64.beta * c64.inv_bp1;
-    double res[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       // the facet contributions include H^-1 sum_i E_i f_i (added by the facet kernel)
       res[q] = -kf * accd[q] - c64.inv_bp1 * nonc[q];
       if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
-      r[((size_t)e * NC + q) * NP + m] = res[q];
     }
+    if constexpr (F64 && VISC) {
+      {
+        // viscous flux from the gradients just formed (gd = D_i w), plus the
+        // folded BO lift a/(2H) at the facet nodes; F^V kept for the flux jump
+        visc_flux<double, D>(nd, c64, visc_heat, gd, Fp);
+        if (sl >= 0) {
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              size_t ix = (((size_t)e * D + i) * NC + q) * NS + sl;
+              fvs[ix] = Fp[i][q];
+              Fp[i][q] += 0.5 * __ldg(&ah[ix]);
+            }
+        }
+      }
+    }
+  }
+  if constexpr (F64 && VISC) {
+    {
+      __syncthreads();      // every thread is done with the fluxes in sm.rf
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+          for (int q = 0; q < NC; ++q) sm.rf[el][i][q][m] = Fp[i][q];
+      }
+      __syncthreads();
+      if (active) {
+        // sum_i D_i (F^V_i + a_i/(2H)) - sum_i nu_i a_i/(2H^2) at the facet nodes
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll 4
+          for (int n = 0; n < NP; ++n) {
+            double dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) res[q] += dt * sm.rf[el][i][q][n];
+          }
+        }
+        if (sl >= 0) {
+          const double ih = 1.0 / Hm;
+          double nv[D];
+#pragma unroll
+          for (int i = 0; i < D; ++i) nv[i] = __ldg(&nu[((size_t)e * NS + sl) * D + i]);
+#pragma unroll
+          for (int q = 0; q < NC; ++q) {
+            double corr = 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) corr += nv[i] * __ldg(&ah[(((size_t)e * D + i) * NC + q) * NS + sl]);
+            res[q] -= 0.5 * corr * ih;
+          }
+        }
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) r[((size_t)e * NC + q) * NP + m] = res[q];
     if (prod) {
 #pragma unroll
       for (int q = 0; q < NC; ++q) hw += nd.W[q] * res[q];
@@ -560,6 +637,12 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
   }
 }
 
+}  // namespace esplit
+
+#include "visc.cuh"
+
+namespace esplit {
+
 template <int NP>
 struct VolCfg {
   static constexpr int EB_SPLIT = (256 / NP) > 0 ? (256 / NP) : 1;
@@ -580,10 +663,19 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     // facet terms are O(1/h) and cancel against the volume's boundary part:
     // they stay float64 in both precision modes
     const int ef_mode = c->prm.scheme == ESPLIT_SCHEME_SPLIT ? 1 : (c->prm.scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0);
-    face_kernel<double, D><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
-                                             c->prm.dissipation, c->b.status, ef_mode, c->b.hflags);
+    const int visc_heat = c->prm.viscous ? c->prm.heat_flux : -1;
+    if (visc_heat >= 0)
+      face_kernel<double, D, true><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
+                                                     c->prm.dissipation, c->b.status, ef_mode, c->b.hflags,
+                                                     visc_heat, c->b.va);
+    else
+      face_kernel<double, D, false><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
+                                                      c->prm.dissipation, c->b.status, ef_mode, c->b.hflags, 0,
+                                                      nullptr);
     c->launches++;
   }
+  constexpr bool F64 = std::is_same<T, double>::value;
+  const bool visc = c->prm.viscous != 0;
   int np_used = 0;
   int scheme = c->prm.scheme;
   int n_split = scheme == ESPLIT_SCHEME_SPLIT ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_split : 0);
@@ -594,9 +686,15 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_kernel<T, D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit,
-                                                             n_split, ph, ph64, c->b.status,
-                                                             prod ? prod + np_used : nullptr);
+    // the float64 split kernel also forms the viscous volume terms (it has D_i w)
+    if (visc && F64)
+      split_volume_kernel<T, D, NP, EB, true><<<nb, EB * NP, 0, s>>>(
+          u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
+          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv);
+    else
+      split_volume_kernel<T, D, NP, EB, false><<<nb, EB * NP, 0, s>>>(
+          u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
+          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr);
     c->launches++;
     np_used += nb;
   }
@@ -616,6 +714,15 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
         u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
+  }
+  if (visc) {
+    ProfScope ps(c, PG_VISC, s);
+    // viscous volume terms of the elements the float64 split kernel did not take
+    if (!F64)
+      viscous_volume_np<D, NP>(c, u, r, nullptr, c->n_e, s);
+    else if (n_had > 0)
+      viscous_volume_np<D, NP>(c, u, r, lhad, n_had, s);
+    viscous_jump<D>(c, r, s);
   }
   if (n_partial) *n_partial = np_used;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -674,8 +781,8 @@ int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStrea
   c->prof = false;
   int rc = c->prm.precision == ESPLIT_FP32_BULK ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
                                                  : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
-  // viscous terms use the context's viscous scratch, allocated when they were switched on
-  if (rc == 0 && c->prm.viscous) rc = launch_viscous(c, u, r, s);
+  // viscous terms (inside the residual launch) use the context's viscous
+  // scratch, allocated when they were switched on
   c->prof = prof;
   return rc;
 }
@@ -1146,7 +1253,6 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 }  // namespace esplit
 
 #include "vjp.cuh"
-#include "visc.cuh"
 #include "visc_vjp.cuh"
 #include "rrk_vjp.cuh"
 #include "hybrid.cuh"
