@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
     int* __restrict__ status, double* __restrict__ prod, int visc_heat, const double* __restrict__ nu,
-    const double* __restrict__ ah, double* __restrict__ fvs) {
+    const double* __restrict__ ah, double* __restrict__ fvs, const double* __restrict__ ops64) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -361,6 +361,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
   double hw = 0.0;
   const int sl = c_ref.node_slot[m];
   const T* op = ops + (size_t)e * (2 * D * NP * NP);
+  const double* op64 = VISC ? ops64 + (size_t)e * (2 * D * NP * NP) : nullptr;
   double res[NC], Fp[D][NC], Hm = 0.0;
   if (active) {
     T acc[NC], g[D][NC];
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       res[q] = -kf * accd[q] - c64.inv_bp1 * nonc[q];
       if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
     }
-    if constexpr (F64 && VISC) {
+    if constexpr (VISC) {
       {
         // viscous flux from the gradients just formed (gd = D_i w), plus the
         // folded BO lift a/(2H) at the facet nodes; F^V kept for the flux jump
@@ -455,7 +456,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       }
     }
   }
-  if constexpr (F64 && VISC) {
+  if constexpr (VISC) {  // float64 in both precision modes
     {
       __syncthreads();      // every thread is done with the fluxes in sm.rf
       if (active) {
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
         for (int i = 0; i < D; ++i) {
 #pragma unroll 4
           for (int n = 0; n < NP; ++n) {
-            double dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
+            double dt = __ldg(&op64[((D + i) * NP + n) * NP + m]);
 #pragma unroll
             for (int q = 0; q < NC; ++q) res[q] += dt * sm.rf[el][i][q][n];
           }
@@ -674,7 +675,6 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
                                                       nullptr);
     c->launches++;
   }
-  constexpr bool F64 = std::is_same<T, double>::value;
   const bool visc = c->prm.viscous != 0;
   int np_used = 0;
   int scheme = c->prm.scheme;
@@ -686,15 +686,15 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     constexpr int EB = VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    // the float64 split kernel also forms the viscous volume terms (it has D_i w)
-    if (visc && F64)
+    // the split kernel also forms the viscous volume terms (it has D_i w)
+    if (visc)
       split_volume_kernel<T, D, NP, EB, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
-          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv);
+          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64);
     else
       split_volume_kernel<T, D, NP, EB, false><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
-          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr);
+          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr);
     c->launches++;
     np_used += nb;
   }
@@ -717,11 +717,8 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   }
   if (visc) {
     ProfScope ps(c, PG_VISC, s);
-    // viscous volume terms of the elements the float64 split kernel did not take
-    if (!F64)
-      viscous_volume_np<D, NP>(c, u, r, nullptr, c->n_e, s);
-    else if (n_had > 0)
-      viscous_volume_np<D, NP>(c, u, r, lhad, n_had, s);
+    // viscous volume terms of the elements the split kernel did not take
+    if (n_had > 0) viscous_volume_np<D, NP>(c, u, r, lhad, n_had, s);
     viscous_jump<D>(c, r, s);
   }
   if (n_partial) *n_partial = np_used;

@@ -12,9 +12,10 @@
 //        + jump / H:
 // one contraction instead of two.  The pieces are computed where their inputs
 // already are: a_i/H by the facet kernel (it has both nodal states), F^V and
-// the divergence by the entropy-split volume kernel (it has D_i w) or, for
-// Hadamard-form and float32 elements, by visc_volume_kernel below; the flux
-// jump needs F^V of both sides and runs last (visc_jump_kernel).  The facet
+// the divergence by the entropy-split volume kernel (it has D_i w; float64 in
+// both precision modes) or, for Hadamard-form elements, by visc_volume_kernel
+// below; the flux jump needs F^V of both sides and runs last
+// (visc_jump_kernel).  The facet
 // arrays: ah [n_e][d][n_c][n_slot] (a/H), fvs [n_e][d][n_c][n_slot] (F^V at
 // the facet nodes).  Included by kernels.cu.
 #pragma once
