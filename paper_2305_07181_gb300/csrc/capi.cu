@@ -544,7 +544,8 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     info->S_before = st.S0;
     info->iterations = st.iters;
     info->status = status;
-    // entropy change at the last evaluated g (within 4 eps g of the returned g)
+    // entropy change at the returned g (the last evaluation, carried to g to
+    // first order when the final Newton correction was accepted without one)
     info->S_after = st.S0 + (st.phase == 3 ? st.dS_last : 0.0);
     for (int i = 0; i < 4; ++i) info->stage_rate[i] = e_stage[i];
   }

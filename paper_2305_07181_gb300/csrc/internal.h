@@ -26,6 +26,7 @@ struct RootState {
   double S0, Sabs, est;      // 1^T H s(u_n), 1^T H |s(u_n)|, dt sum b_i e_i
   double g, ga, gb, lo, hi, flo, fhi;  // ga, gb: next evaluation points (gb < 0: one point)
   double f_last, df_last, dS_last;
+  double dg_last;             // previous Newton step (0: none yet)
   int phase, done, iters, status;
 };
 

@@ -282,6 +282,44 @@ struct SplitSmem {
   T swl[EB][D + 2][NP];
 };
 
+// v = hi + lo with float hi (v's first 24 significant bits, truncated) and
+// float lo (the remaining 29 bits, rounded to 24), by integer operations on
+// the bit patterns: on GB300 a float64<->float32 conversion occupies the FP64
+// pipe, which the kernel's pointwise float64 work already saturates.  |v| below
+// 2^-126 gives hi = lo = 0; |v| below 2^-74 loses lo (both far below the
+// round-off of the float64 terms these variations are added to).
+__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7ffULL);  // biased exponent
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  if (e <= 1023 - 127) {
+    hi = 0.0f;
+    lo = 0.0f;
+    return;
+  }
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFULL;
+  hi = __uint_as_float(sgn | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(mant >> 29));
+  const int E = e - 1075;  // weight of the lowest mantissa bit
+  if (E < -126) {
+    lo = 0.0f;
+    return;
+  }
+  const float lf = __uint2float_rn((unsigned)(mant & 0x1FFFFFFFULL));
+  lo = __uint_as_float(sgn | __float_as_uint(__fmul_rn(lf, __uint_as_float((unsigned)(E + 127) << 23))));
+}
+
+// float -> double by the bit patterns (normal floats and zero; float
+// subnormals, far below the terms these sums are added to, give zero)
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(e - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
 // acc + cmp += (ah + al) (bh + bl), Dot2 step: exact product error by fmaf,
 // TwoSum for the addition; intrinsics keep the compiler from fusing them.
 __device__ __forceinline__ void dot2_step(float ah, float al, float bh, float bl, float& acc, float& cmp) {
@@ -342,18 +380,18 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
           f0[i][q] = sm.rf[el][i][q][0];
-          double v = sm.rf[el][i][q][m] - f0[i][q];
-          T hi = (T)v;
+          float hi, lo;
+          split_f64(sm.rf[el][i][q][m] - f0[i][q], hi, lo);
           sm.sf[el][i][q][m] = hi;
-          sm.sfl[el][i][q][m] = (T)(v - (double)hi);
+          sm.sfl[el][i][q][m] = lo;
         }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         w0[q] = sm.rw[el][q][0];
-        double v = sm.rw[el][q][m] - w0[q];
-        T hi = (T)v;
+        float hi, lo;
+        split_f64(sm.rw[el][q][m] - w0[q], hi, lo);
         sm.sw[el][q][m] = hi;
-        sm.swl[el][q][m] = (T)(v - (double)hi);
+        sm.swl[el][q][m] = lo;
       }
     }
     __syncthreads();
@@ -401,11 +439,21 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     }
     double accd[NC], gd[D][NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) accd[q] = F64 ? (double)acc[q] : (double)acc[q] + (double)cacc[q];
+    for (int q = 0; q < NC; ++q) {
+      if constexpr (F64)
+        accd[q] = acc[q];
+      else
+        accd[q] = widen_f32(acc[q]) + widen_f32(cacc[q]);
+    }
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) gd[i][q] = F64 ? (double)g[i][q] : (double)g[i][q] + (double)cg[i][q];
+      for (int q = 0; q < NC; ++q) {
+        if constexpr (F64)
+          gd[i][q] = g[i][q];
+        else
+          gd[i][q] = widen_f32(g[i][q]) + widen_f32(cg[i][q]);
+      }
     if constexpr (!F64) {
       // add back the node-0 values through the stored operators' row sums
       const double* rs = rows + (size_t)e * (2 * D * NP);
@@ -986,6 +1034,7 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
   st->done = 0;
   st->iters = 0;
   st->status = 0;
+  st->dg_last = 0.0;
 }
 
 // Entropy change s(u + g d) - s(u) and slope w(u + g d) . d at one node,
@@ -1101,6 +1150,7 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
       }
       st->ga = gn;
       st->g = gn;
+      st->dg_last = gn - 1.0;
       return;
     }
     st->phase = 4;  // bracketing path
@@ -1193,13 +1243,22 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
     return;
   }
   double gn = (df > 0.0) ? g - f / df : 0.5 * (st->lo + st->hi);
-  if (!(gn > st->lo && gn < st->hi)) gn = 0.5 * (st->lo + st->hi);
-  if (fabs(gn - g) <= 4.0 * eps * fabs(g) || st->hi - st->lo <= 4.0 * eps * st->hi ||
+  bool newton = df > 0.0 && gn > st->lo && gn < st->hi;
+  if (!newton) gn = 0.5 * (st->lo + st->hi);
+  const double dg = gn - g;
+  // quadratic convergence: with the contraction seen from the previous step,
+  // the next correction would be ~ (|dg| / dg_last^2) dg^2; below round-off,
+  // accept gn without another pass (entropy change carried to gn to first order)
+  const bool converged = newton && st->dg_last != 0.0 && fabs(dg) <= 1e-3 * fabs(st->dg_last) &&
+                         fabs(dg) * (dg / st->dg_last) * (dg / st->dg_last) <= 4.0 * eps * fabs(gn);
+  if (converged || fabs(dg) <= 4.0 * eps * fabs(g) || st->hi - st->lo <= 4.0 * eps * st->hi ||
       st->iters >= ROOT_EVALS_MAX) {
     st->g = gn;
+    st->dS_last = tot[0] + dg * tot[1];
     st->done = 1;
     return;
   }
+  st->dg_last = newton ? dg : 0.0;
   st->ga = gn;
 }
 
