@@ -238,7 +238,10 @@ def run_reference(args):
 
 def residual_sweep(es, device, flush):
     """Residual-only throughput (no RK / root solve) of the split and Hadamard
-    forms, FP64 and FP32-bulk, p = 1..4, on the same 32,768-triangle mesh."""
+    forms (Sjogreen-Yee flux, with dissipation), and of the Sec. 6
+    comparator, the Hadamard form with the Ismail-Roe flux (entropy
+    conservative), FP64 and FP32-bulk, p = 1..4, on the same 32,768-triangle
+    mesh."""
     out = {}
     stream = torch.cuda.current_stream(device)
     for p in (1, 2, 3, 4):
@@ -246,9 +249,10 @@ def residual_sweep(es, device, flush):
         s = es.Solver(op, mesh, es.Params(dissipation=True), device=device)
         ud = s.to_device(u0)
         r = s.empty()
-        for scheme in ("split", "hadamard"):
+        for scheme in ("split", "hadamard", "hadamard_ir"):
             for prec in ("fp64", "fp32"):
-                s.set_params(es.Params(dissipation=True, scheme=scheme, precision=prec))
+                # the Ismail-Roe comparator is entropy conservative only (no dissipation)
+                s.set_params(es.Params(dissipation=scheme != "hadamard_ir", scheme=scheme, precision=prec))
                 for _ in range(3):
                     s.residual(ud, r)
                 ts = []

@@ -219,6 +219,67 @@ def symmetrized_flux_jacobians(U, prm: Params):
 
 
 # ----------------------------------------------------------------------------
+# Comparator of Sec. 6: the Hadamard form with the Ismail-Roe flux, entropy
+# conservative for the standard entropy S = -rho s/(gam-1), s = log(p rho^-gam)
+# (the generalized-entropy family at the physical entropy).  The flux formula
+# is not printed in the paper (it cites Ismail & Roe, J. Comput. Phys. 228,
+# 2009); it is restated here from that published method.
+# ----------------------------------------------------------------------------
+
+def standard_entropy(U, prm: Params):
+    """S = -rho s/(gam-1), s = log(p rho^-gam)."""
+    rho, V, p = primitives(U, prm)
+    return -rho * (torch.log(p) - prm.gam * torch.log(rho)) / (prm.gam - 1.0)
+
+
+def standard_entropy_variables(U, prm: Params):
+    """dS/dU = [(gam - s)/(gam-1) - rho|V|^2/(2p), rho V/p, -rho/p]."""
+    rho, V, p = primitives(U, prm)
+    s = torch.log(p) - prm.gam * torch.log(rho)
+    b = rho / p
+    first = (prm.gam - s) / (prm.gam - 1.0) - 0.5 * b * (V * V).sum(-1)
+    return torch.cat([first[..., None], b[..., None] * V, -b[..., None]], dim=-1)
+
+
+def log_mean(a, b):
+    """Logarithmic mean (a - b)/(log a - log b) of positive a, b, written as
+    b eps / log1p(eps) with eps = a/b - 1 (no cancellation; limit b at a = b)."""
+    eps = a / b - 1.0
+    safe = torch.where(eps == 0, torch.ones_like(eps), eps)
+    q = torch.where(eps == 0, torch.ones_like(eps), safe / torch.log1p(safe))
+    return b * q
+
+
+def ir_flux(Uk, Uv, prm: Params):
+    """Ismail-Roe entropy-conservative flux, all directions: (..., d, n_c).
+    With z = sqrt(rho/p) [1, V, p]:
+      rho^ = {z_1} {z_nc}_log,  V^ = {z V}/{z_1},  p1^ = {z_nc}/{z_1},
+      p2^ = (gam+1)/(2 gam) {z_nc}_log/{z_1}_log + (gam-1)/(2 gam) {z_nc}/{z_1},
+      H^ = gam p2^/((gam-1) rho^) + |V^|^2/2,
+      F_i = [rho^ V^_i, rho^ V^_i V^ + p1^ e_i, rho^ V^_i H^]
+    ({.} arithmetic mean, {.}_log logarithmic mean)."""
+    g = prm.gam
+    rk, Vk, pk = primitives(Uk, prm)
+    rv, Vv, pv = primitives(Uv, prm)
+    z1k, z1v = torch.sqrt(rk / pk), torch.sqrt(rv / pv)
+    znk, znv = torch.sqrt(rk * pk), torch.sqrt(rv * pv)
+    a1, an = arith_avg(z1k, z1v), arith_avg(znk, znv)
+    l1, ln = log_mean(z1k, z1v), log_mean(znk, znv)
+    Vh = arith_avg(z1k[..., None] * Vk, z1v[..., None] * Vv) / a1[..., None]
+    rh = a1 * ln
+    p1 = an / a1
+    p2 = (g + 1.0) / (2.0 * g) * ln / l1 + (g - 1.0) / (2.0 * g) * an / a1
+    Hh = g * p2 / ((g - 1.0) * rh) + 0.5 * (Vh * Vh).sum(-1)
+    d = Uk.shape[-1] - 2
+    out = []
+    for i in range(d):
+        m = rh * Vh[..., i]
+        mom = m[..., None] * Vh + p1[..., None] * torch.nn.functional.one_hot(torch.tensor(i), d).to(Uk)
+        out.append(torch.cat([m[..., None], mom, (m * Hh)[..., None]], -1))
+    return torch.stack(out, dim=-2)
+
+
+# ----------------------------------------------------------------------------
 # Matrix interface dissipation ingredients, Sec. 4.5, Eqs. (69), (73)-(80)
 # ----------------------------------------------------------------------------
 

@@ -34,7 +34,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .physics import (Params, entropy_variables, euler_flux, sy_flux,
+from .physics import (Params, entropy_variables, euler_flux, sy_flux, ir_flux,
                       symmetrized_flux_jacobians, dissipation_matrix,
                       viscous_flux_from_w_grads, viscous_K)
 from .operators import physical_operators
@@ -68,12 +68,14 @@ def split_volume(U, ops, prm: Params, form="weak"):
     return -b / (b + 1.0) * Df - nonc / (b + 1.0) + Ef
 
 
-def hadamard_volume(U, ops, prm: Params, form="weak"):
-    """Hadamard-form volume terms with the Sjogreen-Yee flux, (n, n_p, n_c)."""
+def hadamard_volume(U, ops, prm: Params, form="weak", flux=None):
+    """Hadamard-form volume terms with the Sjogreen-Yee flux (or ``flux``),
+    (n, n_p, n_c)."""
+    flux = sy_flux if flux is None else flux
     n, n_p, nc = U.shape
     Um = U[:, :, None, :].expand(n, n_p, n_p, nc)
     Un = U[:, None, :, :].expand(n, n_p, n_p, nc)
-    F2 = 2.0 * sy_flux(Um, Un, prm)                 # (n, m, k, d, nc): block of Eq. (44)
+    F2 = 2.0 * flux(Um, Un, prm)                    # (n, m, k, d, nc): block of Eq. (44)
     if form == "weak":
         return -torch.einsum("nimk,nmkic->nmc", ops["S"], F2) / ops["H"][..., None]
     vol = -torch.einsum("nimk,nmkic->nmc", ops["D"], F2)
@@ -86,8 +88,12 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     """du/dt for the elements ``elems`` (all if None), layout (n, n_c, n_p).
 
     scheme: "split", "hadamard" or "hybrid" (per-element ``hybrid_flags``,
-    1 = Hadamard).  ``u`` may be a torch tensor requiring grad (the oracle
-    adjoint differentiates through this function)."""
+    1 = Hadamard), or "hadamard_ir": the Hadamard form with the Ismail-Roe
+    flux in the volume and the SATs (entropy conservative for the standard
+    entropy; no dissipation, no viscous terms).  ``u`` may be a torch tensor
+    requiring grad (the oracle adjoint differentiates through this function)."""
+    if scheme == "hadamard_ir" and (dissipation or viscous):
+        raise ValueError("the Ismail-Roe comparator is built without dissipation and viscous terms")
     U_all = _as_U(u)
     n_e, n_p, nc = U_all.shape
     d = nc - 2
@@ -113,6 +119,8 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
         vol = split_volume(Ut, ops_t, prm, form)
     elif scheme == "hadamard":
         vol = hadamard_volume(Ut, ops_t, prm, form)
+    elif scheme == "hadamard_ir":
+        vol = hadamard_volume(Ut, ops_t, prm, form, flux=ir_flux)
     elif scheme == "hybrid":
         flags = torch.as_tensor(np.asarray(hybrid_flags), dtype=torch.long)[tgt]
         vs = split_volume(Ut, ops_t, prm, form)
@@ -127,7 +135,7 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     Uk = Ut[:, fn, :]                                                       # (n, s, nc)
     Uv = U_all[pair[tgt, :, 0], fn[pair[tgt, :, 1]], :]                     # (n, s, nc)
     Hm = H_t[:, fn]                                                         # (n, s)
-    Fs = sy_flux(Uk, Uv, prm)                                               # (n, s, d, nc)
+    Fs = (ir_flux if scheme == "hadamard_ir" else sy_flux)(Uk, Uv, prm)    # (n, s, d, nc)
     sat = -torch.einsum("nsi,nsic->nsc", nu, Fs) / Hm[..., None]
     if dissipation:
         bmag = torch.linalg.norm(nu, dim=-1)

@@ -26,6 +26,7 @@ ESPLIT_FP32_BULK = 1
 ESPLIT_SCHEME_SPLIT = 0
 ESPLIT_SCHEME_HADAMARD = 1
 ESPLIT_SCHEME_HYBRID = 2
+ESPLIT_SCHEME_HADAMARD_IR = 3
 
 ERROR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_MESH", -4: "ERR_NONPHYSICAL",
                -5: "ERR_RRK_NO_ROOT", -6: "ERR_UNSUPPORTED", -7: "ERR_STATE"}

@@ -309,7 +309,9 @@ int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
   double alpha = -p->gam - p->beta * (p->gam - 1.0);
   if (!(alpha < -p->gam || alpha > 0.0)) return fail(c, ESPLIT_ERR_ARG, "beta must give alpha < -gam or alpha > 0");
   if (!(p->R > 0.0) || p->mu < 0.0 || !(p->Pr > 0.0)) return fail(c, ESPLIT_ERR_ARG, "R, Pr must be > 0, mu >= 0");
-  if (p->scheme < 0 || p->scheme > 2) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
+  if (p->scheme < 0 || p->scheme > 3) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
+  if (p->scheme == ESPLIT_SCHEME_HADAMARD_IR && (p->dissipation || p->viscous))
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the Ismail-Roe comparator is built without dissipation and viscous terms");
   if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK) return fail(c, ESPLIT_ERR_ARG, "unknown precision");
   cudaSetDevice(c->device);
   bool beta_changed = p->beta != c->prm.beta;
@@ -493,6 +495,9 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
   if (rc) return rc;
   if (!u) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ESPLIT_ERR_ARG, "dt must be positive and finite");
+  if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the relaxation step uses Harten's entropy; the Ismail-Roe comparator "
+                                           "conserves the standard one");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
   size_t n = (size_t)c->n_e * c->n_c * c->n_p;

@@ -159,7 +159,7 @@ __device__ __forceinline__ void normal_flux(const Node<double, D>& n, const TN* 
 //   ef_mode 0: no side (Hadamard scheme), 1: both sides (split scheme),
 //   2: sides whose hybrid flag is 0.
 // ---------------------------------------------------------------------------
-template <typename T, int D, bool VISC>
+template <typename T, int D, bool VISC, int FLUX = 0>
 __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u, const int2* __restrict__ fp,
                                                    int n_pairs, const double* __restrict__ nu,
                                                    const double* __restrict__ J, double* __restrict__ sat,
@@ -184,31 +184,38 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
   bool ok = node_from_u<T, D>(uk, c, nk);
   ok = node_from_u<T, D>(uv, c, nv) && ok;
   if (!ok) atomicOr(status, 1);
-  ZNode<T, D> zk, zv;
-  znode<T, D>(nk, c, zk);
-  znode<T, D>(nv, c, zv);
-  znode_recips<T, D>(zk);
-  PairAvg<T, D> a;
-  pair_avg<T, D>(zk, zv, c, a);
   T nuv[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) nuv[i] = (T)__ldg(&nu[((size_t)k * NS + s) * D + i]);
   T G[NC];
-  sy_flux_dir<T, D>(a, c, nuv, G);
-  if (dissipation) {
-    T b2 = T(0);
+  if constexpr (FLUX == 1) {  // Ismail-Roe comparator: EC SAT only
+    IRNode<T, D> ik, iv;
+    ir_node<T, D>(nk, ik);
+    ir_node<T, D>(nv, iv);
+    ir_flux_dir<T, D>(ik, iv, c, nuv, G);
+  } else {
+    ZNode<T, D> zk, zv;
+    znode<T, D>(nk, c, zk);
+    znode<T, D>(nv, c, zv);
+    znode_recips<T, D>(zk);
+    PairAvg<T, D> a;
+    pair_avg<T, D>(zk, zv, c, a);
+    sy_flux_dir<T, D>(a, c, nuv, G);
+    if (dissipation) {
+      T b2 = T(0);
 #pragma unroll
-    for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
-    T b = t_sqrt(b2);
-    T nh[D];
+      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+      T b = t_sqrt(b2);
+      T nh[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
-    T dw[NC], out[NC];
+      for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+      T dw[NC], out[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
-    diss_apply<T, D>(a, c, nh, dw, out);
+      for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
+      diss_apply<T, D>(a, c, nh, dw, out);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) G[q] += T(0.5) * b * out[q];
+      for (int q = 0; q < NC; ++q) G[q] += T(0.5) * b * out[q];
+    }
   }
   double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
   double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
@@ -564,7 +571,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
 //   G = sum_i S_i[m][n] F*_i(u_m, u_n),  S_i[m][n] = H_m D_i[m][n]
 //   r_m -= 2 G / H_m,  r_n += 2 G / H_n
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NP, int EB>
+template <typename T, int D, int NP, int EB, int FLUX = 0>
 __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const double* __restrict__ J, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
@@ -588,19 +595,30 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
 #pragma unroll
     for (int q = 0; q < NC; ++q) uu[q] = (T)__ldg(&u[((size_t)e * NC + q) * NP + m]);
     if (!node_from_u<T, D>(uu, c, nd)) atomicOr(status, 1);
-    ZNode<T, D> z;
-    znode<T, D>(nd, c, z);
-    znode_recips<T, D>(z);
     T* zz = sz + el * NZ * NP;
-    zz[0 * NP + m] = z.q;
+    if constexpr (FLUX == 1) {  // Ismail-Roe: z_1, z_nc, their logs, V
+      IRNode<T, D> z;
+      ir_node<T, D>(nd, z);
+      zz[0 * NP + m] = z.z1;
+      zz[1 * NP + m] = z.zn;
+      zz[2 * NP + m] = z.l1;
+      zz[3 * NP + m] = z.ln;
 #pragma unroll
-    for (int i = 0; i < D; ++i) zz[(1 + i) * NP + m] = z.V[i];
-    zz[(D + 1) * NP + m] = z.p;
-    zz[(D + 2) * NP + m] = z.P1;
-    zz[(D + 3) * NP + m] = z.P2;
-    zz[(D + 4) * NP + m] = z.v2;
-    zz[(D + 5) * NP + m] = z.iq;
-    zz[(D + 6) * NP + m] = z.ip;
+      for (int i = 0; i < D; ++i) zz[(4 + i) * NP + m] = z.V[i];
+    } else {
+      ZNode<T, D> z;
+      znode<T, D>(nd, c, z);
+      znode_recips<T, D>(z);
+      zz[0 * NP + m] = z.q;
+#pragma unroll
+      for (int i = 0; i < D; ++i) zz[(1 + i) * NP + m] = z.V[i];
+      zz[(D + 1) * NP + m] = z.p;
+      zz[(D + 2) * NP + m] = z.P1;
+      zz[(D + 3) * NP + m] = z.P2;
+      zz[(D + 4) * NP + m] = z.v2;
+      zz[(D + 5) * NP + m] = z.iq;
+      zz[(D + 6) * NP + m] = z.ip;
+    }
     sH[el * NP + m] = (T)(1.0 / (c_ref.H[m] * __ldg(&J[(size_t)e * NP + m])));  // 1/H
   }
   __syncthreads();
@@ -610,15 +628,25 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
   if (active) {
     const T* zz = sz + el * NZ * NP;
     ZNode<T, D> zm;
-    zm.q = zz[m];
+    IRNode<T, D> im;
+    if constexpr (FLUX == 1) {
+      im.z1 = zz[m];
+      im.zn = zz[NP + m];
+      im.l1 = zz[2 * NP + m];
+      im.ln = zz[3 * NP + m];
 #pragma unroll
-    for (int i = 0; i < D; ++i) zm.V[i] = zz[(1 + i) * NP + m];
-    zm.p = zz[(D + 1) * NP + m];
-    zm.P1 = zz[(D + 2) * NP + m];
-    zm.P2 = zz[(D + 3) * NP + m];
-    zm.v2 = zz[(D + 4) * NP + m];
-    zm.iq = zz[(D + 5) * NP + m];
-    zm.ip = zz[(D + 6) * NP + m];
+      for (int i = 0; i < D; ++i) im.V[i] = zz[(4 + i) * NP + m];
+    } else {
+      zm.q = zz[m];
+#pragma unroll
+      for (int i = 0; i < D; ++i) zm.V[i] = zz[(1 + i) * NP + m];
+      zm.p = zz[(D + 1) * NP + m];
+      zm.P1 = zz[(D + 2) * NP + m];
+      zm.P2 = zz[(D + 3) * NP + m];
+      zm.v2 = zz[(D + 4) * NP + m];
+      zm.iq = zz[(D + 5) * NP + m];
+      zm.ip = zz[(D + 6) * NP + m];
+    }
     T iHm = sH[el * NP + m];
     T Hm = T(1) / iHm;
     const T* op = ops + (size_t)e * (2 * D * NP * NP);
@@ -627,21 +655,32 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
       if ((NP % 2 == 0) && k == K && m >= K) break;
       int n = m + k;
       if (n >= NP) n -= NP;
-      ZNode<T, D> zn;
-      zn.q = zz[n];
-#pragma unroll
-      for (int i = 0; i < D; ++i) zn.V[i] = zz[(1 + i) * NP + n];
-      zn.p = zz[(D + 1) * NP + n];
-      zn.P1 = zz[(D + 2) * NP + n];
-      zn.P2 = zz[(D + 3) * NP + n];
-      zn.v2 = zz[(D + 4) * NP + n];
-      PairAvg<T, D> a;
-      pair_avg<T, D>(zm, zn, c, a);
       T Smn[D];
 #pragma unroll
       for (int i = 0; i < D; ++i) Smn[i] = Hm * __ldg(&op[((D + i) * NP + n) * NP + m]);
       T G[NC];
-      sy_flux_dir<T, D>(a, c, Smn, G);
+      if constexpr (FLUX == 1) {
+        IRNode<T, D> in_;
+        in_.z1 = zz[n];
+        in_.zn = zz[NP + n];
+        in_.l1 = zz[2 * NP + n];
+        in_.ln = zz[3 * NP + n];
+#pragma unroll
+        for (int i = 0; i < D; ++i) in_.V[i] = zz[(4 + i) * NP + n];
+        ir_flux_dir<T, D>(im, in_, c, Smn, G);
+      } else {
+        ZNode<T, D> zn;
+        zn.q = zz[n];
+#pragma unroll
+        for (int i = 0; i < D; ++i) zn.V[i] = zz[(1 + i) * NP + n];
+        zn.p = zz[(D + 1) * NP + n];
+        zn.P1 = zz[(D + 2) * NP + n];
+        zn.P2 = zz[(D + 3) * NP + n];
+        zn.v2 = zz[(D + 4) * NP + n];
+        PairAvg<T, D> a;
+        pair_avg<T, D>(zm, zn, c, a);
+        sy_flux_dir<T, D>(a, c, Smn, G);
+      }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         acc[q] -= T(2) * G[q] * iHm;
@@ -713,7 +752,10 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     // they stay float64 in both precision modes
     const int ef_mode = c->prm.scheme == ESPLIT_SCHEME_SPLIT ? 1 : (c->prm.scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0);
     const int visc_heat = c->prm.viscous ? c->prm.heat_flux : -1;
-    if (visc_heat >= 0)
+    if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
+      face_kernel<double, D, false, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat,
+                                                         ph64, 0, c->b.status, 0, c->b.hflags, 0, nullptr);
+    else if (visc_heat >= 0)
       face_kernel<double, D, true><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
                                                      c->prm.dissipation, c->b.status, ef_mode, c->b.hflags,
                                                      visc_heat, c->b.va);
@@ -727,7 +769,9 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   int np_used = 0;
   int scheme = c->prm.scheme;
   int n_split = scheme == ESPLIT_SCHEME_SPLIT ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_split : 0);
-  int n_had = scheme == ESPLIT_SCHEME_HADAMARD ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_had : 0);
+  int n_had = (scheme == ESPLIT_SCHEME_HADAMARD || scheme == ESPLIT_SCHEME_HADAMARD_IR)
+                  ? c->n_e
+                  : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_had : 0);
   const int* lsplit = scheme == ESPLIT_SCHEME_HYBRID ? c->b.list_split : nullptr;
   const int* lhad = scheme == ESPLIT_SCHEME_HYBRID ? c->b.list_had : nullptr;
   if (n_split > 0) {
@@ -752,14 +796,20 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     size_t smem = sizeof(T) * ((size_t)EB * (D + 7) * NP + (size_t)EB * NP * K * (D + 2) + (size_t)EB * NP);
     static bool attr_set = false;
     if (!attr_set) {
-      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       attr_set = true;
     }
     int nb = (n_had + EB - 1) / EB;
     ProfScope ps(c, PG_HAD, s);
-    hadamard_volume_kernel<T, D, NP, EB><<<nb, EB * NP, smem, s>>>(
-        u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
+    if (scheme == ESPLIT_SCHEME_HADAMARD_IR)
+      hadamard_volume_kernel<T, D, NP, EB, 1><<<nb, EB * NP, smem, s>>>(
+          u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
+    else
+      hadamard_volume_kernel<T, D, NP, EB, 0><<<nb, EB * NP, smem, s>>>(
+          u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
   }

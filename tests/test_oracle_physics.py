@@ -281,3 +281,42 @@ def test_inverse_entropy_map(d):
     Ulm = torch.tensor([[1.0, 0.3, -0.2, 71.43 / 0.4 + 0.065]], dtype=DT)
     back = conservative_from_entropy(entropy_variables(Ulm, P), P)
     assert ((back - Ulm).abs() / Ulm.abs()).max() < 1e-13
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_ir_flux_consistency_symmetry_tadmor(d):
+    """Ismail-Roe flux: F*(U, U) = F(U), symmetric in its arguments, and
+    Tadmor's condition for the standard entropy,
+    (w_v - w_k) . F*_i = psi_v - psi_k with psi_i = rho V_i."""
+    from oracle.physics import ir_flux, standard_entropy_variables
+    Uk = rand_states(400, d, 31)
+    Uv = rand_states(400, d, 32)
+    Fs = ir_flux(Uk, Uk, P)
+    assert (Fs - euler_flux(Uk, P)).abs().max() < 1e-13 * euler_flux(Uk, P).abs().max()
+    assert (ir_flux(Uk, Uv, P) - ir_flux(Uv, Uk, P)).abs().max() < 1e-13
+    F = ir_flux(Uk, Uv, P)
+    dw = standard_entropy_variables(Uv, P) - standard_entropy_variables(Uk, P)
+    for i in range(d):
+        lhs = (dw * F[..., i, :]).sum(-1)
+        rhs = Uv[..., 1 + i] - Uk[..., 1 + i]
+        scale = (dw.abs() * F[..., i, :].abs()).sum(-1) + rhs.abs()
+        assert ((lhs - rhs).abs() / scale).max() < 1e-13
+    # nearly equal states exercise the logarithmic-mean limit
+    Ue = Uk * (1.0 + 1e-9 * torch.randn(Uk.shape, generator=torch.Generator().manual_seed(5), dtype=DT))
+    assert (ir_flux(Uk, Ue, P) - euler_flux(Uk, P)).abs().max() < 1e-7 * euler_flux(Uk, P).abs().max()
+
+
+def test_standard_entropy_variables_are_gradient():
+    from oracle.physics import standard_entropy, standard_entropy_variables
+    U = rand_states(50, 2, 33).requires_grad_(True)
+    (g,) = torch.autograd.grad(standard_entropy(U, P).sum(), U)
+    assert (g - standard_entropy_variables(U.detach(), P)).abs().max() < 1e-12
+
+
+def test_log_mean():
+    from oracle.physics import log_mean
+    a = torch.tensor([1.0, 2.0, 3.0, 1e-3, 5.0], dtype=DT)
+    b = torch.tensor([1.0, 2.0 + 1e-12, 1.5, 2e-3, 5.0 * (1 + 1e-6)], dtype=DT)
+    ref = torch.tensor([float(Decimal(x) if x == y else (Decimal(x) - Decimal(y)) / (Decimal(x).ln() - Decimal(y).ln()))
+                        for x, y in zip(a.tolist(), b.tolist())], dtype=DT)
+    assert ((log_mean(a, b) - ref).abs() / ref).max() < 1e-15

@@ -242,3 +242,27 @@ def test_tet_viscous_bo_identity(heat):
     qf = float(-torch.einsum("nm,nimc,nmijcb,njmb->", ops["H"], g, K, g))
     assert abs(rate - qf) < 1e-11 * abs(qf)
     assert Dg.conservation(rv, op, m).abs().max() < 1e-10 * float(rv.abs().max())
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_ir_hadamard_conserves_standard_entropy(p):
+    """The Ismail-Roe Hadamard form (the Sec. 6 comparator) conserves the
+    standard entropy on any state (Thm. 4 with the standard entropy's Tadmor
+    condition), is conservative, preserves free stream, and weak = strong."""
+    from oracle.physics import standard_entropy_variables
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 4, 10.0, 0.05)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=40 + p)
+    r = R.residual(u, op, m, P, scheme="hadamard_ir")
+    U = torch.as_tensor(u).transpose(1, 2)
+    w = standard_entropy_variables(U, P)
+    H = torch.as_tensor(op.H)[None] * torch.as_tensor(m.J)
+    rt = r.transpose(1, 2)
+    rate = float((H[..., None] * w * rt).sum())
+    scale = float((H[..., None] * w.abs() * rt.abs()).sum())
+    assert abs(rate) < 1e-13 * scale
+    assert Dg.conservation(r, op, m).abs().max() < 1e-12 * float(r.abs().max())
+    uf = states.uniform_state(m.n_e, 2, op.n_p)
+    assert R.residual(uf, op, m, P, scheme="hadamard_ir").abs().max() < 1e-12
+    rs = R.residual(u, op, m, P, scheme="hadamard_ir", form="strong")
+    assert (r - rs).abs().max() < 1e-13 * r.abs().max()
