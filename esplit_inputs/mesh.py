@@ -139,6 +139,88 @@ def periodic_tri_mesh(op: RefOperator, N: int, L: float = 10.0, amp: float = 0.0
                 meta=dict(kind="periodic_tri", N=N, L=L, amp=amp, p=op.p))
 
 
+def chan_warp(xh, yh):
+    """Perturbation of the 2D vortex grids of Sec. 7.3 (the paper takes it from
+    Chan et al.) on [0, 20] x [-5, 5]:
+        x1 = xh1 + 1/8 cos(pi/20 (xh1 - 10)) cos(3 pi/10 xh2),
+        x2 = xh2 + 1/8 sin(pi/5 (x1 - 10)) cos(pi/10 xh2),
+    x2 using the perturbed x1.  Returns the displacements."""
+    dx = 0.125 * np.cos(np.pi / 20.0 * (xh - 10.0)) * np.cos(0.3 * np.pi * yh)
+    x1 = xh + dx
+    dy = 0.125 * np.sin(np.pi / 5.0 * (x1 - 10.0)) * np.cos(np.pi / 10.0 * yh)
+    return dx, dy
+
+
+def periodic_tri_mesh_rect(op: RefOperator, Nx: int, Ny: int, origin=(0.0, 0.0), size=(20.0, 10.0),
+                           warp=chan_warp) -> Mesh:
+    """Periodic rectangle [x0, x0 + Lx] x [y0, y0 + Ly] of Nx x Ny rectangles,
+    each cut along its lower-left to upper-right diagonal into two curved
+    triangles (2 Nx Ny elements), quadratic geometry displaced by
+    warp(xh, yh) -> (dx, dy) evaluated at the unperturbed geometry nodes (on
+    the wrapped lattice, so periodic images move identically; the warp must
+    be periodic).  Element numbering as periodic_tri_mesh; the geometry nodes
+    are kept in meta["geom"] (n_e, 2, 6) for error integration."""
+    assert op.d == 2
+    Lx, Ly = size
+    hx, hy = Lx / Nx, Ly / Ny
+    n_e = 2 * Nx * Ny
+    I = np.zeros((n_e, 6), dtype=np.int64)
+    Jx = np.zeros((n_e, 6), dtype=np.int64)
+    for j in range(Ny):
+        for i in range(Nx):
+            A, B, C, D = (2 * i, 2 * j), (2 * i + 2, 2 * j), (2 * i + 2, 2 * j + 2), (2 * i, 2 * j + 2)
+            for t, (a, b, c) in enumerate([(A, B, C), (A, C, D)]):
+                e = 2 * (j * Nx + i) + t
+                nodes = [a, b, c,
+                         ((a[0] + b[0]) // 2, (a[1] + b[1]) // 2),
+                         ((b[0] + c[0]) // 2, (b[1] + c[1]) // 2),
+                         ((c[0] + a[0]) // 2, (c[1] + a[1]) // 2)]
+                I[e] = [q[0] for q in nodes]
+                Jx[e] = [q[1] for q in nodes]
+    xw = origin[0] + (I % (2 * Nx)) * (hx / 2)
+    yw = origin[1] + (Jx % (2 * Ny)) * (hy / 2)
+    ddx, ddy = warp(xw, yw)
+    G = np.stack([origin[0] + I * (hx / 2) + ddx, origin[1] + Jx * (hy / 2) + ddy], axis=1)  # (n_e, 2, 6)
+
+    Nsh, dN = _quad_shape(op.xi)
+    x = np.einsum("pa,eia->eip", Nsh, G)
+    Jm = np.einsum("jpa,eia->eijp", dN, G)
+    det = Jm[:, 0, 0] * Jm[:, 1, 1] - Jm[:, 0, 1] * Jm[:, 1, 0]
+    Lam = np.empty_like(Jm)
+    Lam[:, 0, 0] = Jm[:, 1, 1]
+    Lam[:, 0, 1] = -Jm[:, 1, 0]
+    Lam[:, 1, 0] = -Jm[:, 0, 1]
+    Lam[:, 1, 1] = Jm[:, 0, 0]
+    fn = op.facet_nodes
+    nu = np.zeros((n_e, op.n_fac, op.n_f, 2))
+    for g in range(op.n_fac):
+        for k in range(op.n_f):
+            m = fn[g, k]
+            nu[:, g, k, :] = op.facet_w[g, k] * np.einsum("eij,j->ei", Lam[:, :, :, m], op.ref_normals[g])
+    mid_of_facet = [3, 4, 5]
+    owners: dict = {}
+    for e in range(n_e):
+        for g in range(op.n_fac):
+            key = (int(I[e, mid_of_facet[g]] % (2 * Nx)), int(Jx[e, mid_of_facet[g]] % (2 * Ny)))
+            owners.setdefault(key, []).append((e, g))
+    pair = np.full((n_e, op.n_fac, op.n_f, 2), -1, dtype=np.int32)
+    for key, lst in owners.items():
+        assert len(lst) == 2, (key, lst)
+        (e0, g0), (e1, g1) = lst
+        for k in range(op.n_f):
+            kk = op.n_f - 1 - k
+            pair[e0, g0, k] = (e1, g1 * op.n_f + kk)
+            pair[e1, g1, kk] = (e0, g0 * op.n_f + k)
+    diff = x[:, :, :, None] - x[:, :, None, :]
+    dist = np.sqrt((diff ** 2).sum(1))
+    dist[:, np.arange(op.n_p), np.arange(op.n_p)] = np.inf
+    hmin = dist.reshape(n_e, -1).min(1)
+    return Mesh(d=2, n_e=n_e, n_p=op.n_p, n_fac=op.n_fac, n_f=op.n_f, L=(Lx, Ly),
+                x=x, J=det, Lam=Lam, nu=nu, pair=pair, hmin=hmin,
+                meta=dict(kind="periodic_tri_rect", Nx=Nx, Ny=Ny, origin=tuple(origin), size=(Lx, Ly),
+                          p=op.p, geom=G))
+
+
 def _quad_tet_shape(xi: np.ndarray):
     """Quadratic (10-node) Lagrange shape functions on the reference tetrahedron
     and their derivatives. Geometry node order: v0..v3, then the edge midpoints

@@ -33,12 +33,14 @@ def isentropic_vortex_prims(x, y, t=0.0, xc=5.0, yc=5.0, alpha=3.0, gam=GAMMA):
     return rho, np.stack([u, v]), p
 
 
-def isentropic_vortex(mesh, t=0.0, alpha=3.0, gam=GAMMA):
-    """Vortex of strength alpha centred at the domain centre. Periodic images
-    are left out: on [0, 10]^2 their perturbation is O(e^-24)."""
+def isentropic_vortex(mesh, t=0.0, alpha=3.0, gam=GAMMA, center=None):
+    """Vortex of strength alpha centred at ``center`` (default: the centre of
+    the [0, L]^2 square). Periodic images are left out: on [0, 10]^2 their
+    perturbation is O(e^-24)."""
     L = mesh.L[0]
+    xc, yc = (L / 2, L / 2) if center is None else center
     x, y = mesh.x[:, 0], mesh.x[:, 1]
-    rho, V, p = isentropic_vortex_prims(x, y, t=t, xc=L / 2, yc=L / 2, alpha=alpha, gam=gam)
+    rho, V, p = isentropic_vortex_prims(x, y, t=t, xc=xc, yc=yc, alpha=alpha, gam=gam)
     return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))
 
 
