@@ -151,7 +151,7 @@ def chan_warp(xh, yh):
     return dx, dy
 
 
-def periodic_tri_mesh_rect(op: RefOperator, Nx: int, Ny: int, origin=(0.0, 0.0), size=(20.0, 10.0),
+def periodic_tri_mesh_rect(op: RefOperator, Nx: int, Ny: int, origin=(0.0, -5.0), size=(20.0, 10.0),
                            warp=chan_warp) -> Mesh:
     """Periodic rectangle [x0, x0 + Lx] x [y0, y0 + Ly] of Nx x Ny rectangles,
     each cut along its lower-left to upper-right diagonal into two curved
