@@ -1,0 +1,82 @@
+"""End-to-end accuracy against the paper's printed grid-convergence study
+(Sec. 7.3, Table 1; fixture tests/golden/vortex2d_table1.txt): the 2D
+isentropic vortex on the Sec. 7.3 curvilinear triangle grids, run with the GPU
+residual and relaxation RK4 (CFL 0.1) to t_f = 2, L^2 error as Sec. 7.3
+measures it (tests/accuracy.py).
+
+The paper does not print its operators' node sets, so errors are compared
+with a factor band rather than digits: for p = 3, 4 (whose node counts match
+the diagonal-E family the paper cites) the errors lie within a factor 2 of
+the printed ones and the 60 -> 80 rates within 0.5 of the printed rates; for
+every p the rates lie in the band [p - 0.2, p + 1.2] the paper reports
+(rates between p and p + 1) and dissipation lowers the error.  Meshes 60^2 x 2
+and 80^2 x 2 (the smallest two of the table) keep the run to about two
+minutes; the full table (observed: p = 3, 4 errors 0.65-0.9 of the printed
+ones at every mesh) is recorded in the design doc."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from esplit_inputs import tri_operator, states
+from esplit_inputs.mesh import periodic_tri_mesh_rect
+from accuracy import l2_error_vortex
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "vortex2d_table1.txt")
+
+
+def _table():
+    rows = np.loadtxt(GOLDEN, comments="#")
+    return {(int(r[0]), int(r[1])): {"split_ec": r[2], "split_diss": r[3]} for r in rows}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_07181_gb300 as es
+    return es
+
+
+def _run(lib, op, m, diss, tf=2.0):
+    u0 = states.isentropic_vortex(m, center=(5.0, 0.0))
+    dt = states.cfl_timestep(m, u0, 0.1)
+    s = lib.Solver(op, m, lib.Params(dissipation=diss))
+    u = s.to_device(u0)
+    t = 0.0
+    while t < tf - 1e-12:
+        h = min(dt, tf - t)
+        g, _ = s.rrk_step(u, h)
+        t += g * h
+    err = l2_error_vortex(u.cpu().numpy(), op, m, t)
+    assert s.status() == 0
+    s.close()
+    return err
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_vortex_convergence_against_table1(lib, p):
+    tab = _table()
+    op = tri_operator(p)
+    errs = {}
+    for N in (60, 80):
+        m = periodic_tri_mesh_rect(op, N, N)
+        for kind, diss in (("split_ec", False), ("split_diss", True)):
+            errs[(N, kind)] = _run(lib, op, m, diss)
+    for kind in ("split_ec", "split_diss"):
+        ours = [errs[(60, kind)], errs[(80, kind)]]
+        paper = [tab[(p, 60)][kind], tab[(p, 80)][kind]]
+        rate = np.log(ours[0] / ours[1]) / np.log(80 / 60)
+        prate = np.log(paper[0] / paper[1]) / np.log(80 / 60)
+        print(f"p={p} {kind}: ours {ours[0]:.3e} {ours[1]:.3e} rate {rate:.2f} | Table 1 {paper[0]:.3e} "
+              f"{paper[1]:.3e} rate {prate:.2f}")
+        assert p - 0.2 <= rate <= p + 1.2
+        if p >= 3:
+            for a, b in zip(ours, paper):
+                assert 0.5 <= a / b <= 2.0
+            assert abs(rate - prate) <= 0.5
+    for N in (60, 80):
+        assert errs[(N, "split_diss")] < errs[(N, "split_ec")]
