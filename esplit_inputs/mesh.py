@@ -238,12 +238,21 @@ def _quad_tet_shape(xi: np.ndarray):
     return np.stack(N, axis=1), dN
 
 
-def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float = 0.02) -> Mesh:
-    """Periodic [0, L]^3 mesh of N^3 cubes, each cut into the six Kuhn
+def vortex3d_warp(xh):
+    """Perturbation of the 3D vortex grids of Sec. 7.3 on [-10, 10]^3:
+    x_i = xh_i + 0.05 sin(pi xh_i / 2).  xh (..., 3) -> displacements."""
+    return 0.05 * np.sin(0.5 * np.pi * xh)
+
+
+def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float = 0.02, origin=0.0,
+                      warp=None) -> Mesh:
+    """Periodic [x0, x0 + L]^3 mesh of N^3 cubes, each cut into the six Kuhn
     tetrahedra around its main diagonal (6 N^3 elements), quadratic geometry
-    warped by x_i = xhat_i + A prod_j sin(2 pi xhat_j / L) (Sec. 7.3 builds its
-    3D grids the same way: hexahedra cut into six tetrahedra, then perturbed).
-    Facet nodes are paired by their (unwarped) positions modulo L."""
+    warped by x_i = xhat_i + A prod_j sin(2 pi (xhat_j - x0) / L) or, when
+    given, by warp(xhat) -> displacements evaluated on the wrapped lattice
+    (Sec. 7.3 builds its 3D grids the same way: hexahedra cut into six
+    tetrahedra, then perturbed).  Facet nodes are paired by their (unwarped)
+    positions modulo L; the geometry nodes are kept in meta["geom"]."""
     import itertools
     assert op.d == 3
     h = L / N
@@ -268,8 +277,12 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
     edges = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
     G_idx = np.concatenate([V, np.stack([(V[:, a] + V[:, b]) // 2 for a, b in edges], axis=1)], axis=1)  # (e,10,3)
     wrap = G_idx % (2 * N)
-    s = np.prod(np.sin(2.0 * np.pi * wrap / (2 * N)), axis=2)  # (e, 10)
-    G = G_idx * (h / 2) + amp * s[..., None]                   # (e, 10, 3)
+    if warp is None:
+        s = np.prod(np.sin(2.0 * np.pi * wrap / (2 * N)), axis=2)  # (e, 10)
+        disp = amp * s[..., None]
+    else:
+        disp = warp(origin + wrap * (h / 2))
+    G = origin + G_idx * (h / 2) + disp                        # (e, 10, 3)
     G = np.transpose(G, (0, 2, 1))                             # (e, 3, 10)
     Nsh, dN = _quad_tet_shape(op.xi)
     x = np.einsum("pa,eia->eip", Nsh, G)
@@ -307,4 +320,5 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
     dist[:, np.arange(op.n_p), np.arange(op.n_p)] = np.inf
     hmin = dist.reshape(n_e, -1).min(1)
     return Mesh(d=3, n_e=n_e, n_p=op.n_p, n_fac=op.n_fac, n_f=op.n_f, L=(L, L, L), x=x, J=det, Lam=Lam, nu=nu,
-                pair=pair, hmin=hmin, meta=dict(kind="periodic_tet", N=N, L=L, amp=amp, p=op.p))
+                pair=pair, hmin=hmin, meta=dict(kind="periodic_tet", N=N, L=L, amp=amp, p=op.p, origin=origin,
+                                                 geom=G))

@@ -44,6 +44,28 @@ def isentropic_vortex(mesh, t=0.0, alpha=3.0, gam=GAMMA, center=None):
     return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))
 
 
+def isentropic_vortex_3d(mesh, t=0.0, gam=GAMMA):
+    """3D isentropic vortex of Sec. 7.3 on [-10, 10]^3, moving with unit speed
+    in x_2: with r^2 = x_1^2 + (x_2 - t)^2,
+      rho = (1 - 2/25 (gam-1) exp(1 - r^2))^(1/(gam-1)),  p = rho^gam / gam,
+      V_1 = -2/5 (x_2 - t) exp((1 - r^2)/2),  V_2 = 1 + 2/5 x_1 exp((1 - r^2)/2),  V_3 = 0.
+    Reading: the printed exponent of V_1 carries (x_1 - t)^2; (x_2 - t)^2, as in
+    V_2 and rho, is the one the radial momentum balance dp/dr = rho v_theta^2 / r
+    of this density requires."""
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(*vortex3d_prims(mesh.x[:, 0], mesh.x[:, 1], t, gam),
+                                                         gam), 0, 1))
+
+
+def vortex3d_prims(x1, x2, t=0.0, gam=GAMMA):
+    a = x2 - t
+    r2 = x1 * x1 + a * a
+    ex = np.exp(0.5 * (1.0 - r2))
+    rho = (1.0 - 2.0 / 25.0 * (gam - 1.0) * ex * ex) ** (1.0 / (gam - 1.0))
+    p = rho ** gam / gam
+    V = np.stack([-0.4 * a * ex, 1.0 + 0.4 * x1 * ex, 0.0 * x1])
+    return rho, V, p
+
+
 def add_uniform_noise(u, amplitude, seed):
     """u + amplitude * U(-1, 1), drawn by numpy's PCG64 in C order of u."""
     rng = np.random.default_rng(seed)

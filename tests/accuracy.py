@@ -55,3 +55,42 @@ def l2_error_vortex(u, op, mesh, t, center=(5.0, 0.0)):
     ue = np.moveaxis(prim_to_cons(rho, V, pr), 0, 1)                             # (n_e, n_c, n_q)
     err2 = np.einsum("q,eq,ecq->", wq, J, (uq - ue) ** 2)
     return float(np.sqrt(err2))
+
+
+def tet_rule(degree):
+    """Collapsed Gauss rule on the reference tetrahedron (vertices 0, e1, e2,
+    e3): x = u, y = v (1 - u), z = w (1 - u)(1 - v), weight (1-u)^2 (1-v)."""
+    n = degree // 2 + 2
+    g, w = np.polynomial.legendre.leggauss(n)
+    g, w = 0.5 * (g + 1.0), 0.5 * w
+    U, Vv, Wd = np.meshgrid(g, g, g, indexing="ij")
+    WU, WV, WW = np.meshgrid(w, w, w, indexing="ij")
+    xi = np.stack([U.ravel(), (Vv * (1 - U)).ravel(), (Wd * (1 - U) * (1 - Vv)).ravel()], axis=1)
+    wt = (WU * WV * WW * (1 - U) ** 2 * (1 - Vv)).ravel()
+    return xi, wt
+
+
+def l2_error_vortex_3d(u, op, mesh, t, chunk=4096):
+    """The Sec. 7.3 L^2 error for the 3D vortex on curved tetrahedra."""
+    from esplit_inputs.mesh import _quad_tet_shape
+    from esplit_inputs.states import vortex3d_prims
+    p = op.p
+    xq, wq = tet_rule(3 * p + 1)
+    ctr = np.full(3, 0.25)
+    Vn, _ = vandermonde(op.xi, p, ctr)
+    Vq, _ = vandermonde(xq, p, ctr)
+    H = op.H
+    fit = Vq @ np.linalg.solve(Vn.T @ (H[:, None] * Vn), Vn.T * H[None, :])
+    N, dN = _quad_tet_shape(xq)                                         # (q, 10), (3, q, 10)
+    G = mesh.meta["geom"]                                               # (n_e, 3, 10)
+    total = 0.0
+    for a in range(0, mesh.n_e, chunk):
+        Gc = G[a:a + chunk]
+        X = np.einsum("qa,eia->eiq", N, Gc)
+        Jm = np.einsum("jqa,eia->eqij", dN, Gc)
+        J = np.linalg.det(Jm)
+        uq = np.einsum("qm,ecm->ecq", fit, u[a:a + chunk])
+        rho, V, pr = vortex3d_prims(X[:, 0], X[:, 1], t)
+        ue = np.moveaxis(prim_to_cons(rho, V, pr), 0, 1)
+        total += float(np.einsum("q,eq,ecq->", wq, J, (uq - ue) ** 2))
+    return float(np.sqrt(total))

@@ -197,3 +197,34 @@ def test_taylor_green_state():
     T = p / rho
     assert np.allclose(T, 1 / (1.4 * 0.01), rtol=1e-12)        # T = T_0 everywhere
     assert abs(p.mean() - 1 / (1.4 * 0.01)) < 0.2
+
+
+def test_vortex3d_solves_euler():
+    """The 3D vortex of Sec. 7.3 (with the exponent reading of V_1) satisfies
+    dU/dt + div F = 0: central differences at random points."""
+    from esplit_inputs.states import vortex3d_prims, prim_to_cons
+    gam = 1.4
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-2.5, 2.5, (200, 3))
+    h = 1e-4
+
+    def U(x, t):
+        rho, V, p = vortex3d_prims(np.atleast_1d(x[..., 0]), np.atleast_1d(x[..., 1]), t)
+        return prim_to_cons(rho, V, p)
+
+    def F(x, t, i):
+        rho, V, p = vortex3d_prims(np.atleast_1d(x[..., 0]), np.atleast_1d(x[..., 1]), t)
+        uu = prim_to_cons(rho, V, p)
+        f = uu * V[i]
+        f[1 + i] += p
+        f[4] += p * V[i]
+        return f
+
+    dUdt = (U(pts, 0.3 + h) - U(pts, 0.3 - h)) / (2 * h)
+    div = sum((F(pts + h * np.eye(3)[i], 0.3, i) - F(pts - h * np.eye(3)[i], 0.3, i)) / (2 * h) for i in range(3))
+    assert np.abs(dUdt + div).max() < 1e-6
+    # the printed V_1 exponent, (x_1 - t)^2, does not solve the equations
+    x1, x2 = pts[:, 0], pts[:, 1]
+    bad = -0.4 * (x2 - 0.3) * np.exp(0.5 * (1 - (x1 - 0.3) ** 2 - x1 ** 2))
+    good = -0.4 * (x2 - 0.3) * np.exp(0.5 * (1 - (x2 - 0.3) ** 2 - x1 ** 2))
+    assert np.abs(bad - good).max() > 1e-2
