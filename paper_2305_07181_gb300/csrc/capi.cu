@@ -157,7 +157,7 @@ void esplit_destroy(esplit_ctx* c) {
   cudaSetDevice(c->device);
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
-                b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
+                b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.vfb, b.vfs, b.vus};
   for (void* p : ps) dfree(p);
   for (auto& r : c->recs) {
@@ -269,6 +269,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.ops32lo, (size_t)n_e * 2 * d * NP * NP))) return rc;
   if ((rc = dalloc(c, &c->b.rows, (size_t)n_e * 2 * d * NP))) return rc;
   if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
+  if ((rc = dalloc(c, &c->b.fcache, (size_t)(d + 9) * n_e * NS))) return rc;
   c->partial_cap = 0;
   if ((rc = ensure_partial(c))) return rc;
   CK(cudaMemcpy(c->b.J, J, sizeof(double) * n_e * NP, cudaMemcpyHostToDevice));

@@ -55,6 +55,7 @@ struct Buffers {
   int* hcount = nullptr;
   // scratch
   double* sat = nullptr;       // [n_e][n_c][n_slot] facet contributions
+  double* fcache = nullptr;    // [d + 9][n_e n_slot] facet-node quantities (split volume -> facet kernel)
   double* partial = nullptr;   // block partial sums
   double* scal = nullptr;      // small device scalars
   RootState* root = nullptr;

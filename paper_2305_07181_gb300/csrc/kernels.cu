@@ -253,6 +253,106 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 }
 
 // ---------------------------------------------------------------------------
+// facet kernel after the split volume kernel (entropy-split scheme, inviscid):
+// the same terms as face_kernel (two-point flux, dissipation, the facet part
+// nu . f / H of the volume term), with the nodal quantities of both sides read
+// from the cache the volume kernel wrote (rho, 1/rho, p, e, q, log q, log p,
+// 1/q, 1/p, V) instead of recomputed, and the result added into r.  The
+// entropy production of the facet terms, w . H sat = w_k . (nu f_k - G) +
+// w_v . (G - nu f_v), goes to block partials after the volume kernel's.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void node_from_cache(const double* __restrict__ fc, size_t S, size_t ix,
+                                                const Phys<double>& c, Node<double, D>& n, double& iq, double& ip) {
+  n.rho = __ldg(&fc[0 * S + ix]);
+  n.ir = __ldg(&fc[1 * S + ix]);
+  n.p = __ldg(&fc[2 * S + ix]);
+  n.e = __ldg(&fc[3 * S + ix]);
+  n.q = __ldg(&fc[4 * S + ix]);
+  n.lnq = __ldg(&fc[5 * S + ix]);
+  n.lnp = __ldg(&fc[6 * S + ix]);
+  iq = __ldg(&fc[7 * S + ix]);
+  ip = __ldg(&fc[8 * S + ix]);
+  n.v2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    n.V[i] = __ldg(&fc[(9 + i) * S + ix]);
+    n.v2 += n.V[i] * n.V[i];
+  }
+  n.W[0] = n.q * (c.w1c * n.p * n.ir - 0.5 * n.v2);
+#pragma unroll
+  for (int i = 0; i < D; ++i) n.W[1 + i] = n.q * n.V[i];
+  n.W[D + 1] = -n.q;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r, const int2* __restrict__ fp,
+                                                          int n_pairs, const double* __restrict__ nu,
+                                                          const double* __restrict__ J,
+                                                          const double* __restrict__ fc, int n_slot_total,
+                                                          Phys<double> c, int dissipation,
+                                                          double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double hw = 0.0;
+  if (t < n_pairs) {
+    const int NP = c_ref.n_p, NS = c_ref.n_slot;
+    const size_t S = (size_t)n_slot_total;
+    int2 pr = __ldg(&fp[t]);
+    int k = pr.x / NS, s = pr.x - k * NS;
+    int v = pr.y / NS, s2 = pr.y - v * NS;
+    int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
+    Node<double, D> nk, nv;
+    double iqk, ipk, iqv, ipv;
+    node_from_cache<D>(fc, S, (size_t)pr.x, c, nk, iqk, ipk);
+    node_from_cache<D>(fc, S, (size_t)pr.y, c, nv, iqv, ipv);
+    ZNode<double, D> zk, zv;
+    znode<double, D>(nk, c, zk);
+    znode<double, D>(nv, c, zv);
+    zk.iq = iqk;
+    zk.ip = ipk;
+    PairAvg<double, D> a;
+    pair_avg<double, D>(zk, zv, c, a);
+    double nuv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nuv[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
+    double G[NC];
+    sy_flux_dir<double, D>(a, c, nuv, G);
+    if (dissipation) {
+      double b2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+      double b = sqrt(b2);
+      double nh[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+      double dw[NC], out[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
+      diss_apply<double, D>(a, c, nh, dw, out);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) G[q] += 0.5 * b * out[q];
+    }
+    double ek[NC], ev[NC];
+    normal_flux<D>(nk, nuv, ek);
+    normal_flux<D>(nv, nuv, ev);
+    double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
+    double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      double gk = ek[q] - G[q], gv = G[q] - ev[q];
+      r[((size_t)k * NC + q) * NP + m] += gk * ihk;
+      r[((size_t)v * NC + q) * NP + n] += gv * ihv;
+      hw += nk.W[q] * gk + nv.W[q] * gv;
+    }
+  }
+  if (prod) {
+    double vv[1] = {hw};
+    block_sum<1>(vv, prod + blockIdx.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // entropy-split volume kernel (Eq. (100)): EB elements per block, one thread
 // per node.  With M_i = H^-1 (Q_i/(beta+1) + Q_i^T) and Q_i + Q_i^T = E_i
 // (Def. 1, E_i diagonal), M_i = H^-1 E_i - beta/(beta+1) D_i, so
@@ -346,13 +446,14 @@ struct SplitSmem<double, D, NP, EB> {
   double rw[EB][D + 2][NP];
 };
 
-template <typename T, int D, int NP, int EB, bool VISC>
+template <typename T, int D, int NP, int EB, bool VISC, bool CACHE = false>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
     int* __restrict__ status, double* __restrict__ prod, int visc_heat, const double* __restrict__ nu,
-    const double* __restrict__ ah, double* __restrict__ fvs, const double* __restrict__ ops64) {
+    const double* __restrict__ ah, double* __restrict__ fvs, const double* __restrict__ ops64,
+    double* __restrict__ fcache, int n_slot_total) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -475,6 +576,25 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       }
     }
     const JvpPrep<double> jp = jvp_prep<double, D>(nd);
+    if constexpr (CACHE) {
+      // nodal quantities of the facet nodes for the facet kernel that runs after
+      // this one (it then needs no logarithm, exponential or division for them)
+      const int sl0 = c_ref.node_slot[m];
+      if (sl0 >= 0) {
+        const size_t S = (size_t)n_slot_total, ix = (size_t)e * NS + sl0;
+        fcache[0 * S + ix] = nd.rho;
+        fcache[1 * S + ix] = nd.ir;
+        fcache[2 * S + ix] = nd.p;
+        fcache[3 * S + ix] = nd.e;
+        fcache[4 * S + ix] = nd.q;
+        fcache[5 * S + ix] = nd.lnq;
+        fcache[6 * S + ix] = nd.lnp;
+        fcache[7 * S + ix] = jp.iq;
+        fcache[8 * S + ix] = jp.itheta * nd.ir;  // 1/p
+#pragma unroll
+        for (int i = 0; i < D; ++i) fcache[(9 + i) * S + ix] = nd.V[i];
+      }
+    }
     double nonc[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) nonc[q] = 0.0;
@@ -491,7 +611,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     for (int q = 0; q < NC; ++q) {
       // the facet contributions include H^-1 sum_i E_i f_i (added by the facet kernel)
       res[q] = -kf * accd[q] - c64.inv_bp1 * nonc[q];
-      if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
+      if (!CACHE && sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
     }
     if constexpr (VISC) {
       {
@@ -743,8 +863,13 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   const Phys<T> ph = make_phys<T>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   const Phys<double> ph64 = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   const T* ops = std::is_same<T, double>::value ? (const T*)c->b.ops64 : (const T*)c->b.ops32;
-  // facet terms first: they fill the sat buffer the volume kernels add
-  {
+  const bool visc = c->prm.viscous != 0;
+  int scheme = c->prm.scheme;
+  // inviscid split scheme: volume kernel first (it caches the facet nodes'
+  // quantities), then the facet kernel adds into r; otherwise the facet terms
+  // come first and fill the sat buffer the volume kernels add
+  const bool cached = scheme == ESPLIT_SCHEME_SPLIT && !visc && sat == c->b.sat && c->b.fcache != nullptr;
+  if (!cached) {
     int bs = 128;
     int nb = (c->n_pairs + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
@@ -765,9 +890,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
                                                       nullptr);
     c->launches++;
   }
-  const bool visc = c->prm.viscous != 0;
   int np_used = 0;
-  int scheme = c->prm.scheme;
   int n_split = scheme == ESPLIT_SCHEME_SPLIT ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_split : 0);
   int n_had = (scheme == ESPLIT_SCHEME_HADAMARD || scheme == ESPLIT_SCHEME_HADAMARD_IR)
                   ? c->n_e
@@ -779,16 +902,31 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
     // the split kernel also forms the viscous volume terms (it has D_i w)
+    const int S = c->n_e * c->n_slot;
     if (visc)
       split_volume_kernel<T, D, NP, EB, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
-          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64);
+          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64, nullptr, S);
+    else if (cached)
+      split_volume_kernel<T, D, NP, EB, false, true><<<nb, EB * NP, 0, s>>>(
+          u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
+          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr, c->b.fcache, S);
     else
       split_volume_kernel<T, D, NP, EB, false><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
-          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr);
+          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr, nullptr, S);
     c->launches++;
     np_used += nb;
+  }
+  if (cached) {
+    int bs = 128;
+    int nb = (c->n_pairs + bs - 1) / bs;
+    ProfScope ps(c, PG_FACE, s);
+    face_cached_kernel<D><<<nb, bs, 0, s>>>(r, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.fcache,
+                                            c->n_e * c->n_slot, ph64, c->prm.dissipation,
+                                            prod ? prod + np_used : nullptr);
+    c->launches++;
+    if (prod) np_used += nb;
   }
   if (n_had > 0) {
     constexpr int EB = VolCfg<NP>::EB_HAD;
