@@ -135,7 +135,9 @@ def test_hybrid_extremes_match_pure_schemes(lib):
     rs = s.residual(ud).cpu().numpy()
     s.set_params(lib.Params(scheme="hadamard", dissipation=True))
     rh = s.residual(ud).cpu().numpy()
-    assert np.array_equal(r0, rs)
+    # the pure split scheme runs its facet kernel after the volume kernel, from
+    # cached nodal quantities (1/p as 1/theta times 1/rho): equal to round-off
+    assert rel_err(r0, rs) <= 1e-14
     assert np.array_equal(r1, rh)
     s.close()
 
