@@ -38,7 +38,7 @@ UNIT = "DOF-residual evals/s"
 FP64_PEAK_NOMINAL = 1.25e12            # recipe table: GB300 FP64 1.25 TFLOP/s
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged
 # kernel (profiles/split_volume_config2_p3_fp64.md); keyed by (kernel, p, precision, N)
-NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 221.257e6}
+NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 230.400e6}
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 
 
