@@ -1225,12 +1225,14 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
   st->dg_last = 0.0;
 }
 
-// Entropy change s(u + g d) - s(u) and slope w(u + g d) . d at one node,
-// from the cached s(u), 1/rho, 1/p, log q of u.
-template <int D>
+// Entropy change s(u + g d) - s(u), slope w(u + g d) . d and (SECOND)
+// curvature d . (dw/dg) at one node, from the cached s(u), 1/rho, 1/p, log q
+// of u.  Along u' = u + g d: drho' = d_0, dV' = (d_m - V' d_0)/rho',
+// dp' = (gam-1)(d_E - V'.d_m + |V'|^2 d_0/2), dq'/q' = a_q d_0/rho' + b_q dp'/p'.
+template <int D, bool SECOND = false>
 __device__ __forceinline__ void entropy_change_and_slope(const double* u, const double* dd, double g, double s0,
                                                          double ir, double ip, double lnq, const Phys<double>& c,
-                                                         double& ds, double& wd) {
+                                                         double& ds, double& wd, double* d2 = nullptr) {
   constexpr int NC = D + 2;
   double rho = u[0];
   double drho = g * dd[0], dE = g * dd[NC - 1];
@@ -1259,6 +1261,24 @@ __device__ __forceinline__ void entropy_change_and_slope(const double* u, const 
   }
   double W0 = q1 * (c.w1c * p1 * ir1 - 0.5 * v2);
   wd = W0 * dd[0] + q1 * vd - q1 * dd[NC - 1];
+  if constexpr (SECOND) {
+    double Vs[D], dV[D], vdm = 0.0, vdv = 0.0, dvd = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      Vs[i] = (u[1 + i] + g * dd[1 + i]) * ir1;
+      vdm += Vs[i] * dd[1 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      dV[i] = (dd[1 + i] - Vs[i] * dd[0]) * ir1;
+      vdv += Vs[i] * dV[i];
+      dvd += dV[i] * dd[1 + i];
+    }
+    double dp1 = c.gm1 * (dd[NC - 1] - vdm + 0.5 * v2 * dd[0]);
+    double dq1 = q1 * (c.a_q * dd[0] * ir1 + c.b_q * dp1 / p1);
+    double dW0 = dq1 * (c.w1c * p1 * ir1 - 0.5 * v2) + q1 * (c.w1c * (dp1 - p1 * dd[0] * ir1) * ir1 - vdv);
+    *d2 = dW0 * dd[0] + dq1 * vd + q1 * dvd - dq1 * dd[NC - 1];
+  }
 }
 
 template <int D>
@@ -1287,10 +1307,12 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
     double ip = __ldg(&cache[2 * n_nodes + t]), lnq = __ldg(&cache[3 * n_nodes + t]);
     double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
     double ds, wd;
-    entropy_change_and_slope<D>(uu, dd, ga, s0, ir, ip, lnq, c, ds, wd);
+    double d2 = 0.0;
+    entropy_change_and_slope<D, true>(uu, dd, ga, s0, ir, ip, lnq, c, ds, wd, &d2);
     v[0] = H * ds;
     v[1] = H * wd;
     v[2] = H * fabs(ds);
+    v[3] = H * d2;  // curvature; replaced below when a second point is evaluated
     if (gb > 0.0) {
       entropy_change_and_slope<D>(uu, dd, gb, s0, ir, ip, lnq, c, ds, wd);
       v[3] = H * ds;
@@ -1315,13 +1337,31 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
   const double eps = 2.220446049250313e-16;
   const double est = st->est;
   st->iters += 1;
-  if (st->phase == 0) {  // f, f' at g = 1
-    double f1 = tot[0] - est, df1 = tot[1] - est;
+  if (st->phase == 0) {  // f, f', f'' at g = 1
+    double f1 = tot[0] - est, df1 = tot[1] - est, d2f = tot[3];
     double floor = 64.0 * eps * st->Sabs;
     if (fabs(f1) <= floor && fabs(df1) <= floor) {
       st->g = 1.0;
       st->done = 1;
       return;
+    }
+    if (df1 > 0.0 && d2f >= 0.0) {
+      // Halley's step from g = 1 (f is convex): its error is third order in the
+      // Newton step dn, ~ (f''/f')^2 |dn|^3 / 4.  Accept it without a further
+      // pass when f' times four times that error stays within the tolerance the
+      // Newton phase stops at, 4 eps (sum H |ds| + |g est|)
+      const double dn = -f1 / df1;
+      const double den = 2.0 * df1 * df1 - f1 * d2f;
+      const double k = d2f / df1;
+      if (den > 0.0 && fabs(dn) < 0.25 &&
+          df1 * k * k * fabs(dn) * dn * dn <= 4.0 * eps * (tot[2] + fabs(est))) {
+        const double dh = -2.0 * f1 * df1 / den;
+        st->g = 1.0 + dh;
+        st->phase = 3;
+        st->dS_last = tot[0] + dh * tot[1] + 0.5 * dh * dh * d2f;
+        st->done = 1;
+        return;
+      }
     }
     double gn = df1 > 0.0 ? 1.0 - f1 / df1 : -1.0;
     if (gn > 0.5 && gn < 1.5) {
