@@ -59,7 +59,7 @@ int check_ready(esplit_ctx* c) {
 }
 
 int ensure_partial(esplit_ctx* c) {
-  size_t need = 6 * ((size_t)c->n_e * c->n_p / 256 + 1) + 2 * ((size_t)c->n_e + 64);
+  size_t need = 8 * ((size_t)c->n_e * c->n_p / 256 + 1) + 4 * ((size_t)c->n_e + 64);
   if (c->partial_cap >= need) return ESPLIT_OK;
   int rc = dalloc(c, &c->b.partial, need);
   if (rc) return rc;
@@ -511,31 +511,64 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
   static const double A[4] = {0.0, 0.5, 0.5, 1.0};
   static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   int np = 0;
-  // S0 and sum H |s| of u_n -> scal[0..1]
-  if (esplit::launch_entropy(c, u, s, &np, c->b.node_cache) ||
-      esplit::launch_reduce(c, c->b.partial, np, 2, c->b.scal, s))
-    return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
+  // block-partial regions: entropy of u_n (width 2) first, then the four stage
+  // productions (width 1); reduced together after the stages
+  esplit::ReduceRegions R{};
+  const int ent_cap = (int)std::max<size_t>((size_t)c->n_e * c->n_p / 256 + 1, (size_t)c->n_e);
+  int off = 2 * ent_cap;
+  // stage 0: the split volume kernel computes the entropy of u_n on the way
+  // (entropy-split scheme); otherwise the entropy kernel does
+  c->ent_part = c->b.partial;
+  c->ent_n = 0;
   for (int i = 0; i < 4; ++i) {
     const double* Ui = (i == 0) ? u : c->b.stage_u;
-    if ((rc = residual_impl(c, Ui, c->b.stage_r, s, c->b.partial, &np))) return rc;
-    if (esplit::launch_reduce(c, c->b.partial, np, 1, c->b.scal + 2 + i, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
+    rc = residual_impl(c, Ui, c->b.stage_r, s, c->b.partial + off, &np);
+    if (i == 0) {
+      c->ent_part = nullptr;
+      if (rc) return rc;
+      int ne = c->ent_n;
+      if (ne == 0 && esplit::launch_entropy(c, u, s, &ne, c->b.node_cache, c->b.partial))
+        return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
+      R.off[0] = 0;
+      R.cnt[0] = ne;
+      R.width[0] = 2;
+      R.out[0] = c->b.scal;
+    }
+    if (rc) return rc;
+    R.off[1 + i] = off;
+    R.cnt[1 + i] = np;
+    R.width[1 + i] = 1;
+    R.out[1 + i] = c->b.scal + 2 + i;
+    off += np;
     double a_next = (i < 3) ? A[i + 1] * dt : 0.0;
     if (esplit::launch_stage(c, u, c->b.stage_r, a_next, B[i] * dt, i == 0, (i < 3) ? c->b.stage_u : nullptr,
                              c->b.dacc, n, s))
       return fail(c, ESPLIT_ERR_CUDA, "stage launch");
   }
+  R.n = 5;
+  if (esplit::launch_reduce_regions(c, c->b.partial, R, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
   if (esplit::launch_root_start(c, dt, s)) return fail(c, ESPLIT_ERR_CUDA, "root init");
   esplit::RootState st{};
-  for (int it = 0; it < esplit::ROOT_EVALS_MAX; ++it) {
+  // two evaluation passes and the (guarded) update go out without a host
+  // round trip: the first pass usually ends the solve (Halley step at g = 1)
+  for (int it = 0; it < 2; ++it)
     if (esplit::launch_root_eval(c, u, c->b.dacc, s, &np) || esplit::launch_root_update(c, np, s))
       return fail(c, ESPLIT_ERR_CUDA, "root launch");
-    if ((it + 1) % esplit::ROOT_CHECK_EVERY == 0) {
-      CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (st.done) break;
-    }
-  }
   if (esplit::launch_root_apply(c, u, c->b.dacc, n, s)) return fail(c, ESPLIT_ERR_CUDA, "apply launch");
+  CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!st.done) {
+    for (int it = 2; it < esplit::ROOT_EVALS_MAX; ++it) {
+      if (esplit::launch_root_eval(c, u, c->b.dacc, s, &np) || esplit::launch_root_update(c, np, s))
+        return fail(c, ESPLIT_ERR_CUDA, "root launch");
+      if ((it + 1) % esplit::ROOT_CHECK_EVERY == 0) {
+        CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (st.done) break;
+      }
+    }
+    if (esplit::launch_root_apply(c, u, c->b.dacc, n, s)) return fail(c, ESPLIT_ERR_CUDA, "apply launch");
+  }
   double e_stage[4];
   CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(e_stage, c->b.scal + 2, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -102,6 +102,11 @@ struct esplit_ctx {
   std::vector<unsigned char> flags;
   std::string err;
   long long launches = 0;
+  // set by the relaxation step around its first stage residual: the split
+  // volume kernel then also writes the entropy of u_n (node cache + block
+  // partials of H s, H |s| at ent_part) and reports its block count in ent_n
+  double* ent_part = nullptr;
+  int ent_n = 0;
   cudaStream_t last_stream = nullptr;
   bool prof = false;
   std::vector<esplit::ProfRec> recs;
@@ -126,7 +131,14 @@ struct ProfScope {
 int launch_build_ops(esplit_ctx* c, cudaStream_t s);
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod_partial,
                     int* n_partial);
-int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache = nullptr);
+int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache = nullptr,
+                   double* part = nullptr);
+struct ReduceRegions {
+  int n;
+  int off[6], cnt[6], width[6];
+  double* out[6];
+};
+int launch_reduce_regions(esplit_ctx* c, const double* partial, const ReduceRegions& R, cudaStream_t s);
 int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStream_t s, int* n_partial,
                         double* part = nullptr, int width = 2);
 int launch_viscous_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);

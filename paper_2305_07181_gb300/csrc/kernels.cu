@@ -446,14 +446,15 @@ struct SplitSmem<double, D, NP, EB> {
   double rw[EB][D + 2][NP];
 };
 
-template <typename T, int D, int NP, int EB, bool VISC, bool CACHE = false>
+template <typename T, int D, int NP, int EB, bool VISC, bool CACHE = false, bool ENT = false>
 __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
     int* __restrict__ status, double* __restrict__ prod, int visc_heat, const double* __restrict__ nu,
     const double* __restrict__ ah, double* __restrict__ fvs, const double* __restrict__ ops64,
-    double* __restrict__ fcache, int n_slot_total) {
+    double* __restrict__ fcache, int n_slot_total, double* __restrict__ ent_part = nullptr,
+    double* __restrict__ ncache = nullptr) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     }
     __syncthreads();
   }
-  double hw = 0.0;
+  double hw = 0.0, ent_s = 0.0, ent_a = 0.0;
   const int sl = c_ref.node_slot[m];
   const T* op = ops + (size_t)e * (2 * D * NP * NP);
   const double* op64 = VISC ? ops64 + (size_t)e * (2 * D * NP * NP) : nullptr;
@@ -576,6 +577,19 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
       }
     }
     const JvpPrep<double> jp = jvp_prep<double, D>(nd);
+    if constexpr (ENT) {
+      // entropy of u_n for the relaxation step (the entropy kernel's outputs):
+      // S_H = beta q p, and the per-node values its evaluation passes reuse
+      const size_t nn = (size_t)n_list * NP, g = (size_t)e * NP + m;
+      const double sH = c64.beta * nd.q * nd.p;
+      ncache[g] = sH;
+      ncache[nn + g] = nd.ir;
+      ncache[2 * nn + g] = jp.itheta * nd.ir;  // 1/p
+      ncache[3 * nn + g] = nd.lnq;
+      const double Hm0 = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
+      ent_s = Hm0 * sH;
+      ent_a = Hm0 * fabs(sH);
+    }
     if constexpr (CACHE) {
       // nodal quantities of the facet nodes for the facet kernel that runs after
       // this one (it then needs no logarithm, exponential or division for them)
@@ -680,6 +694,11 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
   if (prod) {
     double v[1] = {hw};
     block_sum<1>(v, prod + blockIdx.x);
+  }
+  if constexpr (ENT) {
+    __syncthreads();  // the block sum's shared scratch is reused
+    double v2[2] = {ent_s, ent_a};
+    block_sum<2>(v2, ent_part + 2 * blockIdx.x);
   }
 }
 
@@ -907,7 +926,13 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
       split_volume_kernel<T, D, NP, EB, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
           prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64, nullptr, S);
-    else if (cached)
+    else if (cached && c->ent_part && c->b.node_cache) {
+      split_volume_kernel<T, D, NP, EB, false, true, true><<<nb, EB * NP, 0, s>>>(
+          u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
+          prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr, c->b.fcache, S, c->ent_part,
+          c->b.node_cache);
+      c->ent_n = nb;
+    } else if (cached)
       split_volume_kernel<T, D, NP, EB, false, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
           prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr, c->b.fcache, S);
@@ -1090,15 +1115,16 @@ __global__ void __launch_bounds__(256) entropy_rate_kernel(const double* __restr
   }
 }
 
-int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache) {
+int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partial, double* cache, double* part) {
   size_t n = (size_t)c->n_e * c->n_p;
   int nb = (int)((n + 255) / 256);
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ENTROPY, s);
+  double* out = part ? part : c->b.partial;
   if (c->dim == 2)
-    entropy_kernel<2><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial, cache);
+    entropy_kernel<2><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, out, cache);
   else
-    entropy_kernel<3><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, c->b.partial, cache);
+    entropy_kernel<3><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, out, cache);
   c->launches++;
   *n_partial = nb;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -1136,6 +1162,28 @@ __global__ void __launch_bounds__(1024) reduce_partials_kernel(const double* __r
     block_sum<1>(v, out + k);
     __syncthreads();
   }
+}
+
+// several block-partial regions reduced in one launch, one block per region,
+// each in a fixed order (deterministic)
+__global__ void __launch_bounds__(1024) reduce_regions_kernel(const double* __restrict__ part, ReduceRegions R) {
+  const int g = blockIdx.x;
+  if (g >= R.n) return;
+  const double* p = part + R.off[g];
+  const int w = R.width[g], cnt = R.cnt[g];
+  for (int k = 0; k < w; ++k) {
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) v[0] += p[(size_t)i * w + k];
+    block_sum<1>(v, R.out[g] + k);
+    __syncthreads();
+  }
+}
+
+int launch_reduce_regions(esplit_ctx* c, const double* partial, const ReduceRegions& R, cudaStream_t s) {
+  ProfScope ps(c, PG_ENTROPY, s);
+  reduce_regions_kernel<<<R.n, 1024, 0, s>>>(partial, R);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_reduce(esplit_ctx* c, const double* partial, int n_partial, int width, double* out, cudaStream_t s) {
@@ -1513,7 +1561,7 @@ int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s) {
 
 __global__ void root_apply_kernel(double* __restrict__ un, const double* __restrict__ d, size_t n,
                                   const RootState* __restrict__ st, const int* __restrict__ status) {
-  if (st->status != 0 || *status != 0) return;
+  if (!st->done || st->status != 0 || *status != 0) return;
   double g = st->g;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
