@@ -447,7 +447,7 @@ struct SplitSmem<double, D, NP, EB> {
 };
 
 template <typename T, int D, int NP, int EB, bool VISC, bool CACHE = false, bool ENT = false>
-__global__ void __launch_bounds__(EB * NP) split_volume_kernel(
+__global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ? 3 : 1) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
@@ -481,24 +481,21 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
     for (int q = 0; q < NC; ++q) sm.rw[el][q][m] = nd.W[q];
   }
   __syncthreads();
-  double f0[D][NC], w0[NC];
   if constexpr (!F64) {
     if (active) {
 #pragma unroll
       for (int i = 0; i < D; ++i)
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          f0[i][q] = sm.rf[el][i][q][0];
           float hi, lo;
-          split_f64(sm.rf[el][i][q][m] - f0[i][q], hi, lo);
+          split_f64(sm.rf[el][i][q][m] - sm.rf[el][i][q][0], hi, lo);
           sm.sf[el][i][q][m] = hi;
           sm.sfl[el][i][q][m] = lo;
         }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        w0[q] = sm.rw[el][q][0];
         float hi, lo;
-        split_f64(sm.rw[el][q][m] - w0[q], hi, lo);
+        split_f64(sm.rw[el][q][m] - sm.rw[el][q][0], hi, lo);
         sm.sw[el][q][m] = hi;
         sm.swl[el][q][m] = lo;
       }
@@ -571,8 +568,8 @@ __global__ void __launch_bounds__(EB * NP) split_volume_kernel(
         double rd = __ldg(&rs[(D + i) * NP + m]);
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          accd[q] += f0[i][q] * rd;
-          gd[i][q] += w0[q] * rd;
+          accd[q] += sm.rf[el][i][q][0] * rd;  // node-0 values, re-read (fewer live registers)
+          gd[i][q] += sm.rw[el][q][0] * rd;
         }
       }
     }
@@ -922,6 +919,18 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     ProfScope ps(c, PG_SPLIT, s);
     // the split kernel also forms the viscous volume terms (it has D_i w)
     const int S = c->n_e * c->n_slot;
+    if (!std::is_same<T, double>::value) {
+      // the float32 variant is sized for three blocks per SM: ask for the shared
+      // memory they need (48 KB each)
+      static bool carve_set = false;
+      if (!carve_set) {
+        cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, false, true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, false, true, true>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        carve_set = true;
+      }
+    }
     if (visc)
       split_volume_kernel<T, D, NP, EB, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
