@@ -338,6 +338,49 @@ def taylor_green_run(es, device, flush, steps=5):
     return out
 
 
+def small_and_adjoint_run(es, device, flush):
+    """Config 1 (8 x 8 quads -> 128 curved triangles, p = 2, vortex, EC split,
+    relaxation RK4 at CFL 0.1 for 20 steps: launch-latency bound) and config 4
+    (32,768 curved triangles, p = 3, vortex + 1e-3 noise, FP64: reverse mode of
+    the residual and of one relaxation step with dissipation, per call)."""
+    from esplit_inputs import tri_operator, periodic_tri_mesh, states
+    stream = torch.cuda.current_stream(device)
+    out = {}
+    op = tri_operator(2)
+    m = periodic_tri_mesh(op, 8, 10.0, 0.05)
+    u0 = states.isentropic_vortex(m)
+    dt = states.cfl_timestep(m, u0, 0.1)
+    s = es.Solver(op, m, es.Params(), device=device)
+    u = s.to_device(u0)
+    for _ in range(3):
+        s.rrk_step(u, dt)
+    u = s.to_device(u0)
+    ts = _timed(lambda: s.rrk_step(u, dt), stream, flush, 20)
+    out["config1_rrk"] = {"ms_per_step": statistics.median(ts), "steps_per_s": 1e3 / statistics.median(ts),
+                          "n_e": m.n_e, "steps": 20}
+    s.close()
+    op, m, u0, dt = workload(3, 128)
+    s = es.Solver(op, m, es.Params(dissipation=True), device=device)
+    ud = s.to_device(u0)
+    cot = s.to_device(np.random.default_rng(4).normal(size=u0.shape))
+    g = s.empty()
+    for _ in range(3):
+        s.residual_vjp(ud, cot, g)
+    ms_vjp = statistics.median(_timed(lambda: s.residual_vjp(ud, cot, g), stream, flush, 10))
+    r = s.empty()
+    ms_res = statistics.median(_timed(lambda: s.residual(ud, r), stream, flush, 10))
+    for _ in range(2):
+        s.rrk_step_vjp(ud, dt, cot)
+    ms_step_vjp = statistics.median(_timed(lambda: s.rrk_step_vjp(ud, dt, cot), stream, flush, 5))
+    dof = m.n_e * op.n_p
+    out["config4_adjoint"] = {"residual_vjp_ms": ms_vjp, "residual_ms": ms_res, "vjp_over_residual": ms_vjp / ms_res,
+                              "rrk_step_vjp_ms": ms_step_vjp, "dof": dof,
+                              "note": "the step reverse recomputes the step from its checkpoint, then runs four "
+                                      "residual VJPs and the implicit-function term of g"}
+    s.close()
+    return out
+
+
 def quadrant_run(es, device, flush, t_final=None, steps=20):
     """2D Riemann-type problem: periodic [0, 1]^2, 256 x 256 quads -> 131,072
     affine triangles, p = 2, four constant quadrant states (seed 5, pressure
@@ -481,6 +524,8 @@ def main():
         extras["taylor_green"] = taylor_green_run(es, device, flush)
     if rank == 0 and not args.no_quadrants:
         extras["quadrants"] = quadrant_run(es, device, flush, t_final=0.25 if args.quadrants_full else None)
+    if rank == 0 and not args.no_sweep:
+        extras.update(small_and_adjoint_run(es, device, flush))
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(op, mesh, u0)
