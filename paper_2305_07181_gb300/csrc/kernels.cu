@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ?
         }
       }
     }
-    const JvpPrep<double> jp = jvp_prep<double, D>(nd);
+    const JvpPrep<double> jp = jvp_prep<double, D>(nd, c64);
     if constexpr (ENT) {
       // entropy of u_n for the relaxation step (the entropy kernel's outputs):
       // S_H = beta q p, and the per-node values its evaluation passes reuse

@@ -138,15 +138,21 @@ __device__ __forceinline__ void euler_flux(const Node<T, D>& n, int i, T* F) {
 template <typename T>
 struct JvpPrep {
   T iq, ir, theta, itheta;
+  T w0q, rq, ep;  // w1c theta - |V|^2/2, rho/(a_q + b_q), e + p (shared by the directions)
 };
 
-template <typename T, int D>
-__device__ __forceinline__ JvpPrep<T> jvp_prep(const Node<T, D>& n) {
+template <typename T, int D, typename C>
+__device__ __forceinline__ JvpPrep<T> jvp_prep(const Node<T, D>& n, const C& c) {
   JvpPrep<T> j;
-  j.iq = T(1) / n.q;
+  // one division for 1/q and rho/p: y = 1/(q p), 1/q = p y, 1/p = q y
+  const T y = T(1) / (n.q * n.p);
+  j.iq = n.p * y;
   j.ir = n.ir;
   j.theta = n.p * j.ir;
-  j.itheta = n.rho / n.p;
+  j.itheta = n.rho * (n.q * y);
+  j.w0q = c.w1c * j.theta - T(0.5) * n.v2;
+  j.rq = n.rho * c.inv_apb;
+  j.ep = n.e + n.p;
   return j;
 }
 
@@ -163,9 +169,8 @@ __device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& 
     vdv += n.V[j] * dV[j];
   }
   T theta = jp.theta;
-  T w0q = c.w1c * theta - T(0.5) * n.v2;
-  T dtheta = c.inv_w1c * ((v[0] - dq * w0q) * iq + vdv);
-  T drho = n.rho * c.inv_apb * (dq * iq - c.b_q * dtheta * jp.itheta);
+  T dtheta = c.inv_w1c * ((v[0] - dq * jp.w0q) * iq + vdv);
+  T drho = jp.rq * (dq * iq - c.b_q * dtheta * jp.itheta);
   T dp = drho * theta + n.rho * dtheta;
   T dm = drho * n.V[i] + n.rho * dV[i];
   dF[0] = dm;
@@ -173,7 +178,7 @@ __device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& 
 #pragma unroll
   for (int j = 0; j < D; ++j) dF[1 + j] = dm * n.V[j] + rvi * dV[j] + (j == i ? dp : T(0));
   T de = dp * c.inv_gm1 + T(0.5) * drho * n.v2 + n.rho * vdv;
-  dF[D + 1] = (de + dp) * n.V[i] + (n.e + n.p) * dV[i];
+  dF[D + 1] = (de + dp) * n.V[i] + jp.ep * dV[i];
 }
 
 // Powers of the parameter vector used by the two-point flux and the

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(EB * NP) split_vjp_kernel(const double* __rest
 #pragma unroll
         for (int q = 0; q < NC; ++q) g[i][q] += dt * sw[el][q][n];
       }
-    const JvpPrep<double> jp = jvp_prep<double, D>(nd);
+    const JvpPrep<double> jp = jvp_prep<double, D>(nd, c);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       double a[NC];
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(EB * NP) split_vjp_kernel(const double* __rest
   }
   Node<TD, D> ndd;
   node_from_u<TD, D>(ud, c, ndd);
-  const JvpPrep<TD> jpd = jvp_prep<TD, D>(ndd);
+  const JvpPrep<TD> jpd = jvp_prep<TD, D>(ndd, c);
   double gr[NC];
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) gr[cc] = 0.0;
