@@ -38,7 +38,7 @@ UNIT = "DOF-residual evals/s"
 FP64_PEAK_NOMINAL = 1.25e12            # recipe table: GB300 FP64 1.25 TFLOP/s
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged
 # kernel (profiles/split_volume_config2_p3_fp64.md); keyed by (kernel, p, precision, N)
-NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 230.400e6}
+NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 229.968e6}
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 
 
@@ -191,7 +191,7 @@ def cpu_baseline(op, mesh, u0, budget_s=12.0):
     evaluations (split + EC SAT + dissipation) until the time budget is spent."""
     from oracle import residual as R
     from oracle.physics import Params as OP
-    R.residual(u0, op, mesh, OP(), dissipation=True, elems=np.arange(64))  # warm the vmap path
+    R.residual(u0, op, mesh, OP(), dissipation=True, elems=np.arange(min(64, mesh.n_e)))  # warm the vmap path
     n, t0 = 0, time.perf_counter()
     while True:
         R.residual(u0, op, mesh, OP(), dissipation=True)
@@ -212,7 +212,7 @@ def run_reference(args):
     from oracle import residual as R
     from oracle.physics import Params as OP
     op, mesh, u0, dt = workload(args.p, args.N)
-    R.residual(u0, op, mesh, OP(), dissipation=True, elems=np.arange(64))
+    R.residual(u0, op, mesh, OP(), dissipation=True, elems=np.arange(min(64, mesh.n_e)))
     for _ in range(args.warmup):
         R.residual(u0, op, mesh, OP(), dissipation=True)
     times = []
@@ -357,7 +357,16 @@ def small_and_adjoint_run(es, device, flush):
     u = s.to_device(u0)
     ts = _timed(lambda: s.rrk_step(u, dt), stream, flush, 20)
     out["config1_rrk"] = {"ms_per_step": statistics.median(ts), "steps_per_s": 1e3 / statistics.median(ts),
-                          "n_e": m.n_e, "steps": 20}
+                          "n_e": m.n_e, "steps": 20, "launch": "one host-driven step per call"}
+    # the 20 steps as one batch of graph-launched steps (no host round trip
+    # between steps); recorded by the first, untimed batch
+    u = s.to_device(u0)
+    s.rrk_steps(u, dt, 20)
+    u = s.to_device(u0)
+    ms = _timed(lambda: s.rrk_steps(u, dt, 20), stream, flush, 5)
+    out["config1_rrk_graph"] = {"ms_per_step": statistics.median(ms) / 20, "steps_per_s": 20e3 / statistics.median(ms),
+                                "n_e": m.n_e, "steps": 20,
+                                "launch": "esplit_rrk_steps: 20 steps per call, each step one CUDA graph launch"}
     s.close()
     op, m, u0, dt = workload(3, 128)
     s = es.Solver(op, m, es.Params(dissipation=True), device=device)

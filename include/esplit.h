@@ -203,6 +203,25 @@ int esplit_entropy_rate(esplit_ctx* ctx, const double* u_dev, const double* dudt
 int esplit_rrk_step(esplit_ctx* ctx, double* u_dev, double dt, double* g_out, esplit_stepinfo* info,
                     void* stream);
 
+/* n_steps relaxation RK4 steps of Sec. 6.1 with the same dt, without a host
+ * round trip between steps (no counterpart in the paper: a launch-latency
+ * measure for small meshes).  Each step makes exactly the launches of
+ * esplit_rrk_step, so u_dev ends bit-identical to n_steps calls of it; the
+ * step is recorded once as a CUDA graph (the root solve as a device-side
+ * while loop) for this u_dev pointer, dt and configuration, and re-recorded
+ * when any of them changes, the first step of a new recording running the
+ * ordinary way.  With profiling on, the steps run one by one.
+ *   g_out: n_steps doubles (host, may be NULL), each step's g.
+ *   info:  the summary of the last step run (host, may be NULL).
+ *   n_done: the number of completed steps (host, may be NULL).
+ * Hybrid flags and parameters stay as they are for the whole batch.  On a
+ * failing step (ESPLIT_ERR_NONPHYSICAL, ESPLIT_ERR_RRK_NO_ROOT) u_dev holds the
+ * state after the last completed step: the failing step and the rest of the
+ * batch, which still run, leave it unchanged.  Synchronises `stream` once per
+ * 1024 steps and at the end. */
+int esplit_rrk_steps(esplit_ctx* ctx, double* u_dev, double dt, int n_steps, double* g_out,
+                     esplit_stepinfo* info, int* n_done, void* stream);
+
 /* Same step with a host state: copies u_host (pinned or pageable) to the
  * device, steps, copies the new state back, and synchronises `stream`. */
 int esplit_rrk_step_host(esplit_ctx* ctx, double* u_host, double dt, double* g_out, esplit_stepinfo* info,

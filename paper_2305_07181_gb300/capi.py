@@ -68,6 +68,8 @@ _SIGNATURES = {
     "esplit_entropy_rate": (_I, [_P, _P, _P, _D, _P]),
     "esplit_rrk_step": (_I, [_P, _P, ctypes.c_double, _D, ctypes.POINTER(esplit_stepinfo), _P]),
     "esplit_rrk_step_host": (_I, [_P, _P, ctypes.c_double, _D, ctypes.POINTER(esplit_stepinfo), _P]),
+    "esplit_rrk_steps": (_I, [_P, _P, ctypes.c_double, ctypes.c_int, _D, ctypes.POINTER(esplit_stepinfo),
+                              ctypes.POINTER(ctypes.c_int), _P]),
     "esplit_residual_vjp": (_I, [_P, _P, _P, _P, _P]),
     "esplit_entropy_grad": (_I, [_P, _P, _P, _P]),
     "esplit_rrk_step_vjp": (_I, [_P, _P, ctypes.c_double, _P, _P, _D, _P]),
@@ -178,6 +180,14 @@ def esplit_rrk_step(ctx, u_ptr, dt, stream=None):
     info = esplit_stepinfo()
     rc = lib.esplit_rrk_step(ctx, u_ptr, dt, ctypes.byref(g), ctypes.byref(info), stream)
     return rc, g.value, info
+
+
+def esplit_rrk_steps(ctx, u_ptr, dt, n_steps, stream=None):
+    g = (ctypes.c_double * max(n_steps, 1))()
+    info = esplit_stepinfo()
+    done = ctypes.c_int()
+    rc = lib.esplit_rrk_steps(ctx, u_ptr, dt, n_steps, g, ctypes.byref(info), ctypes.byref(done), stream)
+    return rc, list(g)[:done.value], info, done.value
 
 
 def esplit_rrk_step_host(ctx, u_host_ptr, dt, stream=None):

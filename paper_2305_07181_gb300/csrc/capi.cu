@@ -160,6 +160,11 @@ void esplit_destroy(esplit_ctx* c) {
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.vfb, b.vfs, b.vus};
   for (void* p : ps) dfree(p);
+  if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
+  if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
+  if (c->cap_s) cudaStreamDestroy(c->cap_s);
+  if (c->cap_s2) cudaStreamDestroy(c->cap_s2);
+  dfree(c->hist);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -171,6 +176,7 @@ void esplit_destroy(esplit_ctx* c) {
 int esplit_upload_operator(esplit_ctx* c, int n_p, int n_fac, int n_f, const double* H_ref, const double* Q_ref,
                            const int* facet_nodes, const double* facet_w, const double* ref_normals) {
   if (!c) return ESPLIT_ERR_ARG;
+  c->version++;
   if (!H_ref || !Q_ref || !facet_nodes) return fail(c, ESPLIT_ERR_ARG, "null operator array");
   if (n_p <= 0 || n_fac <= 0 || n_f <= 0) return fail(c, ESPLIT_ERR_ARG, "operator sizes must be positive");
   if (!supported(c->dim, n_p))
@@ -229,6 +235,7 @@ static int ensure_hybrid(esplit_ctx* c) {
 int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* Lambda, const double* nu,
                        const int* pair, const double* hmin) {
   if (!c) return ESPLIT_ERR_ARG;
+  c->version++;
   if (!c->have_op) return fail(c, ESPLIT_ERR_STATE, "upload the operator before the mesh");
   if (n_e <= 0 || !J || !Lambda || !nu || !pair) return fail(c, ESPLIT_ERR_ARG, "bad mesh arguments");
   (void)hmin;
@@ -306,6 +313,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
 
 int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
   if (!c || !p) return ESPLIT_ERR_ARG;
+  c->version++;
   if (!(p->gam > 1.0)) return fail(c, ESPLIT_ERR_ARG, "gam must exceed 1");
   double alpha = -p->gam - p->beta * (p->gam - 1.0);
   if (!(alpha < -p->gam || alpha > 0.0)) return fail(c, ESPLIT_ERR_ARG, "beta must give alpha < -gam or alpha > 0");
@@ -333,6 +341,7 @@ int esplit_get_params(esplit_ctx* c, esplit_params* p) {
 
 int esplit_set_hybrid_flags(esplit_ctx* c, const unsigned char* flags, int n_e) {
   if (!c || !flags) return ESPLIT_ERR_ARG;
+  c->version++;
   if (!c->have_mesh) return fail(c, ESPLIT_ERR_STATE, "upload the mesh before the hybrid flags");
   if (n_e != c->n_e) return fail(c, ESPLIT_ERR_ARG, "flags length must equal n_e");
   cudaSetDevice(c->device);
@@ -355,6 +364,7 @@ int esplit_set_hybrid_flags(esplit_ctx* c, const unsigned char* flags, int n_e) 
 int esplit_detect_hybrid(esplit_ctx* c, const double* u, double threshold, int* n_flagged, void* stream) {
   int rc = check_ready(c);
   if (rc) return rc;
+  c->version++;
   if (!u) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
   if (!(threshold >= 1.0) || !std::isfinite(threshold)) return fail(c, ESPLIT_ERR_ARG, "threshold must be finite and >= 1");
   cudaSetDevice(c->device);
@@ -491,7 +501,8 @@ int esplit_entropy_rate(esplit_ctx* c, const double* u, const double* r, double*
   return ESPLIT_OK;
 }
 
-int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_stepinfo* info, void* stream) {
+// Preconditions of a relaxation step; allocates the stage buffers once.
+static int rrk_prepare(esplit_ctx* c, const double* u, double dt) {
   int rc = check_ready(c);
   if (rc) return rc;
   if (!u) return fail(c, ESPLIT_ERR_ARG, "null state pointer");
@@ -500,7 +511,6 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     return fail(c, ESPLIT_ERR_UNSUPPORTED, "the relaxation step uses Harten's entropy; the Ismail-Roe comparator "
                                            "conserves the standard one");
   cudaSetDevice(c->device);
-  cudaStream_t s = as_stream(stream);
   size_t n = (size_t)c->n_e * c->n_c * c->n_p;
   if (!c->b.stage_u) {
     if ((rc = dalloc(c, &c->b.stage_u, n))) return rc;
@@ -508,9 +518,17 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
     if ((rc = dalloc(c, &c->b.dacc, n))) return rc;
     if ((rc = dalloc(c, &c->b.node_cache, 4 * (size_t)c->n_e * c->n_p))) return rc;
   }
+  return ESPLIT_OK;
+}
+
+// The four RK4 stages (Eq. (98) with the classical tableau), the entropy of
+// u_n, the reduction of the stage entropy productions and the root-solve
+// start, all enqueued on s.
+static int rrk_enqueue_stages(esplit_ctx* c, const double* u, double dt, cudaStream_t s) {
   static const double A[4] = {0.0, 0.5, 0.5, 1.0};
   static const double B[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-  int np = 0;
+  const size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  int np = 0, rc;
   // block-partial regions: entropy of u_n (width 2) first, then the four stage
   // productions (width 1); reduced together after the stages
   esplit::ReduceRegions R{};
@@ -548,6 +566,16 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
   R.n = 5;
   if (esplit::launch_reduce_regions(c, c->b.partial, R, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
   if (esplit::launch_root_start(c, dt, s)) return fail(c, ESPLIT_ERR_CUDA, "root init");
+  return ESPLIT_OK;
+}
+
+int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_stepinfo* info, void* stream) {
+  int rc = rrk_prepare(c, u, dt);
+  if (rc) return rc;
+  cudaStream_t s = as_stream(stream);
+  const size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  if ((rc = rrk_enqueue_stages(c, u, dt, s))) return rc;
+  int np = 0;
   esplit::RootState st{};
   // two evaluation passes and the (guarded) update go out without a host
   // round trip: the first pass usually ends the solve (Halley step at g = 1)
@@ -590,6 +618,167 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
   }
   if (status == ESPLIT_ERR_NONPHYSICAL) return fail(c, status, "non-physical state during the step");
   if (status == ESPLIT_ERR_RRK_NO_ROOT) return fail(c, status, "relaxation parameter could not be bracketed");
+  return ESPLIT_OK;
+}
+
+namespace {
+constexpr int HIST_CAP = 1024;  // step records per batch chunk (one host read each)
+
+void drop_step_graph(esplit_ctx* c) {
+  if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
+  if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
+  c->sg = StepGraph{};
+}
+}  // namespace
+
+// Records one relaxation step for state u and dt as a CUDA graph: the stages,
+// reductions and root start as captured from rrk_enqueue_stages, the root
+// solve as a conditional while node whose body is one evaluation pass and one
+// update (the update clears the loop condition once the root is done), then
+// the guarded update of u and the step record.  The launches are the ones
+// esplit_rrk_step makes, in the same order, so the results are identical.
+static int rrk_capture(esplit_ctx* c, double* u, double dt) {
+  drop_step_graph(c);
+  if (!c->cap_s) CK(cudaStreamCreateWithFlags(&c->cap_s, cudaStreamNonBlocking));
+  if (!c->cap_s2) CK(cudaStreamCreateWithFlags(&c->cap_s2, cudaStreamNonBlocking));
+  if (!c->hist) CK(cudaMalloc(&c->hist, HIST_CAP * sizeof(esplit::StepRecord) + 256));
+  esplit::StepRecord* hist = static_cast<esplit::StepRecord*>(c->hist);
+  int* counter = reinterpret_cast<int*>(hist + HIST_CAP);
+  const size_t n = (size_t)c->n_e * c->n_c * c->n_p;
+  cudaStream_t cs = c->cap_s;
+  const long long l0 = c->launches;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  std::string why;
+  int rc = rrk_enqueue_stages(c, u, dt, cs);
+  if (rc) why = "stages";
+  cudaGraphConditionalHandle h = 0;
+  if (!rc) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNode_t cn = nullptr;
+    cudaGraphNodeParams prm = {};
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+    if (e == cudaSuccess && cst != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      prm.type = cudaGraphNodeTypeConditional;
+      prm.conditional.handle = h;
+      prm.conditional.type = cudaGraphCondTypeWhile;
+      prm.conditional.size = 1;
+      e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &prm);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(c->cap_s2, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      int np = 0;
+      int r1 = esplit::launch_root_eval(c, u, c->b.dacc, c->cap_s2, &np);
+      if (!r1) r1 = esplit::launch_root_update_cond(c, np, c->cap_s2, h);
+      cudaGraph_t bg = nullptr;
+      e = cudaStreamEndCapture(c->cap_s2, &bg);
+      if (r1 && e == cudaSuccess) e = cudaErrorLaunchFailure;
+    }
+    if (e != cudaSuccess) {
+      rc = ESPLIT_ERR_CUDA;
+      why = std::string("root loop: ") + cudaGetErrorString(e);
+    }
+  }
+  if (!rc && (esplit::launch_root_apply(c, u, c->b.dacc, n, cs) ||
+              esplit::launch_step_record(c, hist, counter, HIST_CAP, cs))) {
+    rc = ESPLIT_ERR_CUDA;
+    why = "apply / record";
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (!rc && e != cudaSuccess) {
+    rc = ESPLIT_ERR_CUDA;
+    why = std::string("end capture: ") + cudaGetErrorString(e);
+  }
+  if (!rc) {
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+      rc = ESPLIT_ERR_CUDA;
+      why = std::string("instantiate: ") + cudaGetErrorString(e);
+    } else {
+      c->sg.exec = x;
+    }
+  }
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c->launches = l0;
+    return fail(c, rc == ESPLIT_ERR_CUDA ? ESPLIT_ERR_CUDA : rc, "recording the step graph failed (" + why + ")");
+  }
+  c->sg.graph = g;
+  c->sg.u = u;
+  c->sg.dt = dt;
+  c->sg.version = c->version;
+  c->sg.kernels = c->launches - l0 - 2;  // the loop body's two launches are counted per pass
+  c->launches = l0;
+  return ESPLIT_OK;
+}
+
+static void fill_info(esplit_stepinfo* info, const esplit::StepRecord& r) {
+  info->g = r.g;
+  info->estimate = r.est;
+  info->S_before = r.S0;
+  info->S_after = r.S_after;
+  info->iterations = r.iters;
+  info->status = r.status;
+  for (int i = 0; i < 4; ++i) info->stage_rate[i] = r.stage_rate[i];
+}
+
+int esplit_rrk_steps(esplit_ctx* c, double* u, double dt, int n_steps, double* g_out, esplit_stepinfo* info,
+                     int* n_done, void* stream) {
+  if (n_done) *n_done = 0;
+  int rc = rrk_prepare(c, u, dt);
+  if (rc) return rc;
+  if (n_steps < 0) return fail(c, ESPLIT_ERR_ARG, "n_steps must be non-negative");
+  cudaStream_t s = as_stream(stream);
+  int done = 0;
+  const bool fresh = c->sg.exec && c->sg.u == u && c->sg.dt == dt && c->sg.version == c->version;
+  if (c->prof || !fresh) {
+    // profiling brackets every launch with events, which a graph does not
+    // take: steps one by one.  A new recording starts with one ordinary step,
+    // which makes every lazy allocation and set-up before the capture.
+    const int n_plain = c->prof ? n_steps : std::min(n_steps, 1);
+    for (; done < n_plain; ++done) {
+      esplit_stepinfo si{};
+      rc = esplit_rrk_step(c, u, dt, nullptr, &si, stream);
+      if (info) *info = si;
+      if (rc) return rc;
+      if (g_out) g_out[done] = si.g;
+      if (n_done) *n_done = done + 1;
+    }
+    if (done == n_steps) return ESPLIT_OK;
+    if ((rc = rrk_capture(c, u, dt))) return rc;
+  }
+  esplit::StepRecord* hist = static_cast<esplit::StepRecord*>(c->hist);
+  int* counter = reinterpret_cast<int*>(hist + HIST_CAP);
+  std::vector<esplit::StepRecord> h;
+  while (done < n_steps) {
+    const int chunk = std::min(HIST_CAP, n_steps - done);
+    CK(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    for (int k = 0; k < chunk; ++k) CK(cudaGraphLaunch(c->sg.exec, s));
+    h.resize(chunk);
+    CK(cudaMemcpyAsync(h.data(), hist, chunk * sizeof(esplit::StepRecord), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    read_status(c, s, true);
+    c->last_stream = s;
+    for (int k = 0; k < chunk; ++k) {
+      c->launches += c->sg.kernels + 2LL * h[k].iters;
+      if (info) fill_info(info, h[k]);
+      if (h[k].status == ESPLIT_ERR_NONPHYSICAL) return fail(c, h[k].status, "non-physical state during the step");
+      if (h[k].status) return fail(c, h[k].status, "relaxation parameter could not be bracketed");
+      if (g_out) g_out[done] = h[k].g;
+      ++done;
+      if (n_done) *n_done = done;
+    }
+  }
   return ESPLIT_OK;
 }
 

@@ -88,6 +88,18 @@ struct ProfRec {
 };
 }  // namespace esplit
 
+// one relaxation RK4 step recorded as a CUDA graph (stages, reductions, the
+// root solve as a device-side while loop, the update and the step record),
+// valid for one state pointer, dt and configuration version
+struct StepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const double* u = nullptr;
+  double dt = 0.0;
+  unsigned long long version = 0;
+  long long kernels = 0;  // kernel launches per step outside the root loop
+};
+
 struct esplit_ctx {
   int dim = 2, device = 0, n_c = 4;
   int n_p = 0, n_fac = 0, n_f = 0, n_slot = 0;
@@ -108,6 +120,12 @@ struct esplit_ctx {
   double* ent_part = nullptr;
   int ent_n = 0;
   cudaStream_t last_stream = nullptr;
+  // bumped by every change that alters what a step launches (operator, mesh,
+  // parameters, hybrid flags); a recorded step graph of another version is stale
+  unsigned long long version = 1;
+  StepGraph sg;
+  cudaStream_t cap_s = nullptr, cap_s2 = nullptr;  // capture streams (non-blocking)
+  void* hist = nullptr;                            // StepRecord[HIST_CAP] + int counter
   bool prof = false;
   std::vector<esplit::ProfRec> recs;
   std::vector<cudaEvent_t> pool;
@@ -151,6 +169,14 @@ constexpr int ROOT_CHECK_EVERY = 4;
 constexpr int ROOT_EVALS_MAX = 40;
 int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s, int* n_partial);
 int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s);
+int launch_root_update_cond(esplit_ctx* c, int n_partial, cudaStream_t s, cudaGraphConditionalHandle h);
+// per-step summary written on the device by graph-launched step batches
+struct StepRecord {
+  double g, est, S0, S_after;
+  double stage_rate[4];
+  int iters, status;
+};
+int launch_step_record(esplit_ctx* c, StepRecord* hist, int* counter, int cap, cudaStream_t s);
 int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
 int set_ref_tables(const RefTables& t);
 int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);

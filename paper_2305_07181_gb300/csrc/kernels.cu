@@ -1380,9 +1380,21 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
   block_sum<6>(v, part + 6 * blockIdx.x);
 }
 
+__device__ void root_update_body(const double* tot, RootState* st);
+
+// COND: launched inside a graph's while loop over the evaluation passes; the
+// loop continues while the root is not done.  Every path sets done within
+// ROOT_EVALS_MAX + 12 passes (the Newton phase stops at ROOT_EVALS_MAX, the
+// bracket search after 10 halvings or 2 doublings); the hard stop below ends
+// the loop even if that reasoning failed, with status "no root".
+template <bool COND>
 __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restrict__ part, int n,
-                                                           RootState* st) {
-  if (st->done) return;
+                                                           RootState* st, cudaGraphConditionalHandle h) {
+  if (st->done) {
+    if constexpr (COND)
+      if (threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   __shared__ double tot[6];
   for (int k = 0; k < 6; ++k) {
     double v[1] = {0.0};
@@ -1391,6 +1403,17 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
+  root_update_body(tot, st);
+  if constexpr (COND) {
+    if (!st->done && st->iters >= ROOT_EVALS_MAX + 16) {
+      st->status = ESPLIT_ERR_RRK_NO_ROOT;
+      st->done = 1;
+    }
+    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+  }
+}
+
+__device__ void root_update_body(const double* tot, RootState* st) {
   const double eps = 2.220446049250313e-16;
   const double est = st->est;
   st->iters += 1;
@@ -1563,7 +1586,39 @@ int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStrea
 
 int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s) {
   ProfScope ps(c, PG_ROOT, s);
-  root_update_kernel<<<1, 1024, 0, s>>>(c->b.partial, n_partial, c->b.root);
+  root_update_kernel<false><<<1, 1024, 0, s>>>(c->b.partial, n_partial, c->b.root, 0);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_root_update_cond(esplit_ctx* c, int n_partial, cudaStream_t s, cudaGraphConditionalHandle h) {
+  root_update_kernel<true><<<1, 1024, 0, s>>>(c->b.partial, n_partial, c->b.root, h);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// one record per completed step of a graph-launched batch, at the slot the
+// device counter names (the counter is reset by the host before each batch)
+__global__ void step_record_kernel(const RootState* __restrict__ st, const int* __restrict__ status,
+                                   const double* __restrict__ scal, StepRecord* __restrict__ hist, int* counter,
+                                   int cap) {
+  const int k = *counter;
+  if (k < cap) {
+    StepRecord r;
+    r.g = st->g;
+    r.est = st->est;
+    r.S0 = st->S0;
+    r.S_after = st->S0 + (st->phase == 3 ? st->dS_last : 0.0);
+    for (int i = 0; i < 4; ++i) r.stage_rate[i] = scal[2 + i];
+    r.iters = st->iters;
+    r.status = (*status & 1) ? ESPLIT_ERR_NONPHYSICAL : st->status;
+    hist[k] = r;
+  }
+  *counter = k + 1;
+}
+
+int launch_step_record(esplit_ctx* c, StepRecord* hist, int* counter, int cap, cudaStream_t s) {
+  step_record_kernel<<<1, 1, 0, s>>>(c->b.root, c->b.status, c->b.scal, hist, counter, cap);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

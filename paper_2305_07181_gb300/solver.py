@@ -158,6 +158,18 @@ class Solver:
         self._check(rc)
         return g, info
 
+    def rrk_steps(self, u: torch.Tensor, dt: float, n_steps: int, stream=None):
+        """n_steps relaxation RK4 steps in place, launched as a recorded CUDA
+        graph per step; returns (list of g, info of the last step).  On a
+        failing step raises EsplitError with ``n_done`` (completed steps) and
+        ``g`` (their g values) attached; u then holds the state after them."""
+        rc, g, info, done = capi.esplit_rrk_steps(self.ctx, _dptr(u), float(dt), int(n_steps), _stream(stream))
+        if rc:
+            err = EsplitError(rc, capi.esplit_last_error(self.ctx))
+            err.n_done, err.g = done, g
+            raise err
+        return g, info
+
     def rrk_step_host(self, u_host: np.ndarray, dt: float, stream=None):
         if not (u_host.flags.c_contiguous and u_host.dtype == np.float64):
             raise ValueError("host state must be C-contiguous float64")
