@@ -47,9 +47,11 @@ extern "C" {
 #define ESPLIT_SCHEME_HADAMARD 1  /* Sjogreen-Yee Hadamard form, Eq. (99)            */
 #define ESPLIT_SCHEME_HYBRID 2    /* per-element choice (Thm. 4), flags below        */
 #define ESPLIT_SCHEME_HADAMARD_IR 3 /* Hadamard form with the Ismail-Roe flux, the
-                                     * Sec. 6 comparator (standard entropy; EC only:
-                                     * no dissipation, no viscous terms, no RRK step,
-                                     * no VJP -> ESPLIT_ERR_UNSUPPORTED)            */
+                                     * Sec. 6 comparator (standard entropy), with
+                                     * dissipation: the matrix form of Eq. (69) for
+                                     * the standard entropy at the Ismail-Roe mean
+                                     * state (not printed in the paper); no viscous
+                                     * terms, RRK step or VJP -> ESPLIT_ERR_UNSUPPORTED */
 
 typedef struct esplit_ctx esplit_ctx;
 

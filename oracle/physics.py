@@ -250,14 +250,11 @@ def log_mean(a, b):
     return b * q
 
 
-def ir_flux(Uk, Uv, prm: Params):
-    """Ismail-Roe entropy-conservative flux, all directions: (..., d, n_c).
-    With z = sqrt(rho/p) [1, V, p]:
+def ir_averages(Uk, Uv, prm: Params):
+    """The Ismail-Roe averages of a state pair.  With z = sqrt(rho/p) [1, V, p]:
       rho^ = {z_1} {z_nc}_log,  V^ = {z V}/{z_1},  p1^ = {z_nc}/{z_1},
-      p2^ = (gam+1)/(2 gam) {z_nc}_log/{z_1}_log + (gam-1)/(2 gam) {z_nc}/{z_1},
-      H^ = gam p2^/((gam-1) rho^) + |V^|^2/2,
-      F_i = [rho^ V^_i, rho^ V^_i V^ + p1^ e_i, rho^ V^_i H^]
-    ({.} arithmetic mean, {.}_log logarithmic mean)."""
+      p2^ = (gam+1)/(2 gam) {z_nc}_log/{z_1}_log + (gam-1)/(2 gam) {z_nc}/{z_1}
+    ({.} arithmetic mean, {.}_log logarithmic mean); returns rho^, V^, p1^, p2^."""
     g = prm.gam
     rk, Vk, pk = primitives(Uk, prm)
     rv, Vv, pv = primitives(Uv, prm)
@@ -269,6 +266,16 @@ def ir_flux(Uk, Uv, prm: Params):
     rh = a1 * ln
     p1 = an / a1
     p2 = (g + 1.0) / (2.0 * g) * ln / l1 + (g - 1.0) / (2.0 * g) * an / a1
+    return rh, Vh, p1, p2
+
+
+def ir_flux(Uk, Uv, prm: Params):
+    """Ismail-Roe entropy-conservative flux, all directions: (..., d, n_c).
+    With the averages of ``ir_averages``,
+      H^ = gam p2^/((gam-1) rho^) + |V^|^2/2,
+      F_i = [rho^ V^_i, rho^ V^_i V^ + p1^ e_i, rho^ V^_i H^]."""
+    g = prm.gam
+    rh, Vh, p1, p2 = ir_averages(Uk, Uv, prm)
     Hh = g * p2 / ((g - 1.0) * rh) + 0.5 * (Vh * Vh).sum(-1)
     d = Uk.shape[-1] - 2
     out = []
@@ -277,6 +284,45 @@ def ir_flux(Uk, Uv, prm: Params):
         mom = m[..., None] * Vh + p1[..., None] * torch.nn.functional.one_hot(torch.tensor(i), d).to(Uk)
         out.append(torch.cat([m[..., None], mom, (m * Hh)[..., None]], -1))
     return torch.stack(out, dim=-2)
+
+
+def ir_dissipation_matrix(Uk, Uv, n, prm: Params):
+    """Matrix dissipation for the Ismail-Roe comparator (not printed in the
+    paper; the construction of Eq. (69) carried over to the standard entropy):
+    R^ |Lambda_n| T^ R^T at the state rho^, V^, p^ = p1^ of ``ir_averages``,
+    to be applied to the jump of the standard entropy variables.  R^ T^ R^T is
+    the eigenvector factorisation of dU/dw for the standard entropy (Barth's
+    scaling): the acoustic and entropy columns of Eq. (80) with
+    T^ = rho^/(2 gam), (gam-1) rho^/gam, rho^/(2 gam), and the shear modes
+    with weight p^ written through the projector I - n n^T (so that no
+    tangent basis is needed and the 3D form is exact):
+      R^ |Lambda| T^ R^T = sum_k |lambda_k| T_k r_k r_k^T + |V^.n| p^ B^T (I - n n^T) B,
+      B = [0 | I_d | V^] (d x n_c).
+    Symmetric positive semi-definite for any pair, so the entropy production
+    of the term is -|nu|/2 dw^T (...) dw <= 0; for equal states R^ T^ R^T
+    equals dU/dw (pinned in the tests).  Returns (..., n_c, n_c)."""
+    g = prm.gam
+    rh, Vh, p1, _ = ir_averages(Uk, Uv, prm)
+    d = Vh.shape[-1]
+    a = torch.sqrt(g * p1 / rh)
+    vv = (Vh * Vh).sum(-1)
+    Hh = a * a / (g - 1.0) + 0.5 * vv
+    vn = (Vh * n).sum(-1)
+    one = torch.ones_like(vn)
+    c_m = torch.cat([one[..., None], Vh - a[..., None] * n, (Hh - a * vn)[..., None]], -1)
+    c_0 = torch.cat([one[..., None], Vh, (0.5 * vv)[..., None]], -1)
+    c_p = torch.cat([one[..., None], Vh + a[..., None] * n, (Hh + a * vn)[..., None]], -1)
+    w_m = (vn - a).abs() * rh / (2.0 * g)
+    w_0 = vn.abs() * (g - 1.0) * rh / g
+    w_p = (vn + a).abs() * rh / (2.0 * g)
+    D = (w_m[..., None, None] * c_m[..., :, None] * c_m[..., None, :]
+         + w_0[..., None, None] * c_0[..., :, None] * c_0[..., None, :]
+         + w_p[..., None, None] * c_p[..., :, None] * c_p[..., None, :])
+    eye = torch.eye(d, dtype=Vh.dtype).expand(*Vh.shape[:-1], d, d)
+    B = torch.cat([torch.zeros(*Vh.shape[:-1], d, 1, dtype=Vh.dtype), eye, Vh[..., :, None]], -1)   # (..., d, nc)
+    P = eye - n[..., :, None] * n[..., None, :]
+    D = D + (vn.abs() * p1)[..., None, None] * (B.transpose(-1, -2) @ P @ B)
+    return D
 
 
 # ----------------------------------------------------------------------------

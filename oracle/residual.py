@@ -34,7 +34,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .physics import (Params, entropy_variables, euler_flux, sy_flux, ir_flux,
+from .physics import (Params, entropy_variables, euler_flux, sy_flux, ir_flux, ir_dissipation_matrix,
+                      standard_entropy_variables,
                       symmetrized_flux_jacobians, dissipation_matrix,
                       viscous_flux_from_w_grads, viscous_K)
 from .operators import physical_operators
@@ -90,10 +91,12 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     scheme: "split", "hadamard" or "hybrid" (per-element ``hybrid_flags``,
     1 = Hadamard), or "hadamard_ir": the Hadamard form with the Ismail-Roe
     flux in the volume and the SATs (entropy conservative for the standard
-    entropy; no dissipation, no viscous terms).  ``u`` may be a torch tensor
-    requiring grad (the oracle adjoint differentiates through this function)."""
-    if scheme == "hadamard_ir" and (dissipation or viscous):
-        raise ValueError("the Ismail-Roe comparator is built without dissipation and viscous terms")
+    entropy), with its own matrix dissipation (``ir_dissipation_matrix`` on the
+    jump of the standard entropy variables) when ``dissipation``; no viscous
+    terms.  ``u`` may be a torch tensor requiring grad (the oracle adjoint
+    differentiates through this function)."""
+    if scheme == "hadamard_ir" and viscous:
+        raise ValueError("the Ismail-Roe comparator is built without viscous terms")
     U_all = _as_U(u)
     n_e, n_p, nc = U_all.shape
     d = nc - 2
@@ -140,8 +143,12 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     if dissipation:
         bmag = torch.linalg.norm(nu, dim=-1)
         nhat = nu / bmag[..., None]
-        Dm = dissipation_matrix(Uk, Uv, nhat, prm)
-        dw = entropy_variables(Uk, prm) - entropy_variables(Uv, prm)
+        if scheme == "hadamard_ir":
+            Dm = ir_dissipation_matrix(Uk, Uv, nhat, prm)
+            dw = standard_entropy_variables(Uk, prm) - standard_entropy_variables(Uv, prm)
+        else:
+            Dm = dissipation_matrix(Uk, Uv, nhat, prm)
+            dw = entropy_variables(Uk, prm) - entropy_variables(Uv, prm)
         sat = sat - (bmag / (2.0 * Hm))[..., None] * torch.einsum("nscd,nsd->nsc", Dm, dw)
     r = r.index_add(1, fn, sat)
 

@@ -188,11 +188,30 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 #pragma unroll
   for (int i = 0; i < D; ++i) nuv[i] = (T)__ldg(&nu[((size_t)k * NS + s) * D + i]);
   T G[NC];
-  if constexpr (FLUX == 1) {  // Ismail-Roe comparator: EC SAT only
+  if constexpr (FLUX == 1) {  // Ismail-Roe comparator, with its own dissipation
     IRNode<T, D> ik, iv;
     ir_node<T, D>(nk, ik);
     ir_node<T, D>(nv, iv);
-    ir_flux_dir<T, D>(ik, iv, c, nuv, G);
+    IRAvg<T, D> a;
+    ir_avg<T, D>(ik, iv, c, a);
+    ir_flux_dir<T, D>(a, c, nuv, G);
+    if (dissipation) {
+      T b2 = T(0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+      T b = t_sqrt(b2);
+      T nh[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+      T wk[NC], wv[NC], dw[NC], out[NC];
+      std_entropy_vars<T, D>(nk, ik, c, wk);
+      std_entropy_vars<T, D>(nv, iv, c, wv);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) dw[q] = wk[q] - wv[q];
+      ir_diss_apply<T, D>(a, c, nh, dw, out);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) G[q] += T(0.5) * b * out[q];
+    }
   } else {
     ZNode<T, D> zk, zv;
     znode<T, D>(nk, c, zk);
@@ -803,7 +822,9 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
         in_.ln = zz[3 * NP + n];
 #pragma unroll
         for (int i = 0; i < D; ++i) in_.V[i] = zz[(4 + i) * NP + n];
-        ir_flux_dir<T, D>(im, in_, c, Smn, G);
+        IRAvg<T, D> ia;
+        ir_avg<T, D>(im, in_, c, ia);
+        ir_flux_dir<T, D>(ia, c, Smn, G);
       } else {
         ZNode<T, D> zn;
         zn.q = zz[n];
@@ -895,7 +916,8 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     const int visc_heat = c->prm.viscous ? c->prm.heat_flux : -1;
     if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
       face_kernel<double, D, false, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat,
-                                                         ph64, 0, c->b.status, 0, c->b.hflags, 0, nullptr);
+                                                         ph64, c->prm.dissipation, c->b.status, 0, c->b.hflags, 0,
+                                                         nullptr);
     else if (visc_heat >= 0)
       face_kernel<double, D, true><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
                                                      c->prm.dissipation, c->b.status, ef_mode, c->b.hflags,

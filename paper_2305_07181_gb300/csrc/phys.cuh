@@ -27,6 +27,7 @@ struct Phys {
                        // appearing in Eq. (48) (arithmetic and exponential means)
   T inv_bp1;           // 1/(beta+1)
   T gam_gm1;           // gam/(gam-1)
+  T gm1_gam;           // (gam-1)/gam
   T s_ac, s_en;        // S^ entries: 1/(2 gam), (gam-1)(gam+alpha)/(gam alpha), Eq. (76)
   T mu, kappa, R;      // viscosity, conductivity mu gam R/((gam-1) Pr), gas constant
   // Taylor coefficients of g(eps) = ((1+eps)^r - 1)/(r eps) for r = r1, r2
@@ -52,6 +53,7 @@ __host__ inline Phys<T> make_phys(double gam, double beta, double R, double mu, 
   c.r2 = (T)((1.0 - gam) / alpha);
   c.inv_bp1 = (T)(1.0 / (beta + 1.0));
   c.gam_gm1 = (T)(gam / (gam - 1.0));
+  c.gm1_gam = (T)((gam - 1.0) / gam);
   c.s_ac = (T)(1.0 / (2.0 * gam));
   c.s_en = (T)((gam - 1.0) * (gam + alpha) / (gam * alpha));
   c.mu = (T)mu;
@@ -422,28 +424,97 @@ __device__ __forceinline__ T log_mean(T a, T b, T la, T lb) {
   return (a - b) / (la - lb);
 }
 
+// Pair averages of the Ismail-Roe flux (shared with its dissipation)
+template <typename T, int D>
+struct IRAvg {
+  T rh, p1, p2, vv;  // rho^, p1^, p2^, |V^|^2
+  T Vh[D];
+};
+
 template <typename T, int D, typename C>
-__device__ __forceinline__ void ir_flux_dir(const IRNode<T, D>& k, const IRNode<T, D>& v, const C& c, const T* nu,
-                                            T* F) {
+__device__ __forceinline__ void ir_avg(const IRNode<T, D>& k, const IRNode<T, D>& v, const C& c, IRAvg<T, D>& a) {
   T a1 = T(0.5) * (k.z1 + v.z1), an = T(0.5) * (k.zn + v.zn);
   T L1 = log_mean<T>(k.z1, v.z1, k.l1, v.l1), Ln = log_mean<T>(k.zn, v.zn, k.ln, v.ln);
   T ia1 = T(1) / a1;
-  T Vh[D], vv = T(0), vn = T(0);
+  a.vv = T(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    Vh[i] = T(0.5) * (k.z1 * k.V[i] + v.z1 * v.V[i]) * ia1;
-    vv += Vh[i] * Vh[i];
-    vn += Vh[i] * nu[i];
+    a.Vh[i] = T(0.5) * (k.z1 * k.V[i] + v.z1 * v.V[i]) * ia1;
+    a.vv += a.Vh[i] * a.Vh[i];
   }
-  T rh = a1 * Ln;
-  T p1 = an * ia1;
-  T p2 = (c.gam + T(1)) / (T(2) * c.gam) * (Ln / L1) + (c.gam - T(1)) / (T(2) * c.gam) * p1;
-  T Hh = c.gam * c.inv_gm1 * p2 / rh + T(0.5) * vv;
-  T m = rh * vn;
+  a.rh = a1 * Ln;
+  a.p1 = an * ia1;
+  a.p2 = (c.gam + T(1)) / (T(2) * c.gam) * (Ln / L1) + (c.gam - T(1)) / (T(2) * c.gam) * a.p1;
+}
+
+template <typename T, int D, typename C>
+__device__ __forceinline__ void ir_flux_dir(const IRAvg<T, D>& a, const C& c, const T* nu, T* F) {
+  T vn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) vn += a.Vh[i] * nu[i];
+  T Hh = c.gam * c.inv_gm1 * a.p2 / a.rh + T(0.5) * a.vv;
+  T m = a.rh * vn;
   F[0] = m;
 #pragma unroll
-  for (int j = 0; j < D; ++j) F[1 + j] = m * Vh[j] + p1 * nu[j];
+  for (int j = 0; j < D; ++j) F[1 + j] = m * a.Vh[j] + a.p1 * nu[j];
   F[D + 1] = m * Hh;
+}
+
+// Standard entropy variables w = [(gam - s)/(gam-1) - rho|V|^2/(2p), rho V/p,
+// -rho/p], s = log p - gam log rho, from the nodal state and its IR node.
+template <typename T, int D, typename C>
+__device__ __forceinline__ void std_entropy_vars(const Node<T, D>& n, const IRNode<T, D>& z, const C& c, T* w) {
+  const T b = n.rho / n.p;
+  const T lr = z.l1 + z.ln, lp = z.ln - z.l1;  // log rho, log p
+  w[0] = (c.gam - (lp - c.gam * lr)) * c.inv_gm1 - T(0.5) * b * n.v2;
+#pragma unroll
+  for (int i = 0; i < D; ++i) w[1 + i] = b * n.V[i];
+  w[D + 1] = -b;
+}
+
+// Matrix dissipation of the comparator (not printed in the paper; the form of
+// Eq. (69) carried over to the standard entropy), applied to dw = jump of the
+// standard entropy variables, n a unit normal:
+//   out = sum_k |lambda_k| T_k r_k (r_k . dw) + |V^.n| p^ B^T (I - n n^T) B dw
+// at rho^, V^, p^ = p1^; r_k the acoustic and entropy columns of Eq. (80),
+// T = rho^/(2 gam), (gam-1) rho^/gam, rho^/(2 gam); B dw = dw_m + V^ dw_E.
+template <typename T, int D, typename C>
+__device__ __forceinline__ void ir_diss_apply(const IRAvg<T, D>& a, const C& c, const T* n, const T* dw, T* out) {
+  constexpr int NC = D + 2;
+  T ah = t_sqrt(c.gam * a.p1 / a.rh);
+  T Hh = ah * ah * c.inv_gm1 + T(0.5) * a.vv;
+  T vn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) vn += a.Vh[i] * n[i];
+  // r . dw for the three columns
+  T vdm = T(0), ndm = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    vdm += a.Vh[i] * dw[1 + i];
+    ndm += n[i] * dw[1 + i];
+  }
+  const T e = dw[NC - 1];
+  const T base = dw[0] + vdm;
+  T ym = (base - ah * ndm + (Hh - ah * vn) * e) * (t_abs(vn - ah) * a.rh * c.s_ac);
+  T y0 = (base + T(0.5) * a.vv * e) * (t_abs(vn) * a.rh * c.gm1_gam);
+  T yp = (base + ah * ndm + (Hh + ah * vn) * e) * (t_abs(vn + ah) * a.rh * c.s_ac);
+  out[0] = ym + y0 + yp;
+  // shear part
+  T y[D], yn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    y[i] = dw[1 + i] + a.Vh[i] * e;
+    yn += n[i] * y[i];
+  }
+  const T sh = t_abs(vn) * a.p1;
+  T vpy = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const T py = sh * (y[i] - n[i] * yn);
+    out[1 + i] = ym * (a.Vh[i] - ah * n[i]) + y0 * a.Vh[i] + yp * (a.Vh[i] + ah * n[i]) + py;
+    vpy += a.Vh[i] * py;
+  }
+  out[NC - 1] = ym * (Hh - ah * vn) + y0 * (T(0.5) * a.vv) + yp * (Hh + ah * vn) + vpy;
 }
 
 }  // namespace esplit

@@ -18,13 +18,22 @@ def summand_scale(u, op, m, elems, scheme, prm, dissipation=True, viscous=False)
       split:     sum_i |M_i||f_i| + |A~_i||D_i||w|/(beta+1)
       Hadamard:  2 sum_n sum_i |S_i,mn||F*_i(u_m,u_n)|/H_m
       facets:    |nu||F*|/H + |nu|/(2H) |X|L|SX^T| (|dw| + |w_k| + |w_v|)
-      viscous:   sum_i |D_i| G_i + |nu| (G(k) + G(v))/H
+      (the Ismail-Roe comparator: its flux, dissipation and standard entropy
+    variables in the Hadamard and facet terms)
+    viscous:   sum_i |D_i| G_i + |nu| (G(k) + G(v))/H
                  + 1/(2H) sum_j |D_j|^T sum_i |K~_ij||nu_i| (|w_k| + |w_v|)
                  with G_i = |F^V_i| + sum_j |K~_ij||D_j||w|
     Both sides form A~_i and the viscous flux from dU/dW written out in closed
     form (no matrix inverse), so no condition number of dW/dU enters."""
     from oracle.physics import (euler_flux, entropy_variables, symmetrized_flux_jacobians, sy_flux,
-                                dissipation_matrix, viscous_K, viscous_flux_from_w_grads)
+                                dissipation_matrix, viscous_K, viscous_flux_from_w_grads, ir_flux,
+                                ir_dissipation_matrix, standard_entropy_variables)
+    # the Ismail-Roe comparator: its flux, its dissipation and the standard
+    # entropy variables in place of the Sjogreen-Yee ones
+    ir = scheme == "hadamard_ir"
+    flux = ir_flux if ir else sy_flux
+    evars = standard_entropy_variables if ir else entropy_variables
+    dmat = ir_dissipation_matrix if ir else dissipation_matrix
     from oracle.operators import physical_operators
     d = op.d
     el = torch.as_tensor(elems)
@@ -42,18 +51,18 @@ def summand_scale(u, op, m, elems, scheme, prm, dissipation=True, viscous=False)
         sc = sc + torch.einsum("nmicd,nimd->nmc", At, Dw) / (prm.beta + 1)
     else:
         n_, npp, nc = U.shape
-        F2 = 2 * sy_flux(U[:, :, None, :].expand(n_, npp, npp, nc), U[:, None, :, :].expand(n_, npp, npp, nc),
-                         prm).abs()
+        F2 = 2 * flux(U[:, :, None, :].expand(n_, npp, npp, nc), U[:, None, :, :].expand(n_, npp, npp, nc),
+                      prm).abs()
         sc = torch.einsum("nimk,nmkic->nmc", ops["S"].abs(), F2) / H[..., None]
     fn = torch.as_tensor(op.facet_nodes.reshape(-1))
     pr = torch.as_tensor(m.pair.reshape(m.n_e, -1, 2))[el]
     Uk, Uv = U[:, fn], U_all[pr[..., 0], fn[pr[..., 1]]]
     nu = torch.as_tensor(m.nu.reshape(m.n_e, -1, d))[el]
     b = torch.linalg.norm(nu, dim=-1)
-    wk, wv = entropy_variables(Uk, prm), entropy_variables(Uv, prm)
-    fac = torch.einsum("nsi,nsic->nsc", nu.abs(), sy_flux(Uk, Uv, prm).abs())
+    wk, wv = evars(Uk, prm), evars(Uv, prm)
+    fac = torch.einsum("nsi,nsic->nsc", nu.abs(), flux(Uk, Uv, prm).abs())
     if dissipation:
-        Dm = dissipation_matrix(Uk, Uv, nu / b[..., None], prm).abs()
+        Dm = dmat(Uk, Uv, nu / b[..., None], prm).abs()
         dws = (wk - wv).abs() + wk.abs() + wv.abs()
         fac = fac + 0.5 * b[..., None] * torch.einsum("nscd,nsd->nsc", Dm, dws)
     sc = sc.index_add(1, fn, fac / H[:, fn][..., None])

@@ -1,6 +1,8 @@
 """The Sec. 6 comparator on the GPU: the Hadamard form with the Ismail-Roe
-flux (entropy conservative for the standard entropy), against the oracle's
-``scheme="hadamard_ir"`` residual; its standard-entropy rate at round-off."""
+flux (entropy conservative for the standard entropy) and, optionally, its
+matrix dissipation, against the oracle's ``scheme="hadamard_ir"`` residual;
+its standard-entropy rate at round-off without dissipation and equal to the
+closed-form production with it."""
 import numpy as np
 import pytest
 import torch
@@ -36,35 +38,89 @@ def _std_rate(u, r, op, m):
     return float((H[..., None] * w * rt).sum()), float((H[..., None] * w.abs() * rt.abs()).sum())
 
 
+@pytest.mark.parametrize("diss", [False, True])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_ir_hadamard_parity_tri(lib, p):
+def test_ir_hadamard_parity_tri(lib, p, diss):
     from oracle import residual as R
     from oracle.physics import Params as OP
     op = tri_operator(p)
     m = periodic_tri_mesh(op, 5, 10.0, 0.05)
     u = states.random_positive_state(m.n_e, 2, op.n_p, seed=90 + p)
-    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir"))
+    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir", dissipation=diss))
     r = s.residual(s.to_device(u)).cpu().numpy()
     s.close()
-    ro = R.residual(u, op, m, OP(), scheme="hadamard_ir").numpy()
+    ro = R.residual(u, op, m, OP(), scheme="hadamard_ir", dissipation=diss).numpy()
     err = rel_err(r, ro)
-    print(f"IR p={p} rel err {err:.2e}")
+    print(f"IR p={p} diss={diss} rel err {err:.2e}")
     assert err <= FP64_TOL
     rate, scale = _std_rate(u, r, op, m)
-    assert abs(rate) <= 1e-13 * scale
+    if not diss:
+        assert abs(rate) <= 1e-13 * scale
+    else:
+        # the production of the dissipation, from the GPU residuals with and
+        # without it, against the oracle's closed form
+        s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir"))
+        r0 = s.residual(s.to_device(u)).cpu().numpy()
+        s.close()
+        rate_d, _ = _std_rate(u, r - r0, op, m)
+        closed = _ir_closed_form_production(u, op, m)
+        assert closed < 0 and abs(rate_d - closed) <= 1e-11 * abs(closed)
 
 
-def test_ir_hadamard_parity_tets(lib):
+def _ir_closed_form_production(u, op, m):
+    from oracle.physics import Params, ir_dissipation_matrix, standard_entropy_variables
+    d = m.nu.shape[-1]
+    U = torch.as_tensor(u).transpose(1, 2)
+    fn = op.facet_nodes.reshape(-1)
+    pr = m.pair.reshape(m.n_e, -1, 2)
+    Uk = U[:, fn]
+    Uv = U[pr[..., 0], fn[pr[..., 1]]]
+    nu = torch.as_tensor(m.nu.reshape(m.n_e, -1, d))
+    b = torch.linalg.norm(nu, dim=-1)
+    Dm = ir_dissipation_matrix(Uk, Uv, nu / b[..., None], Params())
+    dw = standard_entropy_variables(Uk, Params()) - standard_entropy_variables(Uv, Params())
+    return float(-0.5 * (0.5 * b * torch.einsum("esc,escd,esd->es", dw, Dm, dw)).sum())
+
+
+@pytest.mark.parametrize("diss", [False, True])
+def test_ir_hadamard_parity_tets(lib, diss):
     from oracle import residual as R
     from oracle.physics import Params as OP
     op = tet_operator(2)
     m = periodic_tet_mesh(op, 3, 2 * np.pi, 0.02)
     u = states.random_positive_state(m.n_e, 3, op.n_p, seed=95)
-    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir"))
+    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir", dissipation=diss))
     r = s.residual(s.to_device(u)).cpu().numpy()
     s.close()
-    ro = R.residual(u, op, m, OP(), scheme="hadamard_ir").numpy()
+    ro = R.residual(u, op, m, OP(), scheme="hadamard_ir", dissipation=diss).numpy()
     assert rel_err(r, ro) <= FP64_TOL
+
+
+@pytest.mark.parametrize("diss", [False, True])
+def test_ir_hadamard_full_size_sampled(lib, diss):
+    """The 32,768-triangle p = 3 vortex + noise (the residual sweep's mesh),
+    Ismail-Roe Hadamard form with and without its dissipation, as the sweep
+    times it; the oracle on 100 sampled elements.  As for the other schemes
+    at this size the residual is far smaller than the terms it is summed from,
+    and the bound is the rounding-scale one,
+    |r_gpu - r_oracle| <= 1e-12 max|r| + 64 n_p eps (summand scale)."""
+    from oracle import residual as R
+    from oracle.physics import Params as OP
+    from parity_bounds import summand_scale
+    op = tri_operator(3)
+    m = periodic_tri_mesh(op, 128, 10.0, 0.05)
+    u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
+    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir", dissipation=diss))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    s.close()
+    el = np.random.default_rng(7).choice(m.n_e, 100, replace=False)
+    ro = R.residual(u, op, m, OP(), scheme="hadamard_ir", dissipation=diss, elems=el).numpy()
+    sc = summand_scale(u, op, m, el, "hadamard_ir", OP(), dissipation=diss)
+    eps = np.finfo(float).eps
+    err = np.abs(r[el] - ro)
+    print(f"IR full size diss={diss}: max-norm rel {rel_err(r[el], ro):.2e}, "
+          f"max err/(eps scale) {float((err / (eps * sc)).max()):.2f}")
+    assert np.all(err <= 1e-12 * np.abs(ro).max() + 64 * op.n_p * eps * sc)
 
 
 def test_ir_hadamard_fp32(lib):
@@ -88,7 +144,7 @@ def test_ir_hadamard_restrictions(lib):
     m = periodic_tri_mesh(op, 3, 10.0, 0.05)
     s = lib.Solver(op, m)
     with pytest.raises(lib.EsplitError) as ei:
-        s.set_params(lib.Params(scheme="hadamard_ir", dissipation=True))
+        s.set_params(lib.Params(scheme="hadamard_ir", viscous=True, mu=0.01))
     assert ei.value.code == lib.capi.ESPLIT_ERR_UNSUPPORTED
     s.set_params(lib.Params(scheme="hadamard_ir"))
     u = s.to_device(states.isentropic_vortex(m))

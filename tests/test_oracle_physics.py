@@ -320,3 +320,32 @@ def test_log_mean():
     ref = torch.tensor([float(Decimal(x) if x == y else (Decimal(x) - Decimal(y)) / (Decimal(x).ln() - Decimal(y).ln()))
                         for x, y in zip(a.tolist(), b.tolist())], dtype=DT)
     assert ((log_mean(a, b) - ref).abs() / ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_ir_dissipation_matrix_pins(d):
+    """Matrix dissipation of the Ismail-Roe comparator: for equal states the
+    eigenvector factorisation equals dU/dw of the standard entropy (inverse of
+    the autograd Jacobian of w(U)) when all |lambda| are replaced by one, and
+    R|L|TR^T = |A_n| dU/dw (A_n the normal flux Jacobian); for any pair it is
+    symmetric, positive semi-definite, invariant under n -> -n and symmetric
+    in the two states."""
+    from oracle.physics import ir_dissipation_matrix, standard_entropy_variables
+    U = rand_states(60, d, 51)
+    g = torch.Generator().manual_seed(52)
+    n = torch.randn(60, d, generator=g, dtype=DT)
+    n = n / torch.linalg.norm(n, dim=-1, keepdim=True)
+    Dm = ir_dissipation_matrix(U, U, n, P)
+    dUdw = torch.linalg.inv(_jacobian(lambda x: standard_entropy_variables(x, P), U))
+    An = torch.einsum("ni,nicd->ncd", n, _jacobian(lambda x: euler_flux(x, P), U))
+    # |A_n| dU/dw through the eigen-decomposition of A_n (real spectrum)
+    ev, evec = torch.linalg.eig(An)
+    absA = (evec @ torch.diag_embed(ev.abs().to(evec.dtype)) @ torch.linalg.inv(evec)).real
+    ref = absA @ dUdw
+    assert ((Dm - ref).abs().amax((-1, -2)) / ref.abs().amax((-1, -2))).max() < 1e-11
+    Uv = rand_states(60, d, 53)
+    D2 = ir_dissipation_matrix(U, Uv, n, P)
+    assert (D2 - D2.transpose(-1, -2)).abs().max() < 1e-13 * D2.abs().max()
+    assert torch.linalg.eigvalsh(D2).min() > -1e-12 * D2.abs().max()
+    assert (ir_dissipation_matrix(U, Uv, -n, P) - D2).abs().max() < 1e-13 * D2.abs().max()
+    assert (ir_dissipation_matrix(Uv, U, n, P) - D2).abs().max() < 1e-13 * D2.abs().max()

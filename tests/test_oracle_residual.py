@@ -266,3 +266,35 @@ def test_ir_hadamard_conserves_standard_entropy(p):
     assert R.residual(uf, op, m, P, scheme="hadamard_ir").abs().max() < 1e-12
     rs = R.residual(u, op, m, P, scheme="hadamard_ir", form="strong")
     assert (r - rs).abs().max() < 1e-13 * r.abs().max()
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_ir_dissipation_rate(p):
+    """The comparator's dissipation: the standard-entropy rate of the added
+    term equals -1/2 sum over facet nodes of |nu| dw^T D dw / 2 (each pair seen
+    from both sides) and is negative; the scheme stays conservative and
+    preserves free stream."""
+    from oracle.physics import ir_dissipation_matrix, standard_entropy_variables
+    op = tri_operator(p)
+    m = periodic_tri_mesh(op, 4, 10.0, 0.05)
+    u = states.random_positive_state(m.n_e, 2, op.n_p, seed=60 + p)
+    r0 = R.residual(u, op, m, P, scheme="hadamard_ir")
+    r1 = R.residual(u, op, m, P, scheme="hadamard_ir", dissipation=True)
+    U = torch.as_tensor(u).transpose(1, 2)
+    w = standard_entropy_variables(U, P)
+    H = torch.as_tensor(op.H)[None] * torch.as_tensor(m.J)
+    rate = float((H[..., None] * w * (r1 - r0).transpose(1, 2)).sum())
+    fn = op.facet_nodes.reshape(-1)
+    pr = m.pair.reshape(m.n_e, -1, 2)
+    Uk = U[:, fn]
+    Uv = U[pr[..., 0], fn[pr[..., 1]]]
+    nu = torch.as_tensor(m.nu.reshape(m.n_e, -1, 2))
+    b = torch.linalg.norm(nu, dim=-1)
+    Dm = ir_dissipation_matrix(Uk, Uv, nu / b[..., None], P)
+    dw = standard_entropy_variables(Uk, P) - standard_entropy_variables(Uv, P)
+    closed = float(-0.5 * (0.5 * b * torch.einsum("esc,escd,esd->es", dw, Dm, dw)).sum())
+    assert closed < 0
+    assert abs(rate - closed) < 1e-12 * abs(closed)
+    assert Dg.conservation(r1, op, m).abs().max() < 1e-12 * float(r1.abs().max())
+    uf = states.uniform_state(m.n_e, 2, op.n_p)
+    assert R.residual(uf, op, m, P, scheme="hadamard_ir", dissipation=True).abs().max() < 1e-12
