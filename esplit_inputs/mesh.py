@@ -238,6 +238,29 @@ def _quad_tet_shape(xi: np.ndarray):
     return np.stack(N, axis=1), dN
 
 
+def mms_warp_2d(xh, yh):
+    """Perturbation of the manufactured-solution grids of Sec. 7.4 on
+    [-1, 1]^2 (the paper takes it from Chan et al.):
+        x_i = xh_i + 1/8 cos(pi xh_i / 2) prod_{j != i} sin(pi xh_j).
+    It vanishes on the boundary, so periodic images stay paired.  Returns
+    the displacements (dx, dy)."""
+    dx = 0.125 * np.cos(0.5 * np.pi * xh) * np.sin(np.pi * yh)
+    dy = 0.125 * np.cos(0.5 * np.pi * yh) * np.sin(np.pi * xh)
+    return dx, dy
+
+
+def mms_warp_3d(xh):
+    """The Sec. 7.4 perturbation on [-1, 1]^3, xh (..., 3) -> displacements:
+    dx_i = 1/8 cos(pi xh_i / 2) prod_{j != i} sin(pi xh_j)."""
+    c = np.cos(0.5 * np.pi * xh)
+    sn = np.sin(np.pi * xh)
+    out = np.empty_like(xh)
+    for i in range(3):
+        j, k = [a for a in range(3) if a != i]
+        out[..., i] = 0.125 * c[..., i] * sn[..., j] * sn[..., k]
+    return out
+
+
 def vortex3d_warp(xh):
     """Perturbation of the 3D vortex grids of Sec. 7.3 on [-10, 10]^3:
     x_i = xh_i + 0.05 sin(pi xh_i / 2).  xh (..., 3) -> displacements."""

@@ -66,6 +66,24 @@ def vortex3d_prims(x1, x2, t=0.0, gam=GAMMA):
     return rho, V, p
 
 
+def manufactured_prims(x, t=0.0, gam=GAMMA):
+    """Manufactured solution of Sec. 7.4 on [-1, 1]^d, x (d, ...):
+    rho = 2 + 0.1 sin(pi (sum_i x_i - 0.6 t)), V_i = 1,
+    p = (gam - 1)(rho^2 - rho |V|^2 / 2)  (so that the total energy is rho^2)."""
+    d = x.shape[0]
+    rho = 2.0 + 0.1 * np.sin(np.pi * (np.sum(x, axis=0) - 0.6 * t))
+    V = np.ones((d,) + rho.shape)
+    p = (gam - 1.0) * (rho * rho - 0.5 * rho * d)
+    return rho, V, p
+
+
+def manufactured_state(mesh, t=0.0, gam=GAMMA):
+    """The Sec. 7.4 manufactured solution at the mesh nodes, (n_e, d+2, n_p)."""
+    x = np.moveaxis(mesh.x, 1, 0)                       # (d, n_e, n_p)
+    rho, V, p = manufactured_prims(x, t, gam)
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))
+
+
 def add_uniform_noise(u, amplitude, seed):
     """u + amplitude * U(-1, 1), drawn by numpy's PCG64 in C order of u."""
     rng = np.random.default_rng(seed)

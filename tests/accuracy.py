@@ -1,5 +1,5 @@
-"""L^2 error of a nodal solution on curved triangles, as Sec. 7.3 measures
-it: the solution is carried from the SBP nodes to a quadrature rule of
+"""L^2 error of a nodal solution on curved triangles and tetrahedra, as
+Secs. 7.3 and 7.4 measure it: the solution is carried from the SBP nodes to a quadrature rule of
 degree 3p + 1 on each element (here the H-weighted least-squares fit of
 degree p, exact for degree-p data), the square of the error summed over the
 conservative variables is integrated with the element's Jacobian, summed
@@ -35,8 +35,9 @@ def _quad_shape(xi):
     return N, dNx, dNy
 
 
-def l2_error_vortex(u, op, mesh, t, center=(5.0, 0.0)):
-    """sqrt(sum_e int_e sum_c (u_h,c - u_c(t))^2) for the Sec. 7.3 vortex."""
+def l2_error_2d(u, op, mesh, prims):
+    """sqrt(sum_e int_e sum_c (u_h,c - u_c)^2) on curved triangles, the exact
+    solution given by prims(X (2, ...)) -> (rho, V (2, ...), p)."""
     p = op.p
     xq, wq = triangle_rule(3 * p + 1)
     ctr = np.full(2, 1.0 / 3.0)
@@ -51,10 +52,16 @@ def l2_error_vortex(u, op, mesh, t, center=(5.0, 0.0)):
     dxs = np.einsum("qa,eia->eiq", dNx, G)
     dys = np.einsum("qa,eia->eiq", dNy, G)
     J = dxs[:, 0] * dys[:, 1] - dys[:, 0] * dxs[:, 1]
-    rho, V, pr = isentropic_vortex_prims(X[:, 0], X[:, 1], t=t, xc=center[0], yc=center[1])
+    rho, V, pr = prims(np.moveaxis(X, 1, 0))
     ue = np.moveaxis(prim_to_cons(rho, V, pr), 0, 1)                             # (n_e, n_c, n_q)
     err2 = np.einsum("q,eq,ecq->", wq, J, (uq - ue) ** 2)
     return float(np.sqrt(err2))
+
+
+def l2_error_vortex(u, op, mesh, t, center=(5.0, 0.0)):
+    """sqrt(sum_e int_e sum_c (u_h,c - u_c(t))^2) for the Sec. 7.3 vortex."""
+    return l2_error_2d(u, op, mesh, lambda X: isentropic_vortex_prims(X[0], X[1], t=t, xc=center[0],
+                                                                      yc=center[1]))
 
 
 def tet_rule(degree):
@@ -70,10 +77,9 @@ def tet_rule(degree):
     return xi, wt
 
 
-def l2_error_vortex_3d(u, op, mesh, t, chunk=4096):
-    """The Sec. 7.3 L^2 error for the 3D vortex on curved tetrahedra."""
+def l2_error_3d(u, op, mesh, prims, chunk=4096):
+    """The L^2 error on curved tetrahedra, exact solution prims(X (3, ...))."""
     from esplit_inputs.mesh import _quad_tet_shape
-    from esplit_inputs.states import vortex3d_prims
     p = op.p
     xq, wq = tet_rule(3 * p + 1)
     ctr = np.full(3, 0.25)
@@ -90,7 +96,13 @@ def l2_error_vortex_3d(u, op, mesh, t, chunk=4096):
         Jm = np.einsum("jqa,eia->eqij", dN, Gc)
         J = np.linalg.det(Jm)
         uq = np.einsum("qm,ecm->ecq", fit, u[a:a + chunk])
-        rho, V, pr = vortex3d_prims(X[:, 0], X[:, 1], t)
+        rho, V, pr = prims(np.moveaxis(X, 1, 0))
         ue = np.moveaxis(prim_to_cons(rho, V, pr), 0, 1)
         total += float(np.einsum("q,eq,ecq->", wq, J, (uq - ue) ** 2))
     return float(np.sqrt(total))
+
+
+def l2_error_vortex_3d(u, op, mesh, t, chunk=4096):
+    """The Sec. 7.3 L^2 error for the 3D vortex on curved tetrahedra."""
+    from esplit_inputs.states import vortex3d_prims
+    return l2_error_3d(u, op, mesh, lambda X: vortex3d_prims(X[0], X[1], t), chunk)
