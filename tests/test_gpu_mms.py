@@ -14,9 +14,10 @@ source term; the source is not part of the method).
 3D (p = 2 tetrahedra, 6^3 x 6 .. 12^3 x 6): the errors are within 15 % of
 the printed ones (observed 1.07 times them on every grid) and the rates near
 3 (printed 2.81, 2.90).  2D: the rates are near p + 1 as printed; the printed
-errors themselves are not matched: with the Sec. 7.3 quadrature measure the
-initial state's own projection error on these grids is already 2 to 13 times
-the printed error at t_f (the factor growing with p), and the discrete H-norm
+errors themselves are not matched, and cannot be by any degree-p scheme: the
+best L^2 approximation of the initial state by degree-p polynomials on these
+grids is already 2 to 10 times the printed error at t_f (the factor growing
+with p), and the discrete H-norm
 at the nodes does not match them either (they behave like ours on grids twice
 as fine, divided by about two); Section 7.4 does not restate its 2D setup
 beyond the formulas used here, so the 2D magnitudes are printed, not
