@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--no-tgv", action="store_true", help="skip the 3D Taylor-Green (196,608 tets) measurement")
     ap.add_argument("--no-quadrants", action="store_true", help="skip the 2D quadrant Riemann problem (hybrid)")
     ap.add_argument("--quadrants-full", action="store_true", help="run the quadrant problem to t = 0.25")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 128-triangle step latency and the adjoint (residual / step VJP) timings")
+    ap.add_argument("--tgv-n", type=int, default=32,
+                    help="cubes per direction of the Taylor-Green mesh (6 N^3 tetrahedra; 32 is the workload, "
+                         "smaller meshes serve profiling captures)")
     return ap.parse_args()
 
 
@@ -282,10 +287,11 @@ def _timed(fn, stream, flush, n):
     return ts
 
 
-def taylor_green_run(es, device, flush, steps=5):
+def taylor_green_run(es, device, flush, steps=5, n_cubes=32):
     """Compressible Navier-Stokes Taylor-Green vortex (Re 1600, Ma 0.1, Pr
     0.71, heat flux on) on [0, 2 pi]^3: 32^3 cubes x 6 = 196,608 curved
-    tetrahedra (warp 0.02), p = 2 (25 nodes); entropy split + EC SATs + BO
+    tetrahedra by default (n_cubes^3 x 6 otherwise; warp 0.02), p = 2 (25
+    nodes); entropy split + EC SATs + BO
     viscous SATs + matrix dissipation; relaxation RK4 steps in FP64 and in
     FP32-bulk (entropy, production and root solve in FP64 in both), plus
     residual-only split vs Hadamard times on the same state."""
@@ -293,15 +299,15 @@ def taylor_green_run(es, device, flush, steps=5):
     from esplit_inputs.mesh import periodic_tet_mesh
     t0 = time.perf_counter()
     op = tet_operator(2)
-    mesh = periodic_tet_mesh(op, 32, 2 * np.pi, 0.02)
+    mesh = periodic_tet_mesh(op, n_cubes, 2 * np.pi, 0.02)
     u0 = states.taylor_green(mesh)
     dt = states.cfl_timestep(mesh, u0, 0.1)
     host_s = time.perf_counter() - t0
     mu = 1.0 / 1600.0
     stream = torch.cuda.current_stream(device)
     dof = mesh.n_e * op.n_p
-    out = {"workload": "3D Taylor-Green vortex, Re 1600, Ma 0.1, 32^3 x 6 = 196,608 curved tets, p=2 (25 nodes), "
-                       "entropy split + EC SAT + BO viscous SAT + matrix dissipation, relaxation RK4",
+    out = {"workload": f"3D Taylor-Green vortex, Re 1600, Ma 0.1, {n_cubes}^3 x 6 = {mesh.n_e:,} curved tets, p=2 "
+                       "(25 nodes), entropy split + EC SAT + BO viscous SAT + matrix dissipation, relaxation RK4",
            "n_e": mesh.n_e, "n_p": op.n_p, "dof": dof, "dt": dt, "host_setup_s": host_s}
     s = es.Solver(op, mesh, es.Params(mu=mu, viscous=True, dissipation=True), device=device)
     r = s.empty()
@@ -529,10 +535,10 @@ def main():
     if rank == 0 and not args.no_sweep:
         extras["residual_sweep"] = residual_sweep(es, device, flush)
     if rank == 0 and not args.no_tgv:
-        extras["taylor_green"] = taylor_green_run(es, device, flush)
+        extras["taylor_green"] = taylor_green_run(es, device, flush, n_cubes=args.tgv_n)
     if rank == 0 and not args.no_quadrants:
         extras["quadrants"] = quadrant_run(es, device, flush, t_final=0.25 if args.quadrants_full else None)
-    if rank == 0 and not args.no_sweep:
+    if rank == 0 and not args.no_small:
         extras.update(small_and_adjoint_run(es, device, flush))
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
