@@ -183,6 +183,59 @@ __device__ __forceinline__ void dflux_dw(const Node<T, D>& n, const JvpPrep<T>& 
   dF[D + 1] = (de + dp) * n.V[i] + jp.ep * dV[i];
 }
 
+// (dW/dU) z: the change of the entropy variables (Eq. (25)) for a change z of
+// the conservative variables, by the chain rule through (rho, V, p, q):
+//   dV = (dm - V drho)/rho, dp = (gam-1)(dE - V.dm + |V|^2 drho/2),
+//   dq/q = a_q drho/rho + b_q dp/p, d(p/rho) = (dp - (p/rho) drho)/rho,
+//   dW = [dq (w1c p/rho - |V|^2/2) + q (w1c d(p/rho) - V.dV), dq V + q dV, -dq].
+// dW/dU is the Hessian of the entropy, symmetric.
+template <typename T, int D, typename C>
+__device__ __forceinline__ void dW_dU_apply(const Node<T, D>& n, const JvpPrep<T>& jp, const C& c, const T* z,
+                                            T* out) {
+  const T drho = z[0];
+  T dV[D], vdm = T(0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    vdm += n.V[j] * z[1 + j];
+    dV[j] = (z[1 + j] - n.V[j] * drho) * jp.ir;
+  }
+  const T dp = c.gm1 * (z[D + 1] - vdm + T(0.5) * n.v2 * drho);
+  const T ip = jp.itheta * jp.ir;  // 1/p
+  const T dq = n.q * (c.a_q * drho * jp.ir + c.b_q * dp * ip);
+  const T dth = (dp - jp.theta * drho) * jp.ir;
+  T vdv = T(0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) vdv += n.V[j] * dV[j];
+  out[0] = dq * jp.w0q + n.q * (c.w1c * dth - vdv);
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[1 + j] = dq * n.V[j] + n.q * dV[j];
+  out[D + 1] = -dq;
+}
+
+// (dU/dW) v: the change of the conservative variables for a change v of the
+// entropy variables (the inverse map of Eq. (25), the chain rule dflux_dw
+// starts with): dq = -v_nc, dV = (v_m - dq V)/q,
+// d(p/rho) = ((v_1 - dq W_1/q)/q + V.dV)/w1c, drho from q = rho^(a_q+b_q) (p/rho)^b_q,
+// dU = [drho, drho V + rho dV, dp/(gam-1) + drho |V|^2/2 + rho V.dV].
+template <typename T, int D, typename C>
+__device__ __forceinline__ void dU_dW_apply(const Node<T, D>& n, const JvpPrep<T>& jp, const C& c, const T* v,
+                                            T* out) {
+  const T dq = -v[D + 1];
+  T dV[D], vdv = T(0);
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    dV[j] = (v[1 + j] - dq * n.V[j]) * jp.iq;
+    vdv += n.V[j] * dV[j];
+  }
+  const T dth = c.inv_w1c * ((v[0] - dq * jp.w0q) * jp.iq + vdv);
+  const T drho = jp.rq * (dq * jp.iq - c.b_q * dth * jp.itheta);
+  const T dp = drho * jp.theta + n.rho * dth;
+  out[0] = drho;
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[1 + j] = drho * n.V[j] + n.rho * dV[j];
+  out[D + 1] = dp * c.inv_gm1 + T(0.5) * drho * n.v2 + n.rho * vdv;
+}
+
 // Powers of the parameter vector used by the two-point flux and the
 // dissipation: P1 = z_1^r1 = q^r1, P2 = z_nc^r2 = p^r2.
 template <typename T, int D, typename C>

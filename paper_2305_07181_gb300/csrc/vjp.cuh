@@ -10,8 +10,9 @@
 //   grad_m   = sum_i (df_i/du)^T fbar_i + (dw/du)^T wbar
 //              - 1/(beta+1) d/du [cot_m . sum_i A~_i(u) g_i]|_(g_i = (D_i w)_m)
 //              + facet part (dG/du)^T (-cot_km/H_km + cot_vn/H_vn).
-// The pointwise Jacobians are exact, from the same physics templates run on
-// forward-mode dual numbers (dual.cuh); the contractions are transposed
+// The facet Jacobians are exact, from the same physics templates run on
+// forward-mode dual numbers (dual.cuh); the volume's pointwise part needs one
+// dual direction (see split_vjp_kernel); the contractions are transposed
 // applications of the stored per-element operators.  Float64 throughout.
 // Included by kernels.cu (one device translation unit: the constant-memory
 // operator tables are shared).
@@ -101,7 +102,6 @@ __global__ void __launch_bounds__(EB * NP) split_vjp_kernel(const double* __rest
                                                             const double* __restrict__ gsat, int n_e,
                                                             double* __restrict__ grad, Phys<double> c) {
   constexpr int NC = D + 2;
-  using TD = Dual<NC>;
   __shared__ double sw[EB][NC][NP];
   __shared__ double sv[EB][NC][NP];
   __shared__ double sgb[EB][D][NC][NP];
@@ -167,36 +167,51 @@ __global__ void __launch_bounds__(EB * NP) split_vjp_kernel(const double* __rest
         wb[q] += dt * sgb[el][i][q][n];
       }
     }
-  // exact pointwise Jacobians at u_m by dual numbers
-  TD ud[NC];
+  // pointwise part.  With A~_i = dF_i/dW symmetric and dW/du the symmetric
+  // Hessian of the entropy,
+  //   (dF_i/du)^T fb_i = (dW/du) A~_i fb_i,   (dw/du)^T wb = (dW/du) wb,
+  // and, F_i being the W-gradient of its flux potential (Sec. 2.4), the
+  // derivative of A~_i(W) g along W is symmetric in its three arguments, so the
+  // u-gradient of cot_m . A~_i(u) g_i is (dW/du) applied to the derivative of
+  // A~_i g_i along W in the single direction cot_m (a one-direction dual
+  // number, the state moved by (dU/dW) cot_m):
+  //   grad_m = (dW/du) [sum_i A~_i fb_i + wb - 1/(beta+1) sum_i d_cot(A~_i g_i)].
+  const JvpPrep<double> jp = jvp_prep<double, D>(nd, c);
+  double z[NC];
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    ud[q] = TD(uu[q]);
-    ud[q].d[q] = 1.0;
-  }
-  Node<TD, D> ndd;
-  node_from_u<TD, D>(ud, c, ndd);
-  const JvpPrep<TD> jpd = jvp_prep<TD, D>(ndd, c);
-  double gr[NC];
-#pragma unroll
-  for (int cc = 0; cc < NC; ++cc) gr[cc] = 0.0;
+  for (int q = 0; q < NC; ++q) z[q] = wb[q];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    TD F[NC];
-    euler_flux<TD, D>(ndd, i, F);
-    TD gi[NC], dF[NC];
+    double a[NC];
+    dflux_dw<double, D>(nd, jp, c, i, fb[i], a);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) gi[q] = TD(g[i][q]);
-    dflux_dw<TD, D>(ndd, jpd, c, i, gi, dF);
-#pragma unroll
-    for (int q = 0; q < NC; ++q)
-#pragma unroll
-      for (int cc = 0; cc < NC; ++cc) gr[cc] += fb[i][q] * F[q].d[cc] - c.inv_bp1 * vv[q] * dF[q].d[cc];
+    for (int q = 0; q < NC; ++q) z[q] += a[q];
   }
+  {
+    using T1 = Dual<1>;
+    double du[NC];
+    dU_dW_apply<double, D>(nd, jp, c, vv, du);
+    T1 ud[NC];
 #pragma unroll
-  for (int q = 0; q < NC; ++q)
+    for (int q = 0; q < NC; ++q) {
+      ud[q] = T1(uu[q]);
+      ud[q].d[0] = du[q];
+    }
+    Node<T1, D> n1;
+    node_from_u<T1, D>(ud, c, n1);
+    const JvpPrep<T1> j1 = jvp_prep<T1, D>(n1, c);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) gr[cc] += wb[q] * ndd.W[q].d[cc];
+    for (int i = 0; i < D; ++i) {
+      T1 gi[NC], dF[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) gi[q] = T1(g[i][q]);
+      dflux_dw<T1, D>(n1, j1, c, i, gi, dF);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) z[q] -= c.inv_bp1 * dF[q].d[0];
+    }
+  }
+  double gr[NC];
+  dW_dU_apply<double, D>(nd, jp, c, z, gr);
   int sl = c_ref.node_slot[m];
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
