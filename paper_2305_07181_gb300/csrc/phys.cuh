@@ -277,6 +277,26 @@ __device__ __forceinline__ T exp_avg(T a, T b, T ar, T br, S r, T ia, const S* c
   return ar * ia * sum;
 }
 
+// The same average on dual numbers: the series and its derivative by Horner's
+// rule on the values, then one chain-rule step (d sum = g'(eps) d eps),
+// instead of the series on the duals.
+template <int N, typename S>
+__device__ __forceinline__ Dual<N> exp_avg(const Dual<N>& a, const Dual<N>& b, const Dual<N>& ar,
+                                           const Dual<N>& br, S r, const Dual<N>& ia, const S* coef) {
+  const Dual<N> eps = (b - a) * ia;
+  if (fabs(eps.v) >= ExpAvgCfg<double>::EPS_SWITCH) return (ar - br) / (r * (a - b));
+  double sv = coef[ExpAvgCfg<double>::NTERMS - 1], dv = 0.0;
+#pragma unroll
+  for (int k = ExpAvgCfg<double>::NTERMS - 2; k >= 0; --k) {
+    dv = dv * eps.v + sv;
+    sv = sv * eps.v + coef[k];
+  }
+  Dual<N> sum(sv);
+#pragma unroll
+  for (int i = 0; i < N; ++i) sum.d[i] = dv * eps.d[i];
+  return ar * ia * sum;
+}
+
 // Everything the two-point flux needs at one node.
 template <typename T, int D>
 struct ZNode {
@@ -322,9 +342,9 @@ template <typename T, int D, typename C>
 __device__ __forceinline__ void pair_avg(const ZNode<T, D>& k, const ZNode<T, D>& v, const C& c,
                                          PairAvg<T, D>& a) {
   a.A1 = T(0.5) * (k.P1 + v.P1);
-  a.E1 = exp_avg<T>(k.p, v.p, k.P2, v.P2, c.r2, k.ip, c.ser2);
+  a.E1 = exp_avg(k.p, v.p, k.P2, v.P2, c.r2, k.ip, c.ser2);
   a.A2 = T(0.5) * (k.P2 + v.P2);
-  a.E2 = exp_avg<T>(k.q, v.q, k.P1, v.P1, c.r1, k.iq, c.ser1);
+  a.E2 = exp_avg(k.q, v.q, k.P1, v.P1, c.r1, k.iq, c.ser1);
   a.z1a = T(0.5) * (k.q + v.q);
   a.ke = T(0);
 #pragma unroll

@@ -21,6 +21,118 @@
 namespace esplit {
 
 // facet pairs: each thread writes the facet part of grad at its two slots
+// x (derivatives with respect to one side's four state components) placed at
+// derivative slots [off, off + N) of an M-direction dual
+template <int M, int N>
+__device__ __forceinline__ Dual<M> embed(const Dual<N>& x, int off) {
+  Dual<M> r(x.v);
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[off + i] = x.d[i];
+  return r;
+}
+
+template <int D, int N, int M>
+__device__ __forceinline__ void embed_znode(const ZNode<Dual<N>, D>& a, int off, ZNode<Dual<M>, D>& b) {
+  b.q = embed<M>(a.q, off);
+  b.p = embed<M>(a.p, off);
+  b.P1 = embed<M>(a.P1, off);
+  b.P2 = embed<M>(a.P2, off);
+  b.v2 = embed<M>(a.v2, off);
+  b.iq = embed<M>(a.iq, off);
+  b.ip = embed<M>(a.ip, off);
+#pragma unroll
+  for (int i = 0; i < D; ++i) b.V[i] = embed<M>(a.V[i], off);
+}
+
+// X^ |Lambda_n| S^ X^T dw of Eq. (69), as diss_apply, one column of X^ at a
+// time (the eight-direction dual version would otherwise hold all n_c^2
+// entries); n and dw may be plain doubles (no derivative parts).
+template <typename T, typename TN, typename TW, int D, typename C>
+__device__ __forceinline__ void diss_apply_cols(const PairAvg<T, D>& a, const C& c, const TN* n, const TW* dw,
+                                                T* out) {
+  constexpr int NC = D + 2;
+  T rho_h = a.z1a / (a.A1 * a.E1);
+  T iz = T(1.0) / a.z1a;
+  T Vh[D];
+  T vh2 = T(0.0), vn = T(0.0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Vh[i] = a.qV[i] * iz;
+    vh2 = vh2 + Vh[i] * Vh[i];
+    vn = vn + Vh[i] * n[i];
+  }
+  T p_h = a.pa;
+  T theta = rho_h / (p_h * a.A1 * a.E1);
+  T eta = T(1.0) / (a.z1a * a.E2 * a.E1);
+  T ah = t_sqrt(c.gam * p_h / rho_h);
+  T Hh = ah * ah * c.inv_gm1 + 0.5 * vh2;
+#pragma unroll
+  for (int r = 0; r < NC; ++r) out[r] = T(0.0);
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    T col[NC];
+    T ls;
+    if (k == 0 || k == NC - 1) {
+      const double sg = (k == 0) ? -1.0 : 1.0;
+      col[0] = T(1.0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) col[1 + i] = Vh[i] + sg * (ah * n[i]);
+      col[NC - 1] = Hh + sg * (ah * vn);
+      ls = t_abs(vn + sg * ah) * (c.s_ac * theta);
+    } else if (k == 1) {
+      col[0] = T(1.0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) col[1 + i] = Vh[i];
+      col[NC - 1] = 0.5 * vh2;
+      ls = t_abs(vn) * (c.s_en * theta);
+    } else {
+      // tangential columns as printed: (0, n2, -n1, 0, V1 n2 - V2 n1) and
+      // (0, -n3, 0, n1, V3 n1 - V1 n3) (2D: the first without its 4th row)
+#pragma unroll
+      for (int r = 0; r < NC; ++r) col[r] = T(0.0);
+      if (k == 2) {
+        col[1] = T(n[1]);
+        col[2] = T(-n[0]);
+        col[NC - 1] = Vh[0] * n[1] - Vh[1] * n[0];
+      } else {
+        col[1] = T(-n[D - 1]);
+        col[3] = T(n[0]);
+        col[NC - 1] = Vh[D - 1] * n[0] - Vh[0] * n[D - 1];
+      }
+      ls = t_abs(vn) * eta;
+    }
+    T y = col[0] * dw[0];
+#pragma unroll
+    for (int r = 1; r < NC; ++r) y = y + col[r] * dw[r];
+    y = y * ls;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) out[r] = out[r] + col[r] * y;
+  }
+}
+
+template <int D, int N>
+__device__ __forceinline__ PairAvg<double, D> strip_avg(const PairAvg<Dual<N>, D>& a) {
+  PairAvg<double, D> b;
+  b.A1 = a.A1.v;
+  b.E1 = a.E1.v;
+  b.A2 = a.A2.v;
+  b.E2 = a.E2.v;
+  b.z1a = a.z1a.v;
+  b.pa = a.pa.v;
+  b.ke = a.ke.v;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    b.qV[i] = a.qV[i].v;
+    b.Va[i] = a.Va[i].v;
+  }
+  return b;
+}
+
+// facet pairs: each thread writes the facet part of grad at its two slots.
+// Each side's nodal chain (logarithms, exponentials, divisions) depends on its
+// own four state components only: it runs on four-direction duals, and the
+// results enter the eight-direction pair computation (averages, two-point
+// flux, dissipation) at that side's slots.
 template <int D>
 __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__ u, const double* __restrict__ cot,
                                                       const int2* __restrict__ fp, int n_pairs,
@@ -29,6 +141,7 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
   constexpr int NC = D + 2;
   constexpr int N2 = 2 * NC;
   using T = Dual<N2>;
+  using TS = Dual<NC>;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_pairs) return;
   const int NP = c_ref.n_p, NS = c_ref.n_slot;
@@ -36,21 +149,32 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
   int k = pr.x / NS, s = pr.x - k * NS;
   int v = pr.y / NS, s2 = pr.y - v * NS;
   int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
-  T uk[NC], uv[NC];
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    uk[q] = T(__ldg(&u[((size_t)k * NC + q) * NP + m]));
-    uv[q] = T(__ldg(&u[((size_t)v * NC + q) * NP + n]));
-    uk[q].d[q] = 1.0;
-    uv[q].d[NC + q] = 1.0;
-  }
-  Node<T, D> nk, nv;
-  node_from_u<T, D>(uk, c, nk);
-  node_from_u<T, D>(uv, c, nv);
   ZNode<T, D> zk, zv;
-  znode<T, D>(nk, c, zk);
-  znode<T, D>(nv, c, zv);
-  znode_recips<T, D>(zk);
+  TS Wk[NC], Wv[NC];  // each side's entropy variables with their own Jacobian
+  {
+    TS uk[NC], uv[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      uk[q] = TS(__ldg(&u[((size_t)k * NC + q) * NP + m]));
+      uv[q] = TS(__ldg(&u[((size_t)v * NC + q) * NP + n]));
+      uk[q].d[q] = 1.0;
+      uv[q].d[q] = 1.0;
+    }
+    Node<TS, D> nk, nv;
+    node_from_u<TS, D>(uk, c, nk);
+    node_from_u<TS, D>(uv, c, nv);
+    ZNode<TS, D> sk, sv;
+    znode<TS, D>(nk, c, sk);
+    znode<TS, D>(nv, c, sv);
+    znode_recips<TS, D>(sk);
+    embed_znode<D>(sk, 0, zk);
+    embed_znode<D>(sv, NC, zv);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      Wk[q] = nk.W[q];
+      Wv[q] = nv.W[q];
+    }
+  }
   PairAvg<T, D> a;
   pair_avg<T, D>(zk, zv, c, a);
   double nud[D];
@@ -62,36 +186,51 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
     nuv[i] = T(nud[i]);
     b2 += nud[i] * nud[i];
   }
-  T G[NC];
-  sy_flux_dir<T, D>(a, c, nuv, G);
-  if (dissipation) {
-    double b = sqrt(b2);
-    T nh[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) nh[i] = T(nud[i] / b);
-    T dw[NC], out[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
-    diss_apply<T, D>(a, c, nh, dw, out);
-#pragma unroll
-    for (int q = 0; q < NC; ++q) G[q] += (0.5 * b) * out[q];
-  }
   double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
   double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
   double gb[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q)
     gb[q] = -__ldg(&cot[((size_t)k * NC + q) * NP + m]) * ihk + __ldg(&cot[((size_t)v * NC + q) * NP + n]) * ihv;
+  T G[NC];
+  sy_flux_dir<T, D>(a, c, nuv, G);
+  double gk[NC], gv[NC];
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) gk[cc] = gv[cc] = 0.0;
+  if (dissipation) {
+    // d[gb . M(a) (w_k - w_v)] = gb . (dM) dw + (M gb) . (dw_k - dw_v), M symmetric:
+    // the averages' part on the duals with dw fixed, the states' part from
+    // M gb (plain doubles) and each side's entropy-variable Jacobian
+    const double b = sqrt(b2);
+    double nh[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = nud[i] / b;
+    double dw[NC], Mgb[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) dw[q] = Wk[q].v - Wv[q].v;
+    T out[NC];
+    diss_apply_cols<T, double, double, D>(a, c, nh, dw, out);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) G[q] += (0.5 * b) * out[q];
+    const PairAvg<double, D> ar = strip_avg<D>(a);
+    diss_apply_cols<double, double, double, D>(ar, c, nh, gb, Mgb);
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        gk[cc] += 0.5 * b * Mgb[q] * Wk[q].d[cc];
+        gv[cc] -= 0.5 * b * Mgb[q] * Wv[q].d[cc];
+      }
+  }
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
-    double gk = 0.0, gv = 0.0;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      gk += gb[q] * G[q].d[cc];
-      gv += gb[q] * G[q].d[NC + cc];
+      gk[cc] += gb[q] * G[q].d[cc];
+      gv[cc] += gb[q] * G[q].d[NC + cc];
     }
-    gsat[((size_t)k * NC + cc) * NS + s] = gk;
-    gsat[((size_t)v * NC + cc) * NS + s2] = gv;
+    gsat[((size_t)k * NC + cc) * NS + s] = gk[cc];
+    gsat[((size_t)v * NC + cc) * NS + s2] = gv[cc];
   }
 }
 
