@@ -110,6 +110,112 @@ __device__ __forceinline__ void diss_apply_cols(const PairAvg<T, D>& a, const C&
   }
 }
 
+// Derivative parts (N directions) of s = gb . X^|L|S^X^T dw with gb, dw fixed,
+// the hat state on the duals.  With r_k the columns of X^ and l_k = |lambda_k| S_k,
+// s = sum_k l_k (r_k . gb)(r_k . dw), so
+//   ds = sum_k [(r_k.gb)(r_k.dw) dl_k + l_k ((r_k.dw) gb + (r_k.gb) dw) . dr_k]:
+// only the columns and weights are formed on the duals.
+template <int N, int D, typename C>
+__device__ __forceinline__ void diss_scalar_grad(const PairAvg<Dual<N>, D>& a, const C& c, const double* n,
+                                                 const double* gb, const double* dw, double* ds) {
+  using T = Dual<N>;
+  constexpr int NC = D + 2;
+  T rho_h = a.z1a / (a.A1 * a.E1);
+  T iz = T(1.0) / a.z1a;
+  T Vh[D];
+  T vh2 = T(0.0), vn = T(0.0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Vh[i] = a.qV[i] * iz;
+    vh2 = vh2 + Vh[i] * Vh[i];
+    vn = vn + Vh[i] * n[i];
+  }
+  T p_h = a.pa;
+  T theta = rho_h / (p_h * a.A1 * a.E1);
+  T eta = T(1.0) / (a.z1a * a.E2 * a.E1);
+  T ah = t_sqrt(c.gam * p_h / rho_h);
+  T Hh = ah * ah * c.inv_gm1 + 0.5 * vh2;
+#pragma unroll
+  for (int i = 0; i < N; ++i) ds[i] = 0.0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    T col[NC];
+    T ls;
+    if (k == 0 || k == NC - 1) {
+      const double sg = (k == 0) ? -1.0 : 1.0;
+      col[0] = T(1.0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) col[1 + i] = Vh[i] + sg * (ah * n[i]);
+      col[NC - 1] = Hh + sg * (ah * vn);
+      ls = t_abs(vn + sg * ah) * (c.s_ac * theta);
+    } else if (k == 1) {
+      col[0] = T(1.0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) col[1 + i] = Vh[i];
+      col[NC - 1] = 0.5 * vh2;
+      ls = t_abs(vn) * (c.s_en * theta);
+    } else {
+#pragma unroll
+      for (int r = 0; r < NC; ++r) col[r] = T(0.0);
+      if (k == 2) {
+        col[1] = T(n[1]);
+        col[2] = T(-n[0]);
+        col[NC - 1] = Vh[0] * n[1] - Vh[1] * n[0];
+      } else {
+        col[1] = T(-n[D - 1]);
+        col[3] = T(n[0]);
+        col[NC - 1] = Vh[D - 1] * n[0] - Vh[0] * n[D - 1];
+      }
+      ls = t_abs(vn) * eta;
+    }
+    double al = 0.0, be = 0.0;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+      al += col[r].v * gb[r];
+      be += col[r].v * dw[r];
+    }
+    const double ab = al * be;
+#pragma unroll
+    for (int i = 0; i < N; ++i) ds[i] += ab * ls.d[i];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+      const double w = ls.v * (be * gb[r] + al * dw[r]);
+#pragma unroll
+      for (int i = 0; i < N; ++i) ds[i] += w * col[r].d[i];
+    }
+  }
+}
+
+// Derivative parts of s = gb . sum_i nu_i F*_i (Eq. (48), as sy_flux_dir):
+// F = [mn, mn {V} + nu {p}, mn h], mn = nu.{z_1 V}/({z_1^a}{z_nc^b}_e),
+// h = gam/(gam-1) {.}{.}_e + ke, so s = mn (gb_0 + gb_m.{V} + gb_e h) + {p} gb_m.nu.
+template <int N, int D, typename C>
+__device__ __forceinline__ void flux_scalar_grad(const PairAvg<Dual<N>, D>& a, const C& c, const double* nu,
+                                                 const double* gb, double* ds) {
+  using T = Dual<N>;
+  constexpr int NC = D + 2;
+  T inv_den = T(1.0) / (a.A1 * a.E1);
+  T mq = T(0.0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) mq = mq + nu[i] * a.qV[i];
+  T mn = mq * inv_den;
+  T h = c.gam_gm1 * (a.A2 * a.E2) + a.ke;
+  double gmv = gb[0] + gb[NC - 1] * h.v, gmn = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    gmv += gb[1 + j] * a.Va[j].v;
+    gmn += gb[1 + j] * nu[j];
+  }
+  // ds = gmv dmn + mn (gb_m . d{V} + gb_e dh) + gmn d{p}
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double t = gb[NC - 1] * h.d[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) t += gb[1 + j] * a.Va[j].d[i];
+    ds[i] = gmv * mn.d[i] + mn.v * t + gmn * a.pa.d[i];
+  }
+}
+
 template <int D, int N>
 __device__ __forceinline__ PairAvg<double, D> strip_avg(const PairAvg<Dual<N>, D>& a) {
   PairAvg<double, D> b;
@@ -178,12 +284,10 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
   PairAvg<T, D> a;
   pair_avg<T, D>(zk, zv, c, a);
   double nud[D];
-  T nuv[D];
   double b2 = 0.0;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     nud[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
-    nuv[i] = T(nud[i]);
     b2 += nud[i] * nud[i];
   }
   double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
@@ -192,15 +296,17 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
 #pragma unroll
   for (int q = 0; q < NC; ++q)
     gb[q] = -__ldg(&cot[((size_t)k * NC + q) * NP + m]) * ihk + __ldg(&cot[((size_t)v * NC + q) * NP + n]) * ihv;
-  T G[NC];
-  sy_flux_dir<T, D>(a, c, nuv, G);
+  // gb . G(u_k, u_v): the two-point flux, and with dissipation
+  //   d[gb . M(a) (w_k - w_v)] = gb . (dM) dw + (M gb) . (dw_k - dw_v)   (M symmetric)
+  double ds[N2];
+  flux_scalar_grad<N2, D>(a, c, nud, gb, ds);
   double gk[NC], gv[NC];
 #pragma unroll
-  for (int cc = 0; cc < NC; ++cc) gk[cc] = gv[cc] = 0.0;
+  for (int cc = 0; cc < NC; ++cc) {
+    gk[cc] = ds[cc];
+    gv[cc] = ds[NC + cc];
+  }
   if (dissipation) {
-    // d[gb . M(a) (w_k - w_v)] = gb . (dM) dw + (M gb) . (dw_k - dw_v), M symmetric:
-    // the averages' part on the duals with dw fixed, the states' part from
-    // M gb (plain doubles) and each side's entropy-variable Jacobian
     const double b = sqrt(b2);
     double nh[D];
 #pragma unroll
@@ -208,27 +314,22 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
     double dw[NC], Mgb[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) dw[q] = Wk[q].v - Wv[q].v;
-    T out[NC];
-    diss_apply_cols<T, double, double, D>(a, c, nh, dw, out);
-#pragma unroll
-    for (int q = 0; q < NC; ++q) G[q] += (0.5 * b) * out[q];
+    diss_scalar_grad<N2, D>(a, c, nh, gb, dw, ds);
     const PairAvg<double, D> ar = strip_avg<D>(a);
     diss_apply_cols<double, double, double, D>(ar, c, nh, gb, Mgb);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc)
+    for (int cc = 0; cc < NC; ++cc) {
+      gk[cc] += 0.5 * b * ds[cc];
+      gv[cc] += 0.5 * b * ds[NC + cc];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         gk[cc] += 0.5 * b * Mgb[q] * Wk[q].d[cc];
         gv[cc] -= 0.5 * b * Mgb[q] * Wv[q].d[cc];
       }
+    }
   }
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      gk[cc] += gb[q] * G[q].d[cc];
-      gv[cc] += gb[q] * G[q].d[NC + cc];
-    }
     gsat[((size_t)k * NC + cc) * NS + s] = gk[cc];
     gsat[((size_t)v * NC + cc) * NS + s2] = gv[cc];
   }
