@@ -228,3 +228,43 @@ def test_vortex3d_solves_euler():
     bad = -0.4 * (x2 - 0.3) * np.exp(0.5 * (1 - (x1 - 0.3) ** 2 - x1 ** 2))
     good = -0.4 * (x2 - 0.3) * np.exp(0.5 * (1 - (x2 - 0.3) ** 2 - x1 ** 2))
     assert np.abs(bad - good).max() > 1e-2
+
+
+def test_manufactured_grids_and_state():
+    """Sec. 7.4 inputs: the curving map vanishes on the boundary of [-1, 1]^d,
+    so the periodic grids pair their facet nodes (coincident modulo 2, opposite
+    normals) with J > 0 and total volume 2^d; the manufactured state has total
+    energy rho^2 and unit velocity."""
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import mms_warp_2d, mms_warp_3d, periodic_tet_mesh, periodic_tri_mesh_rect
+    g = np.linspace(-1, 1, 9)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    dx, dy = mms_warp_2d(X, Y)
+    for side in (0, -1):
+        assert np.abs(dx[side, :]).max() < 1e-16 and np.abs(dx[:, side]).max() < 1e-16
+        assert np.abs(dy[side, :]).max() < 1e-16 and np.abs(dy[:, side]).max() < 1e-16
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1)
+    d3 = mms_warp_3d(P)
+    for i in range(3):
+        for side in (0, -1):
+            face = np.take(d3, [side], axis=i)
+            assert np.abs(face).max() < 1e-16
+    op = tri_operator(3)
+    m = periodic_tri_mesh_rect(op, 6, 6, origin=(-1.0, -1.0), size=(2.0, 2.0), warp=mms_warp_2d)
+    assert np.all(m.J > 0) and abs(np.sum(m.J * op.H[None]) - 4.0) < 1e-12
+    fn = op.facet_nodes.reshape(-1)
+    pe, ps = m.pair[..., 0].reshape(m.n_e, -1), m.pair[..., 1].reshape(m.n_e, -1)
+    xs = m.x[:, :, fn].transpose(0, 2, 1)
+    ddx = xs - xs[pe, ps]
+    ddx -= 2.0 * np.round(ddx / 2.0)
+    assert np.abs(ddx).max() < 1e-13
+    nu = m.nu.reshape(m.n_e, -1, 2)
+    assert np.abs(nu + nu[pe, ps]).max() < 1e-13
+    u = states.manufactured_state(m, 0.3)
+    assert np.allclose(u[:, 3], u[:, 0] ** 2, rtol=1e-14)
+    assert np.allclose(u[:, 1], u[:, 0], rtol=1e-14) and np.allclose(u[:, 2], u[:, 0], rtol=1e-14)
+    op3 = tet_operator(2)
+    m3 = periodic_tet_mesh(op3, 3, 2.0, origin=-1.0, warp=mms_warp_3d)
+    assert np.all(m3.J > 0) and abs(np.sum(m3.J * op3.H[None]) - 8.0) < 1e-11
+    u3 = states.manufactured_state(m3, 0.0)
+    assert np.allclose(u3[:, 4], u3[:, 0] ** 2, rtol=1e-14)
