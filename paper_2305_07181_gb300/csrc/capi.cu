@@ -158,7 +158,7 @@ void esplit_destroy(esplit_ctx* c) {
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
-                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.vfb, b.vfs, b.vus};
+                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.wslot, b.vfb, b.vfs, b.vus};
   for (void* p : ps) dfree(p);
   if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
   if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
@@ -301,6 +301,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   dalloc(c, &c->b.fv, 0);
   dalloc(c, &c->b.vsat, 0);
   dalloc(c, &c->b.va, 0);
+  dalloc(c, &c->b.wslot, 0);
   dalloc(c, &c->b.vfb, 0);
   dalloc(c, &c->b.vfs, 0);
   dalloc(c, &c->b.vus, 0);
@@ -397,12 +398,15 @@ static int residual_impl(esplit_ctx* c, const double* u, double* r, cudaStream_t
     return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
   const bool visc = c->prm.viscous != 0;
   if (visc && !c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
-  // with viscous terms the entropy production is taken from the complete
-  // residual after the viscous passes
-  int rc = esplit::launch_residual(c, u, r, s, visc ? nullptr : prod, visc ? nullptr : npart);
+  // the entropy production comes with the residual kernels' block partials:
+  // the split kernel's (everything but the viscous flux jump) and the jump
+  // kernel's; with viscous terms and Hadamard-form elements it is taken from
+  // the complete residual after the viscous passes
+  const bool fused = !visc || c->prm.scheme == ESPLIT_SCHEME_SPLIT;
+  int rc = esplit::launch_residual(c, u, r, s, fused ? prod : nullptr, fused ? npart : nullptr);
   if (rc == -2) return fail(c, ESPLIT_ERR_UNSUPPORTED, "operator size not compiled in");
   if (rc) return fail(c, ESPLIT_ERR_CUDA, std::string("residual launch: ") + cudaGetErrorString(cudaGetLastError()));
-  if (visc && prod && esplit::launch_entropy_rate(c, u, r, s, npart, prod, 1))
+  if (!fused && prod && esplit::launch_entropy_rate(c, u, r, s, npart, prod, 1))
     return fail(c, ESPLIT_ERR_CUDA, "entropy-production launch");
   c->last_stream = s;
   return ESPLIT_OK;
@@ -414,6 +418,7 @@ static int ensure_viscous(esplit_ctx* c) {
   if ((rc = dalloc(c, &c->b.fv, (size_t)c->n_e * c->dim * c->n_c * c->n_p))) return rc;
   if ((rc = dalloc(c, &c->b.vsat, (size_t)c->n_e * c->n_c * c->n_slot))) return rc;
   if ((rc = dalloc(c, &c->b.va, (size_t)c->n_e * c->dim * c->n_c * c->n_slot))) return rc;
+  if ((rc = dalloc(c, &c->b.wslot, (size_t)c->n_e * c->n_c * c->n_slot))) return rc;
   return ESPLIT_OK;
 }
 

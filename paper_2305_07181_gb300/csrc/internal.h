@@ -70,6 +70,8 @@ struct Buffers {
   double* fv = nullptr;
   double* vsat = nullptr;
   double* va = nullptr;
+  double* wslot = nullptr;  // [n_e][n_c][n_slot]: entropy variables at the facet slots, written by
+                            // the viscous split kernel for the flux-jump kernel's entropy production
   // viscous reverse-mode scratch: [n_e][d][n_c][n_p], [n_e][d][n_c][n_slot], [n_e][n_c][n_slot]
   double* vfb = nullptr;
   double* vfs = nullptr;

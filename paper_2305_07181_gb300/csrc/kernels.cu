@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ?
     int* __restrict__ status, double* __restrict__ prod, int visc_heat, const double* __restrict__ nu,
     const double* __restrict__ ah, double* __restrict__ fvs, const double* __restrict__ ops64,
     double* __restrict__ fcache, int n_slot_total, double* __restrict__ ent_part = nullptr,
-    double* __restrict__ ncache = nullptr) {
+    double* __restrict__ ncache = nullptr, double* __restrict__ wsl = nullptr) {
   constexpr int NC = D + 2;
   constexpr bool F64 = sizeof(T) == sizeof(double);
   __shared__ SplitSmem<T, D, NP, EB> sm;
@@ -648,6 +648,12 @@ __global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ?
         // viscous flux from the gradients just formed (gd = D_i w), plus the
         // folded BO lift a/(2H) at the facet nodes; F^V kept for the flux jump
         visc_flux<double, D>(nd, c64, visc_heat, gd, Fp);
+        if (sl >= 0 && wsl) {
+          // entropy variables at the facet slot, for the flux-jump kernel's
+          // share of the entropy production
+#pragma unroll
+          for (int q = 0; q < NC; ++q) wsl[((size_t)e * NC + q) * NS + sl] = nd.W[q];
+        }
         if (sl >= 0) {
 #pragma unroll
           for (int i = 0; i < D; ++i)
@@ -953,10 +959,18 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
         carve_set = true;
       }
     }
-    if (visc)
+    if (visc && c->ent_part && c->b.node_cache) {
+      // first stage of a relaxation step: the kernel also forms the entropy of u_n
+      split_volume_kernel<T, D, NP, EB, true, false, true><<<nb, EB * NP, 0, s>>>(
+          u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
+          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64, nullptr, S,
+          c->ent_part, c->b.node_cache, prod ? c->b.wslot : nullptr);
+      c->ent_n = nb;
+    } else if (visc)
       split_volume_kernel<T, D, NP, EB, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
-          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64, nullptr, S);
+          prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64, nullptr, S,
+          nullptr, nullptr, prod ? c->b.wslot : nullptr);
     else if (cached && c->ent_part && c->b.node_cache) {
       split_volume_kernel<T, D, NP, EB, false, true, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
@@ -1011,7 +1025,9 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     ProfScope ps(c, PG_VISC, s);
     // viscous volume terms of the elements the split kernel did not take
     if (n_had > 0) viscous_volume_np<D, NP>(c, u, r, lhad, n_had, s);
-    viscous_jump<D>(c, r, s);
+    // with the production requested (split scheme only, n_had = 0) the jump
+    // kernel adds its share of the block partials
+    np_used += viscous_jump<D>(c, r, s, (prod && n_had == 0) ? prod + np_used : nullptr);
   }
   if (n_partial) *n_partial = np_used;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -111,34 +111,45 @@ __global__ void __launch_bounds__(EB * NP) visc_volume_kernel(const double* __re
 }
 
 // flux jump, one thread per coincident node pair: -(1/2) nu . (F_k - F_v)
-// divided by the node's H on both sides (identical on both since nu_v = -nu)
+// divided by the node's H on both sides (identical on both since nu_v = -nu).
+// With prod: block partials of its entropy production, (w_k + w_v) . jump
+// (H r . w at both nodes), from the entropy variables at the slots (wsl).
 template <int D>
 __global__ void __launch_bounds__(128) visc_jump_kernel(double* __restrict__ r, const double* __restrict__ fvs,
                                                         const int2* __restrict__ fp, int n_pairs,
-                                                        const double* __restrict__ nu, const double* __restrict__ J) {
+                                                        const double* __restrict__ nu, const double* __restrict__ J,
+                                                        const double* __restrict__ wsl, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_pairs) return;
-  const int NP = c_ref.n_p, NS = c_ref.n_slot;
-  int2 pr = __ldg(&fp[t]);
-  int k = pr.x / NS, s = pr.x - k * NS;
-  int v = pr.y / NS, s2 = pr.y - v * NS;
-  int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
-  double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
-  double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
-  double nuv[D];
+  double hw = 0.0;
+  if (t < n_pairs) {
+    const int NP = c_ref.n_p, NS = c_ref.n_slot;
+    int2 pr = __ldg(&fp[t]);
+    int k = pr.x / NS, s = pr.x - k * NS;
+    int v = pr.y / NS, s2 = pr.y - v * NS;
+    int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
+    double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
+    double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+    double nuv[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) nuv[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
+    for (int i = 0; i < D; ++i) nuv[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    double d = 0.0;
+    for (int q = 0; q < NC; ++q) {
+      double d = 0.0;
 #pragma unroll
-    for (int i = 0; i < D; ++i)
-      d += nuv[i] * (__ldg(&fvs[(((size_t)k * D + i) * NC + q) * NS + s]) -
-                     __ldg(&fvs[(((size_t)v * D + i) * NC + q) * NS + s2]));
-    double jump = -0.5 * d;
-    r[((size_t)k * NC + q) * NP + m] += jump * ihk;
-    r[((size_t)v * NC + q) * NP + n] += jump * ihv;
+      for (int i = 0; i < D; ++i)
+        d += nuv[i] * (__ldg(&fvs[(((size_t)k * D + i) * NC + q) * NS + s]) -
+                       __ldg(&fvs[(((size_t)v * D + i) * NC + q) * NS + s2]));
+      double jump = -0.5 * d;
+      r[((size_t)k * NC + q) * NP + m] += jump * ihk;
+      r[((size_t)v * NC + q) * NP + n] += jump * ihv;
+      if (prod)
+        hw += (__ldg(&wsl[((size_t)k * NC + q) * NS + s]) + __ldg(&wsl[((size_t)v * NC + q) * NS + s2])) * jump;
+    }
+  }
+  if (prod) {
+    double vv[1] = {hw};
+    block_sum<1>(vv, prod + blockIdx.x);
   }
 }
 
@@ -153,12 +164,15 @@ static void viscous_volume_np(esplit_ctx* c, const double* u, double* r, const i
   c->launches += 1;
 }
 
+// returns the number of block partials written to prod (0 without prod)
 template <int D>
-static void viscous_jump(esplit_ctx* c, double* r, cudaStream_t s) {
+static int viscous_jump(esplit_ctx* c, double* r, cudaStream_t s, double* prod = nullptr) {
   int bs = 128;
-  visc_jump_kernel<D><<<(c->n_pairs + bs - 1) / bs, bs, 0, s>>>(r, c->b.fv, c->b.face_pairs, c->n_pairs, c->b.nu,
-                                                                 c->b.J);
+  int nb = (c->n_pairs + bs - 1) / bs;
+  visc_jump_kernel<D><<<nb, bs, 0, s>>>(r, c->b.fv, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.wslot,
+                                        prod);
   c->launches += 1;
+  return prod ? nb : 0;
 }
 
 }  // namespace esplit
