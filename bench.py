@@ -138,7 +138,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-# algorithmic work per launch (stated in the design doc)
+# algorithmic work per launch
 # ---------------------------------------------------------------------------------------------
 def algorithmic_flops(group, n_e, n_p, d, n_pairs):
     nc = d + 2

@@ -56,7 +56,7 @@ def test_reference_arm_json_line():
 
 
 def test_reference_arm_two_ranks():
-    """Launched as the driver launches the N-GPU arm: rank 0 prints, rank 1 exits 0."""
+    """Launched as torch.distributed.run launches the N-GPU arm: rank 0 prints, rank 1 exits 0."""
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
            "127.0.0.1", "--master-port", "29533", os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps",
            "1", "--warmup", "0", "--p", "1", "--N", "4", "--gpus", "2"]

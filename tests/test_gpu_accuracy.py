@@ -11,8 +11,8 @@ the printed ones and the 60 -> 80 rates within 0.5 of the printed rates; for
 every p the rates lie in the band [p - 0.2, p + 1.2] the paper reports
 (rates between p and p + 1) and dissipation lowers the error.  Meshes 60^2 x 2
 and 80^2 x 2 (the smallest two of the table) keep the run to about two
-minutes; the full table (observed: p = 3, 4 errors 0.65-0.9 of the printed
-ones at every mesh) is recorded in the design doc."""
+minutes; over the full table (N = 60..120) the p = 3, 4 errors were
+observed at 0.65-0.9 of the printed ones at every mesh."""
 import os
 
 import numpy as np
