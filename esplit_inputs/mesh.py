@@ -94,10 +94,16 @@ def periodic_tri_mesh(op: RefOperator, N: int, L: float = 10.0, amp: float = 0.0
     s = np.sin(2.0 * np.pi * (I % (2 * N)) / (2 * N)) * np.sin(2.0 * np.pi * (Jx % (2 * N)) / (2 * N))
     disp = amp * s
     G = np.stack([I * (h / 2) + disp, Jx * (h / 2) + disp], axis=1)  # (n_e, 2, 6)
+    # the map's derivatives from element-local offsets (the shape-function
+    # derivatives sum to zero): lattice differences are exact and displacement
+    # differences carry rounding of the displacement's size, where G itself is
+    # rounded at the size of the domain
+    dG = np.stack([(I - I[:, :1]) * (h / 2) + (disp - disp[:, :1]),
+                   (Jx - Jx[:, :1]) * (h / 2) + (disp - disp[:, :1])], axis=1)
 
     Nsh, dN = _quad_shape(op.xi)
     x = np.einsum("pa,eia->eip", Nsh, G)                     # (n_e, 2, n_p)
-    Jm = np.einsum("jpa,eia->eijp", dN, G)                   # dx_i/dxi_j  (n_e, 2, 2, n_p)
+    Jm = np.einsum("jpa,eia->eijp", dN, dG)                  # dx_i/dxi_j  (n_e, 2, 2, n_p)
     det = Jm[:, 0, 0] * Jm[:, 1, 1] - Jm[:, 0, 1] * Jm[:, 1, 0]
     Lam = np.empty_like(Jm)
     Lam[:, 0, 0] = Jm[:, 1, 1]
@@ -181,10 +187,13 @@ def periodic_tri_mesh_rect(op: RefOperator, Nx: int, Ny: int, origin=(0.0, -5.0)
     yw = origin[1] + (Jx % (2 * Ny)) * (hy / 2)
     ddx, ddy = warp(xw, yw)
     G = np.stack([origin[0] + I * (hx / 2) + ddx, origin[1] + Jx * (hy / 2) + ddy], axis=1)  # (n_e, 2, 6)
+    # derivatives from element-local offsets (see periodic_tri_mesh)
+    dG = np.stack([(I - I[:, :1]) * (hx / 2) + (ddx - ddx[:, :1]),
+                   (Jx - Jx[:, :1]) * (hy / 2) + (ddy - ddy[:, :1])], axis=1)
 
     Nsh, dN = _quad_shape(op.xi)
     x = np.einsum("pa,eia->eip", Nsh, G)
-    Jm = np.einsum("jpa,eia->eijp", dN, G)
+    Jm = np.einsum("jpa,eia->eijp", dN, dG)
     det = Jm[:, 0, 0] * Jm[:, 1, 1] - Jm[:, 0, 1] * Jm[:, 1, 0]
     Lam = np.empty_like(Jm)
     Lam[:, 0, 0] = Jm[:, 1, 1]
@@ -307,9 +316,11 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
         disp = warp(origin + wrap * (h / 2))
     G = origin + G_idx * (h / 2) + disp                        # (e, 10, 3)
     G = np.transpose(G, (0, 2, 1))                             # (e, 3, 10)
+    # derivatives from element-local offsets (see periodic_tri_mesh)
+    dG = np.transpose((G_idx - G_idx[:, :1]) * (h / 2) + (disp - disp[:, :1]), (0, 2, 1))
     Nsh, dN = _quad_tet_shape(op.xi)
     x = np.einsum("pa,eia->eip", Nsh, G)
-    Jm = np.einsum("jpa,eia->eijp", dN, G)                     # dx_i/dxi_j (e, 3, 3, n_p)
+    Jm = np.einsum("jpa,eia->eijp", dN, dG)                    # dx_i/dxi_j (e, 3, 3, n_p)
     Jt = np.transpose(Jm, (0, 3, 1, 2))                        # (e, n_p, 3, 3)
     det = np.linalg.det(Jt)
     adj = np.linalg.inv(Jt) * det[..., None, None]             # adj[j][i] = J dxi_j/dx_i
