@@ -268,3 +268,19 @@ def test_manufactured_grids_and_state():
     assert np.all(m3.J > 0) and abs(np.sum(m3.J * op3.H[None]) - 8.0) < 1e-11
     u3 = states.manufactured_state(m3, 0.0)
     assert np.allclose(u3[:, 4], u3[:, 0] ** 2, rtol=1e-14)
+
+
+def test_metric_identity_relative_at_full_size():
+    """On the 128^2 x 2 mesh of [0, 10]^2 the discrete metric identity
+    sum_j D_xi_j Lam_ij = 0 holds to rounding relative to its own terms: the
+    metric terms come from element-local offsets of the geometry nodes, not
+    from positions of the size of the domain, whose rounding (~eps L) would be
+    ~L/h times larger relative to an element (~1e-13 here), and would grow the
+    freestream residual as N^2."""
+    op = tri_operator(3)
+    m = periodic_tri_mesh(op, 128, 10.0, 0.05)
+    el = np.random.default_rng(3).choice(m.n_e, 200, replace=False)
+    for i in range(2):
+        s = sum(np.einsum("mk,ek->em", op.D[j], m.Lam[el, i, j]) for j in range(2))
+        sc = sum(np.einsum("mk,ek->em", np.abs(op.D[j]), np.abs(m.Lam[el, i, j])) for j in range(2))
+        assert (np.abs(s) / sc).max() < 2e-14
