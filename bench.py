@@ -513,6 +513,17 @@ def main():
                     "avg_launch_ms": dom_ms, "launches": groups[dom][1], "units_per_launch": per_launch_units,
                     "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (152 SMs x 4 FLOP/clk x "
                                    "2.07 GHz); FP64 pipe, not the bf16 tensor peak"}
+    # every kernel group with an algorithmic flop count, against the same FP64 peak
+    roofline_by_kernel = {}
+    for g, (ms_tot, nl) in groups.items():
+        fg = algorithmic_flops(g, n_e, n_p, d, solver_pairs(mesh, op))
+        if fg is None:
+            continue
+        ms = ms_tot / nl
+        ach = fg / (ms * 1e-3) / 1e12
+        roofline_by_kernel[g] = {"avg_launch_ms": ms, "launches": nl, "achieved_tflops": ach,
+                                 "frac_fp64_peak": ach / (FP64_PEAK_NOMINAL / 1e12) if args.precision == "fp64"
+                                 else None}
     # ---------------- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     u_host = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
     u_host.copy_(torch.as_tensor(u0))
@@ -531,6 +542,7 @@ def main():
     e2e = {"value": ws * args.steps * 4 * dof / e2e_tot, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
     extras = {"kernel_ms_timed_region": {g: {"ms_total": v[0], "launches": v[1]} for g, v in groups.items()},
+              "roofline_by_kernel": roofline_by_kernel,
               "g_range": [min(gs), max(gs)], "wall_s_timed": t_wall, "dt": dt}
     if rank == 0 and not args.no_sweep:
         extras["residual_sweep"] = residual_sweep(es, device, flush)

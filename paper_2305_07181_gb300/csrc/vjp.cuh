@@ -10,43 +10,20 @@
 //   grad_m   = sum_i (df_i/du)^T fbar_i + (dw/du)^T wbar
 //              - 1/(beta+1) d/du [cot_m . sum_i A~_i(u) g_i]|_(g_i = (D_i w)_m)
 //              + facet part (dG/du)^T (-cot_km/H_km + cot_vn/H_vn).
-// The facet Jacobians are exact, from the same physics templates run on
-// forward-mode dual numbers (dual.cuh); the volume's pointwise part needs one
-// dual direction (see split_vjp_kernel); the contractions are transposed
-// applications of the stored per-element operators.  Float64 throughout.
+// The pointwise derivatives are exact: the facet pair computation (averages,
+// two-point flux, dissipation) by a hand-written reverse sweep, each side's
+// nodal chain on four-direction forward dual numbers (dual.cuh), the volume's
+// pointwise part with one dual direction (see split_vjp_kernel); the
+// contractions are transposed applications of the stored per-element
+// operators.  Float64 throughout.
 // Included by kernels.cu (one device translation unit: the constant-memory
 // operator tables are shared).
 #pragma once
 
 namespace esplit {
 
-// facet pairs: each thread writes the facet part of grad at its two slots
-// x (derivatives with respect to one side's four state components) placed at
-// derivative slots [off, off + N) of an M-direction dual
-template <int M, int N>
-__device__ __forceinline__ Dual<M> embed(const Dual<N>& x, int off) {
-  Dual<M> r(x.v);
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[off + i] = x.d[i];
-  return r;
-}
-
-template <int D, int N, int M>
-__device__ __forceinline__ void embed_znode(const ZNode<Dual<N>, D>& a, int off, ZNode<Dual<M>, D>& b) {
-  b.q = embed<M>(a.q, off);
-  b.p = embed<M>(a.p, off);
-  b.P1 = embed<M>(a.P1, off);
-  b.P2 = embed<M>(a.P2, off);
-  b.v2 = embed<M>(a.v2, off);
-  b.iq = embed<M>(a.iq, off);
-  b.ip = embed<M>(a.ip, off);
-#pragma unroll
-  for (int i = 0; i < D; ++i) b.V[i] = embed<M>(a.V[i], off);
-}
-
 // X^ |Lambda_n| S^ X^T dw of Eq. (69), as diss_apply, one column of X^ at a
-// time (the eight-direction dual version would otherwise hold all n_c^2
-// entries); n and dw may be plain doubles (no derivative parts).
+// time; n and dw may be plain doubles (no derivative parts).
 template <typename T, typename TN, typename TW, int D, typename C>
 __device__ __forceinline__ void diss_apply_cols(const PairAvg<T, D>& a, const C& c, const TN* n, const TW* dw,
                                                 T* out) {
@@ -110,143 +87,270 @@ __device__ __forceinline__ void diss_apply_cols(const PairAvg<T, D>& a, const C&
   }
 }
 
-// Derivative parts (N directions) of s = gb . X^|L|S^X^T dw with gb, dw fixed,
-// the hat state on the duals.  With r_k the columns of X^ and l_k = |lambda_k| S_k,
-// s = sum_k l_k (r_k . gb)(r_k . dw), so
-//   ds = sum_k [(r_k.gb)(r_k.dw) dl_k + l_k ((r_k.dw) gb + (r_k.gb) dw) . dr_k]:
-// only the columns and weights are formed on the duals.
-template <int N, int D, typename C>
-__device__ __forceinline__ void diss_scalar_grad(const PairAvg<Dual<N>, D>& a, const C& c, const double* n,
-                                                 const double* gb, const double* dw, double* ds) {
-  using T = Dual<N>;
-  constexpr int NC = D + 2;
-  T rho_h = a.z1a / (a.A1 * a.E1);
-  T iz = T(1.0) / a.z1a;
-  T Vh[D];
-  T vh2 = T(0.0), vn = T(0.0);
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    Vh[i] = a.qV[i] * iz;
-    vh2 = vh2 + Vh[i] * Vh[i];
-    vn = vn + Vh[i] * n[i];
+__device__ __forceinline__ double sgn0(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+// reverse of exp_avg (Eq. (47)) at the values: E = (ar - br)/(r (a - b)) or
+// ar ia g(eps), eps = (b - a) ia; adds the adjoints of a, b, ar, br, ia for Eb
+__device__ __forceinline__ void exp_avg_rev(double a, double b, double ar, double br, double r, double ia,
+                                            const double* coef, double Eb, double& ab, double& bb, double& arb,
+                                            double& brb, double& iab) {
+  const double eps = (b - a) * ia;
+  if (fabs(eps) >= ExpAvgCfg<double>::EPS_SWITCH) {
+    const double q = 1.0 / (r * (a - b));
+    const double E = (ar - br) * q;
+    arb += Eb * q;
+    brb -= Eb * q;
+    ab -= Eb * E / (a - b);
+    bb += Eb * E / (a - b);
+    return;
   }
-  T p_h = a.pa;
-  T theta = rho_h / (p_h * a.A1 * a.E1);
-  T eta = T(1.0) / (a.z1a * a.E2 * a.E1);
-  T ah = t_sqrt(c.gam * p_h / rho_h);
-  T Hh = ah * ah * c.inv_gm1 + 0.5 * vh2;
+  double sv = coef[ExpAvgCfg<double>::NTERMS - 1], dv = 0.0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) ds[i] = 0.0;
-#pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    T col[NC];
-    T ls;
-    if (k == 0 || k == NC - 1) {
-      const double sg = (k == 0) ? -1.0 : 1.0;
-      col[0] = T(1.0);
-#pragma unroll
-      for (int i = 0; i < D; ++i) col[1 + i] = Vh[i] + sg * (ah * n[i]);
-      col[NC - 1] = Hh + sg * (ah * vn);
-      ls = t_abs(vn + sg * ah) * (c.s_ac * theta);
-    } else if (k == 1) {
-      col[0] = T(1.0);
-#pragma unroll
-      for (int i = 0; i < D; ++i) col[1 + i] = Vh[i];
-      col[NC - 1] = 0.5 * vh2;
-      ls = t_abs(vn) * (c.s_en * theta);
-    } else {
-#pragma unroll
-      for (int r = 0; r < NC; ++r) col[r] = T(0.0);
-      if (k == 2) {
-        col[1] = T(n[1]);
-        col[2] = T(-n[0]);
-        col[NC - 1] = Vh[0] * n[1] - Vh[1] * n[0];
-      } else {
-        col[1] = T(-n[D - 1]);
-        col[3] = T(n[0]);
-        col[NC - 1] = Vh[D - 1] * n[0] - Vh[0] * n[D - 1];
-      }
-      ls = t_abs(vn) * eta;
-    }
-    double al = 0.0, be = 0.0;
-#pragma unroll
-    for (int r = 0; r < NC; ++r) {
-      al += col[r].v * gb[r];
-      be += col[r].v * dw[r];
-    }
-    const double ab = al * be;
-#pragma unroll
-    for (int i = 0; i < N; ++i) ds[i] += ab * ls.d[i];
-#pragma unroll
-    for (int r = 0; r < NC; ++r) {
-      const double w = ls.v * (be * gb[r] + al * dw[r]);
-#pragma unroll
-      for (int i = 0; i < N; ++i) ds[i] += w * col[r].d[i];
-    }
+  for (int k = ExpAvgCfg<double>::NTERMS - 2; k >= 0; --k) {
+    dv = dv * eps + sv;
+    sv = sv * eps + coef[k];
   }
+  // E = ar ia sv(eps)
+  arb += Eb * ia * sv;
+  const double epsb = Eb * ar * ia * dv;
+  iab += Eb * ar * sv + epsb * (b - a);
+  bb += epsb * ia;
+  ab -= epsb * ia;
 }
 
-// Derivative parts of s = gb . sum_i nu_i F*_i (Eq. (48), as sy_flux_dir):
-// F = [mn, mn {V} + nu {p}, mn h], mn = nu.{z_1 V}/({z_1^a}{z_nc^b}_e),
-// h = gam/(gam-1) {.}{.}_e + ke, so s = mn (gb_0 + gb_m.{V} + gb_e h) + {p} gb_m.nu.
-template <int N, int D, typename C>
-__device__ __forceinline__ void flux_scalar_grad(const PairAvg<Dual<N>, D>& a, const C& c, const double* nu,
-                                                 const double* gb, double* ds) {
-  using T = Dual<N>;
+// Adjoints of the nodal quantities of both sides (ZNode fields) for
+//   s = gb . [sum_i nu_i F*_i(k, v) + (|nu|/2) X^|L|S^X^T dw]   (dw held fixed),
+// the reverse sweep of pair_avg, sy_flux_dir and the dissipation's hat state
+// and columns in plain float64.  With r_k the columns of X^ and l_k =
+// |lambda_k| S_k, the dissipation part is (|nu|/2) sum_k l_k (r_k.gb)(r_k.dw):
+// column adjoints (|nu|/2) l_k ((r_k.dw) gb + (r_k.gb) dw), weight adjoints
+// (|nu|/2) (r_k.gb)(r_k.dw).
+template <int D, typename C>
+__device__ __forceinline__ void pair_reverse(const ZNode<double, D>& k, const ZNode<double, D>& v, const C& c,
+                                             const double* nu, int dissipation, double b, const double* n,
+                                             const double* gb, const double* dw, ZNode<double, D>& kb,
+                                             ZNode<double, D>& vb) {
   constexpr int NC = D + 2;
-  T inv_den = T(1.0) / (a.A1 * a.E1);
-  T mq = T(0.0);
+  // ---- forward (values)
+  PairAvg<double, D> a;
+  pair_avg<double, D>(k, v, c, a);
+  double A1b = 0.0, E1b = 0.0, A2b = 0.0, E2b = 0.0, z1ab = 0.0, pab = 0.0, keb = 0.0;
+  double qVb[D], Vab[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) mq = mq + nu[i] * a.qV[i];
-  T mn = mq * inv_den;
-  T h = c.gam_gm1 * (a.A2 * a.E2) + a.ke;
-  double gmv = gb[0] + gb[NC - 1] * h.v, gmn = 0.0;
+  for (int i = 0; i < D; ++i) qVb[i] = Vab[i] = 0.0;
+  // ---- two-point flux: s_f = mn C + pa (gb_m . nu)
+  {
+    const double den = a.A1 * a.E1, iden = 1.0 / den;
+    double mq = 0.0;
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    gmv += gb[1 + j] * a.Va[j].v;
-    gmn += gb[1 + j] * nu[j];
+    for (int i = 0; i < D; ++i) mq += nu[i] * a.qV[i];
+    const double mn = mq * iden;
+    const double h = c.gam_gm1 * a.A2 * a.E2 + a.ke;
+    double Cc = gb[0] + gb[NC - 1] * h, gmn = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      Cc += gb[1 + j] * a.Va[j];
+      gmn += gb[1 + j] * nu[j];
+    }
+    const double mnb = Cc, hb = mn * gb[NC - 1];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Vab[j] += mn * gb[1 + j];
+    pab += gmn;
+    const double mqb = mnb * iden, idenb = mnb * mq;
+#pragma unroll
+    for (int i = 0; i < D; ++i) qVb[i] += mqb * nu[i];
+    A1b -= idenb * iden * iden * a.E1;
+    E1b -= idenb * iden * iden * a.A1;
+    A2b += hb * c.gam_gm1 * a.E2;
+    E2b += hb * c.gam_gm1 * a.A2;
+    keb += hb;
   }
-  // ds = gmv dmn + mn (gb_m . d{V} + gb_e dh) + gmn d{p}
+  // ---- dissipation's averages part
+  if (dissipation) {
+    const double rho_h = a.z1a / (a.A1 * a.E1);
+    const double iz = 1.0 / a.z1a;
+    double Vh[D], vh2 = 0.0, vn = 0.0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    double t = gb[NC - 1] * h.d[i];
+    for (int i = 0; i < D; ++i) {
+      Vh[i] = a.qV[i] * iz;
+      vh2 += Vh[i] * Vh[i];
+      vn += Vh[i] * n[i];
+    }
+    const double p_h = a.pa;
+    const double theta = rho_h / (p_h * a.A1 * a.E1);
+    const double eta = 1.0 / (a.z1a * a.E2 * a.E1);
+    const double ah = sqrt(c.gam * p_h / rho_h);
+    const double Hh = ah * ah * c.inv_gm1 + 0.5 * vh2;
+    double Vhb[D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) t += gb[1 + j] * a.Va[j].d[i];
-    ds[i] = gmv * mn.d[i] + mn.v * t + gmn * a.pa.d[i];
+    for (int i = 0; i < D; ++i) Vhb[i] = 0.0;
+    double vnb = 0.0, ahb = 0.0, Hhb = 0.0, vh2b = 0.0, thetab = 0.0, etab = 0.0;
+    const double hb2 = 0.5 * b;
+#pragma unroll
+    for (int kk = 0; kk < NC; ++kk) {
+      double col[NC];
+      double l;
+      const bool ac = (kk == 0 || kk == NC - 1);
+      const double sg = (kk == 0) ? -1.0 : 1.0;
+      if (ac) {
+        col[0] = 1.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) col[1 + i] = Vh[i] + sg * ah * n[i];
+        col[NC - 1] = Hh + sg * ah * vn;
+        l = fabs(vn + sg * ah) * c.s_ac * theta;
+      } else if (kk == 1) {
+        col[0] = 1.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) col[1 + i] = Vh[i];
+        col[NC - 1] = 0.5 * vh2;
+        l = fabs(vn) * c.s_en * theta;
+      } else {
+#pragma unroll
+        for (int r = 0; r < NC; ++r) col[r] = 0.0;
+        if (kk == 2) {
+          col[1] = n[1];
+          col[2] = -n[0];
+          col[NC - 1] = Vh[0] * n[1] - Vh[1] * n[0];
+        } else {
+          col[1] = -n[D - 1];
+          col[3] = n[0];
+          col[NC - 1] = Vh[D - 1] * n[0] - Vh[0] * n[D - 1];
+        }
+        l = fabs(vn) * eta;
+      }
+      double al = 0.0, be = 0.0;
+#pragma unroll
+      for (int r = 0; r < NC; ++r) {
+        al += col[r] * gb[r];
+        be += col[r] * dw[r];
+      }
+      const double lb = hb2 * al * be;
+      double cb[NC];
+#pragma unroll
+      for (int r = 0; r < NC; ++r) cb[r] = hb2 * l * (be * gb[r] + al * dw[r]);
+      if (ac) {
+        double cn = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          Vhb[i] += cb[1 + i];
+          cn += cb[1 + i] * n[i];
+        }
+        ahb += sg * cn + sg * cb[NC - 1] * vn;
+        Hhb += cb[NC - 1];
+        vnb += sg * cb[NC - 1] * ah;
+        const double t = vn + sg * ah;
+        const double w = lb * c.s_ac;
+        vnb += w * sgn0(t) * theta;
+        ahb += w * sgn0(t) * sg * theta;
+        thetab += w * fabs(t);
+      } else if (kk == 1) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) Vhb[i] += cb[1 + i];
+        vh2b += 0.5 * cb[NC - 1];
+        vnb += lb * sgn0(vn) * c.s_en * theta;
+        thetab += lb * fabs(vn) * c.s_en;
+      } else {
+        if (kk == 2) {
+          Vhb[0] += cb[NC - 1] * n[1];
+          Vhb[1] -= cb[NC - 1] * n[0];
+        } else {
+          Vhb[D - 1] += cb[NC - 1] * n[0];
+          Vhb[0] -= cb[NC - 1] * n[D - 1];
+        }
+        vnb += lb * sgn0(vn) * eta;
+        etab += lb * fabs(vn);
+      }
+    }
+    // hat state back to the averages
+    ahb += Hhb * 2.0 * ah * c.inv_gm1;
+    vh2b += 0.5 * Hhb;
+#pragma unroll
+    for (int i = 0; i < D; ++i) Vhb[i] += 2.0 * vh2b * Vh[i] + vnb * n[i];
+    double p_hb = ahb * ah / (2.0 * p_h);
+    double rho_hb = -ahb * ah / (2.0 * rho_h);
+    z1ab -= etab * eta / a.z1a;
+    E2b -= etab * eta / a.E2;
+    E1b -= etab * eta / a.E1;
+    rho_hb += thetab * theta / rho_h;
+    p_hb -= thetab * theta / p_h;
+    A1b -= thetab * theta / a.A1;
+    E1b -= thetab * theta / a.E1;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      qVb[i] += Vhb[i] * iz;
+      z1ab -= Vhb[i] * Vh[i] * iz;
+    }
+    z1ab += rho_hb * rho_h / a.z1a;
+    A1b -= rho_hb * rho_h / a.A1;
+    E1b -= rho_hb * rho_h / a.E1;
+    pab += p_hb;
   }
+  // ---- pair averages back to the nodal quantities
+  kb.q = kb.p = kb.P1 = kb.P2 = kb.v2 = kb.iq = kb.ip = 0.0;
+  vb.q = vb.p = vb.P1 = vb.P2 = vb.v2 = vb.iq = vb.ip = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) kb.V[i] = vb.V[i] = 0.0;
+  kb.P1 += 0.5 * A1b;
+  vb.P1 += 0.5 * A1b;
+  kb.P2 += 0.5 * A2b;
+  vb.P2 += 0.5 * A2b;
+  kb.q += 0.5 * z1ab;
+  vb.q += 0.5 * z1ab;
+  kb.p += 0.5 * pab;
+  vb.p += 0.5 * pab;
+  kb.v2 -= 0.25 * keb;
+  vb.v2 -= 0.25 * keb;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const double vab = Vab[i] + 2.0 * keb * a.Va[i];
+    kb.V[i] += 0.5 * vab + 0.5 * qVb[i] * k.q;
+    vb.V[i] += 0.5 * vab + 0.5 * qVb[i] * v.q;
+    kb.q += 0.5 * qVb[i] * k.V[i];
+    vb.q += 0.5 * qVb[i] * v.V[i];
+  }
+  exp_avg_rev(k.p, v.p, k.P2, v.P2, c.r2, k.ip, c.ser2, E1b, kb.p, vb.p, kb.P2, vb.P2, kb.ip);
+  exp_avg_rev(k.q, v.q, k.P1, v.P1, c.r1, k.iq, c.ser1, E2b, kb.q, vb.q, kb.P1, vb.P1, kb.iq);
 }
 
 template <int D, int N>
-__device__ __forceinline__ PairAvg<double, D> strip_avg(const PairAvg<Dual<N>, D>& a) {
-  PairAvg<double, D> b;
-  b.A1 = a.A1.v;
-  b.E1 = a.E1.v;
-  b.A2 = a.A2.v;
-  b.E2 = a.E2.v;
-  b.z1a = a.z1a.v;
-  b.pa = a.pa.v;
-  b.ke = a.ke.v;
+__device__ __forceinline__ ZNode<double, D> znode_values(const ZNode<Dual<N>, D>& z) {
+  ZNode<double, D> r;
+  r.q = z.q.v;
+  r.p = z.p.v;
+  r.P1 = z.P1.v;
+  r.P2 = z.P2.v;
+  r.v2 = z.v2.v;
+  r.iq = z.iq.v;
+  r.ip = z.ip.v;
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    b.qV[i] = a.qV[i].v;
-    b.Va[i] = a.Va[i].v;
+  for (int i = 0; i < D; ++i) r.V[i] = z.V[i].v;
+  return r;
+}
+
+// g[cc] += adjoints of the nodal quantities times their state derivatives
+template <int D, int N>
+__device__ __forceinline__ void contract_znode(const ZNode<Dual<N>, D>& z, const ZNode<double, D>& zb, double* g) {
+#pragma unroll
+  for (int cc = 0; cc < N; ++cc) {
+    double t = zb.q * z.q.d[cc] + zb.p * z.p.d[cc] + zb.P1 * z.P1.d[cc] + zb.P2 * z.P2.d[cc] +
+               zb.v2 * z.v2.d[cc] + zb.iq * z.iq.d[cc] + zb.ip * z.ip.d[cc];
+#pragma unroll
+    for (int i = 0; i < D; ++i) t += zb.V[i] * z.V[i].d[cc];
+    g[cc] += t;
   }
-  return b;
 }
 
 // facet pairs: each thread writes the facet part of grad at its two slots.
 // Each side's nodal chain (logarithms, exponentials, divisions) depends on its
-// own four state components only: it runs on four-direction duals, and the
-// results enter the eight-direction pair computation (averages, two-point
-// flux, dissipation) at that side's slots.
+// own four state components only: it runs on four-direction duals; the pair
+// computation (averages, two-point flux, dissipation) is reversed at the
+// values (pair_reverse) and its adjoints contracted with those derivatives.
 template <int D>
 __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__ u, const double* __restrict__ cot,
                                                       const int2* __restrict__ fp, int n_pairs,
                                                       const double* __restrict__ nu, const double* __restrict__ J,
                                                       double* __restrict__ gsat, Phys<double> c, int dissipation) {
   constexpr int NC = D + 2;
-  constexpr int N2 = 2 * NC;
-  using T = Dual<N2>;
   using TS = Dual<NC>;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_pairs) return;
@@ -255,34 +359,22 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
   int k = pr.x / NS, s = pr.x - k * NS;
   int v = pr.y / NS, s2 = pr.y - v * NS;
   int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
-  ZNode<T, D> zk, zv;
-  TS Wk[NC], Wv[NC];  // each side's entropy variables with their own Jacobian
-  {
-    TS uk[NC], uv[NC];
+  // each side's nodal chain on four-direction duals (its own state only)
+  TS uk[NC], uv[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      uk[q] = TS(__ldg(&u[((size_t)k * NC + q) * NP + m]));
-      uv[q] = TS(__ldg(&u[((size_t)v * NC + q) * NP + n]));
-      uk[q].d[q] = 1.0;
-      uv[q].d[q] = 1.0;
-    }
-    Node<TS, D> nk, nv;
-    node_from_u<TS, D>(uk, c, nk);
-    node_from_u<TS, D>(uv, c, nv);
-    ZNode<TS, D> sk, sv;
-    znode<TS, D>(nk, c, sk);
-    znode<TS, D>(nv, c, sv);
-    znode_recips<TS, D>(sk);
-    embed_znode<D>(sk, 0, zk);
-    embed_znode<D>(sv, NC, zv);
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      Wk[q] = nk.W[q];
-      Wv[q] = nv.W[q];
-    }
+  for (int q = 0; q < NC; ++q) {
+    uk[q] = TS(__ldg(&u[((size_t)k * NC + q) * NP + m]));
+    uv[q] = TS(__ldg(&u[((size_t)v * NC + q) * NP + n]));
+    uk[q].d[q] = 1.0;
+    uv[q].d[q] = 1.0;
   }
-  PairAvg<T, D> a;
-  pair_avg<T, D>(zk, zv, c, a);
+  Node<TS, D> nk, nv;
+  node_from_u<TS, D>(uk, c, nk);
+  node_from_u<TS, D>(uv, c, nv);
+  ZNode<TS, D> sk, sv;
+  znode<TS, D>(nk, c, sk);
+  znode<TS, D>(nv, c, sv);
+  znode_recips<TS, D>(sk);
   double nud[D];
   double b2 = 0.0;
 #pragma unroll
@@ -290,43 +382,41 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
     nud[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
     b2 += nud[i] * nud[i];
   }
+  const double b = sqrt(b2);
+  double nh[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) nh[i] = nud[i] / b;
   double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
   double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
-  double gb[NC];
+  double gb[NC], dw[NC];
 #pragma unroll
-  for (int q = 0; q < NC; ++q)
+  for (int q = 0; q < NC; ++q) {
     gb[q] = -__ldg(&cot[((size_t)k * NC + q) * NP + m]) * ihk + __ldg(&cot[((size_t)v * NC + q) * NP + n]) * ihv;
-  // gb . G(u_k, u_v): the two-point flux, and with dissipation
-  //   d[gb . M(a) (w_k - w_v)] = gb . (dM) dw + (M gb) . (dw_k - dw_v)   (M symmetric)
-  double ds[N2];
-  flux_scalar_grad<N2, D>(a, c, nud, gb, ds);
+    dw[q] = nk.W[q].v - nv.W[q].v;
+  }
+  // d[gb . G(u_k, u_v)]: the pair computation by a reverse sweep at the
+  // values, then each side's nodal Jacobian; with dissipation also
+  // (M gb) . (dw_k - dw_v), M = X^|L|S^X^T symmetric
+  const ZNode<double, D> zk = znode_values<D>(sk), zv = znode_values<D>(sv);
+  ZNode<double, D> kb, vb;
+  pair_reverse<D>(zk, zv, c, nud, dissipation, b, nh, gb, dw, kb, vb);
   double gk[NC], gv[NC];
 #pragma unroll
-  for (int cc = 0; cc < NC; ++cc) {
-    gk[cc] = ds[cc];
-    gv[cc] = ds[NC + cc];
-  }
+  for (int cc = 0; cc < NC; ++cc) gk[cc] = gv[cc] = 0.0;
+  contract_znode<D>(sk, kb, gk);
+  contract_znode<D>(sv, vb, gv);
   if (dissipation) {
-    const double b = sqrt(b2);
-    double nh[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) nh[i] = nud[i] / b;
-    double dw[NC], Mgb[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) dw[q] = Wk[q].v - Wv[q].v;
-    diss_scalar_grad<N2, D>(a, c, nh, gb, dw, ds);
-    const PairAvg<double, D> ar = strip_avg<D>(a);
+    PairAvg<double, D> ar;
+    pair_avg<double, D>(zk, zv, c, ar);
+    double Mgb[NC];
     diss_apply_cols<double, double, double, D>(ar, c, nh, gb, Mgb);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) {
-      gk[cc] += 0.5 * b * ds[cc];
-      gv[cc] += 0.5 * b * ds[NC + cc];
+    for (int cc = 0; cc < NC; ++cc)
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        gk[cc] += 0.5 * b * Mgb[q] * Wk[q].d[cc];
-        gv[cc] -= 0.5 * b * Mgb[q] * Wv[q].d[cc];
+        gk[cc] += 0.5 * b * Mgb[q] * nk.W[q].d[cc];
+        gv[cc] -= 0.5 * b * Mgb[q] * nv.W[q].d[cc];
       }
-    }
   }
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
