@@ -521,14 +521,36 @@ __global__ void __launch_bounds__(EB * NP) split_vjp_kernel(const double* __rest
     using T1 = Dual<1>;
     double du[NC];
     dU_dW_apply<double, D>(nd, jp, c, vv, du);
-    T1 ud[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      ud[q] = T1(uu[q]);
-      ud[q].d[0] = du[q];
-    }
+    // the nodal quantities A~_i depends on, with their tangent along du in
+    // closed form (no logarithm or exponential on the duals):
+    //   drho = du_0, dV = (du_m - V drho)/rho, dv2 = 2 V.dV, de = du_E,
+    //   dp = (gam-1)(de - (drho v2 + rho dv2)/2), dq = q (a_q drho/rho + b_q dp/p)
     Node<T1, D> n1;
-    node_from_u<T1, D>(ud, c, n1);
+    {
+      const double drho = du[0];
+      double dv2 = 0.0;
+      n1.rho = T1(nd.rho);
+      n1.rho.d[0] = drho;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const double dVj = (du[1 + j] - nd.V[j] * drho) * nd.ir;
+        n1.V[j] = T1(nd.V[j]);
+        n1.V[j].d[0] = dVj;
+        dv2 += 2.0 * nd.V[j] * dVj;
+      }
+      const double de = du[NC - 1];
+      const double dp = c.gm1 * (de - 0.5 * (drho * nd.v2 + nd.rho * dv2));
+      n1.v2 = T1(nd.v2);
+      n1.v2.d[0] = dv2;
+      n1.e = T1(nd.e);
+      n1.e.d[0] = de;
+      n1.p = T1(nd.p);
+      n1.p.d[0] = dp;
+      n1.ir = T1(nd.ir);
+      n1.ir.d[0] = -nd.ir * nd.ir * drho;
+      n1.q = T1(nd.q);
+      n1.q.d[0] = nd.q * (c.a_q * drho * nd.ir + c.b_q * dp * (jp.itheta * nd.ir));
+    }
     const JvpPrep<T1> j1 = jvp_prep<T1, D>(n1, c);
 #pragma unroll
     for (int i = 0; i < D; ++i) {
