@@ -10,10 +10,9 @@
 //   grad_m   = sum_i (df_i/du)^T fbar_i + (dw/du)^T wbar
 //              - 1/(beta+1) d/du [cot_m . sum_i A~_i(u) g_i]|_(g_i = (D_i w)_m)
 //              + facet part (dG/du)^T (-cot_km/H_km + cot_vn/H_vn).
-// The pointwise derivatives are exact: the facet pair computation (averages,
-// two-point flux, dissipation) by a hand-written reverse sweep, each side's
-// nodal chain on four-direction forward dual numbers (dual.cuh), the volume's
-// pointwise part with one dual direction (see split_vjp_kernel); the
+// The pointwise derivatives are exact: the facet terms by a hand-written
+// reverse sweep at the values, the volume's pointwise part with closed-form
+// products and one dual direction (dual.cuh; see split_vjp_kernel); the
 // contractions are transposed applications of the stored per-element
 // operators.  Float64 throughout.
 // Included by kernels.cu (one device translation unit: the constant-memory
@@ -312,46 +311,39 @@ __device__ __forceinline__ void pair_reverse(const ZNode<double, D>& k, const ZN
   exp_avg_rev(k.q, v.q, k.P1, v.P1, c.r1, k.iq, c.ser1, E2b, kb.q, vb.q, kb.P1, vb.P1, kb.iq);
 }
 
-template <int D, int N>
-__device__ __forceinline__ ZNode<double, D> znode_values(const ZNode<Dual<N>, D>& z) {
-  ZNode<double, D> r;
-  r.q = z.q.v;
-  r.p = z.p.v;
-  r.P1 = z.P1.v;
-  r.P2 = z.P2.v;
-  r.v2 = z.v2.v;
-  r.iq = z.iq.v;
-  r.ip = z.ip.v;
+// Reverse of the nodal chain u -> (q, V, p, P1, P2, v2, 1/q, 1/p) at the
+// values (ZNode adjoints zb -> state adjoint ub):
+//   V = m/rho, v2 = |V|^2, p = (gam-1)(e - rho v2/2), q = rho^a_q p^b_q,
+//   P1 = q^r1, P2 = p^r2.
+template <int D, typename C>
+__device__ __forceinline__ void node_chain_rev(const Node<double, D>& n, const ZNode<double, D>& z,
+                                               const ZNode<double, D>& zb, const C& c, double* ub) {
+  constexpr int NC = D + 2;
+  const double iq = 1.0 / n.q, ip = 1.0 / n.p;
+  const double qb = zb.q + zb.P1 * c.r1 * z.P1 * iq - zb.iq * iq * iq;
+  const double pb = zb.p + zb.P2 * c.r2 * z.P2 * ip - zb.ip * ip * ip + qb * n.q * c.b_q * ip;
+  double rhob = qb * n.q * c.a_q * n.ir - 0.5 * c.gm1 * n.v2 * pb;
+  const double v2b = zb.v2 - 0.5 * c.gm1 * n.rho * pb;
+  ub[NC - 1] = c.gm1 * pb;
 #pragma unroll
-  for (int i = 0; i < D; ++i) r.V[i] = z.V[i].v;
-  return r;
-}
-
-// g[cc] += adjoints of the nodal quantities times their state derivatives
-template <int D, int N>
-__device__ __forceinline__ void contract_znode(const ZNode<Dual<N>, D>& z, const ZNode<double, D>& zb, double* g) {
-#pragma unroll
-  for (int cc = 0; cc < N; ++cc) {
-    double t = zb.q * z.q.d[cc] + zb.p * z.p.d[cc] + zb.P1 * z.P1.d[cc] + zb.P2 * z.P2.d[cc] +
-               zb.v2 * z.v2.d[cc] + zb.iq * z.iq.d[cc] + zb.ip * z.ip.d[cc];
-#pragma unroll
-    for (int i = 0; i < D; ++i) t += zb.V[i] * z.V[i].d[cc];
-    g[cc] += t;
+  for (int j = 0; j < D; ++j) {
+    const double Vb = zb.V[j] + 2.0 * v2b * n.V[j];
+    ub[1 + j] = Vb * n.ir;
+    rhob -= Vb * n.V[j] * n.ir;
   }
+  ub[0] = rhob;
 }
 
 // facet pairs: each thread writes the facet part of grad at its two slots.
-// Each side's nodal chain (logarithms, exponentials, divisions) depends on its
-// own four state components only: it runs on four-direction duals; the pair
-// computation (averages, two-point flux, dissipation) is reversed at the
-// values (pair_reverse) and its adjoints contracted with those derivatives.
+// A reverse sweep at the values: the pair computation (averages, two-point
+// flux, dissipation; pair_reverse), then each side's nodal chain
+// (node_chain_rev); no dual numbers.
 template <int D>
 __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__ u, const double* __restrict__ cot,
                                                       const int2* __restrict__ fp, int n_pairs,
                                                       const double* __restrict__ nu, const double* __restrict__ J,
                                                       double* __restrict__ gsat, Phys<double> c, int dissipation) {
   constexpr int NC = D + 2;
-  using TS = Dual<NC>;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_pairs) return;
   const int NP = c_ref.n_p, NS = c_ref.n_slot;
@@ -359,22 +351,19 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
   int k = pr.x / NS, s = pr.x - k * NS;
   int v = pr.y / NS, s2 = pr.y - v * NS;
   int m = c_ref.slot_node[s], n = c_ref.slot_node[s2];
-  // each side's nodal chain on four-direction duals (its own state only)
-  TS uk[NC], uv[NC];
+  double uk[NC], uv[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
-    uk[q] = TS(__ldg(&u[((size_t)k * NC + q) * NP + m]));
-    uv[q] = TS(__ldg(&u[((size_t)v * NC + q) * NP + n]));
-    uk[q].d[q] = 1.0;
-    uv[q].d[q] = 1.0;
+    uk[q] = __ldg(&u[((size_t)k * NC + q) * NP + m]);
+    uv[q] = __ldg(&u[((size_t)v * NC + q) * NP + n]);
   }
-  Node<TS, D> nk, nv;
-  node_from_u<TS, D>(uk, c, nk);
-  node_from_u<TS, D>(uv, c, nv);
-  ZNode<TS, D> sk, sv;
-  znode<TS, D>(nk, c, sk);
-  znode<TS, D>(nv, c, sv);
-  znode_recips<TS, D>(sk);
+  Node<double, D> nk, nv;
+  node_from_u<double, D>(uk, c, nk);
+  node_from_u<double, D>(uv, c, nv);
+  ZNode<double, D> zk, zv;
+  znode<double, D>(nk, c, zk);
+  znode<double, D>(nv, c, zv);
+  znode_recips<double, D>(zk);
   double nud[D];
   double b2 = 0.0;
 #pragma unroll
@@ -392,31 +381,28 @@ __global__ void __launch_bounds__(64) face_vjp_kernel(const double* __restrict__
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
     gb[q] = -__ldg(&cot[((size_t)k * NC + q) * NP + m]) * ihk + __ldg(&cot[((size_t)v * NC + q) * NP + n]) * ihv;
-    dw[q] = nk.W[q].v - nv.W[q].v;
+    dw[q] = nk.W[q] - nv.W[q];
   }
-  // d[gb . G(u_k, u_v)]: the pair computation by a reverse sweep at the
-  // values, then each side's nodal Jacobian; with dissipation also
-  // (M gb) . (dw_k - dw_v), M = X^|L|S^X^T symmetric
-  const ZNode<double, D> zk = znode_values<D>(sk), zv = znode_values<D>(sv);
+  // d[gb . G(u_k, u_v)]: the pair computation reversed at the values, then
+  // each side's nodal chain; with dissipation also (M gb) . (dw_k - dw_v),
+  // M = X^|L|S^X^T symmetric, through the symmetric dW/du of each side
   ZNode<double, D> kb, vb;
   pair_reverse<D>(zk, zv, c, nud, dissipation, b, nh, gb, dw, kb, vb);
   double gk[NC], gv[NC];
-#pragma unroll
-  for (int cc = 0; cc < NC; ++cc) gk[cc] = gv[cc] = 0.0;
-  contract_znode<D>(sk, kb, gk);
-  contract_znode<D>(sv, vb, gv);
+  node_chain_rev<D>(nk, zk, kb, c, gk);
+  node_chain_rev<D>(nv, zv, vb, c, gv);
   if (dissipation) {
     PairAvg<double, D> ar;
     pair_avg<double, D>(zk, zv, c, ar);
-    double Mgb[NC];
+    double Mgb[NC], wk[NC], wv[NC];
     diss_apply_cols<double, double, double, D>(ar, c, nh, gb, Mgb);
+    dW_dU_apply<double, D>(nk, jvp_prep<double, D>(nk, c), c, Mgb, wk);
+    dW_dU_apply<double, D>(nv, jvp_prep<double, D>(nv, c), c, Mgb, wv);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc)
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        gk[cc] += 0.5 * b * Mgb[q] * nk.W[q].d[cc];
-        gv[cc] -= 0.5 * b * Mgb[q] * nv.W[q].d[cc];
-      }
+    for (int cc = 0; cc < NC; ++cc) {
+      gk[cc] += 0.5 * b * wk[cc];
+      gv[cc] -= 0.5 * b * wv[cc];
+    }
   }
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
