@@ -466,7 +466,7 @@ struct SplitSmem<double, D, NP, EB> {
 };
 
 template <typename T, int D, int NP, int EB, bool VISC, bool CACHE = false, bool ENT = false>
-__global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ? 3 : 1) split_volume_kernel(
+__global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ? 3 : ((VISC && D == 3) ? 2 : 1)) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
@@ -947,14 +947,20 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     ProfScope ps(c, PG_SPLIT, s);
     // the split kernel also forms the viscous volume terms (it has D_i w)
     const int S = c->n_e * c->n_slot;
-    if (!std::is_same<T, double>::value) {
-      // the float32 variant is sized for three blocks per SM: ask for the shared
-      // memory they need (48 KB each)
+    {
+      // the float32 variant is sized for three blocks per SM and the 3D viscous
+      // variants for two: ask for the shared memory they need
       static bool carve_set = false;
       if (!carve_set) {
-        cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, false, true>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, false, true, true>,
+        if (!std::is_same<T, double>::value) {
+          cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, false, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+          cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, false, true, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        }
+        cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(split_volume_kernel<T, D, NP, EB, true, false, true>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         carve_set = true;
       }
