@@ -466,7 +466,7 @@ struct SplitSmem<double, D, NP, EB> {
 };
 
 template <typename T, int D, int NP, int EB, bool VISC, bool CACHE = false, bool ENT = false>
-__global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ? 3 : ((VISC && D == 3) ? 2 : 1)) split_volume_kernel(
+__global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ? 4 : ((VISC && D == 3) ? 2 : 1)) split_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const float* __restrict__ opslo, const double* __restrict__ rows, const double* __restrict__ J,
     const double* __restrict__ sat, const int* __restrict__ list, int n_list, Phys<T> c, Phys<double> c64,
