@@ -948,7 +948,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     // the split kernel also forms the viscous volume terms (it has D_i w)
     const int S = c->n_e * c->n_slot;
     {
-      // the float32 variant is sized for three blocks per SM and the 3D viscous
+      // the float32 variant is sized for four blocks per SM and the 3D viscous
       // variants for two: ask for the shared memory they need
       static bool carve_set = false;
       if (!carve_set) {
