@@ -272,11 +272,12 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
 }
 
 // ---------------------------------------------------------------------------
-// facet kernel after the split volume kernel (entropy-split scheme, inviscid):
-// the same terms as face_kernel (two-point flux, dissipation, the facet part
-// nu . f / H of the volume term), with the nodal quantities of both sides read
-// from the cache the volume kernel wrote (rho, 1/rho, p, e, q, log q, log p,
-// 1/q, 1/p, V) instead of recomputed, and the result added into r.  The
+// facet kernel after the volume kernels (entropy-split or hybrid scheme,
+// inviscid, float64): the same terms as face_kernel (two-point flux,
+// dissipation, the facet part nu . f / H of the split volume term), with the
+// nodal quantities of both sides read from the cache the volume kernels wrote
+// (rho, 1/rho, p, e, q, log q, log p, 1/q, 1/p, V) instead of recomputed, and
+// the result added into r.  The
 // entropy production of the facet terms, w . H sat = w_k . (nu f_k - G) +
 // w_v . (G - nu f_v), goes to block partials after the volume kernel's.
 // ---------------------------------------------------------------------------
@@ -310,7 +311,8 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
                                                           const double* __restrict__ J,
                                                           const double* __restrict__ fc, int n_slot_total,
                                                           Phys<double> c, int dissipation,
-                                                          double* __restrict__ prod) {
+                                                          double* __restrict__ prod,
+                                                          const unsigned char* __restrict__ hflags = nullptr) {
   constexpr int NC = D + 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   double hw = 0.0;
@@ -352,9 +354,13 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
 #pragma unroll
       for (int q = 0; q < NC; ++q) G[q] += 0.5 * b * out[q];
     }
+    // the facet part nu . f / H of the split volume term, for split-form
+    // sides only (hybrid scheme: hflags 1 marks a Hadamard-form element)
     double ek[NC], ev[NC];
-    normal_flux<D>(nk, nuv, ek);
-    normal_flux<D>(nv, nuv, ev);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) ek[q] = ev[q] = 0.0;
+    if (!hflags || __ldg(&hflags[k]) == 0) normal_flux<D>(nk, nuv, ek);
+    if (!hflags || __ldg(&hflags[v]) == 0) normal_flux<D>(nv, nuv, ev);
     double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
     double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
 #pragma unroll
@@ -736,7 +742,8 @@ template <typename T, int D, int NP, int EB, int FLUX = 0>
 __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const double* __restrict__ J, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
-    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod) {
+    Phys<T> c, Phys<double> c64, int* __restrict__ status, double* __restrict__ prod,
+    double* __restrict__ fcache = nullptr, int n_slot_total = 0) {
   constexpr int NC = D + 2;
   constexpr int K = NP / 2;
   constexpr int NZ = D + 7;  // q, V[D], p, P1, P2, v2, 1/q, 1/p
@@ -770,6 +777,25 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
       ZNode<T, D> z;
       znode<T, D>(nd, c, z);
       znode_recips<T, D>(z);
+      if constexpr (sizeof(T) == sizeof(double)) {
+        // nodal quantities of the facet nodes for the cached facet kernel
+        // (hybrid scheme; the split volume kernel writes the others)
+        const int sl0 = c_ref.node_slot[m];
+        if (fcache && sl0 >= 0) {
+          const size_t S = (size_t)n_slot_total, ix = (size_t)e * NS + sl0;
+          fcache[0 * S + ix] = nd.rho;
+          fcache[1 * S + ix] = nd.ir;
+          fcache[2 * S + ix] = nd.p;
+          fcache[3 * S + ix] = nd.e;
+          fcache[4 * S + ix] = nd.q;
+          fcache[5 * S + ix] = nd.lnq;
+          fcache[6 * S + ix] = nd.lnp;
+          fcache[7 * S + ix] = z.iq;
+          fcache[8 * S + ix] = z.ip;
+#pragma unroll
+          for (int i = 0; i < D; ++i) fcache[(9 + i) * S + ix] = nd.V[i];
+        }
+      }
       zz[0 * NP + m] = z.q;
 #pragma unroll
       for (int i = 0; i < D; ++i) zz[(1 + i) * NP + m] = z.V[i];
@@ -868,7 +894,7 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       res[q] = (double)acc[q];
-      if (sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
+      if (sat && sl >= 0) res[q] += __ldg(&sat[((size_t)e * NC + q) * NS + sl]);
       r[((size_t)e * NC + q) * NP + m] = res[q];
     }
     if (prod) {
@@ -911,7 +937,11 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   // inviscid split scheme: volume kernel first (it caches the facet nodes'
   // quantities), then the facet kernel adds into r; otherwise the facet terms
   // come first and fill the sat buffer the volume kernels add
-  const bool cached = scheme == ESPLIT_SCHEME_SPLIT && !visc && sat == c->b.sat && c->b.fcache != nullptr;
+  // (the hybrid scheme too in float64: the Hadamard kernel caches its elements'
+  // facet nodes, and the facet kernel adds nu . f / H for split-form sides only)
+  const bool cached = (scheme == ESPLIT_SCHEME_SPLIT ||
+                       (scheme == ESPLIT_SCHEME_HYBRID && std::is_same<T, double>::value)) &&
+                      !visc && sat == c->b.sat && c->b.fcache != nullptr;
   if (!cached) {
     int bs = 128;
     int nb = (c->n_pairs + bs - 1) / bs;
@@ -977,7 +1007,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
           prod ? prod + np_used : nullptr, c->prm.heat_flux, c->b.nu, c->b.va, c->b.fv, c->b.ops64, nullptr, S,
           nullptr, nullptr, prod ? c->b.wslot : nullptr);
-    else if (cached && c->ent_part && c->b.node_cache) {
+    else if (cached && scheme == ESPLIT_SCHEME_SPLIT && c->ent_part && c->b.node_cache) {
       split_volume_kernel<T, D, NP, EB, false, true, true><<<nb, EB * NP, 0, s>>>(
           u, r, ops, c->b.ops32lo, c->b.rows, c->b.J, sat, lsplit, n_split, ph, ph64, c->b.status,
           prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr, c->b.fcache, S, c->ent_part,
@@ -993,16 +1023,6 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
           prod ? prod + np_used : nullptr, -1, nullptr, nullptr, nullptr, nullptr, nullptr, S);
     c->launches++;
     np_used += nb;
-  }
-  if (cached) {
-    int bs = 128;
-    int nb = (c->n_pairs + bs - 1) / bs;
-    ProfScope ps(c, PG_FACE, s);
-    face_cached_kernel<D><<<nb, bs, 0, s>>>(r, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.fcache,
-                                            c->n_e * c->n_slot, ph64, c->prm.dissipation,
-                                            prod ? prod + np_used : nullptr);
-    c->launches++;
-    if (prod) np_used += nb;
   }
   if (n_had > 0) {
     constexpr int EB = VolCfg<NP>::EB_HAD;
@@ -1021,11 +1041,29 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     if (scheme == ESPLIT_SCHEME_HADAMARD_IR)
       hadamard_volume_kernel<T, D, NP, EB, 1><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
+    else if (cached)
+      // hybrid scheme on the cached path: no facet terms to add here (the facet
+      // kernel adds them after), the facet nodes' quantities written instead
+      hadamard_volume_kernel<T, D, NP, EB, 0><<<nb, EB * NP, smem, s>>>(
+          u, r, ops, c->b.J, nullptr, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr,
+          c->b.fcache, c->n_e * c->n_slot);
     else
       hadamard_volume_kernel<T, D, NP, EB, 0><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
+  }
+  if (cached) {
+    // after both volume kernels (the Hadamard kernel assigns r)
+    int bs = 128;
+    int nb = (c->n_pairs + bs - 1) / bs;
+    ProfScope ps(c, PG_FACE, s);
+    face_cached_kernel<D><<<nb, bs, 0, s>>>(r, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.fcache,
+                                            c->n_e * c->n_slot, ph64, c->prm.dissipation,
+                                            prod ? prod + np_used : nullptr,
+                                            scheme == ESPLIT_SCHEME_HYBRID ? c->b.hflags : nullptr);
+    c->launches++;
+    if (prod) np_used += nb;
   }
   if (visc) {
     ProfScope ps(c, PG_VISC, s);
