@@ -311,8 +311,8 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
                                                           const double* __restrict__ J,
                                                           const double* __restrict__ fc, int n_slot_total,
                                                           Phys<double> c, int dissipation,
-                                                          double* __restrict__ prod,
-                                                          const unsigned char* __restrict__ hflags = nullptr) {
+                                                          double* __restrict__ prod, int ef_mode,
+                                                          const unsigned char* __restrict__ hflags) {
   constexpr int NC = D + 2;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   double hw = 0.0;
@@ -354,13 +354,13 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
 #pragma unroll
       for (int q = 0; q < NC; ++q) G[q] += 0.5 * b * out[q];
     }
-    // the facet part nu . f / H of the split volume term, for split-form
-    // sides only (hybrid scheme: hflags 1 marks a Hadamard-form element)
+    // the facet part nu . f / H of the split volume term, for split-form sides
+    // (ef_mode 1: both, 2: sides whose hybrid flag is 0, 0: none)
     double ek[NC], ev[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) ek[q] = ev[q] = 0.0;
-    if (!hflags || __ldg(&hflags[k]) == 0) normal_flux<D>(nk, nuv, ek);
-    if (!hflags || __ldg(&hflags[v]) == 0) normal_flux<D>(nv, nuv, ev);
+    if (ef_mode == 1 || (ef_mode == 2 && __ldg(&hflags[k]) == 0)) normal_flux<D>(nk, nuv, ek);
+    if (ef_mode == 1 || (ef_mode == 2 && __ldg(&hflags[v]) == 0)) normal_flux<D>(nv, nuv, ev);
     double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
     double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
 #pragma unroll
@@ -779,7 +779,8 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
       znode_recips<T, D>(z);
       if constexpr (sizeof(T) == sizeof(double)) {
         // nodal quantities of the facet nodes for the cached facet kernel
-        // (hybrid scheme; the split volume kernel writes the others)
+        // (Hadamard and hybrid schemes; for the hybrid scheme the split
+        // volume kernel writes the others)
         const int sl0 = c_ref.node_slot[m];
         if (fcache && sl0 >= 0) {
           const size_t S = (size_t)n_slot_total, ix = (size_t)e * NS + sl0;
@@ -937,10 +938,12 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   // inviscid split scheme: volume kernel first (it caches the facet nodes'
   // quantities), then the facet kernel adds into r; otherwise the facet terms
   // come first and fill the sat buffer the volume kernels add
-  // (the hybrid scheme too in float64: the Hadamard kernel caches its elements'
-  // facet nodes, and the facet kernel adds nu . f / H for split-form sides only)
+  // (the Sjogreen-Yee Hadamard and hybrid schemes too in float64: the Hadamard
+  // kernel caches its elements' facet nodes, and the facet kernel adds
+  // nu . f / H for split-form sides only)
   const bool cached = (scheme == ESPLIT_SCHEME_SPLIT ||
-                       (scheme == ESPLIT_SCHEME_HYBRID && std::is_same<T, double>::value)) &&
+                       ((scheme == ESPLIT_SCHEME_HYBRID || scheme == ESPLIT_SCHEME_HADAMARD) &&
+                        std::is_same<T, double>::value)) &&
                       !visc && sat == c->b.sat && c->b.fcache != nullptr;
   if (!cached) {
     int bs = 128;
@@ -1042,8 +1045,9 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
       hadamard_volume_kernel<T, D, NP, EB, 1><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     else if (cached)
-      // hybrid scheme on the cached path: no facet terms to add here (the facet
-      // kernel adds them after), the facet nodes' quantities written instead
+      // Hadamard or hybrid scheme on the cached path: no facet terms to add
+      // here (the facet kernel adds them after), the facet nodes' quantities
+      // written instead
       hadamard_volume_kernel<T, D, NP, EB, 0><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, nullptr, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr,
           c->b.fcache, c->n_e * c->n_slot);
@@ -1061,7 +1065,8 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     face_cached_kernel<D><<<nb, bs, 0, s>>>(r, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.fcache,
                                             c->n_e * c->n_slot, ph64, c->prm.dissipation,
                                             prod ? prod + np_used : nullptr,
-                                            scheme == ESPLIT_SCHEME_HYBRID ? c->b.hflags : nullptr);
+                                            scheme == ESPLIT_SCHEME_SPLIT ? 1 : (scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0),
+                                            c->b.hflags);
     c->launches++;
     if (prod) np_used += nb;
   }
