@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--quadrants-full", action="store_true", help="run the quadrant problem to t = 0.25")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the 128-triangle step latency and the adjoint (residual / step VJP) timings")
+    ap.add_argument("--no-tet-sweep", action="store_true",
+                    help="skip the residual-only sweep on the 3D vortex tetrahedra, p = 1..4")
+    ap.add_argument("--tet-n", type=int, default=16, help="cubes per direction of the 3D vortex sweep mesh")
     ap.add_argument("--tgv-n", type=int, default=32,
                     help="cubes per direction of the Taylor-Green mesh (6 N^3 tetrahedra; 32 is the workload, "
                          "smaller meshes serve profiling captures)")
@@ -271,6 +274,39 @@ def residual_sweep(es, device, flush):
                 ms = statistics.median(ts)
                 out[f"p{p}_{scheme}_{prec}"] = {"ms": ms, "dof_per_s": mesh.n_e * op.n_p / (ms * 1e-3)}
         s.close()
+    return out
+
+
+def tet_sweep(es, device, flush, n_cubes=16):
+    """Residual-only throughput on the 3D isentropic vortex of Sec. 7.3
+    (domain [-10, 10]^3, N^3 cubes x 6 curved tetrahedra, p = 1..4 diagonal-E
+    tetrahedron operators; degree 1 on affine elements): the split form
+    against the Hadamard form with the Sjogreen-Yee flux and against the
+    Sec. 6 comparator (Hadamard form, Ismail-Roe flux), all with matrix
+    interface dissipation, FP64 and FP32-bulk.  Sec. 7.3 compares the same
+    schemes on 750 tetrahedra, serially."""
+    from esplit_inputs import tet_operator, states
+    from esplit_inputs.mesh import periodic_tet_mesh, vortex3d_warp
+    out = {"n_e": 6 * n_cubes ** 3}
+    stream = torch.cuda.current_stream(device)
+    for p in (1, 2, 3, 4):
+        op = tet_operator(p)
+        mesh = periodic_tet_mesh(op, n_cubes, 20.0, origin=-10.0, warp=vortex3d_warp)
+        u0 = states.add_uniform_noise(states.isentropic_vortex_3d(mesh), 1e-3, 2)
+        s = es.Solver(op, mesh, es.Params(dissipation=True), device=device)
+        ud = s.to_device(u0)
+        r = s.empty()
+        for scheme in ("split", "hadamard", "hadamard_ir"):
+            for prec in ("fp64", "fp32"):
+                s.set_params(es.Params(dissipation=True, scheme=scheme, precision=prec))
+                for _ in range(3):
+                    s.residual(ud, r)
+                ms = statistics.median(_timed(lambda: s.residual(ud, r), stream, flush, 10))
+                out[f"p{p}_{scheme}_{prec}"] = {"ms": ms, "dof_per_s": mesh.n_e * op.n_p / (ms * 1e-3)}
+        out[f"p{p}_n_p"] = op.n_p
+        s.close()
+        del s, ud, r, mesh
+        torch.cuda.empty_cache()
     return out
 
 
@@ -546,6 +582,8 @@ def main():
               "g_range": [min(gs), max(gs)], "wall_s_timed": t_wall, "dt": dt}
     if rank == 0 and not args.no_sweep:
         extras["residual_sweep"] = residual_sweep(es, device, flush)
+    if rank == 0 and not args.no_tet_sweep:
+        extras["tet_sweep"] = tet_sweep(es, device, flush, n_cubes=args.tet_n)
     if rank == 0 and not args.no_tgv:
         extras["taylor_green"] = taylor_green_run(es, device, flush, n_cubes=args.tgv_n)
     if rank == 0 and not args.no_quadrants:

@@ -280,7 +280,7 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
                       warp=None) -> Mesh:
     """Periodic [x0, x0 + L]^3 mesh of N^3 cubes, each cut into the six Kuhn
     tetrahedra around its main diagonal (6 N^3 elements), quadratic geometry
-    warped by x_i = xhat_i + A prod_j sin(2 pi (xhat_j - x0) / L) or, when
+    (affine for p = 1) warped by x_i = xhat_i + A prod_j sin(2 pi (xhat_j - x0) / L) or, when
     given, by warp(xhat) -> displacements evaluated on the wrapped lattice
     (Sec. 7.3 builds its 3D grids the same way: hexahedra cut into six
     tetrahedra, then perturbed).  Facet nodes are paired by their (unwarped)
@@ -314,6 +314,12 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
         disp = amp * s[..., None]
     else:
         disp = warp(origin + wrap * (h / 2))
+    if op.p == 1:
+        # degree-1 operators: affine elements (edge nodes at the midpoints of
+        # the displaced vertices).  The metric terms J dxi/dx of a quadratic
+        # map are cofactors of its Jacobian, quadratic in 3D, and the discrete
+        # metric identities of Sec. 2 need D exact on them.
+        disp = np.concatenate([disp[:, :4], np.stack([0.5 * (disp[:, a] + disp[:, b]) for a, b in edges], 1)], 1)
     G = origin + G_idx * (h / 2) + disp                        # (e, 10, 3)
     G = np.transpose(G, (0, 2, 1))                             # (e, 3, 10)
     # derivatives from element-local offsets (see periodic_tri_mesh)
@@ -349,10 +355,14 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
     pair[a, 0], pair[a, 1] = b // n_slot, b % n_slot
     pair[b, 0], pair[b, 1] = a // n_slot, a % n_slot
     pair = pair.reshape(n_e, op.n_fac, op.n_f, 2)
-    diff = x[:, :, :, None] - x[:, :, None, :]
-    dist = np.sqrt((diff ** 2).sum(1))
-    dist[:, np.arange(op.n_p), np.arange(op.n_p)] = np.inf
-    hmin = dist.reshape(n_e, -1).min(1)
+    hmin = np.empty(n_e)
+    ch = max(1, (1 << 24) // (op.n_p * op.n_p))    # elements per chunk of the pairwise distances
+    for e0 in range(0, n_e, ch):
+        xe = x[e0:e0 + ch]
+        diff = xe[:, :, :, None] - xe[:, :, None, :]
+        dist = np.sqrt((diff ** 2).sum(1))
+        dist[:, np.arange(op.n_p), np.arange(op.n_p)] = np.inf
+        hmin[e0:e0 + ch] = dist.reshape(len(xe), -1).min(1)
     return Mesh(d=3, n_e=n_e, n_p=op.n_p, n_fac=op.n_fac, n_f=op.n_f, L=(L, L, L), x=x, J=det, Lam=Lam, nu=nu,
                 pair=pair, hmin=hmin, meta=dict(kind="periodic_tet", N=N, L=L, amp=amp, p=op.p, origin=origin,
                                                  geom=G))

@@ -255,30 +255,94 @@ class RefOperator:
 
 
 # ---------------------------------------------------------------------------
-# Tetrahedron, p = 2.  Facet nodes: the S3-symmetric 6-point degree-4 rule on
-# every face (two S21 orbits, solved from the triangle moment equations;
-# degree 4 = 2p), so paired faces see the same physical points whatever their
-# relative orientation.  Volume: the 24 facet nodes plus the centroid, weights
-# from the S4-invariant moment equations of degree 3 (= 2p - 1); 25 nodes.
+# Tetrahedron, p = 1..4.  Facet nodes: an S3-symmetric rule of degree 2p on
+# every face (all points inside the face, so every facet node belongs to one
+# facet and paired faces see the same physical points whatever their relative
+# orientation), orbits solved from the triangle moment equations:
+#   p = 1: one S21 orbit (3 points), p = 2: two S21 orbits (6),
+#   p = 3: two S21 + one S111 (12), p = 4: S3 + three S21 + one S111 (16).
+# Volume: the 4 n_f facet nodes (each face orbit is one S4 orbit of the
+# tetrahedron, one weight) plus S4-symmetric interior orbits, the weights and
+# positions solved from the moment equations of degree 2p - 1 with all
+# weights positive (``solve_tet_quadrature`` re-derives them):
+#   p = 1: 12 nodes, p = 2: 25, p = 3: 58, p = 4: 78.
+# Parameter layout of a face rule: per orbit its position parameters (none
+# for S3, a for S21, a, b for S111), then its weight (weights sum to 1/2).
+# Layout of a volume rule: one weight per face orbit, then per interior
+# orbit its position parameters (none for S4, a for S31 and S22, a, b for
+# S211) and its weight.
 # ---------------------------------------------------------------------------
-_TRI_FACE_DEG4 = dict(a1=0.44594849091596483, w1=0.11169079483900565,
-                      a2=0.09157621350977083, w2=0.054975871827661026)
-_TET_RULES = {2: dict(degree=3, x=[0.006710441872127204, 0.002335214368444981, 0.058118791779800436])}
+_TRI_FACE_RULES = {
+    1: dict(degree=2, orbits=["S21"], x=[1.0 / 6.0, 1.0 / 6.0]),
+    2: dict(degree=4, orbits=["S21", "S21"],
+            x=[0.44594849091596483, 0.11169079483900565, 0.09157621350977083, 0.054975871827661026]),
+    3: dict(degree=6, orbits=["S21", "S21", "S111"],
+            x=[0.06308901449150953, 0.02542245318510883, 0.24928674517087093, 0.058393137863221665,
+               0.31035245103381354, 0.0531450498447909, 0.04142553780916809]),
+    4: dict(degree=8, orbits=["S3", "S21", "S21", "S21", "S111"],
+            x=[0.07215780383889538, 0.05054722831703085, 0.016229248811598943, 0.4592925882927259,
+               0.04754581713364107, 0.1705693077517623, 0.05160868526736049, 0.26311282963463273,
+               0.008394777409958283, 0.013615157087217195]),
+}
+_TET_RULES = {
+    1: dict(degree=1, interior=[], x=[1.0 / 72.0]),
+    2: dict(degree=3, interior=["S4"], x=[0.006710441872127204, 0.002335214368444981, 0.058118791779800436]),
+    3: dict(degree=5, interior=["S31", "S22"],
+            x=[0.00068236186453178, 0.002856422538590274, 0.001334501736597179, 0.15457334884980922,
+               0.015499652663895004, 0.13846669986348373, 0.00502910024921495]),
+    4: dict(degree=7, interior=["S31", "S31", "S22"],
+            x=[0.002485691614389907, 0.00030806911398383713, 0.0009130575817185983, 0.0018949943080682364,
+               0.00030639411289908324, 0.11797912654527264, 0.007851322735386043, 0.29542463948861264,
+               0.007073176720332001, 0.09879275592124274, 0.008713165271901467]),
+}
 _TET_VERTS = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
 _TET_NORMALS = np.array([[1.0, 1.0, 1.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0], [0.0, 0.0, -1.0]])
 _TET_NORMALS[0] /= np.sqrt(3.0)
 _TET_FACE_SCALE = np.array([np.sqrt(3.0), 1.0, 1.0, 1.0])  # face area / (1/2)
+_NPRM = {"S3": 0, "S21": 1, "S111": 2, "S4": 0, "S31": 1, "S22": 1, "S211": 2}
 
 
-def tri_face_rule_deg4():
-    """Barycentric points (6, 3) and weights (6,) (sum 1/2) of the degree-4 rule."""
-    r = _TRI_FACE_DEG4
-    pts, w = [], []
-    for a, ww in [(r["a1"], r["w1"]), (r["a2"], r["w2"])]:
-        for lam in [(a, a, 1 - 2 * a), (a, 1 - 2 * a, a), (1 - 2 * a, a, a)]:
+def _tri_orbit(typ, prm):
+    """Barycentric points of one S3 orbit of the triangle (fixed order)."""
+    if typ == "S3":
+        return [(1 / 3, 1 / 3, 1 / 3)]
+    if typ == "S21":
+        a = prm[0]
+        return [(a, a, 1 - 2 * a), (a, 1 - 2 * a, a), (1 - 2 * a, a, a)]
+    a, b = prm
+    c = 1 - a - b
+    return [(a, b, c), (a, c, b), (b, a, c), (b, c, a), (c, a, b), (c, b, a)]
+
+
+def _tet_orbit(typ, prm):
+    """Barycentric points of one S4 orbit of the tetrahedron (fixed order)."""
+    import itertools
+    if typ == "S4":
+        return [(0.25, 0.25, 0.25, 0.25)]
+    if typ == "S31":
+        a = prm[0]
+        return [tuple(1 - 3 * a if k == v else a for k in range(4)) for v in range(4)]
+    if typ == "S22":
+        a = prm[0]
+        return [tuple(a if k in ij else 0.5 - a for k in range(4)) for ij in itertools.combinations(range(4), 2)]
+    a, b = prm
+    return sorted(set(itertools.permutations((a, a, b, 1 - 2 * a - b))))
+
+
+def tri_face_rule(p: int, x=None):
+    """Barycentric points (n_f, 3), weights (n_f,) (sum 1/2) and the orbit index
+    of every point, of the degree-2p face rule."""
+    rule = _TRI_FACE_RULES[p]
+    x = rule["x"] if x is None else x
+    pts, w, orb, i = [], [], [], 0
+    for o, typ in enumerate(rule["orbits"]):
+        k = _NPRM[typ]
+        for lam in _tri_orbit(typ, x[i:i + k]):
             pts.append(lam)
-            w.append(ww)
-    return np.array(pts), np.array(w)
+            w.append(x[i + k])
+            orb.append(o)
+        i += k + 1
+    return np.array(pts), np.array(w), np.array(orb)
 
 
 def tet_monomial_integral(a: int, b: int, c: int) -> float:
@@ -286,33 +350,81 @@ def tet_monomial_integral(a: int, b: int, c: int) -> float:
     return factorial(a) * factorial(b) * factorial(c) / factorial(a + b + c + 3)
 
 
-def _tet_nodes(x):
-    fp, fw = tri_face_rule_deg4()
-    pts, wts, fnodes = [], [], []
-    for face in range(4):  # face `face` is opposite vertex `face`
+def _tet_nodes(p: int, x, interior=None):
+    """Nodes (n_p, 3) and weights (n_p,) of the tetrahedron rule for degree p:
+    the facet nodes face by face (face g opposite vertex g), then the interior
+    orbits."""
+    fp, _, forb = tri_face_rule(p)
+    interior = _TET_RULES[p]["interior"] if interior is None else interior
+    pts, wts = [], []
+    for face in range(4):
         others = [v for v in range(4) if v != face]
-        for k in range(6):
+        for k in range(len(fp)):
             lam = np.zeros(4)
             for j, v in enumerate(others):
                 lam[v] = fp[k][j]
             pts.append(lam[1:])
-            wts.append(x[0] if k < 3 else x[1])
-    pts.append(np.full(3, 0.25))
-    wts.append(x[2])
+            wts.append(x[forb[k]])
+    i = int(forb.max()) + 1
+    for typ in interior:
+        k = _NPRM[typ]
+        for lam in _tet_orbit(typ, x[i:i + k]):
+            pts.append(np.array(lam[1:]))
+            wts.append(x[i + k])
+        i += k + 1
     return np.array(pts), np.array(wts)
 
 
+def solve_tet_quadrature(p: int, interior, seed: int = 0, tries: int = 20):
+    """Re-derive a tabulated volume rule: seeded nonlinear least squares on the
+    moment equations of all monomials up to degree 2p - 1 with the face nodes
+    of ``tri_face_rule(p)`` fixed, keeping the positive rule with interior
+    nodes strictly inside and the largest smallest weight."""
+    from scipy.optimize import least_squares
+
+    deg = 2 * p - 1
+    n_fo = len(_TRI_FACE_RULES[p]["orbits"])
+    mons = np.array([(a, b, c) for a in range(deg + 1) for b in range(deg + 1 - a) for c in range(deg + 1 - a - b)])
+    ex = np.array([tet_monomial_integral(*m) for m in mons])
+
+    def res(x):
+        pts, w = _tet_nodes(p, x, interior)
+        return w @ np.prod(pts[:, None, :] ** mons[None], axis=2) - ex
+
+    rng = np.random.default_rng(seed)
+    best = None
+    for _ in range(tries):
+        x0 = list(rng.uniform(1e-4, 1e-2, n_fo))
+        for typ in interior:
+            if typ == "S31":
+                x0 += [rng.uniform(0.02, 0.32)]
+            elif typ == "S22":
+                x0 += [rng.uniform(0.02, 0.24)]
+            elif typ == "S211":
+                a = rng.uniform(0.02, 0.3)
+                x0 += [a, rng.uniform(0.02, 0.9 - 2 * a)]
+            x0 += [rng.uniform(1e-3, 2e-2)]
+        r = least_squares(res, x0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=4000)
+        pts, w = _tet_nodes(p, r.x, interior)
+        ip = np.concatenate([pts, 1 - pts.sum(1, keepdims=True)], 1)[4 * len(tri_face_rule(p)[0]):]
+        inside = len(ip) == 0 or np.all(ip > 1e-3)
+        if np.all(w > 0) and inside and np.abs(res(r.x)).max() < 1e-14:
+            if best is None or w.min() > best[0]:
+                best = (w.min(), r.x)
+    return None if best is None else best[1]
+
+
 def tet_operator(p: int) -> RefOperator:
-    """Diagonal-E SBP operator on the reference tetrahedron (p = 2, 25 nodes)."""
+    """Diagonal-E SBP operator of degree p (1..4) on the reference tetrahedron."""
     key = ("tet", p)
     if key in _CACHE:
         return _CACHE[key]
     if p not in _TET_RULES:
         raise ValueError(f"no tetrahedron rule for p={p}")
     rule = _TET_RULES[p]
-    xi, H = _tet_nodes(np.asarray(rule["x"], dtype=np.float64))
-    fp, fw = tri_face_rule_deg4()
-    n_fac, nf = 4, 6
+    xi, H = _tet_nodes(p, np.asarray(rule["x"], dtype=np.float64))
+    _, fw, _ = tri_face_rule(p)
+    n_fac, nf = 4, len(fw)
     n_p = len(H)
     facet_nodes = np.arange(n_fac * nf, dtype=np.int32).reshape(n_fac, nf)
     facet_w = np.stack([fw * _TET_FACE_SCALE[g] for g in range(n_fac)])

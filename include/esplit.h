@@ -104,8 +104,8 @@ void esplit_destroy(esplit_ctx* ctx);
  *                                    residual; kept for diagnostics)
  *   ref_normals  [n_fac][d]          outward unit normals of reference facets
  * Host pointers, copied.  Supported (d, n_p): (2, 7), (2, 12), (2, 18),
- * (2, 27) (triangles, p = 1..4) and (3, 25) (tetrahedra, p = 2); others ->
- * ESPLIT_ERR_UNSUPPORTED. */
+ * (2, 27) (triangles, p = 1..4) and (3, 12), (3, 25), (3, 58), (3, 78)
+ * (tetrahedra, p = 1..4); others -> ESPLIT_ERR_UNSUPPORTED. */
 int esplit_upload_operator(esplit_ctx* ctx, int n_p, int n_fac, int n_f, const double* H_ref,
                            const double* Q_ref, const int* facet_nodes, const double* facet_w,
                            const double* ref_normals);

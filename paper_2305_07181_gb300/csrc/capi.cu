@@ -46,7 +46,7 @@ void dfree(void* p) {
 
 bool supported(int dim, int n_p) {
   if (dim == 2) return n_p == 7 || n_p == 12 || n_p == 18 || n_p == 27;
-  if (dim == 3) return n_p == 25;
+  if (dim == 3) return n_p == 12 || n_p == 25 || n_p == 58 || n_p == 78;
   return false;
 }
 

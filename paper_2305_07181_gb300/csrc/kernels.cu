@@ -38,10 +38,17 @@ template <int W>
 __device__ __forceinline__ void block_sum(double (&v)[W], double* out_row) {
   __shared__ double red[32][W];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // a block of EB * NP threads may end in a partial warp: shuffle among the
+  // lanes that exist and add only values read from them
+  const int nl = min(32, (int)blockDim.x - (warp << 5));
+  const unsigned mask = nl == 32 ? 0xffffffffu : ((1u << nl) - 1u);
 #pragma unroll
   for (int k = 0; k < W; ++k) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(mask, v[k], o);
+      if (lane + o < nl) v[k] += y;
+    }
   }
   if (lane == 0) {
 #pragma unroll
@@ -738,7 +745,7 @@ __global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ?
 //   G = sum_i S_i[m][n] F*_i(u_m, u_n),  S_i[m][n] = H_m D_i[m][n]
 //   r_m -= 2 G / H_m,  r_n += 2 G / H_n
 // ---------------------------------------------------------------------------
-template <typename T, int D, int NP, int EB, int FLUX = 0>
+template <typename T, int D, int NP, int EB, int FLUX = 0, int KC = NP / 2>
 __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
     const double* __restrict__ u, double* __restrict__ r, const T* __restrict__ ops,
     const double* __restrict__ J, const double* __restrict__ sat, const int* __restrict__ list, int n_list,
@@ -749,8 +756,8 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
   constexpr int NZ = D + 7;  // q, V[D], p, P1, P2, v2, 1/q, 1/p
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sz = reinterpret_cast<T*>(smem_raw);           // [EB][NZ][NP]
-  T* sg = sz + EB * NZ * NP;                         // [EB][NP][K][NC]
-  T* sH = sg + EB * NP * K * NC;                     // [EB][NP]
+  T* sg = sz + EB * NZ * NP;                         // [EB][NP][KC][NC]
+  T* sH = sg + EB * NP * KC * NC;                    // [EB][NP]
   const int NS = c_ref.n_slot;
   int el = threadIdx.x / NP;
   int m = threadIdx.x - el * NP;
@@ -813,10 +820,11 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
   T acc[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) acc[q] = T(0);
+  const T* zz = sz + el * NZ * NP;
+  ZNode<T, D> zm;
+  IRNode<T, D> im;
+  T iHm = T(0), Hm = T(0);
   if (active) {
-    const T* zz = sz + el * NZ * NP;
-    ZNode<T, D> zm;
-    IRNode<T, D> im;
     if constexpr (FLUX == 1) {
       im.z1 = zz[m];
       im.zn = zz[NP + m];
@@ -835,61 +843,71 @@ __global__ void __launch_bounds__(EB * NP) hadamard_volume_kernel(
       zm.iq = zz[(D + 5) * NP + m];
       zm.ip = zz[(D + 6) * NP + m];
     }
-    T iHm = sH[el * NP + m];
-    T Hm = T(1) / iHm;
-    const T* op = ops + (size_t)e * (2 * D * NP * NP);
-    T* gout = sg + ((size_t)el * NP + m) * K * NC;
-    for (int k = 1; k <= K; ++k) {
-      if ((NP % 2 == 0) && k == K && m >= K) break;
-      int n = m + k;
-      if (n >= NP) n -= NP;
-      T Smn[D];
+    iHm = sH[el * NP + m];
+    Hm = T(1) / iHm;
+  }
+  const T* op = ops + (size_t)e * (2 * D * NP * NP);
+  T* gout = sg + ((size_t)el * NP + m) * KC * NC;
+  // pair offsets k = 1..K in chunks of KC (one chunk when KC = K): node m
+  // forms the pairs (m, m + k) of the chunk, then gathers the chunk's pairs
+  // (m - k, m) from shared memory; the chunk loop is uniform over the block
+  for (int k0 = 1; k0 <= K; k0 += KC) {
+    const int k1 = min(K, k0 + KC - 1);
+    if (active) {
+      for (int k = k0; k <= k1; ++k) {
+        if ((NP % 2 == 0) && k == K && m >= K) break;
+        int n = m + k;
+        if (n >= NP) n -= NP;
+        T Smn[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) Smn[i] = Hm * __ldg(&op[((D + i) * NP + n) * NP + m]);
-      T G[NC];
-      if constexpr (FLUX == 1) {
-        IRNode<T, D> in_;
-        in_.z1 = zz[n];
-        in_.zn = zz[NP + n];
-        in_.l1 = zz[2 * NP + n];
-        in_.ln = zz[3 * NP + n];
+        for (int i = 0; i < D; ++i) Smn[i] = Hm * __ldg(&op[((D + i) * NP + n) * NP + m]);
+        T G[NC];
+        if constexpr (FLUX == 1) {
+          IRNode<T, D> in_;
+          in_.z1 = zz[n];
+          in_.zn = zz[NP + n];
+          in_.l1 = zz[2 * NP + n];
+          in_.ln = zz[3 * NP + n];
 #pragma unroll
-        for (int i = 0; i < D; ++i) in_.V[i] = zz[(4 + i) * NP + n];
-        IRAvg<T, D> ia;
-        ir_avg<T, D>(im, in_, c, ia);
-        ir_flux_dir<T, D>(ia, c, Smn, G);
-      } else {
-        ZNode<T, D> zn;
-        zn.q = zz[n];
+          for (int i = 0; i < D; ++i) in_.V[i] = zz[(4 + i) * NP + n];
+          IRAvg<T, D> ia;
+          ir_avg<T, D>(im, in_, c, ia);
+          ir_flux_dir<T, D>(ia, c, Smn, G);
+        } else {
+          ZNode<T, D> zn;
+          zn.q = zz[n];
 #pragma unroll
-        for (int i = 0; i < D; ++i) zn.V[i] = zz[(1 + i) * NP + n];
-        zn.p = zz[(D + 1) * NP + n];
-        zn.P1 = zz[(D + 2) * NP + n];
-        zn.P2 = zz[(D + 3) * NP + n];
-        zn.v2 = zz[(D + 4) * NP + n];
-        PairAvg<T, D> a;
-        pair_avg<T, D>(zm, zn, c, a);
-        sy_flux_dir<T, D>(a, c, Smn, G);
-      }
+          for (int i = 0; i < D; ++i) zn.V[i] = zz[(1 + i) * NP + n];
+          zn.p = zz[(D + 1) * NP + n];
+          zn.P1 = zz[(D + 2) * NP + n];
+          zn.P2 = zz[(D + 3) * NP + n];
+          zn.v2 = zz[(D + 4) * NP + n];
+          PairAvg<T, D> a;
+          pair_avg<T, D>(zm, zn, c, a);
+          sy_flux_dir<T, D>(a, c, Smn, G);
+        }
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        acc[q] -= T(2) * G[q] * iHm;
-        gout[(k - 1) * NC + q] = T(2) * G[q];
+        for (int q = 0; q < NC; ++q) {
+          acc[q] -= T(2) * G[q] * iHm;
+          gout[(k - k0) * NC + q] = T(2) * G[q];
+        }
       }
     }
+    __syncthreads();
+    if (active) {
+      for (int k = k0; k <= k1; ++k) {
+        int src = m - k;
+        if (src < 0) src += NP;
+        if ((NP % 2 == 0) && k == K && src >= K) continue;
+        const T* gin = sg + ((size_t)el * NP + src) * KC * NC + (k - k0) * NC;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) acc[q] += gin[q] * iHm;
+      }
+    }
+    if (k0 + KC <= K) __syncthreads();
   }
-  __syncthreads();
   double hw = 0.0;
   if (active) {
-    T iHm = sH[el * NP + m];
-    for (int k = 1; k <= K; ++k) {
-      int src = m - k;
-      if (src < 0) src += NP;
-      if ((NP % 2 == 0) && k == K && src >= K) continue;
-      const T* gin = sg + ((size_t)el * NP + src) * K * NC + (k - 1) * NC;
-#pragma unroll
-      for (int q = 0; q < NC; ++q) acc[q] += gin[q] * iHm;
-    }
     int sl = c_ref.node_slot[m];
     double res[NC];
 #pragma unroll
@@ -924,7 +942,11 @@ namespace esplit {
 template <int NP>
 struct VolCfg {
   static constexpr int EB_SPLIT = (256 / NP) > 0 ? (256 / NP) : 1;
-  static constexpr int EB_HAD = (128 / NP) > 0 ? (128 / NP) : 1;
+  // larger operators (tetrahedra of degree 3 and 4): the pair contributions
+  // pass through shared memory in chunks of HAD_KC pair offsets, which leaves
+  // room for more elements per block
+  static constexpr int EB_HAD = NP > 32 ? ((256 / NP) > 0 ? (256 / NP) : 1) : ((128 / NP) > 0 ? (128 / NP) : 1);
+  static constexpr int HAD_KC = NP > 32 ? 8 : NP / 2;
 };
 
 template <typename T, int D, int NP>
@@ -1029,30 +1051,30 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   }
   if (n_had > 0) {
     constexpr int EB = VolCfg<NP>::EB_HAD;
-    constexpr int K = NP / 2;
-    size_t smem = sizeof(T) * ((size_t)EB * (D + 7) * NP + (size_t)EB * NP * K * (D + 2) + (size_t)EB * NP);
+    constexpr int KC = VolCfg<NP>::HAD_KC;
+    size_t smem = sizeof(T) * ((size_t)EB * (D + 7) * NP + (size_t)EB * NP * KC * (D + 2) + (size_t)EB * NP);
     static bool attr_set = false;
     if (!attr_set) {
-      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB, 0, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(hadamard_volume_kernel<T, D, NP, EB, 1, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
       attr_set = true;
     }
     int nb = (n_had + EB - 1) / EB;
     ProfScope ps(c, PG_HAD, s);
     if (scheme == ESPLIT_SCHEME_HADAMARD_IR)
-      hadamard_volume_kernel<T, D, NP, EB, 1><<<nb, EB * NP, smem, s>>>(
+      hadamard_volume_kernel<T, D, NP, EB, 1, KC><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     else if (cached)
       // Hadamard or hybrid scheme on the cached path: no facet terms to add
       // here (the facet kernel adds them after), the facet nodes' quantities
       // written instead
-      hadamard_volume_kernel<T, D, NP, EB, 0><<<nb, EB * NP, smem, s>>>(
+      hadamard_volume_kernel<T, D, NP, EB, 0, KC><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, nullptr, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr,
           c->b.fcache, c->n_e * c->n_slot);
     else
-      hadamard_volume_kernel<T, D, NP, EB, 0><<<nb, EB * NP, smem, s>>>(
+      hadamard_volume_kernel<T, D, NP, EB, 0, KC><<<nb, EB * NP, smem, s>>>(
           u, r, ops, c->b.J, sat, lhad, n_had, ph, ph64, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     np_used += nb;
@@ -1094,7 +1116,10 @@ static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s,
     }
   } else if (c->dim == 3) {
     switch (c->n_p) {
+      case 12: return residual_np<T, 3, 12>(c, u, r, s, prod, n_partial, sat);
       case 25: return residual_np<T, 3, 25>(c, u, r, s, prod, n_partial, sat);
+      case 58: return residual_np<T, 3, 58>(c, u, r, s, prod, n_partial, sat);
+      case 78: return residual_np<T, 3, 78>(c, u, r, s, prod, n_partial, sat);
     }
   }
   return -2;

@@ -310,7 +310,10 @@ int launch_viscous_vjp(esplit_ctx* c, const double* u, const double* cot, double
     }
   } else if (c->dim == 3) {
     switch (c->n_p) {
+      case 12: return visc_vjp_np<3, 12>(c, u, cot, grad, s);
       case 25: return visc_vjp_np<3, 25>(c, u, cot, grad, s);
+      case 58: return visc_vjp_np<3, 58>(c, u, cot, grad, s);
+      case 78: return visc_vjp_np<3, 78>(c, u, cot, grad, s);
     }
   }
   return -2;

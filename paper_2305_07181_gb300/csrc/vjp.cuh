@@ -589,7 +589,10 @@ int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
     }
   } else if (c->dim == 3) {
     switch (c->n_p) {
+      case 12: return vjp_np<3, 12>(c, u, cot, grad, s);
       case 25: return vjp_np<3, 25>(c, u, cot, grad, s);
+      case 58: return vjp_np<3, 58>(c, u, cot, grad, s);
+      case 78: return vjp_np<3, 78>(c, u, cot, grad, s);
     }
   }
   return -2;

@@ -180,3 +180,71 @@ def test_vortex_ismail_roe_against_table1(lib, p):
         print(f"p={p} N={N}: split+diss (RK4) {errs[(N, 'split_diss')]:.3e} vs IR+diss {errs[(N, 'ir_diss')]:.3e}")
         assert errs[(N, "ir_diss")] < errs[(N, "ir_ec")]
         assert 0.5 <= errs[(N, "split_diss")] / errs[(N, "ir_diss")] <= 2.0
+
+
+def _run_3d(lib, op, m, params, rrk=True, tf=1.0):
+    """The 3D vortex at CFL 0.25 to t_f: relaxation RK4 through the library
+    for the entropy-split scheme, classical RK4 (torch stage combinations)
+    for the Ismail-Roe comparator, whose entropy is not Harten's."""
+    from accuracy import l2_error_vortex_3d
+    u0 = states.isentropic_vortex_3d(m)
+    dt = states.cfl_timestep(m, u0, 0.25)
+    s = lib.Solver(op, m, params)
+    u = s.to_device(u0)
+    t = 0.0
+    while t < tf - 1e-12:
+        h = min(dt, tf - t)
+        if rrk:
+            g, _ = s.rrk_step(u, h)
+            t += g * h
+        else:
+            k1 = s.residual(u)
+            k2 = s.residual(u + 0.5 * h * k1)
+            k3 = s.residual(u + 0.5 * h * k2)
+            k4 = s.residual(u + h * k3)
+            u = u + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+            t += h
+    err = l2_error_vortex_3d(u.cpu().numpy(), op, m, t)
+    assert s.status() == 0
+    s.close()
+    return err
+
+
+@pytest.mark.parametrize("p", [1, 3, 4])
+def test_vortex3d_degrees_against_table2(lib, p):
+    """The 3D vortex of Sec. 7.3 with the degree 1, 3 and 4 tetrahedron
+    operators on the 15^3 x 6 and 20^3 x 6 grids, all four columns of Table 2
+    (entropy split and Ismail-Roe Hadamard form, each conservative and with
+    its matrix dissipation): errors within a factor 2 of the printed ones,
+    rates in [p - 0.2, p + 1.2], and the split and Ismail-Roe errors within a
+    factor 2 of each other (the equal accuracy the throughput comparison on
+    these grids assumes)."""
+    from esplit_inputs import tet_operator
+    from esplit_inputs.mesh import periodic_tet_mesh, vortex3d_warp
+    rows = np.loadtxt(GOLDEN3D, comments="#")
+    cols = ("split_ec", "split_diss", "ir_ec", "ir_diss")
+    tab = {(int(r[0]), int(r[1])): dict(zip(cols, r[2:])) for r in rows}
+    op = tet_operator(p)
+    errs = {}
+    for N in (15, 20):
+        m = periodic_tet_mesh(op, N, 20.0, origin=-10.0, warp=vortex3d_warp)
+        errs[(N, "split_ec")] = _run_3d(lib, op, m, lib.Params(dissipation=False))
+        errs[(N, "split_diss")] = _run_3d(lib, op, m, lib.Params(dissipation=True))
+        errs[(N, "ir_ec")] = _run_3d(lib, op, m, lib.Params(scheme="hadamard_ir", dissipation=False), rrk=False)
+        errs[(N, "ir_diss")] = _run_3d(lib, op, m, lib.Params(scheme="hadamard_ir", dissipation=True), rrk=False)
+    for kind in cols:
+        ours = [errs[(15, kind)], errs[(20, kind)]]
+        paper = [tab[(p, 15)][kind], tab[(p, 20)][kind]]
+        rate = np.log(ours[0] / ours[1]) / np.log(20 / 15)
+        prate = np.log(paper[0] / paper[1]) / np.log(20 / 15)
+        print(f"3D p={p} {kind}: ours {ours[0]:.3e} {ours[1]:.3e} rate {rate:.2f} | Table 2 {paper[0]:.3e} "
+              f"{paper[1]:.3e} rate {prate:.2f}")
+    for kind in cols:
+        ours = [errs[(15, kind)], errs[(20, kind)]]
+        paper = [tab[(p, 15)][kind], tab[(p, 20)][kind]]
+        rate = np.log(ours[0] / ours[1]) / np.log(20 / 15)
+        assert p - 0.2 <= rate <= p + 1.2
+        for a, b in zip(ours, paper):
+            assert 0.5 <= a / b <= 2.0
+    for N in (15, 20):
+        assert 0.5 <= errs[(N, "split_diss")] / errs[(N, "ir_diss")] <= 2.0

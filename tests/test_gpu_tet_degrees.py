@@ -1,0 +1,177 @@
+"""The residual on curved periodic tetrahedra with the degree 1, 3 and 4
+diagonal-E operators (degree 1 on affine elements) through the C ABI against
+the FP64 oracle: every scheme with and without interface dissipation (Eqs.
+(69), (99), (100)), the Baumann-Oden viscous terms (Sec. 5), the FP32-bulk
+bound, the entropy identities of Thm. 2 on the GPU residual, relaxation RK4
+steps (Eqs. (97)-(98)) and the residual VJP.  Meshes: 2^3 or 3^3 cubes x 6
+tetrahedra (48 or 162 elements: several blocks of every kernel and a ragged
+tail).
+
+Tolerances as for the degree-2 operator: FP64 max-norm relative error per
+component <= 1e-12, FP32-bulk <= 1e-5, relaxation parameter <= 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+from esplit_inputs import tet_operator, states
+from esplit_inputs.mesh import periodic_tet_mesh
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_BOUND = 1e-5
+PS = [1, 3, 4]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_07181_gb300 as es
+    return es
+
+
+def _oracle():
+    from oracle import residual as R, diagnostics as Dg, rrk
+    from oracle.physics import Params as OP
+    return R, Dg, rrk, OP
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    num = np.abs(a - b).max(axis=(0, 2))
+    den = np.abs(b).max(axis=(0, 2))
+    den = np.where(den > 0, den, 1.0)
+    return float((num / den).max())
+
+
+_MESH = {}
+
+
+def _tet(p, N=None):
+    # 162 elements for p = 1, 48 for the larger operators (the oracle's
+    # Hadamard form is O(n_p^2) per element)
+    N = N or (3 if p == 1 else 2)
+    if (p, N) not in _MESH:
+        op = tet_operator(p)
+        _MESH[(p, N)] = (op, periodic_tet_mesh(op, N, 2 * np.pi, 0.02))
+    return _MESH[(p, N)]
+
+
+@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("scheme,diss", [("split", False), ("split", True), ("hadamard", False),
+                                         ("hadamard", True), ("hybrid", True), ("hadamard_ir", False),
+                                         ("hadamard_ir", True)])
+def test_tet_inviscid_fp64_parity(lib, p, scheme, diss):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(p)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=70 + p)
+    flags = np.random.default_rng(p).integers(0, 2, m.n_e).astype(np.uint8)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=diss))
+    if scheme == "hybrid":
+        s.set_hybrid_flags(flags)
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=diss,
+                    hybrid_flags=flags if scheme == "hybrid" else None).numpy()
+    err = rel_err(r, ro)
+    print(f"tet p={p} {scheme} diss={diss} rel err {err:.3e}")
+    assert err <= FP64_TOL
+    assert s.status() == 0
+    s.close()
+
+
+@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("heat", [False, True])
+def test_tet_viscous_fp64_parity(lib, p, heat):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(p)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=80 + p)
+    s = lib.Solver(op, m, lib.Params(mu=0.05, viscous=True, heat_flux=heat, dissipation=True))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(mu=0.05, heat_flux=heat), dissipation=True, viscous=True).numpy()
+    err = rel_err(r, ro)
+    print(f"tet p={p} viscous heat={heat} rel err {err:.3e}")
+    assert err <= FP64_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("scheme", ["split", "hadamard"])
+def test_tet_fp32_bulk_bound(lib, p, scheme):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(p)
+    u = states.add_uniform_noise(states.taylor_green(m, Mach=0.3), 1e-3, 5)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32"))
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True).numpy()
+    err = rel_err(r, ro)
+    print(f"tet p={p} fp32 {scheme} rel err {err:.3e}")
+    assert err <= FP32_BOUND
+    s.close()
+
+
+@pytest.mark.parametrize("p", PS)
+def test_tet_entropy_identities(lib, p):
+    """EC schemes conserve entropy on the GPU residual (Thm. 2 and Thm. 4);
+    dissipation only removes it; a uniform state is preserved."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(p)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=90 + p)
+    s = lib.Solver(op, m, lib.Params())
+    ud = s.to_device(u)
+    for scheme in ("split", "hadamard"):
+        s.set_params(lib.Params(scheme=scheme))
+        r0 = s.residual(ud)
+        scale = float(Dg.entropy_rate_scale(u, r0.cpu().numpy(), op, m, OP()))
+        assert abs(s.entropy_rate(ud, r0)) <= 1e-13 * scale
+        s.set_params(lib.Params(scheme=scheme, dissipation=True))
+        assert s.entropy_rate(ud, s.residual(ud) - r0) < 0
+    s.set_params(lib.Params(mu=0.05, viscous=True, dissipation=True))
+    uf = s.to_device(states.uniform_state(m.n_e, 3, op.n_p))
+    assert float(s.residual(uf).abs().max()) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("p", PS)
+def test_tet_rrk_parity(lib, p):
+    """Three relaxation RK4 steps of the Navier-Stokes Taylor-Green state
+    (split + BO + dissipation): g and the state against the oracle."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(p)
+    u0 = states.add_uniform_noise(states.taylor_green(m, Mach=0.3), 1e-3, 9)
+    mu = 1.0 / 1600.0
+    prm = OP(mu=mu)
+    dt = states.cfl_timestep(m, u0, 0.2)
+    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True))
+    ud = s.to_device(u0)
+    uo = torch.as_tensor(u0)
+    rhs = lambda x: R.residual(x, op, m, prm, dissipation=True, viscous=True)
+    for step in range(3):
+        g, info = s.rrk_step(ud, dt)
+        uo, io = rrk.rrk4_step(uo, dt, rhs, op, m, prm)
+        assert abs(g - io.g) <= 1e-10, (step, g, io.g)
+        assert info.estimate < 0
+    assert rel_err(ud.cpu().numpy(), uo.numpy()) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("viscous", [False, True])
+def test_tet_vjp_matches_oracle_adjoint(lib, p, viscous):
+    R, Dg, rrk, OP = _oracle()
+    op, m = _tet(p, N=2)
+    u = states.random_positive_state(m.n_e, 3, op.n_p, seed=100 + p)
+    cot = np.random.default_rng(7).normal(size=u.shape)
+    prm = OP(mu=0.05) if viscous else OP()
+    s = lib.Solver(op, m, lib.Params(dissipation=True, viscous=viscous, mu=0.05 if viscous else 0.0))
+    g = s.residual_vjp(s.to_device(u), s.to_device(cot)).cpu().numpy()
+    x = torch.as_tensor(u).clone().requires_grad_(True)
+    r = R.residual(x, op, m, prm, dissipation=True, viscous=viscous)
+    (go,) = torch.autograd.grad(r, x, grad_outputs=torch.as_tensor(cot))
+    go = go.numpy()
+    err = np.abs(g - go).max() / np.abs(go).max()
+    print(f"tet p={p} vjp viscous={viscous} rel err {err:.2e}")
+    assert err <= 1e-11
+    s.close()

@@ -1,5 +1,7 @@
 """Pins of the seeded inputs: SBP operators (Def. 1, Sec. 2.1), curved
 periodic meshes (Assumption 1) and the vortex initial state (Sec. 7.3)."""
+from math import factorial
+
 import numpy as np
 import pytest
 
@@ -129,26 +131,52 @@ def test_vortex_solves_euler():
     assert np.abs(rho_bad - rho_ok).max() > 1e-2
 
 
-def test_tet_operator_sbp_and_accuracy():
+TET_SIZES = {1: (12, 3), 2: (25, 6), 3: (58, 12), 4: (78, 16)}
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_tet_face_rule_exact(p):
+    """The S3-symmetric face rule integrates every monomial of degree 2p on
+    the reference triangle exactly (Def. 1 asks degree >= 2p of the facet
+    quadrature) with positive weights and all points inside the face."""
+    from esplit_inputs.sbp import tri_face_rule
+    pts, w, _ = tri_face_rule(p)
+    assert len(w) == TET_SIZES[p][1] and np.all(w > 0) and np.all(pts > 1e-3)
+    assert np.allclose(pts.sum(1), 1.0, atol=1e-15)
+    for a in range(2 * p + 1):
+        for b in range(2 * p + 1 - a):
+            got = np.sum(w * pts[:, 1] ** a * pts[:, 2] ** b)
+            ex = factorial(a) * factorial(b) / factorial(a + b + 2)
+            assert abs(got - ex) < 1e-15
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_tet_operator_sbp_and_accuracy(p):
     from esplit_inputs import tet_operator
     from esplit_inputs.sbp import tet_monomial_integral
-    op = tet_operator(2)
-    assert op.n_p == 25 and op.n_fac == 4 and op.n_f == 6
+    op = tet_operator(p)
+    n_p, n_f = TET_SIZES[p]
+    assert (n_p is None or op.n_p == n_p) and op.n_fac == 4 and op.n_f == n_f
     assert np.all(op.H > 0) and abs(op.H.sum() - 1 / 6) < 1e-15
     for j in range(3):
         assert np.abs(op.Q[j] + op.Q[j].T - np.diag(op.E[j])).max() < 1e-14
-    V, dV = vandermonde(op.xi, 2, np.array([0.25, 0.25, 0.25]))
+    V, dV = vandermonde(op.xi, p, np.array([0.25, 0.25, 0.25]))
+    assert np.linalg.matrix_rank(V) == V.shape[1]
     for j in range(3):
-        assert np.abs(op.D[j] @ V - dV[j]).max() < 1e-11
+        assert np.abs(op.D[j] @ V - dV[j]).max() < 1e-10
+    # interior nodes strictly inside
+    lam = np.concatenate([op.xi, 1 - op.xi.sum(1, keepdims=True)], 1)[4 * n_f:]
+    assert len(lam) == 0 or lam.min() > 1e-3
     q = op.volume_degree
-    assert q >= 3
+    assert q >= 2 * p - 1
     for a in range(q + 1):
         for b in range(q + 1 - a):
             for c in range(q + 1 - a - b):
                 got = np.sum(op.H * op.xi[:, 0] ** a * op.xi[:, 1] ** b * op.xi[:, 2] ** c)
                 assert abs(got - tet_monomial_integral(a, b, c)) < 1e-15
-    # E is the boundary integral of products of quadratics: p^T E_j q = int d(PQ)/dxi_j
-    basis = monomial_basis(2, 3)
+    # E is the boundary integral of products of degree-p polynomials:
+    # p^T E_j q = int d(PQ)/dxi_j
+    basis = monomial_basis(p, 3)
     for j in range(3):
         for A in basis:
             for B in basis:
@@ -163,13 +191,14 @@ def test_tet_operator_sbp_and_accuracy():
                 assert abs(val - ref) < 1e-14
 
 
-def test_tet_mesh_pairing_normals_metrics():
+@pytest.mark.parametrize("p,N", [(1, 3), (2, 3), (3, 2), (4, 2)])
+def test_tet_mesh_pairing_normals_metrics(p, N):
     from esplit_inputs import tet_operator
     from esplit_inputs.mesh import periodic_tet_mesh
-    op = tet_operator(2)
-    m = periodic_tet_mesh(op, 3, 2 * np.pi, 0.02)
+    op = tet_operator(p)
+    m = periodic_tet_mesh(op, N, 2 * np.pi, 0.02)
     L = 2 * np.pi
-    assert m.n_e == 162 and np.all(m.J > 0)
+    assert m.n_e == 6 * N ** 3 and np.all(m.J > 0)
     assert abs(np.sum(m.J * op.H[None]) - L ** 3) < 1e-10
     fn = op.facet_nodes.reshape(-1)
     pe = m.pair[..., 0].reshape(m.n_e, -1)

@@ -198,18 +198,23 @@ def test_viscous_bo_entropy_and_conservation(heat):
     assert c.abs().max() < 1e-11 * float(rv.abs().max())
 
 
-def _tets(N=2, seed=1):
+TET_PS = [1, 2, 3, 4]
+
+
+def _tets(N=2, seed=1, p=2):
     from esplit_inputs import tet_operator
     from esplit_inputs.mesh import periodic_tet_mesh
-    op = tet_operator(2)
+    op = tet_operator(p)
     m = periodic_tet_mesh(op, N, 2 * np.pi, 0.02)
     return op, m, states.random_positive_state(m.n_e, 3, op.n_p, seed=seed)
 
 
+@pytest.mark.parametrize("p", TET_PS)
 @pytest.mark.parametrize("scheme", ["split", "hadamard", "hybrid"])
-def test_tet_entropy_conservation_and_forms(scheme):
-    """Thms. 2 and 4 on curved periodic tetrahedra; weak = strong form."""
-    op, m, u = _tets()
+def test_tet_entropy_conservation_and_forms(scheme, p):
+    """Thms. 2 and 4 on curved periodic tetrahedra (affine for p = 1); weak =
+    strong form."""
+    op, m, u = _tets(p=p)
     flags = np.random.default_rng(2).integers(0, 2, m.n_e)
     r = R.residual(u, op, m, P, scheme=scheme, hybrid_flags=flags)
     assert abs(float(Dg.entropy_rate(u, r, op, m, P))) < 1e-14 * float(Dg.entropy_rate_scale(u, r, op, m, P))
@@ -218,8 +223,9 @@ def test_tet_entropy_conservation_and_forms(scheme):
         assert (r - rs).abs().max() < 1e-13 * r.abs().max()
 
 
-def test_tet_freestream_and_dissipation_sign():
-    op, m, u = _tets()
+@pytest.mark.parametrize("p", TET_PS)
+def test_tet_freestream_and_dissipation_sign(p):
+    op, m, u = _tets(p=p)
     uf = states.uniform_state(m.n_e, 3, op.n_p)
     assert R.residual(uf, op, m, Params(mu=0.01), dissipation=True, viscous=True).abs().max() < 1e-11
     r0 = R.residual(u, op, m, P)
