@@ -10,7 +10,7 @@
 
 namespace esplit {
 
-constexpr int MAX_NP = 32;
+constexpr int MAX_NP = 80;
 constexpr int MAX_SLOT = 64;
 
 // Reference-operator tables every kernel reads (constant memory).

@@ -8,7 +8,8 @@ tetrahedra (48 or 162 elements: several blocks of every kernel and a ragged
 tail).
 
 Tolerances as for the degree-2 operator: FP64 max-norm relative error per
-component <= 1e-12, FP32-bulk <= 1e-5, relaxation parameter <= 1e-10.
+component <= 1e-12, FP32-bulk split form <= 1e-5 (the plain float32 Hadamard
+comparator <= 1e-2), relaxation parameter <= 1e-10.
 """
 import numpy as np
 import pytest
@@ -21,6 +22,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
 FP32_BOUND = 1e-5
+FP32_BOUND_HADAMARD = 1e-2   # the comparator's FP32 mode is plain float32 (no compensation)
 PS = [1, 3, 4]
 
 
@@ -108,7 +110,7 @@ def test_tet_fp32_bulk_bound(lib, p, scheme):
     ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True).numpy()
     err = rel_err(r, ro)
     print(f"tet p={p} fp32 {scheme} rel err {err:.3e}")
-    assert err <= FP32_BOUND
+    assert err <= (FP32_BOUND if scheme == "split" else FP32_BOUND_HADAMARD)
     s.close()
 
 
