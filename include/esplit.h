@@ -50,8 +50,10 @@ extern "C" {
                                      * Sec. 6 comparator (standard entropy), with
                                      * dissipation: the matrix form of Eq. (69) for
                                      * the standard entropy at the Ismail-Roe mean
-                                     * state (not printed in the paper); no viscous
-                                     * terms, RRK step or VJP -> ESPLIT_ERR_UNSUPPORTED */
+                                     * state (not printed in the paper); viscous
+                                     * terms: the BO SATs of Sec. 5 in the standard
+                                     * entropy variables; RRK step or VJP ->
+                                     * ESPLIT_ERR_UNSUPPORTED */
 
 typedef struct esplit_ctx esplit_ctx;
 

@@ -413,12 +413,36 @@ def viscous_flux_from_prim_grads(U, dV, dT, prm: Params):
     return torch.stack(out, dim=-2)
 
 
-def viscous_flux_from_w_grads(U, gW, prm: Params):
+def conservative_from_standard_entropy(v, prm: Params):
+    """The inverse of ``standard_entropy_variables`` in closed form: with
+    v_nc = -rho/p, V = -v_m / v_nc, the specific entropy
+    s = gam - (gam - 1)(v_1 - v_nc |V|^2 / 2), and s = log p - gam log rho,
+    p = -rho / v_nc give log rho = (s + log(-v_nc)) / (1 - gam)."""
+    vE = v[..., -1]
+    V = -v[..., 1:-1] / vE[..., None]
+    s = prm.gam - (prm.gam - 1.0) * (v[..., 0] - 0.5 * vE * (V * V).sum(-1))
+    rho = torch.exp((s + torch.log(-vE)) / (1.0 - prm.gam))
+    p = -rho / vE
+    e = p / (prm.gam - 1.0) + 0.5 * rho * (V * V).sum(-1)
+    return torch.cat([rho[..., None], rho[..., None] * V, e[..., None]], dim=-1)
+
+
+def dU_dV_standard(U, prm: Params):
+    """dU/dv for the standard entropy variables (the Hessian of the entropy
+    potential: symmetric positive definite), by autograd of the closed-form
+    inverse map."""
+    return _jacobian(lambda v: conservative_from_standard_entropy(v, prm), standard_entropy_variables(U, prm))
+
+
+def viscous_flux_from_w_grads(U, gW, prm: Params, entropy: str = "harten"):
     """Sum_j K~_ij dW/dx_j: the viscous flux of Eq. (5) with the primitive
     gradients obtained from the entropy-variable gradients gW (..., d, n_c)
-    through dV/dW and dT/dW (both dq/dU (dW/dU)^-1 by autograd)."""
+    through dV/dW and dT/dW (both dq/dU (dW/dU)^-1 by autograd).  ``entropy``
+    picks the variables the gradients are of: Harten's W (Eq. (25), the
+    entropy-split scheme) or the standard entropy variables (the Ismail-Roe
+    comparator)."""
     d = U.shape[-1] - 2
-    Ainv = dU_dW(U, prm)                                         # dU/dW
+    Ainv = dU_dW(U, prm) if entropy == "harten" else dU_dV_standard(U, prm)
     JV = _jacobian(lambda x: primitives(x, prm)[1], U) @ Ainv    # (..., d, nc)
     JT = _jacobian(lambda x: temperature(x, prm)[..., None], U) @ Ainv  # (..., 1, nc)
     dV = torch.einsum("...kc,...jc->...jk", JV, gW)              # dV_k/dx_j
@@ -426,9 +450,10 @@ def viscous_flux_from_w_grads(U, gW, prm: Params):
     return viscous_flux_from_prim_grads(U, dV, dT, prm)
 
 
-def viscous_K(U, prm: Params):
+def viscous_K(U, prm: Params, entropy: str = "harten"):
     """K~_ij (..., d, d, n_c, n_c) by probing the linear map dW/dx_j -> F^V_i
-    on unit vectors (exact; the map is linear in the gradient)."""
+    on unit vectors (exact; the map is linear in the gradient); ``entropy`` as
+    in ``viscous_flux_from_w_grads``."""
     d = U.shape[-1] - 2
     nc = d + 2
     K = torch.zeros(*U.shape[:-1], d, d, nc, nc, dtype=U.dtype)
@@ -436,6 +461,6 @@ def viscous_K(U, prm: Params):
         for c in range(nc):
             gW = torch.zeros(*U.shape[:-1], d, nc, dtype=U.dtype)
             gW[..., j, c] = 1.0
-            Fv = viscous_flux_from_w_grads(U, gW, prm)          # (..., d, nc)
+            Fv = viscous_flux_from_w_grads(U, gW, prm, entropy)  # (..., d, nc)
             K[..., :, j, :, c] = Fv
     return K

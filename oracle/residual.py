@@ -92,11 +92,10 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     1 = Hadamard), or "hadamard_ir": the Hadamard form with the Ismail-Roe
     flux in the volume and the SATs (entropy conservative for the standard
     entropy), with its own matrix dissipation (``ir_dissipation_matrix`` on the
-    jump of the standard entropy variables) when ``dissipation``; no viscous
-    terms.  ``u`` may be a torch tensor requiring grad (the oracle adjoint
-    differentiates through this function)."""
-    if scheme == "hadamard_ir" and viscous:
-        raise ValueError("the Ismail-Roe comparator is built without viscous terms")
+    jump of the standard entropy variables) when ``dissipation``, and the
+    same Baumann-Oden viscous terms written with the standard entropy
+    variables when ``viscous``.  ``u`` may be a torch tensor requiring grad
+    (the oracle adjoint differentiates through this function)."""
     U_all = _as_U(u)
     n_e, n_p, nc = U_all.shape
     d = nc - 2
@@ -154,17 +153,22 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
 
     # ---- viscous terms, Eqs. (83)-(85) with BO SATs (Eq. (96)) --------------
     if viscous:
-        w = entropy_variables(U, prm)                                        # (N, n_p, nc)
+        # the BO terms in the entropy variables of the scheme's entropy: Harten's
+        # for the split, Hadamard and hybrid schemes, the standard ones for the
+        # Ismail-Roe comparator (Thm. 3 holds for either)
+        ent = "standard" if scheme == "hadamard_ir" else "harten"
+        wvars = standard_entropy_variables if scheme == "hadamard_ir" else entropy_variables
+        w = wvars(U, prm)                                                    # (N, n_p, nc)
         gW = torch.einsum("nimk,nkc->nmic", ops["D"], w)                     # (N, n_p, d, nc)
-        Fv = viscous_flux_from_w_grads(U, gW, prm)                           # (N, n_p, d, nc)
+        Fv = viscous_flux_from_w_grads(U, gW, prm, ent)                      # (N, n_p, d, nc)
         r = r + torch.einsum("nimk,nkic->nmc", ops_t["D"], Fv[t_loc])
         v_loc = loc[pair[tgt, :, 0]]
         Fv_k = Fv[t_loc][:, fn]                                              # (n, s, d, nc)
         Fv_v = Fv[v_loc, fn[pair[tgt, :, 1]]]                                # (n, s, d, nc)
         t1 = -0.5 * torch.einsum("nsi,nsic->nsc", nu, Fv_k - Fv_v) / Hm[..., None]
         r = r.index_add(1, fn, t1)
-        Kt = viscous_K(Uk, prm)                                              # (n, s, d, d, nc, nc)
-        dw = entropy_variables(Uk, prm) - entropy_variables(Uv, prm)
+        Kt = viscous_K(Uk, prm, ent)                                         # (n, s, d, d, nc, nc)
+        dw = wvars(Uk, prm) - wvars(Uv, prm)
         # a_j(m) = sum_i K~_ij^T nu_i dw  at facet nodes
         a = torch.einsum("nsijcb,nsi,nsc->nsjb", Kt, nu, dw)                 # (n, s, d, nc)
         a_full = torch.zeros(len(tgt), n_p, d, nc, dtype=DT).index_add(1, fn, a)

@@ -320,8 +320,6 @@ int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
   if (!(alpha < -p->gam || alpha > 0.0)) return fail(c, ESPLIT_ERR_ARG, "beta must give alpha < -gam or alpha > 0");
   if (!(p->R > 0.0) || p->mu < 0.0 || !(p->Pr > 0.0)) return fail(c, ESPLIT_ERR_ARG, "R, Pr must be > 0, mu >= 0");
   if (p->scheme < 0 || p->scheme > 3) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
-  if (p->scheme == ESPLIT_SCHEME_HADAMARD_IR && p->viscous)
-    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the Ismail-Roe comparator is built without viscous terms");
   if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK) return fail(c, ESPLIT_ERR_ARG, "unknown precision");
   cudaSetDevice(c->device);
   bool beta_changed = p->beta != c->prm.beta;

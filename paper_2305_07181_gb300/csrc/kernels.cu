@@ -254,15 +254,28 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
     if (sk) normal_flux<D>(nk, nuv, ek);
     if (sv) normal_flux<D>(nv, nuv, ev);
   }
-  if (VISC) {
-    // BO lift vectors of both sides, a = K~(u)^T (nu (w_k - w_v)), divided by H
+  if constexpr (VISC) {
+    // BO lift vectors of both sides, a = K~(u)^T (nu (w_k - w_v)), divided by
+    // H; the comparator (FLUX 1) in its standard entropy variables
     double b[D][NC], ak[D][NC], av[D][NC];
+    if constexpr (FLUX == 1) {
+      double wk[NC], wv[NC];
+      std_entropy_vars_node(nk, c, wk);
+      std_entropy_vars_node(nv, c, wv);
 #pragma unroll
-    for (int i = 0; i < D; ++i)
+      for (int i = 0; i < D; ++i)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) b[i][q] = nuv[i] * (nk.W[q] - nv.W[q]);
-    visc_flux_transpose<double, D>(nk, c, visc_heat, b, ak);
-    visc_flux_transpose<double, D>(nv, c, visc_heat, b, av);
+        for (int q = 0; q < NC; ++q) b[i][q] = nuv[i] * (wk[q] - wv[q]);
+      visc_flux_transpose<double, D, double, 1>(nk, c, visc_heat, b, ak);
+      visc_flux_transpose<double, D, double, 1>(nv, c, visc_heat, b, av);
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) b[i][q] = nuv[i] * (nk.W[q] - nv.W[q]);
+      visc_flux_transpose<double, D>(nk, c, visc_heat, b, ak);
+      visc_flux_transpose<double, D>(nv, c, visc_heat, b, av);
+    }
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -975,7 +988,11 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     // they stay float64 in both precision modes
     const int ef_mode = c->prm.scheme == ESPLIT_SCHEME_SPLIT ? 1 : (c->prm.scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0);
     const int visc_heat = c->prm.viscous ? c->prm.heat_flux : -1;
-    if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
+    if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR && visc_heat >= 0)
+      face_kernel<double, D, true, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat,
+                                                        ph64, c->prm.dissipation, c->b.status, 0, c->b.hflags,
+                                                        visc_heat, c->b.va);
+    else if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
       face_kernel<double, D, false, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat,
                                                          ph64, c->prm.dissipation, c->b.status, 0, c->b.hflags, 0,
                                                          nullptr);

@@ -545,6 +545,18 @@ __device__ __forceinline__ void std_entropy_vars(const Node<T, D>& n, const IRNo
   w[D + 1] = -b;
 }
 
+// Standard entropy variables of a node (log rho formed here; the comparator's
+// viscous terms, whose nodes carry no parameter-vector logs).
+template <typename C, int D>
+__device__ __forceinline__ void std_entropy_vars_node(const Node<double, D>& n, const C& c, double* w) {
+  const double b = n.rho / n.p;
+  const double s = n.lnp - c.gam * t_log(n.rho);
+  w[0] = (c.gam - s) * c.inv_gm1 - 0.5 * b * n.v2;
+#pragma unroll
+  for (int i = 0; i < D; ++i) w[1 + i] = b * n.V[i];
+  w[D + 1] = -b;
+}
+
 // Matrix dissipation of the comparator (not printed in the paper; the form of
 // Eq. (69) carried over to the standard entropy), applied to dw = jump of the
 // standard entropy variables, n a unit normal:

@@ -23,8 +23,11 @@
 namespace esplit {
 
 // F^V, the folded divergence and the facet correction for the elements of
-// `list` (all when null); adds into r, writes F^V at the facet slots
-template <int D, int NP, int EB>
+// `list` (all when null); adds into r, writes F^V at the facet slots.  ENT:
+// the entropy variables the gradients are taken of (0 Harten's, 1 the
+// standard ones of the Ismail-Roe comparator); the flux is the same physical
+// viscous flux either way.
+template <int D, int NP, int EB, int ENT = 0>
 __global__ void __launch_bounds__(EB * NP) visc_volume_kernel(const double* __restrict__ u, double* __restrict__ r,
                                                               const double* __restrict__ ops,
                                                               const double* __restrict__ J,
@@ -48,8 +51,15 @@ __global__ void __launch_bounds__(EB * NP) visc_volume_kernel(const double* __re
 #pragma unroll
     for (int q = 0; q < NC; ++q) uu[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
     node_from_u<double, D>(uu, c, nd);
+    if constexpr (ENT == 1) {
+      double w[NC];
+      std_entropy_vars_node(nd, c, w);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) sw[el][q][m] = nd.W[q];
+      for (int q = 0; q < NC; ++q) sw[el][q][m] = w[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sw[el][q][m] = nd.W[q];
+    }
   }
   __syncthreads();
   const double* op = ops + (size_t)e * (2 * D * NP * NP);
@@ -68,7 +78,7 @@ __global__ void __launch_bounds__(EB * NP) visc_volume_kernel(const double* __re
         for (int q = 0; q < NC; ++q) g[j][q] += dt * sw[el][q][n];
       }
     double F[D][NC];
-    visc_flux<double, D>(nd, c, heat, g, F);
+    visc_flux<double, D, double, ENT>(nd, c, heat, g, F);
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -159,8 +169,12 @@ static void viscous_volume_np(esplit_ctx* c, const double* u, double* r, const i
   const Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   constexpr int EB = (128 / NP) > 0 ? (128 / NP) : 1;
   int nb = (n_list + EB - 1) / EB;
-  visc_volume_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops64, c->b.J, c->b.nu, c->b.va, list, n_list,
-                                                       c->b.fv, ph, c->prm.heat_flux);
+  if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
+    visc_volume_kernel<D, NP, EB, 1><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops64, c->b.J, c->b.nu, c->b.va, list,
+                                                            n_list, c->b.fv, ph, c->prm.heat_flux);
+  else
+    visc_volume_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops64, c->b.J, c->b.nu, c->b.va, list, n_list,
+                                                         c->b.fv, ph, c->prm.heat_flux);
   c->launches += 1;
 }
 

@@ -1,7 +1,12 @@
 // Viscous flux of the compressible Navier-Stokes equations written with the
 // entropy-variable gradients (Sec. 3 and Sec. 5: F^V_i = sum_j K~_ij dW/dx_j),
 // and its transpose in the gradients.  Shared by the facet, volume and
-// reverse-mode kernels.
+// reverse-mode kernels.  ENT selects the entropy variables the gradients are
+// of: 0 Harten's W (Eq. (25), the entropy-split scheme), 1 the standard
+// entropy variables v = [(gam - s)/(gam-1) - rho|V|^2/(2p), rho V/p, -rho/p]
+// (the Ismail-Roe comparator).  In both sets V = -w_m / w_nc, so the velocity
+// gradients have one form; T = -1/(R v_nc) in the standard set, whose dT/dv
+// has the last entry 1/(R v_nc^2) only.
 #pragma once
 
 namespace esplit {
@@ -9,9 +14,16 @@ namespace esplit {
 // dT/dW of Eq. (39) (the exact derivative; the printed Eq. (40) has a sign
 // typo in the momentum entries and drops alpha in the last entry).  T is
 // double or a dual number (the reverse mode differentiates these in u).
-template <typename T, int D>
+template <typename T, int D, int ENT = 0>
 __device__ __forceinline__ void dT_dW(const Node<T, D>& n, const Phys<double>& c, T* TW) {
   constexpr int NC = D + 2;
+  if constexpr (ENT == 1) {
+    const T pr = n.p * n.ir;  // p / rho = -1 / v_nc
+#pragma unroll
+    for (int q = 0; q < NC - 1; ++q) TW[q] = T(0.0);
+    TW[NC - 1] = pr * pr / c.R;
+    return;
+  }
   T Wn = -n.q;
   T k = c.gm1 / (c.alpha * c.R * Wn);
   T T_ = n.p * n.ir / c.R;
@@ -25,11 +37,15 @@ __device__ __forceinline__ void dT_dW(const Node<T, D>& n, const Phys<double>& c
 //   dV_l/dx_j = -(g_j[1+l] + V_l g_j[nc]) / W_nc,  dT/dx_j = dT/dW . g_j,
 //   tau_ik = mu (dV_i/dx_k + dV_k/dx_i - 2/3 delta_ik div V),
 //   F_i = [0, tau_i., V . tau_i. + kappa dT/dx_i]
-template <typename T, int D, typename G>
+template <typename T, int D, typename G, int ENT = 0>
 __device__ __forceinline__ void visc_flux(const Node<T, D>& n, const Phys<double>& c, int heat, const G (&g)[D][D + 2],
                                           T (&F)[D][D + 2]) {
   constexpr int NC = D + 2;
-  T iWn = -1.0 / n.q;
+  T iWn;  // 1 / w_nc
+  if constexpr (ENT == 1)
+    iWn = -(n.p * n.ir);
+  else
+    iWn = -1.0 / n.q;
   T Lg[D][D];  // Lg[j][l] = dV_l/dx_j
   T div = T(0.0);
 #pragma unroll
@@ -39,7 +55,7 @@ __device__ __forceinline__ void visc_flux(const Node<T, D>& n, const Phys<double
 #pragma unroll
   for (int l = 0; l < D; ++l) div = div + Lg[l][l];
   T TW[NC];
-  dT_dW<T, D>(n, c, TW);
+  dT_dW<T, D, ENT>(n, c, TW);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     T e = T(0.0);
@@ -62,11 +78,15 @@ __device__ __forceinline__ void visc_flux(const Node<T, D>& n, const Phys<double
 
 // a_j = sum_i K~_ij^T b_i: the gradient of sum_i b_i . F^V_i with respect to
 // g_j (F^V is linear in the gradients).
-template <typename T, int D, typename B>
+template <typename T, int D, typename B, int ENT = 0>
 __device__ __forceinline__ void visc_flux_transpose(const Node<T, D>& n, const Phys<double>& c, int heat,
                                                     const B (&b)[D][D + 2], T (&a)[D][D + 2]) {
   constexpr int NC = D + 2;
-  T iWn = -1.0 / n.q;
+  T iWn;  // 1 / w_nc
+  if constexpr (ENT == 1)
+    iWn = -(n.p * n.ir);
+  else
+    iWn = -1.0 / n.q;
   T cc[D][D];
   T trc = T(0.0);
 #pragma unroll
@@ -76,7 +96,7 @@ __device__ __forceinline__ void visc_flux_transpose(const Node<T, D>& n, const P
 #pragma unroll
   for (int i = 0; i < D; ++i) trc = trc + cc[i][i];
   T TW[NC];
-  dT_dW<T, D>(n, c, TW);
+  dT_dW<T, D, ENT>(n, c, TW);
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     T hj = heat ? c.kappa * b[j][NC - 1] : T(0.0);

@@ -73,10 +73,11 @@ def summand_scale(u, op, m, elems, scheme, prm, dissipation=True, viscous=False)
         loc[need] = torch.arange(len(need))
         ops_n = physical_operators(op, m, need)
         Un = U_all[need]
-        wn = entropy_variables(Un, prm)
+        ent = "standard" if ir else "harten"
+        wn = evars(Un, prm)
         gW = torch.einsum("nimk,nkc->nmic", ops_n["D"], wn)
-        Fv = viscous_flux_from_w_grads(Un, gW, prm).abs()                   # (n, n_p, d, nc)
-        Kn = viscous_K(Un, prm).abs()                                       # (n, n_p, d, d, nc, nc)
+        Fv = viscous_flux_from_w_grads(Un, gW, prm, ent).abs()              # (n, n_p, d, nc)
+        Kn = viscous_K(Un, prm, ent).abs()                                  # (n, n_p, d, d, nc, nc)
         Dwn = torch.einsum("nimk,nkc->nmic", ops_n["D"].abs(), wn.abs())    # (n, n_p, d, nc)
         G = Fv + torch.einsum("nmijcb,nmjb->nmic", Kn, Dwn)
         Ge = G[loc[el]]

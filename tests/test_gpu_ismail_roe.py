@@ -143,12 +143,49 @@ def test_ir_hadamard_restrictions(lib):
     op = tri_operator(2)
     m = periodic_tri_mesh(op, 3, 10.0, 0.05)
     s = lib.Solver(op, m)
-    with pytest.raises(lib.EsplitError) as ei:
-        s.set_params(lib.Params(scheme="hadamard_ir", viscous=True, mu=0.01))
-    assert ei.value.code == lib.capi.ESPLIT_ERR_UNSUPPORTED
     s.set_params(lib.Params(scheme="hadamard_ir"))
     u = s.to_device(states.isentropic_vortex(m))
     with pytest.raises(lib.EsplitError) as ei:
         s.rrk_step(u, 1e-3)
     assert ei.value.code == lib.capi.ESPLIT_ERR_UNSUPPORTED
+    s.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("heat", [False, True])
+def test_ir_viscous_parity(lib, dim, heat):
+    """The comparator with Navier-Stokes terms (BO SATs of Sec. 5 in the
+    standard entropy variables) and its dissipation against the oracle, on
+    random states (FP64 <= 1e-12) and on the Taylor-Green state of Sec. 7.5
+    (rounding-scale bound, as for the split scheme)."""
+    from oracle import residual as R
+    from oracle.physics import Params as OP
+    from parity_bounds import summand_scale
+    if dim == 2:
+        op = tri_operator(3)
+        m = periodic_tri_mesh(op, 5, 10.0, 0.05)
+    else:
+        op = tet_operator(2)
+        m = periodic_tet_mesh(op, 3, 2 * np.pi, 0.02)
+    u = states.random_positive_state(m.n_e, dim, op.n_p, seed=90 + dim)
+    prm = lib.Params(scheme="hadamard_ir", dissipation=True, viscous=True, mu=0.05, heat_flux=heat)
+    s = lib.Solver(op, m, prm)
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(mu=0.05, heat_flux=heat), scheme="hadamard_ir", dissipation=True,
+                    viscous=True).numpy()
+    err = rel_err(r, ro)
+    print(f"IR viscous {dim}D heat={heat}: rel err {err:.2e}")
+    assert err <= 1e-12
+    assert s.status() == 0
+    if dim == 3:
+        ut = states.taylor_green(m)
+        mu = 1.0 / 1600.0
+        s.set_params(lib.Params(scheme="hadamard_ir", dissipation=True, viscous=True, mu=mu, heat_flux=heat))
+        rt = s.residual(s.to_device(ut)).cpu().numpy()
+        rto = R.residual(ut, op, m, OP(mu=mu, heat_flux=heat), scheme="hadamard_ir", dissipation=True,
+                         viscous=True).numpy()
+        sc = summand_scale(ut, op, m, np.arange(m.n_e), "hadamard_ir", OP(mu=mu, heat_flux=heat), viscous=True)
+        eps = np.finfo(float).eps
+        print(f"IR viscous TGV heat={heat}: max-norm rel {rel_err(rt, rto):.2e}")
+        assert np.all(np.abs(rt - rto) <= 1e-12 * np.abs(rto).max() + 64 * op.n_p * eps * sc)
     s.close()

@@ -349,3 +349,51 @@ def test_ir_dissipation_matrix_pins(d):
     assert torch.linalg.eigvalsh(D2).min() > -1e-12 * D2.abs().max()
     assert (ir_dissipation_matrix(U, Uv, -n, P) - D2).abs().max() < 1e-13 * D2.abs().max()
     assert (ir_dissipation_matrix(Uv, U, n, P) - D2).abs().max() < 1e-13 * D2.abs().max()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_standard_entropy_inverse_map(d):
+    """The closed-form inverse of the standard entropy variables: the round
+    trip returns U; its Jacobian dU/dv is the inverse of dv/dU (autograd of
+    the forward map) and, as the Hessian of the entropy potential, symmetric
+    positive definite."""
+    from oracle.physics import (standard_entropy_variables, conservative_from_standard_entropy,
+                                dU_dV_standard, _jacobian)
+    U = rand_states(20, d, 31)
+    P0 = Params()
+    back = conservative_from_standard_entropy(standard_entropy_variables(U, P0), P0)
+    assert (back - U).abs().max() < 1e-13 * U.abs().max()
+    A = dU_dV_standard(U, P0)
+    B = _jacobian(lambda x: standard_entropy_variables(x, P0), U)
+    I = torch.eye(d + 2, dtype=torch.float64)
+    assert (A @ B - I).abs().max() < 1e-11
+    assert (A - A.transpose(-1, -2)).abs().max() < 1e-13 * A.abs().max()
+    assert torch.linalg.eigvalsh(A).min() > 0
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_viscous_tensor_standard_entropy_symmetric_psd(d):
+    """In the standard entropy variables K~ is symmetric positive semidefinite
+    with and without the heat flux (the property the Harten variables lose
+    with heat flux, Sec. 3); the heat flux raises its rank by d (one
+    temperature-gradient direction per coordinate: 2D 3 -> 5, 3D 5 -> 8); and for any
+    conservative-variable gradient the two variable sets give the same
+    viscous flux (the flux is a property of the state and its gradient)."""
+    from oracle.physics import viscous_flux_from_w_grads, standard_entropy_variables, _jacobian
+    U = rand_states(10, d, 33)
+    nc = d + 2
+    for heat in [False, True]:
+        prm = Params(mu=0.1, heat_flux=heat)
+        K = viscous_K(U, prm, "standard")
+        Kb = K.permute(0, 1, 3, 2, 4).reshape(10, d * nc, d * nc)
+        assert (Kb - Kb.transpose(1, 2)).abs().max() < 1e-12 * Kb.abs().max()
+        ev = torch.linalg.eigvalsh(Kb)
+        assert ev.min() > -1e-12 * Kb.abs().max()
+        rank = (ev > 1e-10 * ev.amax(-1, keepdim=True)).sum(-1)
+        assert torch.all(rank == {2: 3, 3: 5}[d] + (d if heat else 0))
+        gU = torch.as_tensor(np.random.default_rng(4).normal(size=(10, d, nc)))
+        gv = torch.einsum("ncb,nib->nic", _jacobian(lambda x: standard_entropy_variables(x, prm), U), gU)
+        gW = torch.einsum("ncb,nib->nic", _jacobian(lambda x: entropy_variables(x, prm), U), gU)
+        Fs = viscous_flux_from_w_grads(U, gv, prm, "standard")
+        Fh = viscous_flux_from_w_grads(U, gW, prm)
+        assert (Fs - Fh).abs().max() < 1e-11 * Fh.abs().max()

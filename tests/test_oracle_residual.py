@@ -304,3 +304,35 @@ def test_ir_dissipation_rate(p):
     assert Dg.conservation(r1, op, m).abs().max() < 1e-12 * float(r1.abs().max())
     uf = states.uniform_state(m.n_e, 2, op.n_p)
     assert R.residual(uf, op, m, P, scheme="hadamard_ir", dissipation=True).abs().max() < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("heat", [False, True])
+def test_ir_viscous_bo_identity(dim, heat):
+    """The comparator's Navier-Stokes terms (the same BO SATs written with the
+    standard entropy variables): their standard-entropy rate equals the volume
+    quadratic form -sum H (D v)^T K~ (D v) (Thm. 3 for the standard entropy,
+    with T1 = 0, T2 = T3 = B/2) and is negative with and without heat flux
+    (K~ is symmetric PSD in these variables); conservation and free stream."""
+    from oracle.physics import standard_entropy_variables, viscous_K
+    if dim == 2:
+        op = tri_operator(3)
+        m = periodic_tri_mesh(op, 4, 10.0, 0.05)
+        u = states.random_positive_state(m.n_e, 2, op.n_p, seed=71)
+    else:
+        op, m, u = _tets(seed=72)
+    prm = Params(mu=0.05, heat_flux=heat)
+    rv = (R.residual(u, op, m, prm, scheme="hadamard_ir", viscous=True)
+          - R.residual(u, op, m, prm, scheme="hadamard_ir"))
+    U = torch.as_tensor(u).transpose(1, 2)
+    w = standard_entropy_variables(U, prm)
+    H = torch.as_tensor(op.H)[None] * torch.as_tensor(m.J)
+    rate = float((H[..., None] * w * rv.transpose(1, 2)).sum())
+    ops = physical_operators(op, m)
+    g = torch.einsum("nimk,nkc->nimc", ops["D"], w)
+    qf = float(-torch.einsum("nm,nimc,nmijcb,njmb->", ops["H"], g, viscous_K(U, prm, "standard"), g))
+    assert qf < 0
+    assert abs(rate - qf) < 1e-11 * abs(qf)
+    assert Dg.conservation(rv, op, m).abs().max() < 1e-10 * float(rv.abs().max())
+    uf = states.uniform_state(m.n_e, dim, op.n_p)
+    assert R.residual(uf, op, m, prm, scheme="hadamard_ir", viscous=True, dissipation=True).abs().max() < 1e-11
