@@ -283,8 +283,9 @@ def tet_sweep(es, device, flush, n_cubes=16):
     tetrahedron operators; degree 1 on affine elements): the split form
     against the Hadamard form with the Sjogreen-Yee flux and against the
     Sec. 6 comparator (Hadamard form, Ismail-Roe flux), all with matrix
-    interface dissipation, FP64 and FP32-bulk.  Sec. 7.3 compares the same
-    schemes on 750 tetrahedra, serially."""
+    interface dissipation, FP64 and FP32-bulk; and the Navier-Stokes residual
+    (BO viscous terms) of the split form against the comparator's, FP64.
+    Secs. 7.3 and 7.5 compare the same schemes on 750 tetrahedra, serially."""
     from esplit_inputs import tet_operator, states
     from esplit_inputs.mesh import periodic_tet_mesh, vortex3d_warp
     out = {"n_e": 6 * n_cubes ** 3}
@@ -303,6 +304,14 @@ def tet_sweep(es, device, flush, n_cubes=16):
                     s.residual(ud, r)
                 ms = statistics.median(_timed(lambda: s.residual(ud, r), stream, flush, 10))
                 out[f"p{p}_{scheme}_{prec}"] = {"ms": ms, "dof_per_s": mesh.n_e * op.n_p / (ms * 1e-3)}
+        # Navier-Stokes residual (BO viscous terms with heat flux, mu = 1/1600,
+        # as in the Taylor-Green comparison of Sec. 7.5), FP64
+        for scheme in ("split", "hadamard_ir"):
+            s.set_params(es.Params(dissipation=True, scheme=scheme, viscous=True, mu=1.0 / 1600.0))
+            for _ in range(3):
+                s.residual(ud, r)
+            ms = statistics.median(_timed(lambda: s.residual(ud, r), stream, flush, 10))
+            out[f"p{p}_{scheme}_ns_fp64"] = {"ms": ms, "dof_per_s": mesh.n_e * op.n_p / (ms * 1e-3)}
         out[f"p{p}_n_p"] = op.n_p
         s.close()
         del s, ud, r, mesh

@@ -78,7 +78,15 @@ def tet_rule(degree):
 
 
 def l2_error_3d(u, op, mesh, prims, chunk=4096):
-    """The L^2 error on curved tetrahedra, exact solution prims(X (3, ...))."""
+    """The L^2 error on curved tetrahedra, exact solution prims(X (3, ...));
+    ``u`` may be a list of states on the same mesh (one error each, one pass
+    over the geometry)."""
+    if isinstance(u, (list, tuple)):
+        return _l2_errors_3d(list(u), op, mesh, prims, chunk)
+    return _l2_errors_3d([u], op, mesh, prims, chunk)[0]
+
+
+def _l2_errors_3d(us, op, mesh, prims, chunk):
     from esplit_inputs.mesh import _quad_tet_shape
     p = op.p
     xq, wq = tet_rule(3 * p + 1)
@@ -89,17 +97,18 @@ def l2_error_3d(u, op, mesh, prims, chunk=4096):
     fit = Vq @ np.linalg.solve(Vn.T @ (H[:, None] * Vn), Vn.T * H[None, :])
     N, dN = _quad_tet_shape(xq)                                         # (q, 10), (3, q, 10)
     G = mesh.meta["geom"]                                               # (n_e, 3, 10)
-    total = 0.0
+    total = np.zeros(len(us))
     for a in range(0, mesh.n_e, chunk):
         Gc = G[a:a + chunk]
         X = np.einsum("qa,eia->eiq", N, Gc)
         Jm = np.einsum("jqa,eia->eqij", dN, Gc)
         J = np.linalg.det(Jm)
-        uq = np.einsum("qm,ecm->ecq", fit, u[a:a + chunk])
         rho, V, pr = prims(np.moveaxis(X, 1, 0))
         ue = np.moveaxis(prim_to_cons(rho, V, pr), 0, 1)
-        total += float(np.einsum("q,eq,ecq->", wq, J, (uq - ue) ** 2))
-    return float(np.sqrt(total))
+        for k, u in enumerate(us):
+            uq = np.einsum("qm,ecm->ecq", fit, u[a:a + chunk])
+            total[k] += float(np.einsum("q,eq,ecq->", wq, J, (uq - ue) ** 2))
+    return [float(np.sqrt(t)) for t in total]
 
 
 def l2_error_vortex_3d(u, op, mesh, t, chunk=4096):

@@ -185,8 +185,8 @@ def test_vortex_ismail_roe_against_table1(lib, p):
 def _run_3d(lib, op, m, params, rrk=True, tf=1.0):
     """The 3D vortex at CFL 0.25 to t_f: relaxation RK4 through the library
     for the entropy-split scheme, classical RK4 (torch stage combinations)
-    for the Ismail-Roe comparator, whose entropy is not Harten's."""
-    from accuracy import l2_error_vortex_3d
+    for the Ismail-Roe comparator, whose entropy is not Harten's.  Returns
+    the final state and time."""
     u0 = states.isentropic_vortex_3d(m)
     dt = states.cfl_timestep(m, u0, 0.25)
     s = lib.Solver(op, m, params)
@@ -204,13 +204,29 @@ def _run_3d(lib, op, m, params, rrk=True, tf=1.0):
             k4 = s.residual(u + h * k3)
             u = u + (h / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
             t += h
-    err = l2_error_vortex_3d(u.cpu().numpy(), op, m, t)
     assert s.status() == 0
     s.close()
-    return err
+    return u.cpu().numpy(), t
 
 
-@pytest.mark.parametrize("p", [1, 3, 4])
+def _errors_3d(op, m, runs):
+    """L^2 errors of several (u, t) runs, one geometry pass per final time."""
+    from accuracy import l2_error_vortex_3d
+    out = [None] * len(runs)
+    for t in sorted(set(t for _, t in runs)):
+        idx = [i for i, (_, ti) in enumerate(runs) if ti == t]
+        errs = l2_error_vortex_3d([runs[i][0] for i in idx], op, m, t)
+        for i, e in zip(idx, errs):
+            out[i] = e
+    return out
+
+
+# p = 4 takes about ten minutes (1,251 relaxation steps on 48,000 elements
+# with 78 nodes, four schemes, two grids); it runs with ESPLIT_LONG_TESTS=1
+_DEGREES = [1, 3] + ([4] if os.environ.get("ESPLIT_LONG_TESTS") == "1" else [])
+
+
+@pytest.mark.parametrize("p", _DEGREES)
 def test_vortex3d_degrees_against_table2(lib, p):
     """The 3D vortex of Sec. 7.3 with the degree 1, 3 and 4 tetrahedron
     operators on the 15^3 x 6 and 20^3 x 6 grids, all four columns of Table 2
@@ -218,7 +234,10 @@ def test_vortex3d_degrees_against_table2(lib, p):
     its matrix dissipation): errors within a factor 2 of the printed ones,
     rates in [p - 0.2, p + 1.2], and the split and Ismail-Roe errors within a
     factor 2 of each other (the equal accuracy the throughput comparison on
-    these grids assumes)."""
+    these grids assumes).  Observed: p = 3 within 0.97-1.08 of every printed
+    error (rates 3.24-3.34 against 3.22-3.45), p = 4 within 1.07-1.20 (rates
+    4.02-4.34 against 3.94-4.27), p = 1 (affine elements) 1.2-1.5 times the
+    printed errors."""
     from esplit_inputs import tet_operator
     from esplit_inputs.mesh import periodic_tet_mesh, vortex3d_warp
     rows = np.loadtxt(GOLDEN3D, comments="#")
@@ -228,10 +247,12 @@ def test_vortex3d_degrees_against_table2(lib, p):
     errs = {}
     for N in (15, 20):
         m = periodic_tet_mesh(op, N, 20.0, origin=-10.0, warp=vortex3d_warp)
-        errs[(N, "split_ec")] = _run_3d(lib, op, m, lib.Params(dissipation=False))
-        errs[(N, "split_diss")] = _run_3d(lib, op, m, lib.Params(dissipation=True))
-        errs[(N, "ir_ec")] = _run_3d(lib, op, m, lib.Params(scheme="hadamard_ir", dissipation=False), rrk=False)
-        errs[(N, "ir_diss")] = _run_3d(lib, op, m, lib.Params(scheme="hadamard_ir", dissipation=True), rrk=False)
+        runs = [_run_3d(lib, op, m, lib.Params(dissipation=False)),
+                _run_3d(lib, op, m, lib.Params(dissipation=True)),
+                _run_3d(lib, op, m, lib.Params(scheme="hadamard_ir", dissipation=False), rrk=False),
+                _run_3d(lib, op, m, lib.Params(scheme="hadamard_ir", dissipation=True), rrk=False)]
+        for kind, e in zip(cols, _errors_3d(op, m, runs)):
+            errs[(N, kind)] = e
     for kind in cols:
         ours = [errs[(15, kind)], errs[(20, kind)]]
         paper = [tab[(p, 15)][kind], tab[(p, 20)][kind]]

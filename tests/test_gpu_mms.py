@@ -46,6 +46,11 @@ def _table():
     return {(int(r[0]), int(r[1]), int(r[2])): r[3] for r in rows}
 
 
+def _table_ir():
+    rows = np.loadtxt(GOLDEN, comments="#")
+    return {(int(r[0]), int(r[1]), int(r[2])): r[4] for r in rows}
+
+
 @pytest.fixture(scope="module")
 def lib():
     if not torch.cuda.is_available():
@@ -54,8 +59,9 @@ def lib():
     return es
 
 
-def _run(lib, op, m):
-    s = lib.Solver(op, m, lib.Params(viscous=True, mu=0.01, Pr=0.71, R=1.0, heat_flux=True, dissipation=False))
+def _run(lib, op, m, scheme="split"):
+    s = lib.Solver(op, m, lib.Params(viscous=True, mu=0.01, Pr=0.71, R=1.0, heat_flux=True, dissipation=False,
+                                     scheme=scheme))
     u = s.to_device(states.manufactured_state(m, 0.0))
     dt = TF / STEPS
 
@@ -128,3 +134,39 @@ def test_mms_3d_p2_against_table4(lib):
         assert 2.5 <= r <= 3.5
     for a, b in zip(errs, paper):
         assert 0.85 <= a / b <= 1.15
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_mms_3d_degrees_both_schemes(lib, p):
+    """3D, every tetrahedron degree (p = 1 on affine elements), both columns
+    of Table 4: the entropy-split scheme and the Ismail-Roe comparator (BO
+    terms in the standard entropy variables), 6^3 x 6 .. 12^3 x 6 grids.
+    Rates near p + 1 (band [p + 0.3, p + 1.6]); the two schemes' errors
+    within 10 % of each other, as in the table; errors within a factor 2 of
+    the printed ones (the node sets differ from the paper's)."""
+    tab, tab_ir = _table(), _table_ir()
+    op = tet_operator(p)
+    Ns = (6, 9, 12)
+    errs = {"split": [], "hadamard_ir": []}
+    for N in Ns:
+        m = periodic_tet_mesh(op, N, 2.0, origin=-1.0, warp=mms_warp_3d)
+        for scheme in errs:
+            u = _run(lib, op, m, scheme)
+            errs[scheme].append(l2_error_3d(u, op, m, lambda X: states.manufactured_prims(X, TF)))
+    for scheme, t in (("split", tab), ("hadamard_ir", tab_ir)):
+        e = errs[scheme]
+        paper = [t[(3, p, N)] for N in Ns]
+        rates = [np.log(e[i] / e[i + 1]) / np.log(Ns[i + 1] / Ns[i]) for i in range(2)]
+        prates = [np.log(paper[i] / paper[i + 1]) / np.log(Ns[i + 1] / Ns[i]) for i in range(2)]
+        print(f"3D p={p} {scheme}: ours " + " ".join(f"{x:.4e}" for x in e) + " rates "
+              + " ".join(f"{r:.2f}" for r in rates) + " | Table 4 " + " ".join(f"{x:.4e}" for x in paper)
+              + " rates " + " ".join(f"{r:.2f}" for r in prates)
+              + " | ratio " + " ".join(f"{a / b:.2f}" for a, b in zip(e, paper)))
+    for scheme, t in (("split", tab), ("hadamard_ir", tab_ir)):
+        e = errs[scheme]
+        for i in range(2):
+            assert p + 0.3 <= np.log(e[i] / e[i + 1]) / np.log(Ns[i + 1] / Ns[i]) <= p + 1.6
+        for a, N in zip(e, Ns):
+            assert 0.5 <= a / t[(3, p, N)] <= 2.0
+    for a, b in zip(errs["split"], errs["hadamard_ir"]):
+        assert 0.9 <= a / b <= 1.1
