@@ -142,8 +142,9 @@ def test_mms_3d_degrees_both_schemes(lib, p):
     of Table 4: the entropy-split scheme and the Ismail-Roe comparator (BO
     terms in the standard entropy variables), 6^3 x 6 .. 12^3 x 6 grids.
     Rates near p + 1 (band [p + 0.3, p + 1.6]); the two schemes' errors
-    within 10 % of each other, as in the table; errors within a factor 2 of
-    the printed ones (the node sets differ from the paper's)."""
+    within 5 % of each other, as in the table; errors within 20 % of the
+    printed ones (observed 0.88-1.07 for the split scheme and 0.94-1.07 for
+    the comparator over p = 1..4; the node sets differ from the paper's)."""
     tab, tab_ir = _table(), _table_ir()
     op = tet_operator(p)
     Ns = (6, 9, 12)
@@ -167,6 +168,6 @@ def test_mms_3d_degrees_both_schemes(lib, p):
         for i in range(2):
             assert p + 0.3 <= np.log(e[i] / e[i + 1]) / np.log(Ns[i + 1] / Ns[i]) <= p + 1.6
         for a, N in zip(e, Ns):
-            assert 0.5 <= a / t[(3, p, N)] <= 2.0
+            assert 0.8 <= a / t[(3, p, N)] <= 1.2
     for a, b in zip(errs["split"], errs["hadamard_ir"]):
-        assert 0.9 <= a / b <= 1.1
+        assert 0.95 <= a / b <= 1.05
