@@ -14,8 +14,8 @@ of the residual itself:
 No flux, entropy, SAT, dissipation or time-integration arithmetic lives here;
 both the oracle and the library receive these arrays as plain inputs.
 """
-from .sbp import RefOperator, tri_operator, tet_operator
+from .sbp import RefOperator, tri_operator, tet_operator, line_operator
 from .mesh import Mesh, periodic_tri_mesh
 from . import states
 
-__all__ = ["RefOperator", "tri_operator", "tet_operator", "Mesh", "periodic_tri_mesh", "states"]
+__all__ = ["RefOperator", "tri_operator", "tet_operator", "line_operator", "Mesh", "periodic_tri_mesh", "states"]

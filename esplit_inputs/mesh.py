@@ -366,3 +366,34 @@ def periodic_tet_mesh(op: RefOperator, N: int, L: float = 2 * np.pi, amp: float 
     return Mesh(d=3, n_e=n_e, n_p=op.n_p, n_fac=op.n_fac, n_f=op.n_f, L=(L, L, L), x=x, J=det, Lam=Lam, nu=nu,
                 pair=pair, hmin=hmin, meta=dict(kind="periodic_tet", N=N, L=L, amp=amp, p=op.p, origin=origin,
                                                  geom=G))
+
+
+def periodic_line_mesh(op: RefOperator, N: int, L: float = 1.0, origin: float = 0.0, amp: float = 0.0) -> Mesh:
+    """Periodic [x0, x0 + L) cut into N elements, vertices moved by
+    amp * h * sin(2 pi (x_k - x0) / L) (amp = 0: uniform).  Element k maps the
+    reference interval affinely onto [x_k, x_k+1]: J = h_k, Lam = J dxi/dx = 1,
+    nu = -1 at facet 0 (left end) and +1 at facet 1; facet 1 of element k
+    pairs with facet 0 of element k + 1 (periodically)."""
+    assert op.d == 1
+    h0 = L / N
+    xv = origin + h0 * np.arange(N + 1)
+    xv = xv + amp * h0 * np.sin(2.0 * np.pi * (xv - origin) / L)
+    xv[-1] = xv[0] + L
+    h = np.diff(xv)
+    x = (xv[:-1, None] + h[:, None] * op.xi[None, :, 0])[:, None, :]     # (n_e, 1, n_p)
+    J = np.repeat(h[:, None], op.n_p, axis=1)
+    Lam = np.ones((N, 1, 1, op.n_p))
+    nu = np.zeros((N, 2, 1, 1))
+    nu[:, 0, 0, 0] = -1.0
+    nu[:, 1, 0, 0] = 1.0
+    pair = np.zeros((N, 2, 1, 2), dtype=np.int32)
+    k = np.arange(N)
+    pair[:, 0, 0, 0] = (k - 1) % N      # left end: the previous element's facet 1 (slot 1)
+    pair[:, 0, 0, 1] = 1
+    pair[:, 1, 0, 0] = (k + 1) % N      # right end: the next element's facet 0 (slot 0)
+    pair[:, 1, 0, 1] = 0
+    xs = np.sort(op.xi[:, 0])
+    hmin = h * np.diff(xs).min()
+    return Mesh(d=1, n_e=N, n_p=op.n_p, n_fac=2, n_f=1, L=(L,), x=x, J=J, Lam=Lam, nu=nu, pair=pair, hmin=hmin,
+                meta=dict(kind="periodic_line", N=N, L=L, amp=amp, p=op.p, origin=origin, vertices=xv))
+

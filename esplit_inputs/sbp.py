@@ -167,6 +167,8 @@ def solve_tri_quadrature(p: int, degree: int, interior, seed: int = 0, tries: in
 
 def monomial_basis(p: int, d: int):
     """Exponent tuples of the monomial basis of P^p in d variables."""
+    if d == 1:
+        return [(i,) for i in range(p + 1)]
     if d == 2:
         return [(i, j) for tot in range(p + 1) for i in range(tot, -1, -1) for j in [tot - i]]
     if d == 3:
@@ -475,3 +477,44 @@ def tri_operator(p: int) -> RefOperator:
                      ref_normals=_TRI_NORMALS.copy(), volume_degree=rule["degree"])
     _CACHE[p] = op
     return op
+
+
+# ---------------------------------------------------------------------------
+# Interval, p = 1..4 (the 1D problems of Secs. 7.1-7.2): the p + 1
+# Gauss-Lobatto-Legendre points on the reference interval [0, 1], H their
+# quadrature weights (exact to degree 2p - 1), E = diag(-1, 0, ..., 0, 1); with
+# p + 1 nodes the accuracy conditions fix S uniquely.  Node order: the two end
+# points (facet 0 at 0, facet 1 at 1), then the interior points ascending.
+# ---------------------------------------------------------------------------
+def lgl_points01(p: int):
+    """Gauss-Lobatto-Legendre points (ascending) and weights on [0, 1]: the
+    end points and the roots of P_p', weights 2 / (p (p + 1) P_p(x)^2) on
+    [-1, 1], halved."""
+    Pp = np.polynomial.legendre.Legendre.basis(p)
+    inner = np.sort(Pp.deriv().roots().real) if p > 1 else np.array([])
+    x = np.concatenate([[-1.0], inner, [1.0]])
+    w = 2.0 / (p * (p + 1) * Pp(x) ** 2)
+    return (x + 1.0) / 2.0, w / 2.0
+
+
+def line_operator(p: int) -> RefOperator:
+    """Diagonal-E SBP operator of degree p on the reference interval [0, 1]."""
+    key = ("line", p)
+    if key in _CACHE:
+        return _CACHE[key]
+    t, w = lgl_points01(p)
+    order = [0, p] + list(range(1, p))
+    xi = t[order][:, None]
+    H = w[order]
+    n_p = p + 1
+    E = np.zeros((1, n_p))
+    E[0, 0], E[0, 1] = -1.0, 1.0
+    V, dV = vandermonde(xi, p, np.array([0.5]))
+    S = min_norm_skew(H, E[0], V, dV[0])
+    Q = (S + 0.5 * np.diag(E[0]))[None]
+    op = RefOperator(d=1, p=p, n_p=n_p, n_fac=2, n_f=1, xi=xi, H=H, Q=Q, E=E,
+                     facet_nodes=np.array([[0], [1]], dtype=np.int32), facet_w=np.ones((2, 1)),
+                     ref_normals=np.array([[-1.0], [1.0]]), volume_degree=2 * p - 1)
+    _CACHE[key] = op
+    return op
+

@@ -150,3 +150,19 @@ def taylor_green(mesh, Mach=0.1, gam=GAMMA, R=1.0):
     p = p0 + (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0) / 16.0
     rho = p / (R * T0)
     return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))
+
+
+def sod_periodic(mesh, gam=GAMMA):
+    """The Sod shock tube of Sec. 7.1 (rho, u, p = 1, 0, 1 left of x = 0.5 and
+    0.125, 0, 0.1 right of it on [0, 1]) on the periodic [0, 2) with its mirror
+    image on [1, 2): elements whose centre lies in [0.5, 1.5) take the right
+    state.  Up to t = 0.2 no wave reaches x = 0 or x = 1 (rarefaction head
+    0.26, shock 0.85 and their mirrors), so on [0, 1] the solution is the one
+    of the shock tube with its walls.  Element-wise constant data."""
+    xc = mesh.x[:, 0, :].mean(axis=1)
+    right = (xc >= 0.5) & (xc < 1.5)
+    r = np.where(right, 0.125, 1.0)[:, None] * np.ones((1, mesh.n_p))
+    pr = np.where(right, 0.1, 1.0)[:, None] * np.ones((1, mesh.n_p))
+    V = np.zeros((1, mesh.n_e, mesh.n_p))
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(r, V, pr, gam), 0, 1))
+

@@ -334,7 +334,8 @@ def dissipation_factors(Uk, Uv, n, prm: Params):
     eigenvalues Lambda_n (..., n_c) of Eq. (79) (signed) and the diagonal of
     S^ (..., n_c) of Eqs. (76)-(78), at the intermediate state of Eqs.
     (73)-(75) between U_k and U_v, for unit normal n (..., d).  3D as printed;
-    2D by deleting the fourth row and column."""
+    2D by deleting the fourth row and column; 1D by deleting both shear
+    modes."""
     g, a = prm.gam, prm.alpha
     zk, zv = param_vector(Uk, prm), param_vector(Uv, prm)
     d = Uk.shape[-1] - 2
@@ -353,7 +354,17 @@ def dissipation_factors(Uk, Uv, n, prm: Params):
     vn = (V_h * n).sum(-1)
     one = torch.ones_like(vn)
     zero = torch.zeros_like(vn)
-    if d == 2:
+    if d == 1:
+        # 1D (the problems of Secs. 7.1-7.2): no shear modes
+        n1, V1 = n[..., 0], V_h[..., 0]
+        cols = [
+            torch.stack([one, V1 - a_h * n1, H_h - a_h * vn], -1),
+            torch.stack([one, V1, 0.5 * V1 * V1], -1),
+            torch.stack([one, V1 + a_h * n1, H_h + a_h * vn], -1),
+        ]
+        lam = [vn - a_h, vn, vn + a_h]
+        sc = [theta / (2 * g), (g - 1) * (g + a) * theta / (g * a), theta / (2 * g)]
+    elif d == 2:
         n1, n2 = n[..., 0], n[..., 1]
         V1, V2 = V_h[..., 0], V_h[..., 1]
         cols = [

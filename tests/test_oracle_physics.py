@@ -109,17 +109,19 @@ def _nhat(n, d, seed):
     return v / torch.linalg.norm(v, dim=-1, keepdim=True)
 
 
-def test_dissipation_scaling_2d():
-    """Barth scaling: X^ S^ X^T = dU/dW at coincident states (Sec. 4.5, 2D)."""
-    U = rand_states(200, 2, 9)
-    n = _nhat(200, 2, 10)
+@pytest.mark.parametrize("d", [1, 2])
+def test_dissipation_scaling_2d(d):
+    """Barth scaling: X^ S^ X^T = dU/dW at coincident states (Sec. 4.5, 2D;
+    1D with the shear modes deleted)."""
+    U = rand_states(200, d, 9)
+    n = _nhat(200, d, 10)
     X, lam, sc = dissipation_factors(U, U, n, P)
     A0 = dU_dW(U, P)
     got = X @ torch.diag_embed(sc) @ X.transpose(-1, -2)
     assert ((got - A0).abs().amax((-1, -2)) / A0.abs().amax((-1, -2))).max() < 1e-12
 
 
-@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("d", [1, 2, 3])
 def test_dissipation_eigenvectors(d):
     """A_n X^ = X^ Lambda_n (Eqs. (79)-(80)) at coincident states, n_1 != 0."""
     U = rand_states(100, d, 16)
@@ -131,7 +133,7 @@ def test_dissipation_eigenvectors(d):
         assert (Ak @ X[k] - X[k] * lam[k]).abs().max() < 1e-12 * (1 + Ak.abs().max())
 
 
-@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("d", [1, 2, 3])
 def test_dissipation_symmetric_psd_and_flip(d):
     Uk, Uv = rand_states(100, d, 11), rand_states(100, d, 12)
     n = _nhat(100, d, 13)
