@@ -8,7 +8,7 @@
  * Equation numbers below are the paper's.
  *
  * Conventions shared by every call
- *   d      spatial dimension (2 or 3), n_c = d + 2 components
+ *   d      spatial dimension (1, 2 or 3), n_c = d + 2 components
  *   state  u: float64 conservative variables [rho, rho V_1..V_d, e],
  *          layout [n_e][n_c][n_p] (element-major, node fastest)
  *   all pointers named *_dev are device pointers owned by the caller;
@@ -90,7 +90,8 @@ int esplit_version(void);
  * Asynchronous on `stream`; ESPLIT_ERR_ARG for fn outside 0..7. */
 int esplit_math_eval(int fn, const double* x_dev, double* y_dev, size_t n, void* stream);
 
-/* Create a context on CUDA device `device` for dimension `dim` (2 or 3).
+/* Create a context on CUDA device `device` for dimension `dim` (1, 2 or 3;
+ * 1: the inviscid problems of Secs. 7.1-7.2, no VJP).
  * The context owns every device copy it makes (operators, mesh, scratch).
  * Defaults: gam 1.4, beta 2.5, R 1, mu 0, Pr 0.71, split scheme, FP64,
  * no dissipation, no viscous terms, heat flux on. */
@@ -105,7 +106,8 @@ void esplit_destroy(esplit_ctx* ctx);
  *   facet_w      [n_fac][n_f]        facet quadrature weights (unused by the
  *                                    residual; kept for diagnostics)
  *   ref_normals  [n_fac][d]          outward unit normals of reference facets
- * Host pointers, copied.  Supported (d, n_p): (2, 7), (2, 12), (2, 18),
+ * Host pointers, copied.  Supported (d, n_p): (1, 2..5) (Gauss-Lobatto-
+ * Legendre, p = 1..4), (2, 7), (2, 12), (2, 18),
  * (2, 27) (triangles, p = 1..4) and (3, 12), (3, 25), (3, 58), (3, 78)
  * (tetrahedra, p = 1..4); others -> ESPLIT_ERR_UNSUPPORTED. */
 int esplit_upload_operator(esplit_ctx* ctx, int n_p, int n_fac, int n_f, const double* H_ref,

@@ -45,6 +45,7 @@ void dfree(void* p) {
 }
 
 bool supported(int dim, int n_p) {
+  if (dim == 1) return n_p >= 2 && n_p <= 5;
   if (dim == 2) return n_p == 7 || n_p == 12 || n_p == 18 || n_p == 27;
   if (dim == 3) return n_p == 12 || n_p == 25 || n_p == 58 || n_p == 78;
   return false;
@@ -121,7 +122,7 @@ int esplit_math_eval(int fn, const double* x, double* y, size_t n, void* stream)
 int esplit_create(esplit_ctx** out, int dim, int device) {
   if (!out) return ESPLIT_ERR_ARG;
   *out = nullptr;
-  if (dim != 2 && dim != 3) return ESPLIT_ERR_ARG;
+  if (dim < 1 || dim > 3) return ESPLIT_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return ESPLIT_ERR_CUDA;
   if (device < 0 || device >= ndev) return ESPLIT_ERR_ARG;
@@ -321,6 +322,7 @@ int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
   if (!(p->R > 0.0) || p->mu < 0.0 || !(p->Pr > 0.0)) return fail(c, ESPLIT_ERR_ARG, "R, Pr must be > 0, mu >= 0");
   if (p->scheme < 0 || p->scheme > 3) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
   if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK) return fail(c, ESPLIT_ERR_ARG, "unknown precision");
+  if (p->viscous && c->dim == 1) return fail(c, ESPLIT_ERR_UNSUPPORTED, "1D: inviscid only");
   cudaSetDevice(c->device);
   bool beta_changed = p->beta != c->prm.beta;
   c->prm = *p;
@@ -832,8 +834,8 @@ int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
   if (rc) return rc;
   if (!u || !cot || !grad) return fail(c, ESPLIT_ERR_ARG, "null pointer");
   if (grad == u || grad == cot) return fail(c, ESPLIT_ERR_ARG, "grad must not alias u or cot");
-  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT)
-    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the residual VJP is built for the entropy-split scheme");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->dim == 1)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the residual VJP is built for the entropy-split scheme in 2D and 3D");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
   return vjp_impl(c, u, cot, grad, s);
@@ -856,8 +858,8 @@ int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double*
   if (!u || !ubar1 || !ubar0) return fail(c, ESPLIT_ERR_ARG, "null pointer");
   if (ubar0 == u || ubar0 == ubar1) return fail(c, ESPLIT_ERR_ARG, "ubar0 must not alias u or ubar1");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ESPLIT_ERR_ARG, "dt must be positive and finite");
-  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT)
-    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the step reverse is built for the entropy-split scheme");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->dim == 1)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the step reverse is built for the entropy-split scheme in 2D and 3D");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
   size_t n = (size_t)c->n_e * c->n_c * c->n_p;

@@ -128,7 +128,9 @@ int launch_detect_hybrid(esplit_ctx* c, const double* u, double threshold, cudaS
   const double gm1 = c->prm.gam - 1.0;
   int nb256 = (c->n_e + 255) / 256;
   int nb1k = (c->n_e + 1023) / 1024;
-  if (c->dim == 2)
+  if (c->dim == 1)
+    detect_ratio_kernel<1><<<nb256, 256, 0, s>>>(u, c->b.pair, c->n_e, gm1, threshold, c->b.hflag0);
+  else if (c->dim == 2)
     detect_ratio_kernel<2><<<nb256, 256, 0, s>>>(u, c->b.pair, c->n_e, gm1, threshold, c->b.hflag0);
   else
     detect_ratio_kernel<3><<<nb256, 256, 0, s>>>(u, c->b.pair, c->n_e, gm1, threshold, c->b.hflag0);

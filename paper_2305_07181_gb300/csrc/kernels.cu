@@ -130,7 +130,10 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   int bs = 256;
   unsigned nb = (unsigned)((total + bs - 1) / bs);
   double inv_bp1 = 1.0 / (c->prm.beta + 1.0);
-  if (c->dim == 2)
+  if (c->dim == 1)
+    build_ops_kernel<1><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
+                                          c->b.ops32, c->b.ops32lo);
+  else if (c->dim == 2)
     build_ops_kernel<2><<<nb, bs, 0, s>>>(c->b.Qref, c->b.Lam, c->b.J, c->b.nu, c->n_e, inv_bp1, c->b.ops64,
                                           c->b.ops32, c->b.ops32lo);
   else
@@ -1124,7 +1127,14 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
 template <typename T>
 static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial,
                       double* sat) {
-  if (c->dim == 2) {
+  if (c->dim == 1) {
+    switch (c->n_p) {
+      case 2: return residual_np<T, 1, 2>(c, u, r, s, prod, n_partial, sat);
+      case 3: return residual_np<T, 1, 3>(c, u, r, s, prod, n_partial, sat);
+      case 4: return residual_np<T, 1, 4>(c, u, r, s, prod, n_partial, sat);
+      case 5: return residual_np<T, 1, 5>(c, u, r, s, prod, n_partial, sat);
+    }
+  } else if (c->dim == 2) {
     switch (c->n_p) {
       case 7: return residual_np<T, 2, 7>(c, u, r, s, prod, n_partial, sat);
       case 12: return residual_np<T, 2, 12>(c, u, r, s, prod, n_partial, sat);
@@ -1259,7 +1269,9 @@ int launch_entropy(esplit_ctx* c, const double* u, cudaStream_t s, int* n_partia
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ENTROPY, s);
   double* out = part ? part : c->b.partial;
-  if (c->dim == 2)
+  if (c->dim == 1)
+    entropy_kernel<1><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, out, cache);
+  else if (c->dim == 2)
     entropy_kernel<2><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, out, cache);
   else
     entropy_kernel<3><<<nb, 256, 0, s>>>(u, c->b.J, n, ph, out, cache);
@@ -1275,7 +1287,12 @@ int launch_entropy_rate(esplit_ctx* c, const double* u, const double* r, cudaStr
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ENTROPY, s);
   if (!part) part = c->b.partial;
-  if (c->dim == 2) {
+  if (c->dim == 1) {
+    if (width == 1)
+      entropy_rate_kernel<1, 1><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
+    else
+      entropy_rate_kernel<1, 2><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
+  } else if (c->dim == 2) {
     if (width == 1)
       entropy_rate_kernel<2, 1><<<nb, 256, 0, s>>>(u, r, c->b.J, n, ph, part);
     else
@@ -1704,7 +1721,9 @@ int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStrea
   int nb = (int)((n + 255) / 256);
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   ProfScope ps(c, PG_ROOT, s);
-  if (c->dim == 2)
+  if (c->dim == 1)
+    root_eval_kernel<1><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
+  else if (c->dim == 2)
     root_eval_kernel<2><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
   else
     root_eval_kernel<3><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);

@@ -407,7 +407,9 @@ __device__ __forceinline__ void diss_apply(const PairAvg<T, D>& a, const C& c, c
   X[NC - 1][0] = Hh - ah * vn;
   X[NC - 1][1] = T(0.5) * vh2;
   X[NC - 1][NC - 1] = Hh + ah * vn;
-  if constexpr (D == 2) {
+  if constexpr (D == 1) {
+    // no shear modes: the acoustic and entropy columns only
+  } else if constexpr (D == 2) {
     X[0][2] = T(0);
     X[1][2] = n[1];
     X[2][2] = -n[0];

@@ -147,7 +147,9 @@ static inline unsigned nblocks(size_t n, int bs) { return (unsigned)((n + bs - 1
 int launch_wH(esplit_ctx* c, const double* u, double scale, double* out, cudaStream_t s) {
   size_t n = (size_t)c->n_e * c->n_p;
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
-  if (c->dim == 2)
+  if (c->dim == 1)
+    wH_kernel<1><<<nblocks(n, 256), 256, 0, s>>>(u, c->b.J, n, ph, scale, out);
+  else if (c->dim == 2)
     wH_kernel<2><<<nblocks(n, 256), 256, 0, s>>>(u, c->b.J, n, ph, scale, out);
   else
     wH_kernel<3><<<nblocks(n, 256), 256, 0, s>>>(u, c->b.J, n, ph, scale, out);
@@ -160,7 +162,9 @@ int launch_rrk_vjp_dots(esplit_ctx* c, const double* u1, const double* d, const 
   size_t n = (size_t)c->n_e * c->n_p;
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   unsigned nb = nblocks(n, 256);
-  if (c->dim == 2)
+  if (c->dim == 1)
+    rrk_vjp_dots_kernel<1><<<nb, 256, 0, s>>>(u1, d, ubar1, c->b.J, n, ph, c->b.partial);
+  else if (c->dim == 2)
     rrk_vjp_dots_kernel<2><<<nb, 256, 0, s>>>(u1, d, ubar1, c->b.J, n, ph, c->b.partial);
   else
     rrk_vjp_dots_kernel<3><<<nb, 256, 0, s>>>(u1, d, ubar1, c->b.J, n, ph, c->b.partial);
@@ -173,7 +177,9 @@ int launch_rrk_vjp_combine(esplit_ctx* c, const double* un, const double* u1, co
                            double g, double* ubar0, double* dbar, cudaStream_t s) {
   size_t n = (size_t)c->n_e * c->n_p;
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
-  if (c->dim == 2)
+  if (c->dim == 1)
+    rrk_vjp_combine_kernel<1><<<nblocks(n, 256), 256, 0, s>>>(un, u1, ubar1, c->b.J, n, ph, lam, g, ubar0, dbar);
+  else if (c->dim == 2)
     rrk_vjp_combine_kernel<2><<<nblocks(n, 256), 256, 0, s>>>(un, u1, ubar1, c->b.J, n, ph, lam, g, ubar0, dbar);
   else
     rrk_vjp_combine_kernel<3><<<nblocks(n, 256), 256, 0, s>>>(un, u1, ubar1, c->b.J, n, ph, lam, g, ubar0, dbar);
@@ -186,7 +192,10 @@ int launch_rrk_vjp_stage(esplit_ctx* c, const double* U, const double* r, const 
                          cudaStream_t s) {
   size_t n = (size_t)c->n_e * c->n_p;
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
-  if (c->dim == 2)
+  if (c->dim == 1)
+    rrk_vjp_stage_kernel<1><<<nblocks(n, 128), 128, 0, s>>>(U, r, dbar, ubar_next, c->b.J, n, ph, c_d, c_e, c_u,
+                                                            rbar, extra);
+  else if (c->dim == 2)
     rrk_vjp_stage_kernel<2><<<nblocks(n, 128), 128, 0, s>>>(U, r, dbar, ubar_next, c->b.J, n, ph, c_d, c_e, c_u,
                                                             rbar, extra);
   else
