@@ -1,4 +1,6 @@
-"""Reference diagonal-E SBP operators on the reference triangle.
+"""Reference diagonal-E SBP operators on the reference triangle, the
+reference tetrahedron and the reference interval (the last two in their own
+sections below).
 
 Definition 1 (Sec. 2.1) asks for D_xi = H^-1 Q_xi exact on P^p, H symmetric
 positive definite, Q_xi = S_xi + E_xi/2 with S_xi skew and E_xi symmetric and
