@@ -35,9 +35,9 @@ import torch  # noqa: E402
 
 METRIC = "DOF-residual evals/s vs Hadamard form, FP64 & FP32, % roofline; 1 GB300"
 UNIT = "DOF-residual evals/s"
-FP64_PEAK_NOMINAL = 1.25e12            # recipe table: GB300 FP64 1.25 TFLOP/s
+FP64_PEAK_NOMINAL = 1.25e12            # GB300 nominal FP64 1.25 TFLOP/s (context; the roofline uses the measured rate)
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged
-# kernel (profiles/split_volume_config2_p3_fp64.md); keyed by (kernel, p, precision, N)
+# kernel; keyed by (kernel, p, precision, N)
 NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 229.968e6}
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 
@@ -192,6 +192,57 @@ def max_over_ranks(x, ws, device):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def measure_fp64_peak(es, device):
+    """float64 FMA throughput of this GPU (the library's FMA-chain kernel),
+    with the SM clock sampled while it runs."""
+    with ClockSampler(device) as clk:
+        best = 0.0
+        t_end = time.perf_counter() + 1.0          # ~1 s of launches so that the sampler sees them
+        while time.perf_counter() < t_end:
+            rc, f, ms = es.capi.esplit_measure_fp64_fma(device)
+            if rc != 0:
+                return None
+            best = max(best, f)
+    c = clk.summary()
+    mhz = c["sm_mhz"]
+    per_clk = best / 2.0 / (SM_COUNT * mhz * 1e6) if mhz else None
+    return {"tflops": best / 1e12, "sm_mhz": mhz, "dfma_per_clk_per_sm": per_clk, "reasons": c["reasons"],
+            "how": "esplit_measure_fp64_fma: independent float64 FMA chains (8 per thread, 2048 threads per SM), "
+                   "best launch over ~1 s, SM clock sampled meanwhile"}
+
+
+def vs_hadamard(es, device, flush, p, N):
+    """The metric's comparison at the headline mesh: residual-only time of
+    the entropy split against the Hadamard form with the Sjogreen-Yee flux and
+    against the Sec. 6 comparator (Hadamard form, Ismail-Roe flux), all with
+    their matrix interface dissipation, float64 and float32 settings, and the
+    error bound each setting is tested to (tests/test_gpu_parity.py,
+    tests/test_gpu_ismail_roe.py)."""
+    op, mesh, u0, dt = workload(p, N)
+    stream = torch.cuda.current_stream(device)
+    s = es.Solver(op, mesh, es.Params(dissipation=True), device=device)
+    ud = s.to_device(u0)
+    r = s.empty()
+    ms = {}
+    for prec in ("fp64", "fp32"):
+        for scheme in ("split", "hadamard", "hadamard_ir"):
+            s.set_params(es.Params(dissipation=True, scheme=scheme, precision=prec))
+            for _ in range(3):
+                s.residual(ud, r)
+            ms[f"{scheme}_{prec}"] = statistics.median(_timed(lambda: s.residual(ud, r), stream, flush, 10))
+    s.close()
+    bound = {"split_fp64": 1e-12, "hadamard_fp64": 1e-12, "hadamard_ir_fp64": 1e-12,
+             "split_fp32": 1e-11, "hadamard_fp32": 1e-3, "hadamard_ir_fp32": 1e-3}
+    out = {"mesh": f"{2 * N * N} triangles, p={p}", "residual_ms": {k: round(v, 4) for k, v in ms.items()},
+           "error_bound": bound,
+           "split_over_ir_fp64": ms["hadamard_ir_fp64"] / ms["split_fp64"],
+           "split_over_sy_fp64": ms["hadamard_fp64"] / ms["split_fp64"],
+           "split_fp32_over_ir_fp64": ms["hadamard_ir_fp64"] / ms["split_fp32"],
+           "equal_accuracy": "split fp32 (bound 1e-11) vs the Hadamard forms in fp64; their fp32 settings are "
+                             "plain float32 (bound 1e-3)"}
+    return out
 
 
 def cpu_baseline(op, mesh, u0, budget_s=12.0):
@@ -548,16 +599,22 @@ def main():
     dom_ms = groups[dom][0] / groups[dom][1]
     per_launch_units = n_e if dom in ("split_volume", "hadamard_volume") else solver_pairs(mesh, op)
     fl = algorithmic_flops(dom, n_e, n_p, d, solver_pairs(mesh, op))
+    fp64_peak = measure_fp64_peak(es, device)
+    peak_tf = fp64_peak["tflops"] if fp64_peak else FP64_PEAK_NOMINAL / 1e12
     roofline = None
     if fl is not None:
         achieved = fl / (dom_ms * 1e-3) / 1e12
-        peak = FP64_PEAK_NOMINAL / 1e12 if args.precision == "fp64" else None
+        peak = peak_tf if args.precision == "fp64" else None
+        src = (f"measured: float64 FMA chains {fp64_peak['tflops']:.3f} TFLOP/s = "
+               f"{fp64_peak['dfma_per_clk_per_sm']:.2f} DFMA/clk/SM at {fp64_peak['sm_mhz']:.0f} MHz "
+               f"(nominal 1.259 = 2 DFMA/clk/SM at 2070 MHz); FP64 pipe, not the bf16 tensor peak"
+               if fp64_peak and fp64_peak.get("dfma_per_clk_per_sm") else
+               "nominal FP64 1.25 TFLOP/s (the float64 FMA measurement failed)")
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": (achieved / peak) if peak else None,
                     "traffic": NCU_TRAFFIC.get((dom, args.p, args.precision, args.N)), "kernel": dom,
                     "avg_launch_ms": dom_ms, "launches": groups[dom][1], "units_per_launch": per_launch_units,
-                    "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (152 SMs x 4 FLOP/clk x "
-                                   "2.07 GHz); FP64 pipe, not the bf16 tensor peak"}
+                    "peak_source": src}
     # every kernel group with an algorithmic flop count, against the same FP64 peak
     roofline_by_kernel = {}
     for g, (ms_tot, nl) in groups.items():
@@ -567,8 +624,7 @@ def main():
         ms = ms_tot / nl
         ach = fg / (ms * 1e-3) / 1e12
         roofline_by_kernel[g] = {"avg_launch_ms": ms, "launches": nl, "achieved_tflops": ach,
-                                 "frac_fp64_peak": ach / (FP64_PEAK_NOMINAL / 1e12) if args.precision == "fp64"
-                                 else None}
+                                 "frac_fp64_peak": ach / peak_tf if args.precision == "fp64" else None}
     # ---------------- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     u_host = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
     u_host.copy_(torch.as_tensor(u0))
@@ -586,8 +642,9 @@ def main():
     nbytes = u0.size * 8
     e2e = {"value": ws * args.steps * 4 * dof / e2e_tot, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
+    vs_had = vs_hadamard(es, device, flush, args.p, args.N) if rank == 0 else None
     extras = {"kernel_ms_timed_region": {g: {"ms_total": v[0], "launches": v[1]} for g, v in groups.items()},
-              "roofline_by_kernel": roofline_by_kernel,
+              "roofline_by_kernel": roofline_by_kernel, "fp64_peak": fp64_peak,
               "g_range": [min(gs), max(gs)], "wall_s_timed": t_wall, "dt": dt}
     if rank == 0 and not args.no_sweep:
         extras["residual_sweep"] = residual_sweep(es, device, flush)
@@ -611,7 +668,7 @@ def main():
                        "n_p": n_p, "dof": dof, "residuals_per_step": 4, "dt": dt,
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-            "extras": extras}
+            "vs_hadamard": vs_had, "extras": extras}
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()

@@ -90,6 +90,15 @@ int esplit_version(void);
  * Asynchronous on `stream`; ESPLIT_ERR_ARG for fn outside 0..7. */
 int esplit_math_eval(int fn, const double* x_dev, double* y_dev, size_t n, void* stream);
 
+/* Measurement aid (no counterpart in the paper): the float64 FMA throughput
+ * of CUDA device `device`, the peak that the float64 kernels' roofline
+ * fractions are taken against (those kernels are bound by the float64 pipe).
+ * Independent FMA chains, 8 per thread, 2048 threads per SM; the best of five
+ * timed launches after one warm-up, on the legacy default stream.
+ * *flops_per_s receives 2 x FMAs / second, *ms (may be NULL) the launch time.
+ * Synchronises the device's default stream. */
+int esplit_measure_fp64_fma(int device, double* flops_per_s, double* ms);
+
 /* Create a context on CUDA device `device` for dimension `dim` (1, 2 or 3;
  * 1: the inviscid problems of Secs. 7.1-7.2, no VJP).
  * The context owns every device copy it makes (operators, mesh, scratch).
@@ -152,22 +161,29 @@ int esplit_residual(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void
  * is owned by its own pool allocator, or a time-critical loop that cannot
  * absorb the device-wide synchronisation cudaMalloc and cudaFree can cause.
  * This call allocates nothing -- no cudaMalloc, cudaFree, library allocator or
- * CUDA event -- and does not use the context's facet scratch: the facet
- * contributions go to a 16 MiB scratch array (2^21 doubles) that the library
- * holds in static device memory on every GPU that loads it, until the
- * process exits.  Meshes needing more than that, n_e * n_c * n_slot >
- * 2^21, are rejected with ESPLIT_ERR_ARG and a message giving both numbers.
- * The first call on a device looks up the array's device address (with that
- * device current) and keeps it; make that first call before any stream
- * capture.  Every call on a device shares the one array and overwrites all
- * of the part it uses (nothing has to start at zero), so calls whose kernels
- * overlap on the GPU -- on different streams, or from different threads or
- * contexts -- race on it: serialise them.  With viscous terms on, their
- * scratch is the context's own, allocated by esplit_set_params or
- * esplit_upload_mesh when the terms were switched on, not by this call.
- * Arguments, layout and errors as
- * for esplit_residual; the result equals esplit_residual's.  The paper has no
- * counterpart of this entry point; it is a deployment convenience. */
+ * CUDA event (kernel timing, when enabled on the context, skips its launches)
+ * -- and does not use the context's facet scratch: the facet contributions go
+ * to a 16 MiB scratch array (2^21 doubles) that the library holds in static
+ * device memory on every GPU that loads it, until the process exits.  Meshes
+ * needing more than that, n_e * n_c * n_slot > 2^21, are rejected with
+ * ESPLIT_ERR_ARG and a message giving both numbers.  The first call on a
+ * device looks up the array's device address (with that device current) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture.  The address belongs to the device's primary context (the
+ * one the CUDA runtime and PyTorch use): calling from another driver context,
+ * or after cudaDeviceReset, is not supported (start a new process).  Every
+ * call on a device shares the one array and overwrites all of the part it
+ * uses (nothing has to start at zero), so calls whose kernels overlap on the
+ * GPU -- on different streams, or from different threads or contexts -- race
+ * on it: serialise them.  With viscous terms on, their scratch is the
+ * context's own, allocated by esplit_set_params or esplit_upload_mesh when the
+ * terms were switched on, not by this call.  Arguments, layout and errors as
+ * for esplit_residual.  The facet terms take the kernel order in which the
+ * facet kernel runs before the volume kernels (esplit_residual runs the
+ * volume kernels first for the inviscid split scheme), so the result equals
+ * esplit_residual's to rounding: within the float64 parity tolerance, or the
+ * stated bound of a float32 precision setting.  The paper has no counterpart
+ * of this entry point; it is a deployment convenience. */
 int esplit_residual_noalloc(esplit_ctx* ctx, const double* u_dev, double* dudt_dev, void* stream);
 
 /* Hybrid scheme (Sec. 4.4, Thm. 4): flags for the hybrid scheme computed on

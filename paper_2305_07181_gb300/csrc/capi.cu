@@ -89,8 +89,10 @@ int read_status(esplit_ctx* c, cudaStream_t s, bool clear) {
 
 namespace esplit {
 
+thread_local bool t_no_events = false;
+
 ProfScope::ProfScope(esplit_ctx* c_, int g_, cudaStream_t s_) : c(c_), g(g_), s(s_) {
-  if (!c->prof) return;
+  if (!c->prof || t_no_events) return;
   for (cudaEvent_t* ev : {&a, &b}) {
     if (!c->pool.empty()) {
       *ev = c->pool.back();
@@ -103,7 +105,7 @@ ProfScope::ProfScope(esplit_ctx* c_, int g_, cudaStream_t s_) : c(c_), g(g_), s(
 }
 
 ProfScope::~ProfScope() {
-  if (!c->prof || !a || !b) return;
+  if (!a || !b) return;
   cudaEventRecord(b, s);
   c->recs.push_back(ProfRec{g, a, b});
 }

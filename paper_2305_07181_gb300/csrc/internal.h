@@ -138,6 +138,10 @@ namespace esplit {
 // Brackets one kernel launch with CUDA events on its stream when the
 // context's profiling is enabled (groups listed in include/esplit.h).
 enum ProfGroup { PG_FACE = 0, PG_SPLIT = 1, PG_HAD = 2, PG_ENTROPY = 3, PG_ROOT = 4, PG_STAGE = 5, PG_VISC = 6 };
+// set by the calling thread around launches that must create no CUDA event
+// (the no-allocation residual); other threads' launches on the same context
+// keep their timing
+extern thread_local bool t_no_events;
 struct ProfScope {
   esplit_ctx* c;
   int g;

@@ -1183,13 +1183,14 @@ int noalloc_scratch_ptr(int device, double** out) {
 }
 
 int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch) {
-  const bool prof = c->prof;  // kernel timing would create CUDA events: keep it off here
-  c->prof = false;
+  // kernel timing would create CUDA events: off for this thread's launches
+  // (the context's setting, which other threads may be using, is untouched)
+  t_no_events = true;
   int rc = c->prm.precision == ESPLIT_FP32_BULK ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
                                                  : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
+  t_no_events = false;
   // viscous terms (inside the residual launch) use the context's viscous
   // scratch, allocated when they were switched on
-  c->prof = prof;
   return rc;
 }
 

@@ -6,11 +6,27 @@ the oracle) is a few eps times this, whatever the size of the result itself;
 where the residual is much smaller than its terms (a state near a constant,
 a low-Mach flow) a plain relative bound on the result is not met by either
 side, and the parity tests bound |r_gpu - r_oracle| by
-1e-12 max|r| + 64 n_p eps (summand scale)
-(a length-n_p dot product of rounded terms on each side, as in the standard
-gamma_n bound).
+1e-12 max|r| + ROUNDING_C eps (summand scale).
+
+ROUNDING_C = 8: against the residual evaluated at 50 digits
+(oracle/extended.py, tests/test_oracle_extended.py) the float64 oracle is
+within 1.1 eps (summand scale) of the exact value on the 32,768-triangle
+vortex mesh, and the GPU path within 2.5; the largest GPU-vs-oracle
+difference seen on any workload is 4.2 eps (summand scale) (Taylor-Green,
+Hadamard form with viscous terms).  The plain max-norm relative error is
+printed beside every such check: at these sizes it is 1e-12 to 2e-10 for
+either float64 implementation.
 """
+import numpy as np
 import torch
+
+ROUNDING_C = 8.0
+EPS = float(np.finfo(float).eps)
+
+
+def rounding_bound(ro, sc, rel=1e-12):
+    """|r_gpu - r_oracle| allowed per entry: rel max|r| + ROUNDING_C eps sc."""
+    return rel * np.abs(ro).max() + ROUNDING_C * EPS * sc
 
 
 def summand_scale(u, op, m, elems, scheme, prm, dissipation=True, viscous=False):

@@ -7,7 +7,7 @@ exact shock position, the hybrid scheme with the device detector puts the
 shock in the right place, the entropy-split scheme does not.
 
 Tolerances as in 2D and 3D: FP64 max-norm relative error per component
-<= 1e-12, FP32-bulk split <= 1e-5, relaxation parameter <= 1e-10, hybrid
+<= 1e-12, FP32-bulk split <= 1e-11 (observed 1.3e-13), relaxation parameter <= 1e-10, hybrid
 flags bit-exact."""
 import numpy as np
 import pytest
@@ -77,7 +77,7 @@ def test_1d_fp32_and_entropy(lib, p):
     ud = s.to_device(u)
     err = rel_err(s.residual(ud).cpu().numpy(), R.residual(u, op, m, OP(), dissipation=True).numpy())
     print(f"1D p={p} fp32 split rel err {err:.2e}")
-    assert err <= 1e-5
+    assert err <= 1e-11
     ur = states.random_positive_state(m.n_e, 1, op.n_p, seed=40 + p)
     udr = s.to_device(ur)
     for scheme in ("split", "hadamard"):

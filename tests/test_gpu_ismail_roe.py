@@ -103,10 +103,10 @@ def test_ir_hadamard_full_size_sampled(lib, diss):
     times it; the oracle on 100 sampled elements.  As for the other schemes
     at this size the residual is far smaller than the terms it is summed from,
     and the bound is the rounding-scale one,
-    |r_gpu - r_oracle| <= 1e-12 max|r| + 64 n_p eps (summand scale)."""
+    |r_gpu - r_oracle| <= 1e-12 max|r| + 8 eps (summand scale)."""
     from oracle import residual as R
     from oracle.physics import Params as OP
-    from parity_bounds import summand_scale
+    from parity_bounds import summand_scale, rounding_bound
     op = tri_operator(3)
     m = periodic_tri_mesh(op, 128, 10.0, 0.05)
     u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
@@ -120,12 +120,14 @@ def test_ir_hadamard_full_size_sampled(lib, diss):
     err = np.abs(r[el] - ro)
     print(f"IR full size diss={diss}: max-norm rel {rel_err(r[el], ro):.2e}, "
           f"max err/(eps scale) {float((err / (eps * sc)).max()):.2f}")
-    assert np.all(err <= 1e-12 * np.abs(ro).max() + 64 * op.n_p * eps * sc)
+    assert np.all(err <= rounding_bound(ro, sc))
 
 
 def test_ir_hadamard_fp32(lib):
     """All-float32 two-point fluxes, as the float32 Sjogreen-Yee Hadamard
-    form: the same stated bound 1e-2 (observed error printed)."""
+    form: the same stated bound 1e-3 (observed 2.5e-5, printed).  Plain
+    float32 with no compensation: context for the FP32 comparison, not a
+    comparator at the 1e-5 accuracy of the float32 split residual."""
     from oracle import residual as R
     from oracle.physics import Params as OP
     op = tri_operator(3)
@@ -136,7 +138,7 @@ def test_ir_hadamard_fp32(lib):
     s.close()
     err = rel_err(r, R.residual(u, op, m, OP(), scheme="hadamard_ir").numpy())
     print(f"IR fp32 rel err {err:.2e}")
-    assert err <= 1e-2
+    assert err <= 1e-3
 
 
 def test_ir_hadamard_restrictions(lib):
@@ -160,7 +162,7 @@ def test_ir_viscous_parity(lib, dim, heat):
     (rounding-scale bound, as for the split scheme)."""
     from oracle import residual as R
     from oracle.physics import Params as OP
-    from parity_bounds import summand_scale
+    from parity_bounds import summand_scale, rounding_bound
     if dim == 2:
         op = tri_operator(3)
         m = periodic_tri_mesh(op, 5, 10.0, 0.05)
@@ -187,5 +189,5 @@ def test_ir_viscous_parity(lib, dim, heat):
         sc = summand_scale(ut, op, m, np.arange(m.n_e), "hadamard_ir", OP(mu=mu, heat_flux=heat), viscous=True)
         eps = np.finfo(float).eps
         print(f"IR viscous TGV heat={heat}: max-norm rel {rel_err(rt, rto):.2e}")
-        assert np.all(np.abs(rt - rto) <= 1e-12 * np.abs(rto).max() + 64 * op.n_p * eps * sc)
+        assert np.all(np.abs(rt - rto) <= rounding_bound(rto, sc))
     s.close()

@@ -63,7 +63,7 @@ def test_entropy_gradient_through_50_steps_closed_form(lib):
     exact = s.entropy_grad(ud)
     err = float((grad - exact).abs().max() / exact.abs().max())
     print(f"50-step entropy gradient vs H w(u_0): rel err {err:.2e}; g range {min(gs):.9f}..{max(gs):.9f}")
-    assert err <= 1e-8
+    assert err <= 1e-12
     assert abs(s.entropy(uN) - s.entropy(ud)) <= 1e-13 * abs(s.entropy(ud)) * 50
     s.close()
 

@@ -8,8 +8,8 @@ tetrahedra (48 or 162 elements: several blocks of every kernel and a ragged
 tail).
 
 Tolerances as for the degree-2 operator: FP64 max-norm relative error per
-component <= 1e-12, FP32-bulk split form <= 1e-5 (the plain float32 Hadamard
-comparator <= 1e-2), relaxation parameter <= 1e-10.
+component <= 1e-12, FP32-bulk split form <= 1e-11 (the plain float32 Hadamard
+comparator <= 1e-3), relaxation parameter <= 1e-10.
 """
 import numpy as np
 import pytest
@@ -21,8 +21,8 @@ from esplit_inputs.mesh import periodic_tet_mesh
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-FP32_BOUND = 1e-5
-FP32_BOUND_HADAMARD = 1e-2   # the comparator's FP32 mode is plain float32 (no compensation)
+FP32_BOUND = 1e-11           # FP32-bulk split: observed <= 2.4e-12
+FP32_BOUND_HADAMARD = 1e-3   # the comparator's FP32 mode is plain float32 (no compensation): observed <= 1.2e-4
 PS = [1, 3, 4]
 
 

@@ -11,12 +11,14 @@ import torch
 
 from esplit_inputs import tri_operator, tet_operator, periodic_tri_mesh, states
 from esplit_inputs.mesh import periodic_tet_mesh
-from parity_bounds import summand_scale
+from parity_bounds import summand_scale, rounding_bound
 
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-FP32_BOUND = 1e-5
+FP32_BOUND = 1e-11        # FP32-bulk, small meshes: observed 2.9e-13
+FP32_BOUND_TGV_FULL = 1e-9  # FP32-bulk, full-size Taylor-Green: observed 2.0e-10 (the float64
+                            # path's plain max-norm error there is 1.4e-10)
 
 
 @pytest.fixture(scope="module")
@@ -113,7 +115,7 @@ def test_tet_taylor_green_parity(lib, scheme):
     terms and matrix dissipation.  At M = 0.1 the pressure is ~71 and its
     variation ~0.1, so the residual is ~1e3 times smaller than the terms it
     is summed from: the bound is the rounding-scale one of parity_bounds
-    (1e-12 max|r| + 64 n_p eps times the summand scale); the plain max-norm
+    (1e-12 max|r| + 8 eps times the summand scale); the plain max-norm
     relative error and the observed constant are printed."""
     R, Dg, rrk, OP = _oracle()
     op, m = _tet(3)
@@ -127,7 +129,7 @@ def test_tet_taylor_green_parity(lib, scheme):
     eps = np.finfo(float).eps
     print(f"TGV {scheme}: max-norm rel {rel_err(r, ro):.2e}, max err/(eps scale) "
           f"{float((err / (eps * sc)).max()):.2f}, cond ~{float(sc.max() / np.abs(ro).max()):.1e}")
-    assert np.all(err <= FP64_TOL * np.abs(ro).max() + 64 * op.n_p * eps * sc)
+    assert np.all(err <= rounding_bound(ro, sc, FP64_TOL))
     s.close()
 
 
@@ -242,13 +244,14 @@ def test_full_size_taylor_green_sampled(lib, scheme):
     eps = np.finfo(float).eps
     print(f"TGV full {scheme}: max-norm rel {rel_err(r, ro):.2e}, max err/(eps scale) "
           f"{float((err / (eps * sc)).max()):.2f}")
-    assert np.all(err <= FP64_TOL * np.abs(ro).max() + 64 * op.n_p * eps * sc)
+    assert np.all(err <= rounding_bound(ro, sc, FP64_TOL))
 
 
 def test_full_size_taylor_green_fp32_bulk(lib):
     """FP32-bulk on the full-size Taylor-Green workload against the FP64
-    oracle on sampled elements; the bound is the stated FP32-bulk bound
-    relative to each component's max-norm."""
+    oracle on sampled elements; the bound, FP32_BOUND_TGV_FULL, is relative
+    to each component's max-norm (at this low Mach number the float64 path
+    itself is only 1.4e-10 from the oracle in that norm)."""
     R, Dg, rrk, OP = _oracle()
     op, m, u = _tgv_full()
     mu = 1.0 / 1600.0
@@ -259,4 +262,4 @@ def test_full_size_taylor_green_fp32_bulk(lib):
     ro = R.residual(u, op, m, OP(mu=mu), dissipation=True, viscous=True, elems=sample).numpy()
     err = rel_err(r, ro)
     print(f"TGV full fp32-bulk rel err {err:.3e}")
-    assert err <= FP32_BOUND
+    assert err <= FP32_BOUND_TGV_FULL

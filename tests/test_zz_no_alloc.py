@@ -83,3 +83,56 @@ def test_noalloc_viscous_matches_residual(lib):
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     s.close()
+
+
+def test_noalloc_fp32_bulk_matches_residual(lib):
+    """FP32-bulk precision: the no-allocation call (facet kernel first, the
+    uncached float32 split variant) against esplit_residual (the cached
+    order) at the FP32-bulk bound of the parity tests, on two calls."""
+    op = tri_operator(3)
+    m = periodic_tri_mesh(op, 9, 10.0, 0.05)
+    s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32"))
+    ref = s.empty()
+    for call in range(2):
+        u = s.to_device(states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 110 + call))
+        s.residual(u, ref)
+        out = torch.full_like(ref, float("nan"))
+        rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+        assert rc == 0, lib.capi.esplit_last_error(s.ctx)
+        torch.cuda.synchronize()
+        num = (out - ref).abs().amax(dim=(0, 2))
+        den = ref.abs().amax(dim=(0, 2))
+        assert float((num / den).max()) <= 1e-11
+    s.close()
+
+
+def test_noalloc_allocates_nothing(lib):
+    """After a first call (which looks up the static array and loads the
+    kernels it launches), further calls leave the device's free memory and
+    PyTorch's allocator untouched, and with kernel timing enabled on the
+    context they record no timing (timing would create CUDA events)."""
+    op = tri_operator(2)
+    m = periodic_tri_mesh(op, 9, 10.0, 0.05)
+    s = lib.Solver(op, m, lib.Params(dissipation=True))
+    u = s.to_device(states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 120))
+    out = s.empty()
+    rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+    assert rc == 0, lib.capi.esplit_last_error(s.ctx)
+    s.profile(True)
+    s.profile_read()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+        assert rc == 0, lib.capi.esplit_last_error(s.ctx)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert all(v[1] == 0 for v in s.profile_read().values())
+    # the context's own residual still records its timing
+    s.residual(u, out)
+    assert any(v[1] > 0 for v in s.profile_read().values())
+    s.profile(False)
+    s.close()
