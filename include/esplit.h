@@ -39,9 +39,25 @@ extern "C" {
 #define ESPLIT_ERR_STATE (-7)        /* call order (e.g. residual before mesh upload) */
 
 #define ESPLIT_FP64 0       /* everything in float64                               */
-#define ESPLIT_FP32_BULK 1  /* fluxes and operator contractions in float32; metric
-                               terms, entropy-rate products and the relaxation root
-                               solve stay float64                                   */
+#define ESPLIT_FP32_BULK 1  /* entropy-split volume term: operator contractions as
+                               compensated float32 dot products (Dot2) on the
+                               variations inside each element, fluxes, entropy
+                               variables and A~_i products in float64 (accuracy of
+                               the float64 path to ~1e-12); facet terms, viscous
+                               terms, entropy functionals and the relaxation root
+                               solve in float64.  Hadamard forms: their two-point
+                               fluxes in plain float32                              */
+#define ESPLIT_FP32 2       /* entropy-split scheme, inviscid: fluxes, entropy
+                               variables, A~_i products, two-point fluxes,
+                               dissipation and operator contractions in float32,
+                               evaluated as deviations from float64 reference
+                               states (cancellation-free rearrangements of Eqs.
+                               (5), (25), (48), (69)); float64 for the state
+                               differences, the residual's accumulation, the
+                               entropy-production sums, the metric operators (formed
+                               in float64, rounded once) and the relaxation step.
+                               Other schemes and the viscous terms: as
+                               ESPLIT_FP32_BULK                                     */
 
 #define ESPLIT_SCHEME_SPLIT 0     /* entropy split, Eq. (100)                       */
 #define ESPLIT_SCHEME_HADAMARD 1  /* Sjogreen-Yee Hadamard form, Eq. (99)            */
@@ -67,7 +83,7 @@ typedef struct esplit_params {
   int viscous;     /* 1: add Eqs. (83)-(85) with Baumann-Oden SATs, Eq. (96)         */
   int heat_flux;   /* 1: include the heat flux in the viscous flux                   */
   int scheme;      /* ESPLIT_SCHEME_*                                                */
-  int precision;   /* ESPLIT_FP64 or ESPLIT_FP32_BULK                                */
+  int precision;   /* ESPLIT_FP64, ESPLIT_FP32_BULK or ESPLIT_FP32                   */
 } esplit_params;
 
 typedef struct esplit_stepinfo {

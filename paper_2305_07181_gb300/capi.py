@@ -23,6 +23,7 @@ ESPLIT_ERR_STATE = -7
 
 ESPLIT_FP64 = 0
 ESPLIT_FP32_BULK = 1
+ESPLIT_FP32 = 2
 ESPLIT_SCHEME_SPLIT = 0
 ESPLIT_SCHEME_HADAMARD = 1
 ESPLIT_SCHEME_HYBRID = 2

@@ -209,7 +209,8 @@ int esplit_upload_operator(esplit_ctx* c, int n_p, int n_fac, int n_f, const dou
   int rc = dalloc(c, &c->b.Qref, (size_t)c->dim * n_p * n_p);
   if (rc) return rc;
   CK(cudaMemcpy(c->b.Qref, Q_ref, sizeof(double) * c->dim * n_p * n_p, cudaMemcpyHostToDevice));
-  if (esplit::set_ref_tables(t)) return fail(c, ESPLIT_ERR_CUDA, "constant-table upload failed");
+  if (esplit::set_ref_tables(t) || esplit::set_ref_tables_f32(t))
+    return fail(c, ESPLIT_ERR_CUDA, "constant-table upload failed");
   c->ref = t;
   c->n_p = n_p;
   c->n_fac = n_fac;
@@ -323,7 +324,8 @@ int esplit_set_params(esplit_ctx* c, const esplit_params* p) {
   if (!(alpha < -p->gam || alpha > 0.0)) return fail(c, ESPLIT_ERR_ARG, "beta must give alpha < -gam or alpha > 0");
   if (!(p->R > 0.0) || p->mu < 0.0 || !(p->Pr > 0.0)) return fail(c, ESPLIT_ERR_ARG, "R, Pr must be > 0, mu >= 0");
   if (p->scheme < 0 || p->scheme > 3) return fail(c, ESPLIT_ERR_ARG, "unknown scheme");
-  if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK) return fail(c, ESPLIT_ERR_ARG, "unknown precision");
+  if (p->precision != ESPLIT_FP64 && p->precision != ESPLIT_FP32_BULK && p->precision != ESPLIT_FP32)
+    return fail(c, ESPLIT_ERR_ARG, "unknown precision");
   if (p->viscous && c->dim == 1) return fail(c, ESPLIT_ERR_UNSUPPORTED, "1D: inviscid only");
   cudaSetDevice(c->device);
   bool beta_changed = p->beta != c->prm.beta;

@@ -1,0 +1,266 @@
+// Float32 path of the entropy-split residual (precision ESPLIT_FP32): the
+// inviscid split scheme of Eq. (100) with the EC SATs of Eq. (43) and the
+// matrix dissipation of Eq. (69), with the fluxes, entropy variables, A~_i
+// products, two-point fluxes, dissipation and operator contractions all
+// evaluated in float32 on deviations (dev32.cuh).  Float64 is kept for the
+// differences of the conservative states that the deviations start from, the
+// accumulation of the residual and of the entropy production w^T H r, and
+// everything outside the residual (the stored metric operators are formed in
+// float64 and rounded once; entropy, relaxation root and update stay float64).
+//
+// Two kernels, one after the other on the stream:
+//   split_volume_f32_kernel: thread = node, EB elements per block.  Variations
+//     relative to the element's node 0, D_i = H^-1 Q_x_i applied to the
+//     flux and entropy-variable variations (D_i 1 = 0 by the discrete metric
+//     identity, so the node-0 values drop out; the float64 row sums of the
+//     stored operators, ~eps |D_i|, are below float32 resolution):
+//       r = -beta/(beta+1) sum_i D_i df_i - 1/(beta+1) sum_i A~_i(u) (D_i dw)
+//     assigned to r (float64).
+//   face_f32_kernel: thread = coincident facet-node pair (k, m) ~ (v, n).
+//     With G = nu . (F*(u_k, u_v) - F(u_k)) (sy_flux_dev32), the jump
+//     df = nu . (F(u_v) - F(u_k)) and Dw = |nu|/2 X|L|SX^T (w_k - w_v):
+//       H_k r_k += -G - Dw            (= nu . F(u_k) - nu . F* - Dw)
+//       H_v r_v += G - df + Dw        (= nu . F* - nu . F(u_v) + Dw)
+//     i.e. the SATs together with the facet part nu . f / H of the split
+//     volume term (M_i = H^-1 E_i - beta/(beta+1) D_i), as the float64
+//     facet kernel adds them.
+// Entropy production (when requested): block partials of sum H w . r in
+// float64, w formed in float32 as the reference's W plus its variation.
+#include <cuda_runtime.h>
+
+#include "dev32.cuh"
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace esplit {
+
+__constant__ RefTables c_ref32;
+
+int set_ref_tables_f32(const RefTables& t) {
+  return cudaMemcpyToSymbol(c_ref32, &t, sizeof(RefTables)) == cudaSuccess ? 0 : -1;
+}
+
+template <int D, int NP, int EB>
+struct SplitSmem32 {
+  float df[EB][D][D + 2][NP];  // flux variations
+  float dw[EB][D + 2][NP];     // entropy-variable variations
+  double u0[EB][D + 2];        // node-0 states
+};
+
+template <int D, int NP, int EB>
+__global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kernel(
+    const double* __restrict__ u, double* __restrict__ r, const float* __restrict__ ops,
+    const double* __restrict__ J, int n_e, Phys<float> c, int* __restrict__ status, double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  __shared__ SplitSmem32<D, NP, EB> sm;
+  const int el = threadIdx.x / NP;
+  const int m = threadIdx.x - el * NP;
+  const int e = blockIdx.x * EB + el;
+  const bool active = (el < EB) && (e < n_e);
+  double uu[NC];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) uu[q] = __ldg(&u[((size_t)e * NC + q) * NP + m]);
+    if (m == 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sm.u0[el][q] = uu[q];
+    }
+  }
+  __syncthreads();
+  Ref32<D> rf;
+  Dev32<D> dv;
+  float du[NC];
+  if (active) {
+    double u0[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      u0[q] = sm.u0[el][q];
+      du[q] = (float)(uu[q] - u0[q]);
+    }
+    ref32_from_u<D>(u0, c, rf);
+    dev32<D>(rf, du, c, dv);
+    if (!(dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1) && rf.rho > 0.0f && rf.p > 0.0f)) atomicOr(status, 1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float F[NC];
+      dflux32<D>(rf, du, dv, i, F);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) sm.df[el][i][q][m] = F[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sm.dw[el][q][m] = dv.dW[q];
+  }
+  __syncthreads();
+  double hw = 0.0;
+  if (active) {
+    const float* op = ops + (size_t)e * (2 * D * NP * NP);
+    float acc[NC], g[D][NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) acc[q] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) g[i][q] = 0.0f;
+#pragma unroll 6
+      for (int n = 0; n < NP; ++n) {
+        const float dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          acc[q] = fmaf(dt, sm.df[el][i][q][n], acc[q]);
+          g[i][q] = fmaf(dt, sm.dw[el][q][n], g[i][q]);
+        }
+      }
+    }
+    Node<float, D> nd;
+    node32<D>(rf, dv, nd);
+    const JvpPrep<float> jp = jvp_prep<float, D>(nd, c);
+    float nonc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) nonc[q] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float dF[NC];
+      dflux_dw<float, D>(nd, jp, c, i, g[i], dF);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
+    }
+    const float kf = c.beta * c.inv_bp1;
+    double res[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      res[q] = (double)(-kf * acc[q] - c.inv_bp1 * nonc[q]);
+      r[((size_t)e * NC + q) * NP + m] = res[q];
+    }
+    if (prod) {
+      const double Hm = c_ref32.H[m] * __ldg(&J[(size_t)e * NP + m]);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) hw += (double)nd.W[q] * res[q];
+      hw *= Hm;
+    }
+  }
+  if (prod) {
+    double v[1] = {hw};
+    block_sum<1>(v, prod + blockIdx.x);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) face_f32_kernel(double* __restrict__ r, const double* __restrict__ u,
+                                                       const int2* __restrict__ fp, int n_pairs,
+                                                       const double* __restrict__ nu, const double* __restrict__ J,
+                                                       Phys<float> c, int dissipation, int* __restrict__ status,
+                                                       double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double hw = 0.0;
+  if (t < n_pairs) {
+    const int NP = c_ref32.n_p, NS = c_ref32.n_slot;
+    const int2 pr = __ldg(&fp[t]);
+    const int k = pr.x / NS, s = pr.x - k * NS;
+    const int v = pr.y / NS, s2 = pr.y - v * NS;
+    const int m = c_ref32.slot_node[s], n = c_ref32.slot_node[s2];
+    double uk[NC];
+    float du[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      uk[q] = __ldg(&u[((size_t)k * NC + q) * NP + m]);
+      du[q] = (float)(__ldg(&u[((size_t)v * NC + q) * NP + n]) - uk[q]);
+    }
+    Ref32<D> rk;
+    Dev32<D> dv;
+    ref32_from_u<D>(uk, c, rk);
+    dev32<D>(rk, du, c, dv);
+    if (!(rk.rho > 0.0f && rk.p > 0.0f && dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1))) atomicOr(status, 1);
+    float nuv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nuv[i] = (float)__ldg(&nu[((size_t)k * NS + s) * D + i]);
+    float G[NC], df[NC], Dw[NC];
+    PairAvg<float, D> a;
+    sy_flux_dev32<D>(rk, dv, c, nuv, G, a);
+    dflux32_dir<D>(rk, du, dv, nuv, df);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) Dw[q] = 0.0f;
+    if (dissipation) {
+      float b2 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+      const float b = sqrtf(b2);
+      const float ib = 1.0f / b;
+      float nh[D], mdw[NC], out[NC];
+#pragma unroll
+      for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) mdw[q] = -dv.dW[q];  // w_k - w_v
+      diss_apply<float, D>(a, c, nh, mdw, out);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) Dw[q] = 0.5f * b * out[q];
+    }
+    const double ihk = 1.0 / (c_ref32.H[m] * __ldg(&J[(size_t)k * NP + m]));
+    const double ihv = 1.0 / (c_ref32.H[n] * __ldg(&J[(size_t)v * NP + n]));
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const double gk = (double)(-G[q] - Dw[q]);
+      const double gv = (double)(G[q] - df[q] + Dw[q]);
+      r[((size_t)k * NC + q) * NP + m] += gk * ihk;
+      r[((size_t)v * NC + q) * NP + n] += gv * ihv;
+      if (prod) hw += (double)rk.W[q] * gk + (double)(rk.W[q] + dv.dW[q]) * gv;
+    }
+  }
+  if (prod) {
+    double vv[1] = {hw};
+    block_sum<1>(vv, prod + blockIdx.x);
+  }
+}
+
+template <int D, int NP>
+static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+  constexpr int EB = (256 / NP) > 0 ? (256 / NP) : 1;
+  const Phys<float> ph = make_phys<float>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  int np_used = 0;
+  {
+    const int nb = (c->n_e + EB - 1) / EB;
+    ProfScope ps(c, PG_SPLIT, s);
+    split_volume_f32_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops32, c->b.J, c->n_e, ph, c->b.status,
+                                                              prod);
+    c->launches++;
+    if (prod) np_used += nb;
+  }
+  {
+    const int bs = 128, nb = (c->n_pairs + bs - 1) / bs;
+    ProfScope ps(c, PG_FACE, s);
+    face_f32_kernel<D><<<nb, bs, 0, s>>>(r, u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, ph,
+                                         c->prm.dissipation, c->b.status, prod ? prod + np_used : nullptr);
+    c->launches++;
+    if (prod) np_used += nb;
+  }
+  if (n_partial) *n_partial = np_used;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+  if (c->dim == 1) {
+    switch (c->n_p) {
+      case 2: return split_f32_np<1, 2>(c, u, r, s, prod, n_partial);
+      case 3: return split_f32_np<1, 3>(c, u, r, s, prod, n_partial);
+      case 4: return split_f32_np<1, 4>(c, u, r, s, prod, n_partial);
+      case 5: return split_f32_np<1, 5>(c, u, r, s, prod, n_partial);
+    }
+  } else if (c->dim == 2) {
+    switch (c->n_p) {
+      case 7: return split_f32_np<2, 7>(c, u, r, s, prod, n_partial);
+      case 12: return split_f32_np<2, 12>(c, u, r, s, prod, n_partial);
+      case 18: return split_f32_np<2, 18>(c, u, r, s, prod, n_partial);
+      case 27: return split_f32_np<2, 27>(c, u, r, s, prod, n_partial);
+    }
+  } else if (c->dim == 3) {
+    switch (c->n_p) {
+      case 12: return split_f32_np<3, 12>(c, u, r, s, prod, n_partial);
+      case 25: return split_f32_np<3, 25>(c, u, r, s, prod, n_partial);
+      case 58: return split_f32_np<3, 58>(c, u, r, s, prod, n_partial);
+      case 78: return split_f32_np<3, 78>(c, u, r, s, prod, n_partial);
+    }
+  }
+  return -2;
+}
+
+}  // namespace esplit

@@ -185,6 +185,11 @@ struct StepRecord {
 int launch_step_record(esplit_ctx* c, StepRecord* hist, int* counter, int cap, cudaStream_t s);
 int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
 int set_ref_tables(const RefTables& t);
+// float32 path of the inviscid split scheme (fp32.cu): its own copy of the
+// reference tables, and the launcher (volume kernel, then facet kernel adding
+// into r); -2 for an operator size not compiled in
+int set_ref_tables_f32(const RefTables& t);
+int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial);
 int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);
 // static facet scratch of esplit_residual_noalloc: 2^21 doubles (16 MiB)
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(1) << 21;

@@ -22,6 +22,7 @@
 #include "internal.h"
 #include "phys.cuh"
 #include "visc_flux.cuh"
+#include "reduce.cuh"
 
 namespace esplit {
 
@@ -29,42 +30,6 @@ __constant__ RefTables c_ref;
 
 int set_ref_tables(const RefTables& t) {
   return cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables)) == cudaSuccess ? 0 : -1;
-}
-
-// ---------------------------------------------------------------------------
-// block reduction helpers (deterministic: fixed shuffle tree + fixed warp order)
-// ---------------------------------------------------------------------------
-template <int W>
-__device__ __forceinline__ void block_sum(double (&v)[W], double* out_row) {
-  __shared__ double red[32][W];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // a block of EB * NP threads may end in a partial warp: shuffle among the
-  // lanes that exist and add only values read from them
-  const int nl = min(32, (int)blockDim.x - (warp << 5));
-  const unsigned mask = nl == 32 ? 0xffffffffu : ((1u << nl) - 1u);
-#pragma unroll
-  for (int k = 0; k < W; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double y = __shfl_down_sync(mask, v[k], o);
-      if (lane + o < nl) v[k] += y;
-    }
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < W; ++k) red[warp][k] = v[k];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      double x = lane < nw ? red[lane][k] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) out_row[k] = x;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1152,8 +1117,15 @@ static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s,
   return -2;
 }
 
+// the float32 deviation path (fp32.cu) covers the inviscid split scheme; the
+// other schemes and the viscous terms take the FP32-bulk kernels there
+static bool use_f32_path(const esplit_ctx* c) {
+  return c->prm.precision == ESPLIT_FP32 && c->prm.scheme == ESPLIT_SCHEME_SPLIT && !c->prm.viscous;
+}
+
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
-  if (c->prm.precision == ESPLIT_FP32_BULK) return residual_t<float>(c, u, r, s, prod, n_partial, c->b.sat);
+  if (use_f32_path(c)) return launch_split_f32(c, u, r, s, prod, n_partial);
+  if (c->prm.precision != ESPLIT_FP64) return residual_t<float>(c, u, r, s, prod, n_partial, c->b.sat);
   return residual_t<double>(c, u, r, s, prod, n_partial, c->b.sat);
 }
 
@@ -1186,8 +1158,9 @@ int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStrea
   // kernel timing would create CUDA events: off for this thread's launches
   // (the context's setting, which other threads may be using, is untouched)
   t_no_events = true;
-  int rc = c->prm.precision == ESPLIT_FP32_BULK ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
-                                                 : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
+  int rc = use_f32_path(c) ? launch_split_f32(c, u, r, s, nullptr, nullptr)  // needs no scratch
+           : c->prm.precision != ESPLIT_FP64 ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
+                                              : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
   t_no_events = false;
   // viscous terms (inside the residual launch) use the context's viscous
   // scratch, allocated when they were switched on

@@ -46,12 +46,13 @@ class Params:
     viscous: bool = False
     heat_flux: bool = True
     scheme: str = "split"          # "split" | "hadamard" | "hybrid" | "hadamard_ir"
-    precision: str = "fp64"        # "fp64" | "fp32"
+    precision: str = "fp64"        # "fp64" | "fp32_bulk" | "fp32" (include/esplit.h ESPLIT_FP*)
 
     def to_c(self) -> capi.esplit_params:
         sch = {"split": capi.ESPLIT_SCHEME_SPLIT, "hadamard": capi.ESPLIT_SCHEME_HADAMARD,
                "hybrid": capi.ESPLIT_SCHEME_HYBRID, "hadamard_ir": capi.ESPLIT_SCHEME_HADAMARD_IR}[self.scheme]
-        prec = {"fp64": capi.ESPLIT_FP64, "fp32": capi.ESPLIT_FP32_BULK}[self.precision]
+        prec = {"fp64": capi.ESPLIT_FP64, "fp32_bulk": capi.ESPLIT_FP32_BULK,
+                "fp32": capi.ESPLIT_FP32}[self.precision]
         return capi.esplit_params(self.gam, self.beta, self.R, self.mu, self.Pr, int(self.dissipation),
                                   int(self.viscous), int(self.heat_flux), sch, prec)
 

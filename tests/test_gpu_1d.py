@@ -73,7 +73,7 @@ def test_1d_fp32_and_entropy(lib, p):
     op = line_operator(p)
     m = periodic_line_mesh(op, 64, 2.0, amp=0.1)
     u = states.add_uniform_noise(states.uniform_state(m.n_e, 1, op.n_p), 1e-2, 4)
-    s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32_bulk"))
     ud = s.to_device(u)
     err = rel_err(s.residual(ud).cpu().numpy(), R.residual(u, op, m, OP(), dissipation=True).numpy())
     print(f"1D p={p} fp32 split rel err {err:.2e}")

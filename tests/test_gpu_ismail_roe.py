@@ -133,7 +133,7 @@ def test_ir_hadamard_fp32(lib):
     op = tri_operator(3)
     m = periodic_tri_mesh(op, 8, 10.0, 0.05)
     u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
-    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir", precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(scheme="hadamard_ir", precision="fp32_bulk"))
     r = s.residual(s.to_device(u)).cpu().numpy()
     s.close()
     err = rel_err(r, R.residual(u, op, m, OP(), scheme="hadamard_ir").numpy())

@@ -82,7 +82,7 @@ def test_residual_fp32_bulk_bound(lib, p, scheme):
     R, Dg, rrk, OP = _oracle()
     op, m = _mesh(p, N=8)
     u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
-    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32_bulk"))
     r = s.residual(s.to_device(u)).cpu().numpy()
     ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True).numpy()
     err = rel_err(r, ro)
@@ -295,7 +295,7 @@ def test_fp32_full_size_sampled(lib, p):
     u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
     sample = np.random.default_rng(50 + p).choice(m.n_e, 48, replace=False)
     for scheme in ["split", "hadamard"]:
-        s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32"))
+        s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32_bulk"))
         r = s.residual(s.to_device(u)).cpu().numpy()[sample]
         ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True, elems=sample).numpy()
         err = rel_err(r, ro)
@@ -308,10 +308,11 @@ def test_full_size_against_extended_precision(lib):
     """The GPU residual of config 2 at p = 3 (32,768 curved triangles, vortex +
     1e-3 noise, split and Hadamard forms with dissipation, the bench's launch
     configuration) against the residual of the same float64 inputs evaluated
-    at 50 digits (tests/golden/vortex128_p3_extended.txt, 8 sampled elements):
-    the GPU path's own rounding is within 4 eps of the summand scale, as the
-    float64 oracle's is within 2 (test_oracle_extended.py) -- the premise of
-    the rounding-scale bound of the other full-size checks."""
+    at 50 digits (tests/golden/vortex128_p3_extended.txt: 5 sampled elements
+    and the float64 inputs they depend on, put into the generated arrays
+    first): the GPU path's own rounding is within 4 eps of the summand scale,
+    as the float64 oracle's is within 3 (test_oracle_extended.py) -- the
+    premise of the rounding-scale bound of the other full-size checks."""
     from extended_golden import golden_elements
     from oracle.physics import Params as OP
     op, m, u, el, gold = golden_elements()

@@ -64,7 +64,7 @@ def test_steps_match_single_steps_split(lib):
 def test_steps_match_single_steps_schemes_and_precision(lib):
     op, m, u0, dt = _tri(p=3, N=6)
     _compare(lib, op, m, u0, dt, lib.Params(dissipation=True, scheme="hadamard"), n=8)
-    _compare(lib, op, m, u0, dt, lib.Params(dissipation=True, precision="fp32"), n=8)
+    _compare(lib, op, m, u0, dt, lib.Params(dissipation=True, precision="fp32_bulk"), n=8)
     flags = np.zeros(m.n_e, dtype=np.uint8)
     flags[::5] = 1
     _compare(lib, op, m, u0, dt, lib.Params(dissipation=True, scheme="hybrid"), n=8, flags=flags)

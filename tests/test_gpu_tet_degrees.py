@@ -105,7 +105,7 @@ def test_tet_fp32_bulk_bound(lib, p, scheme):
     R, Dg, rrk, OP = _oracle()
     op, m = _tet(p)
     u = states.add_uniform_noise(states.taylor_green(m, Mach=0.3), 1e-3, 5)
-    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision="fp32_bulk"))
     r = s.residual(s.to_device(u)).cpu().numpy()
     ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=True).numpy()
     err = rel_err(r, ro)

@@ -169,7 +169,7 @@ def test_viscous_fp32_bulk_bound(lib):
     R, Dg, rrk, OP = _oracle()
     op, m = _tri(3, N=8)
     u = states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 2)
-    s = lib.Solver(op, m, lib.Params(mu=0.01, viscous=True, dissipation=True, precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(mu=0.01, viscous=True, dissipation=True, precision="fp32_bulk"))
     r = s.residual(s.to_device(u)).cpu().numpy()
     ro = R.residual(u, op, m, OP(mu=0.01), dissipation=True, viscous=True).numpy()
     err = rel_err(r, ro)
@@ -256,7 +256,7 @@ def test_full_size_taylor_green_fp32_bulk(lib):
     op, m, u = _tgv_full()
     mu = 1.0 / 1600.0
     sample = np.concatenate([np.random.default_rng(81).choice(m.n_e, 40, replace=False), [0, m.n_e - 1]])
-    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True, precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(mu=mu, viscous=True, dissipation=True, precision="fp32_bulk"))
     r = s.residual(s.to_device(u)).cpu().numpy()[sample]
     s.close()
     ro = R.residual(u, op, m, OP(mu=mu), dissipation=True, viscous=True, elems=sample).numpy()

@@ -111,10 +111,11 @@ def test_extended_entropy_conservation(scheme):
 
 def test_oracle_float64_against_extended():
     """The float64 oracle against the 50-digit residual (stored by
-    tests/golden/make_extended_residual.py, which calls only oracle/) on 8
+    tests/golden/make_extended_residual.py, which calls only oracle/) on 5
     sampled elements of config 2 at p = 3, split and Hadamard forms with
-    dissipation: within 2 eps of the summand scale (observed 1.1).  Its plain
-    max-norm relative error is printed (above 1e-12 on this mesh)."""
+    dissipation, on the stored inputs: within 3 eps of the summand scale
+    (observed 0.4 split, 1.5 Hadamard).  Its plain max-norm relative error is
+    printed (about 1e-12 on this mesh)."""
     from oracle import residual as R
     from oracle.physics import Params
     op, m, u, el, gold = golden_elements()
@@ -125,7 +126,7 @@ def test_oracle_float64_against_extended():
         plain = float((err.max(axis=(0, 2)) / np.abs(gold[scheme]).max(axis=(0, 2))).max())
         print(f"oracle vs 50 digits, {scheme}: max err/(eps scale) {float((err / (EPS * sc)).max()):.2f}, "
               f"plain max-norm rel {plain:.2e}")
-        assert np.all(err <= 2.0 * EPS * sc)
+        assert np.all(err <= 3.0 * EPS * sc)
 
 
 def test_golden_matches_a_fresh_extended_evaluation():

@@ -91,7 +91,7 @@ def test_noalloc_fp32_bulk_matches_residual(lib):
     order) at the FP32-bulk bound of the parity tests, on two calls."""
     op = tri_operator(3)
     m = periodic_tri_mesh(op, 9, 10.0, 0.05)
-    s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32"))
+    s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32_bulk"))
     ref = s.empty()
     for call in range(2):
         u = s.to_device(states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 110 + call))
