@@ -397,3 +397,16 @@ def periodic_line_mesh(op: RefOperator, N: int, L: float = 1.0, origin: float = 
     return Mesh(d=1, n_e=N, n_p=op.n_p, n_fac=2, n_f=1, L=(L,), x=x, J=J, Lam=Lam, nu=nu, pair=pair, hmin=hmin,
                 meta=dict(kind="periodic_line", N=N, L=L, amp=amp, p=op.p, origin=origin, vertices=xv))
 
+
+def line_mesh(op: RefOperator, N: int, L: float = 1.0, origin: float = 0.0, amp: float = 0.0) -> Mesh:
+    """The interval [x0, x0 + L] cut into N elements as periodic_line_mesh
+    does, with two boundary facets instead of the periodic wrap: facet 0 of
+    element 0 (x = x0, nu = -1) and facet 1 of element N - 1 (x = x0 + L,
+    nu = +1) pair with no element, marked (-1, -1) in ``pair``; their flat
+    slot indices (element * 2 + facet) are meta["boundary_slots"] = [0, 2N - 1]."""
+    m = periodic_line_mesh(op, N, L, origin, amp)
+    m.pair[0, 0, 0] = (-1, -1)
+    m.pair[N - 1, 1, 0] = (-1, -1)
+    m.meta["kind"] = "line"
+    m.meta["boundary_slots"] = np.array([0, 2 * N - 1], dtype=np.int32)
+    return m

@@ -166,3 +166,38 @@ def sod_periodic(mesh, gam=GAMMA):
     V = np.zeros((1, mesh.n_e, mesh.n_p))
     return np.ascontiguousarray(np.moveaxis(prim_to_cons(r, V, pr, gam), 0, 1))
 
+
+SHU_OSHER_LEFT = (3.857143, 2.629369, 10.33333)   # rho, u, p for x <= -4 (Sec. 7.2)
+
+
+def shu_osher_right(x):
+    """rho, u, p of the Sec. 7.2 initial state for x > -4: 1 + 0.2 sin(5x), 0, 1."""
+    x = np.asarray(x, dtype=float)
+    return 1.0 + 0.2 * np.sin(5.0 * x), np.zeros_like(x), np.ones_like(x)
+
+
+def shu_osher(mesh, gam=GAMMA):
+    """The Shu-Osher problem of Sec. 7.2 on [-5, 5]: the left state (3.857143,
+    2.629369, 10.33333) on elements whose centre is left of x = -4, the
+    sinusoidal right state at the nodes elsewhere (a mesh with a vertex at
+    x = -4 puts the jump on an element boundary)."""
+    x = mesh.x[:, 0, :]
+    left = (x.mean(axis=1) <= -4.0)[:, None] * np.ones((1, mesh.n_p), dtype=bool)
+    rr, ur, pr = shu_osher_right(x)
+    rl, ul, pl = SHU_OSHER_LEFT
+    rho = np.where(left, rl, rr)
+    V = np.where(left, ul, ur)[None]
+    p = np.where(left, pl, pr)
+    return np.ascontiguousarray(np.moveaxis(prim_to_cons(rho, V, p, gam), 0, 1))
+
+
+def shu_osher_boundary(gam=GAMMA):
+    """Exterior states of the two boundary facets of [-5, 5] (slots in the
+    order of line_mesh's meta["boundary_slots"]): the supersonic inflow state
+    at x = -5 and the undisturbed right state at x = 5, which no wave reaches
+    before t = 1.8 (the shock is near x = 2.4 then).  (2, n_c) conservative."""
+    rl, ul, pl = SHU_OSHER_LEFT
+    rr, ur, pr = shu_osher_right(np.array([5.0]))
+    left = prim_to_cons(np.array([rl]), np.array([[ul]]), np.array([pl]), gam)[:, 0]
+    right = prim_to_cons(rr, ur[None], pr, gam)[:, 0]
+    return np.stack([left, right])

@@ -139,19 +139,40 @@ int esplit_upload_operator(esplit_ctx* ctx, int n_p, int n_fac, int n_f, const d
                            const double* Q_ref, const int* facet_nodes, const double* facet_w,
                            const double* ref_normals);
 
-/* Curved periodic mesh (every facet interior, Sec. 2.1 conforming meshes).
+/* Curved mesh (Sec. 2.1 conforming meshes): periodic, or with boundary facets.
  *   J      [n_e][n_p]               mapping Jacobian at the nodes, > 0
  *   Lambda [n_e][d][d][n_p]         Lambda_ij = J dxi_j/dx_i at the nodes
  *   nu     [n_e][n_fac][n_f][d]     scaled outward normal b n at facet slots
  *                                   (the diagonal of E_x_i, Eq. (2))
- *   pair   [n_e][n_fac][n_f][2]     (neighbour element, neighbour flat slot)
+ *   pair   [n_e][n_fac][n_f][2]     (neighbour element, neighbour flat slot),
+ *                                   or (-1, -1) for a boundary facet slot
  *   hmin   [n_e]                    smallest node distance (may be NULL)
- * Host pointers, copied.  Validation: pair is an involution, nu of paired
- * slots are opposite (relative 1e-10), J > 0; else ESPLIT_ERR_MESH.  The
- * per-element physical operators Q_x_i = 1/2 sum_j (Lam_ij Q_xi_j -
- * Q_xi_j^T Lam_ij) + 1/2 E_x_i are formed on the device here. */
+ * Host pointers, copied.  Validation: pair restricted to the other slots is
+ * an involution, nu of paired slots are opposite (relative 1e-10), boundary
+ * slots have a nonzero nu, J > 0; else ESPLIT_ERR_MESH.  A mesh with
+ * boundary slots needs their exterior states (esplit_set_boundary_states)
+ * before a residual.  The per-element physical operators Q_x_i = 1/2 sum_j
+ * (Lam_ij Q_xi_j - Q_xi_j^T Lam_ij) + 1/2 E_x_i are formed on the device
+ * here. */
 int esplit_upload_mesh(esplit_ctx* ctx, int n_e, const double* J, const double* Lambda,
                        const double* nu, const int* pair, const double* hmin);
+
+/* Exterior states of the boundary facet slots (bounded domains, e.g. the
+ * shock tubes of Secs. 7.1-7.2; the paper's analysis is periodic and it does
+ * not print its boundary treatment).  A boundary slot takes the interface
+ * terms of an interior one -- the EC SAT of Eq. (43) with the two-point flux
+ * of the scheme and, when on, the dissipation of Eq. (69) -- with the
+ * neighbour's state replaced by its exterior state u_b (weak imposition of
+ * the boundary data through the interface coupling; a supersonic inflow
+ * state, or the undisturbed outer state at an outflow).
+ *   slots  [n_b]        flat slot indices element * n_slot + slot, each a
+ *                       boundary slot of the mesh, each given once
+ *   states [n_b][n_c]   conservative exterior states (rho > 0, p > 0)
+ * n_b must equal the mesh's number of boundary slots.  Host pointers,
+ * copied; ESPLIT_ERR_ARG otherwise.  Inviscid only: a residual with viscous
+ * terms on such a mesh, and the reverse-mode calls, return
+ * ESPLIT_ERR_UNSUPPORTED. */
+int esplit_set_boundary_states(esplit_ctx* ctx, int n_b, const int* slots, const double* states);
 
 /* Parameters (host struct, copied).  Changing beta re-forms the stored
  * split operators. */

@@ -45,11 +45,17 @@ def detect(u, ref, mesh, threshold=1.1, gam=1.4):
     p = detector_pressure(u, gam)                               # (n_e, n_p)
     fn = np.asarray(ref.facet_nodes).reshape(-1)
     pair = np.asarray(mesh.pair).reshape(mesh.n_e, -1, 2)       # (n_e, n_slot, 2)
-    p_nb = p[pair[..., 0], fn[pair[..., 1]]]                    # neighbours' coincident facet nodes
+    # boundary facets (pair (-1, -1)) have no neighbour: their own facet node
+    # stands in for it (it changes neither the max nor the min) and they widen nothing
+    own = np.broadcast_to(np.arange(mesh.n_e)[:, None], pair.shape[:2])
+    bnd = pair[..., 0] < 0
+    nb_e = np.where(bnd, own, pair[..., 0])
+    nb_n = np.where(bnd, fn[None, :], fn[np.maximum(pair[..., 1], 0)])
+    p_nb = p[nb_e, nb_n]                                        # neighbours' coincident facet nodes
     allp = np.concatenate([p, p_nb], axis=1)
     good = np.all((allp > 0) & (allp < np.inf), axis=1)
     with np.errstate(invalid="ignore", divide="ignore"):
         ratio = allp.max(axis=1) / allp.min(axis=1)
     flag0 = ~good | ~(ratio <= threshold)
-    flags = flag0 | np.any(flag0[pair[..., 0]], axis=1)
+    flags = flag0 | np.any(flag0[nb_e], axis=1)
     return flags.astype(np.uint8)

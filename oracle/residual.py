@@ -15,6 +15,12 @@ Facet terms, once per facet node of the element (diagonal E, Sec. 4 Remark):
     on curved facets
 Viscous terms (Sec. 5, Eqs. (83)-(85)) with Baumann-Oden coefficients
 (Eq. (96)): T1 = 0, T2 = T3 = B/2.
+Boundary facets (bounded 1D domains of Secs. 7.1-7.2; the paper's theory is
+periodic and it does not print its boundary treatment): a facet slot whose
+pair is (-1, -1) takes the same SAT and dissipation as an interior one, with
+the neighbour's state replaced by a prescribed exterior state u_b (reading:
+the interface coupling of Eq. (43) with a ghost state, weak imposition of
+the boundary data; inviscid only).
 
 Readings (the paper is ambiguous or has typos there):
   * Eq. (100): the facet sum runs over Gamma^I_k (printed Gamma^I);
@@ -85,7 +91,7 @@ def hadamard_volume(U, ops, prm: Params, form="weak", flux=None):
 
 
 def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak",
-             dissipation=False, viscous=False, hybrid_flags=None, elems=None):
+             dissipation=False, viscous=False, hybrid_flags=None, elems=None, boundary=None):
     """du/dt for the elements ``elems`` (all if None), layout (n, n_c, n_p).
 
     scheme: "split", "hadamard" or "hybrid" (per-element ``hybrid_flags``,
@@ -95,7 +101,9 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     jump of the standard entropy variables) when ``dissipation``, and the
     same Baumann-Oden viscous terms written with the standard entropy
     variables when ``viscous``.  ``u`` may be a torch tensor requiring grad
-    (the oracle adjoint differentiates through this function)."""
+    (the oracle adjoint differentiates through this function).
+    ``boundary`` = (slots, states): flat facet slots (element * n_slot + slot)
+    whose pair is (-1, -1), and their exterior states (n_b, n_c)."""
     U_all = _as_U(u)
     n_e, n_p, nc = U_all.shape
     d = nc - 2
@@ -103,6 +111,17 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     n_slot = ref.n_fac * ref.n_f
     pair = pair.reshape(n_e, n_slot, 2)
     fn = torch.as_tensor(ref.facet_nodes.reshape(-1), dtype=torch.long)
+    bmask = pair[..., 0] < 0                                      # boundary facet slots
+    if bool(bmask.any()):
+        if viscous:
+            raise NotImplementedError("viscous terms on boundary facets")
+        if boundary is None:
+            raise ValueError("the mesh has boundary facets: pass boundary=(slots, states)")
+        bslots = torch.as_tensor(np.asarray(boundary[0]), dtype=torch.long)
+        Ub_all = torch.zeros(n_e * n_slot, nc, dtype=DT)
+        Ub_all[bslots] = torch.as_tensor(np.asarray(boundary[1]), dtype=DT)
+        Ub_all = Ub_all.reshape(n_e, n_slot, nc)
+        pair = torch.where(bmask[..., None], torch.zeros_like(pair), pair)
     tgt = torch.arange(n_e) if elems is None else torch.as_tensor(elems, dtype=torch.long)
     nb = pair[tgt, :, 0]                                          # (n, slots)
     need = torch.unique(torch.cat([tgt, nb.reshape(-1)])) if viscous else tgt
@@ -136,6 +155,8 @@ def residual(u, ref, mesh, prm: Params = Params(), *, scheme="split", form="weak
     nu = torch.as_tensor(mesh.nu, dtype=DT).reshape(n_e, n_slot, d)[tgt]   # (n, s, d)
     Uk = Ut[:, fn, :]                                                       # (n, s, nc)
     Uv = U_all[pair[tgt, :, 0], fn[pair[tgt, :, 1]], :]                     # (n, s, nc)
+    if bool(bmask.any()):
+        Uv = torch.where(bmask[tgt][..., None], Ub_all[tgt], Uv)           # exterior states
     Hm = H_t[:, fn]                                                         # (n, s)
     Fs = (ir_flux if scheme == "hadamard_ir" else sy_flux)(Uk, Uv, prm)    # (n, s, d, nc)
     sat = -torch.einsum("nsi,nsic->nsc", nu, Fs) / Hm[..., None]

@@ -61,6 +61,7 @@ _SIGNATURES = {
     "esplit_set_params": (_I, [_P, ctypes.POINTER(esplit_params)]),
     "esplit_get_params": (_I, [_P, ctypes.POINTER(esplit_params)]),
     "esplit_set_hybrid_flags": (_I, [_P, _P, _I]),
+    "esplit_set_boundary_states": (_I, [_P, _I, _P, _P]),
     "esplit_detect_hybrid": (_I, [_P, _P, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _P]),
     "esplit_get_hybrid_flags": (_I, [_P, _P]),
     "esplit_residual": (_I, [_P, _P, _P, _P]),
@@ -138,6 +139,10 @@ def esplit_get_params(ctx):
 
 def esplit_set_hybrid_flags(ctx, flags_ptr, n_e) -> int:
     return lib.esplit_set_hybrid_flags(ctx, flags_ptr, n_e)
+
+
+def esplit_set_boundary_states(ctx, n_b, slots_ptr, states_ptr) -> int:
+    return lib.esplit_set_boundary_states(ctx, n_b, slots_ptr, states_ptr)
 
 
 def esplit_detect_hybrid(ctx, u_ptr, threshold, stream=None):

@@ -161,7 +161,8 @@ void esplit_destroy(esplit_ctx* c) {
   esplit::Buffers& b = c->b;
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
-                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.wslot, b.vfb, b.vfs, b.vus};
+                b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.wslot, b.vfb, b.vfs, b.vus,
+                b.bslot, b.bstate};
   for (void* p : ps) dfree(p);
   if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
   if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
@@ -249,11 +250,19 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   for (size_t i = 0; i < (size_t)n_e * NP; ++i)
     if (!(J[i] > 0.0)) return fail(c, ESPLIT_ERR_MESH, "J must be positive at every node");
   std::vector<int2> fpairs;
+  std::vector<int> bslots;
   fpairs.reserve((size_t)n_e * NS / 2);
   for (int k = 0; k < n_e; ++k) {
     for (int s = 0; s < NS; ++s) {
       size_t a = (size_t)k * NS + s;
       int v = pair[2 * a], s2 = pair[2 * a + 1];
+      if (v == -1 && s2 == -1) {  // boundary facet slot: exterior state from esplit_set_boundary_states
+        bool ok = false;
+        for (int i = 0; i < d; ++i) ok = ok || nu[a * d + i] != 0.0;
+        if (!ok) return fail(c, ESPLIT_ERR_MESH, "boundary facet slot with a zero normal");
+        bslots.push_back((int)a);
+        continue;
+      }
       if (v < 0 || v >= n_e || s2 < 0 || s2 >= NS) return fail(c, ESPLIT_ERR_MESH, "pair index out of range");
       size_t b2 = (size_t)v * NS + s2;
       if (pair[2 * b2] != k || pair[2 * b2 + 1] != s) return fail(c, ESPLIT_ERR_MESH, "pairing is not an involution");
@@ -269,6 +278,9 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   }
   c->n_e = n_e;
   c->n_pairs = (int)fpairs.size();
+  c->n_bslot = (int)bslots.size();
+  c->bslots = bslots;
+  c->have_bstate = false;
   int rc;
   if ((rc = dalloc(c, &c->b.J, (size_t)n_e * NP))) return rc;
   if ((rc = dalloc(c, &c->b.nu, (size_t)n_e * NS * d))) return rc;
@@ -288,6 +300,10 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   CK(cudaMemcpy(c->b.pair, pair, sizeof(int) * n_e * NS * 2, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->b.Lam, Lambda, sizeof(double) * n_e * d * d * NP, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->b.face_pairs, fpairs.data(), sizeof(int2) * fpairs.size(), cudaMemcpyHostToDevice));
+  dalloc(c, &c->b.bstate, 0);
+  if ((rc = dalloc(c, &c->b.bslot, bslots.size()))) return rc;
+  if (!bslots.empty())
+    CK(cudaMemcpy(c->b.bslot, bslots.data(), sizeof(int) * bslots.size(), cudaMemcpyHostToDevice));
   // RRK / host-path scratch is (re)allocated lazily
   dalloc(c, &c->b.stage_u, 0);
   dalloc(c, &c->b.stage_r, 0);
@@ -366,6 +382,40 @@ int esplit_set_hybrid_flags(esplit_ctx* c, const unsigned char* flags, int n_e) 
   return ESPLIT_OK;
 }
 
+int esplit_set_boundary_states(esplit_ctx* c, int n_b, const int* slots, const double* states) {
+  if (!c) return ESPLIT_ERR_ARG;
+  c->version++;
+  if (!c->have_mesh) return fail(c, ESPLIT_ERR_STATE, "upload the mesh first");
+  if (n_b != c->n_bslot)
+    return fail(c, ESPLIT_ERR_ARG, "n_b must equal the mesh's number of boundary facet slots (" +
+                                       std::to_string(c->n_bslot) + ")");
+  if (n_b == 0) return ESPLIT_OK;
+  if (!slots || !states) return fail(c, ESPLIT_ERR_ARG, "null pointer");
+  const int nc = c->n_c;
+  std::vector<double> ordered((size_t)n_b * nc);
+  std::vector<char> seen(n_b, 0);
+  for (int i = 0; i < n_b; ++i) {
+    auto it = std::lower_bound(c->bslots.begin(), c->bslots.end(), slots[i]);
+    if (it == c->bslots.end() || *it != slots[i]) return fail(c, ESPLIT_ERR_ARG, "slot is not a boundary facet slot");
+    const size_t pos = (size_t)(it - c->bslots.begin());
+    if (seen[pos]) return fail(c, ESPLIT_ERR_ARG, "boundary facet slot given twice");
+    seen[pos] = 1;
+    const double* st = states + (size_t)i * nc;
+    double ke = 0.0;
+    for (int j = 0; j < c->dim; ++j) ke += 0.5 * st[1 + j] * st[1 + j] / st[0];
+    const double p = (c->prm.gam - 1.0) * (st[nc - 1] - ke);
+    if (!(st[0] > 0.0) || !(p > 0.0) || !std::isfinite(st[nc - 1]))
+      return fail(c, ESPLIT_ERR_ARG, "exterior state not physical (rho, p must be positive and finite)");
+    for (int q = 0; q < nc; ++q) ordered[pos * nc + q] = st[q];
+  }
+  cudaSetDevice(c->device);
+  int rc;
+  if (!c->b.bstate && (rc = dalloc(c, &c->b.bstate, ordered.size()))) return rc;
+  CK(cudaMemcpy(c->b.bstate, ordered.data(), sizeof(double) * ordered.size(), cudaMemcpyHostToDevice));
+  c->have_bstate = true;
+  return ESPLIT_OK;
+}
+
 int esplit_detect_hybrid(esplit_ctx* c, const double* u, double threshold, int* n_flagged, void* stream) {
   int rc = check_ready(c);
   if (rc) return rc;
@@ -397,9 +447,17 @@ int esplit_get_hybrid_flags(esplit_ctx* c, unsigned char* flags) {
   return ESPLIT_OK;
 }
 
+static int boundary_ready(esplit_ctx* c) {
+  if (c->n_bslot == 0) return ESPLIT_OK;
+  if (!c->have_bstate) return fail(c, ESPLIT_ERR_STATE, "the mesh has boundary facets: esplit_set_boundary_states");
+  if (c->prm.viscous) return fail(c, ESPLIT_ERR_UNSUPPORTED, "viscous terms on boundary facets are not built");
+  return ESPLIT_OK;
+}
+
 static int residual_impl(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* npart) {
   if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
     return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
+  if (int brc = boundary_ready(c)) return brc;
   const bool visc = c->prm.viscous != 0;
   if (visc && !c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
   // the entropy production comes with the residual kernels' block partials:
@@ -443,6 +501,7 @@ int esplit_residual_noalloc(esplit_ctx* c, const double* u, double* r, void* str
   if (c->prm.scheme == ESPLIT_SCHEME_HYBRID && !c->b.list_split)
     return fail(c, ESPLIT_ERR_STATE, "hybrid scheme needs esplit_set_hybrid_flags");
   if (c->prm.viscous && !c->b.fv) return fail(c, ESPLIT_ERR_STATE, "viscous scratch missing");
+  if ((rc = boundary_ready(c))) return rc;
   size_t need = (size_t)c->n_e * c->n_c * c->n_slot;
   if (need > esplit::NOALLOC_SCRATCH_DOUBLES)
     return fail(c, ESPLIT_ERR_ARG,
@@ -838,8 +897,9 @@ int esplit_residual_vjp(esplit_ctx* c, const double* u, const double* cot, doubl
   if (rc) return rc;
   if (!u || !cot || !grad) return fail(c, ESPLIT_ERR_ARG, "null pointer");
   if (grad == u || grad == cot) return fail(c, ESPLIT_ERR_ARG, "grad must not alias u or cot");
-  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->dim == 1)
-    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the residual VJP is built for the entropy-split scheme in 2D and 3D");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->dim == 1 || c->n_bslot > 0)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED,
+                "the residual VJP is built for the entropy-split scheme in 2D and 3D on periodic meshes");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
   return vjp_impl(c, u, cot, grad, s);
@@ -862,8 +922,9 @@ int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double*
   if (!u || !ubar1 || !ubar0) return fail(c, ESPLIT_ERR_ARG, "null pointer");
   if (ubar0 == u || ubar0 == ubar1) return fail(c, ESPLIT_ERR_ARG, "ubar0 must not alias u or ubar1");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ESPLIT_ERR_ARG, "dt must be positive and finite");
-  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->dim == 1)
-    return fail(c, ESPLIT_ERR_UNSUPPORTED, "the step reverse is built for the entropy-split scheme in 2D and 3D");
+  if (c->prm.scheme != ESPLIT_SCHEME_SPLIT || c->dim == 1 || c->n_bslot > 0)
+    return fail(c, ESPLIT_ERR_UNSUPPORTED,
+                "the step reverse is built for the entropy-split scheme in 2D and 3D on periodic meshes");
   cudaSetDevice(c->device);
   cudaStream_t s = as_stream(stream);
   size_t n = (size_t)c->n_e * c->n_c * c->n_p;

@@ -212,6 +212,74 @@ __global__ void __launch_bounds__(128) face_f32_kernel(double* __restrict__ r, c
   }
 }
 
+// boundary facet slots (pair (-1, -1)): the terms of face_f32_kernel for
+// side k alone, the exterior state u_b in place of the neighbour's:
+//   H_k r_k += -G - Dw,  G = nu . (F*(u_k, u_b) - F(u_k)), Dw = |nu|/2 X|L|SX^T (w_k - w_b)
+template <int D>
+__global__ void __launch_bounds__(128) face_bc_f32_kernel(double* __restrict__ r, const double* __restrict__ u,
+                                                          const int* __restrict__ bslot,
+                                                          const double* __restrict__ bstate, int n_b,
+                                                          const double* __restrict__ nu,
+                                                          const double* __restrict__ J, Phys<float> c,
+                                                          int dissipation, int* __restrict__ status,
+                                                          double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double hw = 0.0;
+  if (t < n_b) {
+    const int NP = c_ref32.n_p, NS = c_ref32.n_slot;
+    const int a = __ldg(&bslot[t]);
+    const int k = a / NS, s = a - k * NS;
+    const int m = c_ref32.slot_node[s];
+    double uk[NC];
+    float du[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      uk[q] = __ldg(&u[((size_t)k * NC + q) * NP + m]);
+      du[q] = (float)(__ldg(&bstate[(size_t)t * NC + q]) - uk[q]);
+    }
+    Ref32<D> rk;
+    Dev32<D> dv;
+    ref32_from_u<D>(uk, c, rk);
+    dev32<D>(rk, du, c, dv);
+    if (!(rk.rho > 0.0f && rk.p > 0.0f && dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1))) atomicOr(status, 1);
+    float nuv[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nuv[i] = (float)__ldg(&nu[((size_t)k * NS + s) * D + i]);
+    float G[NC], Dw[NC];
+    PairAvg<float, D> av;
+    sy_flux_dev32<D>(rk, dv, c, nuv, G, av);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) Dw[q] = 0.0f;
+    if (dissipation) {
+      float b2 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+      const float b = sqrtf(b2);
+      const float ib = 1.0f / b;
+      float nh[D], mdw[NC], o[NC];
+#pragma unroll
+      for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) mdw[q] = -dv.dW[q];
+      diss_apply<float, D>(av, c, nh, mdw, o);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) Dw[q] = 0.5f * b * o[q];
+    }
+    const double ihk = 1.0 / (c_ref32.H[m] * __ldg(&J[(size_t)k * NP + m]));
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const double gk = (double)(-G[q] - Dw[q]);
+      r[((size_t)k * NC + q) * NP + m] += gk * ihk;
+      if (prod) hw += (double)rk.W[q] * gk;
+    }
+  }
+  if (prod) {
+    double vv[1] = {hw};
+    block_sum<1>(vv, prod + blockIdx.x);
+  }
+}
+
 template <int D, int NP>
 static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
   constexpr int EB = (256 / NP) > 0 ? (256 / NP) : 1;
@@ -230,6 +298,14 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
     ProfScope ps(c, PG_FACE, s);
     face_f32_kernel<D><<<nb, bs, 0, s>>>(r, u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, ph,
                                          c->prm.dissipation, c->b.status, prod ? prod + np_used : nullptr);
+    c->launches++;
+    if (prod) np_used += nb;
+  }
+  if (c->n_bslot > 0) {
+    const int bs = 128, nb = (c->n_bslot + bs - 1) / bs;
+    ProfScope ps(c, PG_FACE, s);
+    face_bc_f32_kernel<D><<<nb, bs, 0, s>>>(r, u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.J, ph,
+                                            c->prm.dissipation, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     if (prod) np_used += nb;
   }

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(256) detect_ratio_kernel(const double* __restr
   for (int s = 0; s < NS; ++s) {
     int v = __ldg(&pair[((size_t)e * NS + s) * 2]);
     int s2 = __ldg(&pair[((size_t)e * NS + s) * 2 + 1]);
+    if (v < 0) continue;  // boundary facet: no neighbour node
     double p = det_pressure<D>(u, (size_t)v, c_ref.slot_node[s2], NP, gm1);
     bad = bad || !(p > 0.0 && p < CUDART_INF);
     mn = fmin(mn, p);
@@ -67,7 +68,10 @@ __global__ void __launch_bounds__(1024) detect_widen_kernel(const unsigned char*
   int f = 0;
   if (e < n_e) {
     f = flag0[e];
-    for (int s = 0; s < NS; ++s) f |= flag0[__ldg(&pair[((size_t)e * NS + s) * 2])];
+    for (int s = 0; s < NS; ++s) {
+      const int v = __ldg(&pair[((size_t)e * NS + s) * 2]);
+      if (v >= 0) f |= flag0[v];  // boundary facets (v = -1) widen nothing
+    }
     flags[e] = (unsigned char)f;
   }
   int cnt = __syncthreads_count(f);

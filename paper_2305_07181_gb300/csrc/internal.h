@@ -77,6 +77,9 @@ struct Buffers {
   double* vfs = nullptr;
   double* vus = nullptr;
   double* vjp_work = nullptr;    // 12 state-sized arrays for the RRK step reverse
+  // boundary facet slots (pair (-1, -1)) and their exterior states [n_b][n_c]
+  int* bslot = nullptr;
+  double* bstate = nullptr;
   double* host_u = nullptr;    // device copies for the host-buffer entry point
   double* host_r = nullptr;
 };
@@ -107,6 +110,9 @@ struct esplit_ctx {
   int n_p = 0, n_fac = 0, n_f = 0, n_slot = 0;
   int n_e = 0, n_pairs = 0;
   int n_split = 0, n_had = 0;
+  int n_bslot = 0;                 // boundary facet slots of the mesh
+  bool have_bstate = false;        // their exterior states are set
+  std::vector<int> bslots;         // flat slot indices (element * n_slot + slot), ascending
   bool have_op = false, have_mesh = false, ops_beta_valid = false;
   double ops_beta = 0.0;
   esplit_params prm{};
@@ -204,6 +210,12 @@ int launch_rrk_vjp_stage(esplit_ctx* c, const double* U, const double* r, const 
                          const double* ubar_next, double c_d, double c_e, double c_u, double* rbar, double* extra,
                          cudaStream_t s);
 int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* scratch);
+// boundary facets, float64 (kernels.cu): the SAT and dissipation with the
+// exterior state, written to the facet scratch `out` before the volume
+// kernels (add = 0) or added into the residual `out` after them (add = 1,
+// with entropy-production block partials at prod when not null); returns
+// the number of partials written
+int launch_face_bc(esplit_ctx* c, const double* u, double* out, int add, double* prod, cudaStream_t s);
 int launch_detect_hybrid(esplit_ctx* c, const double* u, double threshold, cudaStream_t s);
 int launch_math_eval(int fn, const double* x, double* y, size_t n, cudaStream_t s);
 

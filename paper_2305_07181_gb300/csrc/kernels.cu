@@ -366,6 +366,135 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
 }
 
 // ---------------------------------------------------------------------------
+// boundary facet slots (pair (-1, -1), bounded domains): the terms of
+// face_kernel for side k alone, with the neighbour's state replaced by the
+// prescribed exterior state u_b:
+//   G = nu . F*(u_km, u_b) + |nu|/2 X|L|SX^T (w_km - w_b),
+//   H_k,m r_k,m gets nu . f(u_km) [split-form element] - G.
+// ADD = false: written to the facet scratch before the volume kernels (which
+// add it); ADD = true: added into r after them, with the entropy-production
+// block partials w . (H r) when prod is given.  FLUX 1: the Ismail-Roe
+// comparator with its dissipation (standard entropy variables).
+// ---------------------------------------------------------------------------
+template <int D, int FLUX, bool ADD>
+__global__ void __launch_bounds__(128) face_bc_kernel(const double* __restrict__ u, const int* __restrict__ bslot,
+                                                      const double* __restrict__ bstate, int n_b,
+                                                      const double* __restrict__ nu, const double* __restrict__ J,
+                                                      double* __restrict__ out, Phys<double> c, int dissipation,
+                                                      int* __restrict__ status, int ef_mode,
+                                                      const unsigned char* __restrict__ hflags,
+                                                      double* __restrict__ prod) {
+  constexpr int NC = D + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double hw = 0.0;
+  if (t < n_b) {
+    const int NP = c_ref.n_p, NS = c_ref.n_slot;
+    const int a = __ldg(&bslot[t]);
+    const int k = a / NS, s = a - k * NS;
+    const int m = c_ref.slot_node[s];
+    double uk[NC], ub[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      uk[q] = __ldg(&u[((size_t)k * NC + q) * NP + m]);
+      ub[q] = __ldg(&bstate[(size_t)t * NC + q]);
+    }
+    Node<double, D> nk, nb;
+    bool ok = node_from_u<double, D>(uk, c, nk);
+    ok = node_from_u<double, D>(ub, c, nb) && ok;
+    if (!ok) atomicOr(status, 1);
+    double nuv[D], nh[D], b2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      nuv[i] = __ldg(&nu[((size_t)k * NS + s) * D + i]);
+      b2 += nuv[i] * nuv[i];
+    }
+    const double b = sqrt(b2);
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+    double G[NC], dw[NC], o[NC];
+    if constexpr (FLUX == 1) {
+      IRNode<double, D> ik, ib;
+      ir_node<double, D>(nk, ik);
+      ir_node<double, D>(nb, ib);
+      IRAvg<double, D> av;
+      ir_avg<double, D>(ik, ib, c, av);
+      ir_flux_dir<double, D>(av, c, nuv, G);
+      if (dissipation) {
+        double wk[NC], wb[NC];
+        std_entropy_vars<double, D>(nk, ik, c, wk);
+        std_entropy_vars<double, D>(nb, ib, c, wb);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) dw[q] = wk[q] - wb[q];
+        ir_diss_apply<double, D>(av, c, nh, dw, o);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) G[q] += 0.5 * b * o[q];
+      }
+    } else {
+      ZNode<double, D> zk, zb;
+      znode<double, D>(nk, c, zk);
+      znode<double, D>(nb, c, zb);
+      znode_recips<double, D>(zk);
+      PairAvg<double, D> av;
+      pair_avg<double, D>(zk, zb, c, av);
+      sy_flux_dir<double, D>(av, c, nuv, G);
+      if (dissipation) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nb.W[q];
+        diss_apply<double, D>(av, c, nh, dw, o);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) G[q] += 0.5 * b * o[q];
+      }
+    }
+    double ek[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) ek[q] = 0.0;
+    if (ef_mode == 1 || (ef_mode == 2 && __ldg(&hflags[k]) == 0)) normal_flux<D>(nk, nuv, ek);
+    const double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const double g = ek[q] - G[q];
+      if constexpr (ADD) {
+        out[((size_t)k * NC + q) * NP + m] += g * ihk;
+        hw += nk.W[q] * g;
+      } else {
+        out[((size_t)k * NC + q) * NS + s] = g * ihk;
+      }
+    }
+  }
+  if (ADD && prod) {
+    double vv[1] = {hw};
+    block_sum<1>(vv, prod + blockIdx.x);
+  }
+}
+
+template <int D>
+static int face_bc_d(esplit_ctx* c, const double* u, double* out, int add, double* prod, cudaStream_t s) {
+  const Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  const int sch = c->prm.scheme;
+  const int ef_mode = sch == ESPLIT_SCHEME_SPLIT ? 1 : (sch == ESPLIT_SCHEME_HYBRID ? 2 : 0);
+  const int bs = 128, nb = (c->n_bslot + bs - 1) / bs;
+  ProfScope ps(c, PG_FACE, s);
+  if (add)
+    face_bc_kernel<D, 0, true><<<nb, bs, 0, s>>>(u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.J, out, ph,
+                                                 c->prm.dissipation, c->b.status, ef_mode, c->b.hflags, prod);
+  else if (sch == ESPLIT_SCHEME_HADAMARD_IR)
+    face_bc_kernel<D, 1, false><<<nb, bs, 0, s>>>(u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.J, out,
+                                                  ph, c->prm.dissipation, c->b.status, 0, c->b.hflags, nullptr);
+  else
+    face_bc_kernel<D, 0, false><<<nb, bs, 0, s>>>(u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.J, out,
+                                                  ph, c->prm.dissipation, c->b.status, ef_mode, c->b.hflags, nullptr);
+  c->launches++;
+  return (add && prod) ? nb : 0;
+}
+
+int launch_face_bc(esplit_ctx* c, const double* u, double* out, int add, double* prod, cudaStream_t s) {
+  if (c->n_bslot == 0) return 0;
+  if (c->dim == 1) return face_bc_d<1>(c, u, out, add, prod, s);
+  if (c->dim == 2) return face_bc_d<2>(c, u, out, add, prod, s);
+  return face_bc_d<3>(c, u, out, add, prod, s);
+}
+
+// ---------------------------------------------------------------------------
 // entropy-split volume kernel (Eq. (100)): EB elements per block, one thread
 // per node.  With M_i = H^-1 (Q_i/(beta+1) + Q_i^T) and Q_i + Q_i^T = E_i
 // (Def. 1, E_i diagonal), M_i = H^-1 E_i - beta/(beta+1) D_i, so
@@ -973,6 +1102,8 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
                                                       c->prm.dissipation, c->b.status, ef_mode, c->b.hflags, 0,
                                                       nullptr);
     c->launches++;
+    // boundary facet slots into the same scratch (the volume kernels add them)
+    launch_face_bc(c, u, sat, 0, nullptr, s);
   }
   int np_used = 0;
   int n_split = scheme == ESPLIT_SCHEME_SPLIT ? c->n_e : (scheme == ESPLIT_SCHEME_HYBRID ? c->n_split : 0);
@@ -1076,6 +1207,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
                                             c->b.hflags);
     c->launches++;
     if (prod) np_used += nb;
+    np_used += launch_face_bc(c, u, r, 1, prod ? prod + np_used : nullptr, s);
   }
   if (visc) {
     ProfScope ps(c, PG_VISC, s);

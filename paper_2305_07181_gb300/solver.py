@@ -114,6 +114,13 @@ class Solver:
         f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
         self._check(capi.esplit_set_hybrid_flags(self.ctx, _ptr(f), self.n_e))
 
+    def set_boundary_states(self, slots, states):
+        """Exterior states (n_b, n_c) of the mesh's boundary facet slots
+        (flat indices element * n_slot + slot)."""
+        sl = np.ascontiguousarray(np.asarray(slots, dtype=np.int32))
+        st = np.ascontiguousarray(np.asarray(states, dtype=np.float64))
+        self._check(capi.esplit_set_boundary_states(self.ctx, len(sl), _ptr(sl), _ptr(st)))
+
     def detect_hybrid(self, u: torch.Tensor, threshold: float = 1.1, stream=None) -> int:
         rc, n = capi.esplit_detect_hybrid(self.ctx, _dptr(u), float(threshold), _stream(stream))
         self._check(rc)

@@ -1,0 +1,203 @@
+"""Boundary facets on the GPU (esplit_set_boundary_states): bounded line
+meshes whose two end facets take the interface SAT and dissipation with a
+prescribed exterior state, against the oracle; and the Shu-Osher problem of
+Sec. 7.2 on [-5, 5] (supersonic inflow at x = -5, the undisturbed state at
+x = 5) run to t = 1.8.
+
+Tolerances: FP64 max-norm relative error per component <= 1e-12, float32
+path <= 1e-5, FP32-bulk <= 1e-11, relaxation parameter <= 1e-10, hybrid
+flags bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+from esplit_inputs import line_operator, states
+from esplit_inputs.mesh import line_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_07181_gb300 as es
+    return es
+
+
+def _oracle():
+    from oracle import residual as R, rrk, hybrid as Hy
+    from oracle.physics import Params as OP
+    return R, rrk, Hy, OP
+
+
+def rel_err(a, b):
+    num = np.abs(np.asarray(a) - np.asarray(b)).max(axis=(0, 2))
+    den = np.abs(np.asarray(b)).max(axis=(0, 2))
+    return float((num / den).max())
+
+
+def _case(p, seed=3, N=40):
+    op = line_operator(p)
+    m = line_mesh(op, N, 1.0, 0.0, amp=0.2)
+    u = states.random_positive_state(m.n_e, 1, op.n_p, seed=seed)
+    ub = states.random_positive_state(2, 1, 1, seed=seed + 100)[:, :, 0]
+    return op, m, u, (m.meta["boundary_slots"], ub)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("scheme", ["split", "hadamard", "hybrid", "hadamard_ir"])
+@pytest.mark.parametrize("diss", [False, True])
+def test_boundary_parity_fp64(lib, p, scheme, diss):
+    R, rrk, Hy, OP = _oracle()
+    op, m, u, bnd = _case(p, seed=10 + p)
+    flags = np.random.default_rng(p).integers(0, 2, m.n_e).astype(np.uint8)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=diss))
+    s.set_boundary_states(*bnd)
+    if scheme == "hybrid":
+        s.set_hybrid_flags(flags)
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), scheme=scheme, dissipation=diss, hybrid_flags=flags, boundary=bnd).numpy()
+    assert rel_err(r, ro) <= 1e-12
+    assert s.status() == 0
+    s.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("prec,bound", [("fp32", 1e-5), ("fp32_bulk", 1e-11)])
+def test_boundary_parity_float32(lib, p, prec, bound):
+    R, rrk, Hy, OP = _oracle()
+    op = line_operator(p)
+    m = line_mesh(op, 60, 10.0, -5.0, amp=0.2)
+    u = states.add_uniform_noise(states.shu_osher(m), 1e-3, 7)
+    bnd = (m.meta["boundary_slots"], states.shu_osher_boundary())
+    s = lib.Solver(op, m, lib.Params(dissipation=True, precision=prec))
+    s.set_boundary_states(*bnd)
+    r = s.residual(s.to_device(u)).cpu().numpy()
+    ro = R.residual(u, op, m, OP(), dissipation=True, boundary=bnd).numpy()
+    err = rel_err(r, ro)
+    print(f"boundary {prec} p={p}: rel err {err:.2e}")
+    assert err <= bound
+    s.close()
+
+
+def test_boundary_states_required_and_checked(lib):
+    op, m, u, bnd = _case(2)
+    s = lib.Solver(op, m, lib.Params())
+    ud = s.to_device(u)
+    with pytest.raises(lib.EsplitError) as ei:
+        s.residual(ud)
+    assert ei.value.code == lib.capi.ESPLIT_ERR_STATE
+    with pytest.raises(lib.EsplitError) as ei:
+        s.set_boundary_states(bnd[0][:1], bnd[1][:1])        # one of the two
+    assert ei.value.code == lib.capi.ESPLIT_ERR_ARG
+    with pytest.raises(lib.EsplitError) as ei:
+        s.set_boundary_states([0, 1], bnd[1])                 # slot 1 is interior
+    assert ei.value.code == lib.capi.ESPLIT_ERR_ARG
+    bad = bnd[1].copy()
+    bad[0, 0] = -1.0
+    with pytest.raises(lib.EsplitError) as ei:
+        s.set_boundary_states(bnd[0], bad)
+    assert ei.value.code == lib.capi.ESPLIT_ERR_ARG
+    s.set_boundary_states(bnd[0][::-1], bnd[1][::-1])         # any order
+    R, rrk, Hy, OP = _oracle()
+    r = s.residual(ud).cpu().numpy()
+    assert rel_err(r, R.residual(u, op, m, OP(), boundary=bnd).numpy()) <= 1e-12
+    s.close()
+
+
+def test_shu_osher_steps_parity(lib):
+    """Five relaxation RK4 steps of the Shu-Osher problem (p = 2, 100
+    elements on [-5, 5], hybrid scheme with the device detector re-run before
+    every step, matrix dissipation) against the oracle's steps with the
+    oracle's detector: flags bit-exact, g to 1e-10, states to 1e-12."""
+    R, rrk, Hy, OP = _oracle()
+    op = line_operator(2)
+    m = line_mesh(op, 100, 10.0, -5.0)
+    u0 = states.shu_osher(m)
+    bnd = (m.meta["boundary_slots"], states.shu_osher_boundary())
+    dt = states.cfl_timestep(m, u0, 0.1)
+    s = lib.Solver(op, m, lib.Params(scheme="hybrid", dissipation=True))
+    s.set_boundary_states(*bnd)
+    ud = s.to_device(u0)
+    uo = torch.as_tensor(u0)
+    for _ in range(5):
+        s.detect_hybrid(ud, 1.1)
+        fo = Hy.detect(uo.numpy(), op, m, 1.1)
+        assert np.array_equal(s.hybrid_flags(), fo)
+        g, info = s.rrk_step(ud, dt)
+        uo, io = rrk.rrk4_step(uo, dt, lambda x: R.residual(x, op, m, OP(), scheme="hybrid", dissipation=True,
+                                                             hybrid_flags=fo, boundary=bnd), op, m, OP())
+        assert abs(g - io.g) <= 1e-10
+        assert rel_err(ud.cpu().numpy(), uo.numpy()) <= 1e-12
+    s.close()
+
+
+def _run_shu_osher(lib, p, n_e, scheme, t_final=1.8, cfl=0.1):
+    """Density at the nodes at t_final (and the node coordinates), or None if
+    positivity was lost."""
+    op = line_operator(p)
+    m = line_mesh(op, n_e, 10.0, -5.0)
+    u0 = states.shu_osher(m)
+    bnd = (m.meta["boundary_slots"], states.shu_osher_boundary())
+    dt = states.cfl_timestep(m, u0, cfl)
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True))
+    s.set_boundary_states(*bnd)
+    u = s.to_device(u0)
+    t = 0.0
+    try:
+        if scheme == "hadamard_ir":
+            # the comparator conserves the standard entropy, not Harten's:
+            # classical RK4 (as for its accuracy runs)
+            n = int(np.ceil(t_final / dt))
+            h = t_final / n
+            for _ in range(n):
+                k1 = s.residual(u)
+                k2 = s.residual(u + 0.5 * h * k1)
+                k3 = s.residual(u + 0.5 * h * k2)
+                k4 = s.residual(u + h * k3)
+                u += (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+            if s.status() != 0:
+                return None, m
+        else:
+            while t < t_final - 1e-12:
+                h = min(dt, (t_final - t) / 1.0)
+                if scheme == "hybrid":
+                    s.detect_hybrid(u, 1.1)
+                g, _ = s.rrk_step(u, h)
+                t += g * h
+    except lib.EsplitError:
+        return None, m
+    finally:
+        s.close()
+    return u[:, 0, :].cpu().numpy(), m
+
+
+def test_shu_osher_hybrid_converges(lib):
+    """Sec. 7.2: the hybrid scheme (p = 2, device detector) converges to the
+    reference solution as the mesh is refined (L1 error of the density at the
+    nodes halves or better from 200 to 400 elements), while the
+    nonconservative entropy-split scheme stays far from it; the reference is
+    the Sec. 6 comparator (Ismail-Roe Hadamard form, p = 3, 2000 elements,
+    its matrix dissipation, classical RK4), as in the paper (which takes
+    10000 elements)."""
+    rho_ref, mref = _run_shu_osher(lib, 3, 2000, "hadamard_ir")
+    assert rho_ref is not None
+    xr = mref.x[:, 0, :].reshape(-1)
+    order = np.argsort(xr, kind="stable")
+    xr, rr = xr[order], rho_ref.reshape(-1)[order]
+
+    def l1(rho, m):
+        x = m.x[:, 0, :].reshape(-1)
+        return float(np.mean(np.abs(rho.reshape(-1) - np.interp(x, xr, rr))))
+
+    errs = {}
+    for n_e in (200, 400):
+        rho, m = _run_shu_osher(lib, 2, n_e, "hybrid")
+        assert rho is not None, f"hybrid lost positivity at n_e = {n_e}"
+        errs[("hybrid", n_e)] = l1(rho, m)
+    rho, m = _run_shu_osher(lib, 2, 400, "split")
+    errs[("split", 400)] = l1(rho, m) if rho is not None else np.inf
+    print("Shu-Osher L1 density errors:", {f"{k[0]} {k[1]}": f"{v:.3e}" for k, v in errs.items()})
+    assert errs[("hybrid", 400)] <= 0.5 * errs[("hybrid", 200)]
+    assert errs[("split", 400)] >= 2.0 * errs[("hybrid", 400)]
