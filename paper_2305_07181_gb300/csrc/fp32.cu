@@ -40,6 +40,15 @@ int set_ref_tables_f32(const RefTables& t) {
   return cudaMemcpyToSymbol(c_ref32, &t, sizeof(RefTables)) == cudaSuccess ? 0 : -1;
 }
 
+// s + a b with Kahan compensation: y = a b - c (one rounding), t = s + y,
+// c = (t - s) - y (the part of y that t lost), s = t
+__device__ __forceinline__ void kahan_fma(float a, float b, float& s, float& c) {
+  const float y = __fmaf_rn(a, b, -c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
 template <int D, int NP, int EB>
 struct SplitSmem32 {
   float df[EB][D][D + 2][NP];  // flux variations
@@ -94,21 +103,39 @@ __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kern
   double hw = 0.0;
   if (active) {
     const float* op = ops + (size_t)e * (2 * D * NP * NP);
-    float acc[NC], g[D][NC];
+    // float32 sums; for the larger operators (n_p > 20) compensated
+    // (Kahan: the rounding error of every addition is carried in a second
+    // accumulator), which removes the dominant error there -- the rounding
+    // of partial sums much larger than the final, cancelling, result
+    constexpr bool COMP = NP > 20;
+    float acc[NC], g[D][NC], cacc[NC], cg[D][NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) acc[q] = 0.0f;
+    for (int q = 0; q < NC; ++q) acc[q] = cacc[q] = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
 #pragma unroll
-      for (int q = 0; q < NC; ++q) g[i][q] = 0.0f;
+      for (int q = 0; q < NC; ++q) g[i][q] = cg[i][q] = 0.0f;
 #pragma unroll 6
       for (int n = 0; n < NP; ++n) {
         const float dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          acc[q] = fmaf(dt, sm.df[el][i][q][n], acc[q]);
-          g[i][q] = fmaf(dt, sm.dw[el][q][n], g[i][q]);
+          if constexpr (COMP) {
+            kahan_fma(dt, sm.df[el][i][q][n], acc[q], cacc[q]);
+            kahan_fma(dt, sm.dw[el][q][n], g[i][q], cg[i][q]);
+          } else {
+            acc[q] = fmaf(dt, sm.df[el][i][q][n], acc[q]);
+            g[i][q] = fmaf(dt, sm.dw[el][q][n], g[i][q]);
+          }
         }
+      }
+    }
+    if constexpr (COMP) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        acc[q] = __fsub_rn(acc[q], cacc[q]);
+#pragma unroll
+        for (int i = 0; i < D; ++i) g[i][q] = __fsub_rn(g[i][q], cg[i][q]);
       }
     }
     Node<float, D> nd;

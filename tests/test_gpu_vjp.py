@@ -159,8 +159,12 @@ def test_config4_full_size(lib):
     cotangent N(0, 1) (seed 4).
 
     (a) esplit_residual_vjp against the oracle adjoint (torch.autograd through
-        the oracle residual on the whole mesh): max-norm relative 1e-11, as on
-        the small meshes.
+        the oracle residual on the whole mesh), per component in max-norm
+        relative to the gradient, within twice the oracle adjoint's own
+        change when its input state is moved by one unit in the last place
+        (random signs): at this size that rounding-level sensitivity is
+        ~4e-9 (1e-8 for one component), so no float64 implementation meets
+        the 1e-11 of the small meshes here; observed 2.4e-9.
     (b) Central differences of the GPU residual, h = 1e-6, on 200 random unit
         directions (seed 40): |<cot, (r(u+hd) - r(u-hd))/2h> - <J^T cot, d>|
         <= 2e-6 |<J^T cot, d>| + 2e-3.  The absolute part is the rounding of
@@ -177,9 +181,14 @@ def test_config4_full_size(lib):
     g = s.residual_vjp(ud, cd)
     gh = g.cpu().numpy()
     go = oracle_vjp(u, cot, op, m, True)
-    err = np.abs(gh - go).max() / np.abs(go).max()
-    print(f"config-4 full-size vjp vs oracle adjoint: rel err {err:.2e}")
-    assert err <= 1e-11
+    u1 = u * (1.0 + np.finfo(float).eps * np.random.default_rng(9).choice([-1.0, 1.0], size=u.shape))
+    go1 = oracle_vjp(u1, cot, op, m, True)
+    scale = np.abs(go).max(axis=(0, 2))
+    err = np.abs(gh - go).max(axis=(0, 2)) / scale
+    sens = np.abs(go1 - go).max(axis=(0, 2)) / scale
+    print(f"config-4 full-size vjp vs oracle adjoint: rel err {err.max():.2e} per component {err}, "
+          f"oracle's 1-ulp sensitivity {sens}")
+    assert np.all(err <= 2.0 * sens)
     rng = np.random.default_rng(40)
     h = 1e-6
     worst = 0.0
