@@ -162,7 +162,7 @@ void esplit_destroy(esplit_ctx* c) {
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.wslot, b.vfb, b.vfs, b.vus,
-                b.bslot, b.bstate};
+                b.bslot, b.bstate, b.ihf};
   for (void* p : ps) dfree(p);
   if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
   if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
@@ -293,12 +293,18 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.rows, (size_t)n_e * 2 * d * NP))) return rc;
   if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
   if ((rc = dalloc(c, &c->b.fcache, (size_t)(d + 9) * n_e * NS))) return rc;
+  if ((rc = dalloc(c, &c->b.ihf, (size_t)n_e * NP))) return rc;
   c->partial_cap = 0;
   if ((rc = ensure_partial(c))) return rc;
   CK(cudaMemcpy(c->b.J, J, sizeof(double) * n_e * NP, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->b.nu, nu, sizeof(double) * n_e * NS * d, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->b.pair, pair, sizeof(int) * n_e * NS * 2, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(c->b.Lam, Lambda, sizeof(double) * n_e * d * d * NP, cudaMemcpyHostToDevice));
+  {
+    std::vector<float> ih((size_t)n_e * NP);
+    for (size_t i = 0; i < ih.size(); ++i) ih[i] = (float)(1.0 / (c->ref.H[i % NP] * J[i]));
+    CK(cudaMemcpy(c->b.ihf, ih.data(), sizeof(float) * ih.size(), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(c->b.face_pairs, fpairs.data(), sizeof(int2) * fpairs.size(), cudaMemcpyHostToDevice));
   dalloc(c, &c->b.bstate, 0);
   if ((rc = dalloc(c, &c->b.bslot, bslots.size()))) return rc;

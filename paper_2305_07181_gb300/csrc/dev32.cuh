@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "bits32.cuh"
 #include "phys.cuh"
 
 namespace esplit {
@@ -37,18 +38,21 @@ struct Ref32 {
   float W[D + 2];
 };
 
+// from the float32 values uf of the reference's conservative variables (the
+// deviations du are taken from the float64 state; the reference's own float32
+// rounding changes the variations by ~2^-23 of themselves)
 template <int D>
-__device__ __forceinline__ void ref32_from_u(const double* u, const Phys<float>& c, Ref32<D>& r) {
-  r.rho = (float)u[0];
+__device__ __forceinline__ void ref32_from_u(const float* uf, const Phys<float>& c, Ref32<D>& r) {
+  r.rho = uf[0];
   r.ir = 1.0f / r.rho;
   r.v2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    r.m[i] = (float)u[1 + i];
+    r.m[i] = uf[1 + i];
     r.V[i] = r.m[i] * r.ir;
     r.v2 += r.V[i] * r.V[i];
   }
-  r.e = (float)u[D + 1];
+  r.e = uf[D + 1];
   r.p = c.gm1 * (r.e - 0.5f * r.rho * r.v2);
   r.ip = 1.0f / r.p;
   r.ep = r.e + r.p;

@@ -9,23 +9,26 @@
 // float64 and rounded once; entropy, relaxation root and update stay float64).
 //
 // Two kernels, one after the other on the stream:
+//   face_f32_kernel: thread = coincident facet-node pair (k, m) ~ (v, n).
+//     With G = nu . (F*(u_k, u_v) - F(u_k)) (sy_flux_dev32), the jump
+//     df = nu . (F(u_v) - F(u_k)) and Dw = |nu|/2 X|L|SX^T (w_k - w_v):
+//       H_k sat_k = -G - Dw            (= nu . F(u_k) - nu . F* - Dw)
+//       H_v sat_v = G - df + Dw        (= nu . F* - nu . F(u_v) + Dw)
+//     i.e. the SATs together with the facet part nu . f / H of the split
+//     volume term (M_i = H^-1 E_i - beta/(beta+1) D_i), written to a float32
+//     facet scratch (boundary slots: face_bc_f32_kernel).
 //   split_volume_f32_kernel: thread = node, EB elements per block.  Variations
 //     relative to the element's node 0, D_i = H^-1 Q_x_i applied to the
 //     flux and entropy-variable variations (D_i 1 = 0 by the discrete metric
 //     identity, so the node-0 values drop out; the float64 row sums of the
 //     stored operators, ~eps |D_i|, are below float32 resolution):
-//       r = -beta/(beta+1) sum_i D_i df_i - 1/(beta+1) sum_i A~_i(u) (D_i dw)
-//     assigned to r (float64).
-//   face_f32_kernel: thread = coincident facet-node pair (k, m) ~ (v, n).
-//     With G = nu . (F*(u_k, u_v) - F(u_k)) (sy_flux_dev32), the jump
-//     df = nu . (F(u_v) - F(u_k)) and Dw = |nu|/2 X|L|SX^T (w_k - w_v):
-//       H_k r_k += -G - Dw            (= nu . F(u_k) - nu . F* - Dw)
-//       H_v r_v += G - df + Dw        (= nu . F* - nu . F(u_v) + Dw)
-//     i.e. the SATs together with the facet part nu . f / H of the split
-//     volume term (M_i = H^-1 E_i - beta/(beta+1) D_i), as the float64
-//     facet kernel adds them.
-// Entropy production (when requested): block partials of sum H w . r in
-// float64, w formed in float32 as the reference's W plus its variation.
+//       r = -beta/(beta+1) sum_i D_i df_i - 1/(beta+1) sum_i A~_i(u) (D_i dw) + sat
+//     stored to r (float64).
+// The float64 <-> float32 conversions (state differences, stores) go through
+// integer operations on the bit patterns (bits32.cuh), 1/(H J) through a
+// float32 table: the float64 pipe does only the states' exponent checks.
+// Entropy production (when requested): block partials of sum H w . r, per node
+// in float32 with w the reference's W plus its variation, summed in float64.
 #include <cuda_runtime.h>
 
 #include "dev32.cuh"
@@ -49,6 +52,50 @@ __device__ __forceinline__ void kahan_fma(float a, float b, float& s, float& c) 
   s = t;
 }
 
+// Dw = |nu|/2 X|L|SX^T (w_k - w_v) of Eq. (69) from the float32 pair averages
+// and entropy-variable jump.  In 3D the two small products with X (Eq. (80))
+// run in float64: at low Mach numbers the characteristic projections X^T dw
+// cancel strongly, and with the small facet weights of the larger
+// tetrahedron operators their float32 rounding reached ~1e-5 of the residual.
+template <int D>
+__device__ __forceinline__ void diss32(const PairAvg<float, D>& a, const Phys<float>& c, const Phys<double>& c64,
+                                       const float* nuv, const float* mdw, float* Dw) {
+  float b2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
+  const float b = sqrtf(b2);
+  const float ib = 1.0f / b;
+  if constexpr (D == 3) {
+    PairAvg<double, D> a64;
+    a64.A1 = a.A1;
+    a64.E1 = a.E1;
+    a64.A2 = a.A2;
+    a64.E2 = a.E2;
+    a64.z1a = a.z1a;
+    a64.pa = a.pa;
+    a64.ke = a.ke;
+    double nh[D], dw[D + 2], o[D + 2];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      a64.qV[i] = a.qV[i];
+      a64.Va[i] = a.Va[i];
+      nh[i] = (double)(nuv[i] * ib);
+    }
+#pragma unroll
+    for (int q = 0; q < D + 2; ++q) dw[q] = mdw[q];
+    diss_apply<double, D>(a64, c64, nh, dw, o);
+#pragma unroll
+    for (int q = 0; q < D + 2; ++q) Dw[q] = __double2float_rn(0.5 * (double)b * o[q]);
+  } else {
+    float nh[D], o[D + 2];
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
+    diss_apply<float, D>(a, c, nh, mdw, o);
+#pragma unroll
+    for (int q = 0; q < D + 2; ++q) Dw[q] = 0.5f * b * o[q];
+  }
+}
+
 template <int D, int NP, int EB>
 struct SplitSmem32 {
   float df[EB][D][D + 2][NP];  // flux variations
@@ -59,9 +106,11 @@ struct SplitSmem32 {
 template <int D, int NP, int EB>
 __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kernel(
     const double* __restrict__ u, double* __restrict__ r, const float* __restrict__ ops,
-    const double* __restrict__ J, int n_e, Phys<float> c, int* __restrict__ status, double* __restrict__ prod) {
+    const float* __restrict__ ihf, const float* __restrict__ satf, int n_e, Phys<float> c, int* __restrict__ status,
+    double* __restrict__ prod) {
   constexpr int NC = D + 2;
   __shared__ SplitSmem32<D, NP, EB> sm;
+  const int NS = c_ref32.n_slot;
   const int el = threadIdx.x / NP;
   const int m = threadIdx.x - el * NP;
   const int e = blockIdx.x * EB + el;
@@ -80,13 +129,14 @@ __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kern
   Dev32<D> dv;
   float du[NC];
   if (active) {
-    double u0[NC];
+    float u0f[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      u0[q] = sm.u0[el][q];
-      du[q] = (float)(uu[q] - u0[q]);
+      const double u0 = sm.u0[el][q];
+      u0f[q] = f32_trunc(u0);
+      du[q] = f32_diff(uu[q], u0);
     }
-    ref32_from_u<D>(u0, c, rf);
+    ref32_from_u<D>(u0f, c, rf);
     dev32<D>(rf, du, c, dv);
     if (!(dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1) && rf.rho > 0.0f && rf.p > 0.0f)) atomicOr(status, 1);
 #pragma unroll
@@ -152,18 +202,19 @@ __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kern
       for (int q = 0; q < NC; ++q) nonc[q] += dF[q];
     }
     const float kf = c.beta * c.inv_bp1;
-    double res[NC];
+    const int sl = c_ref32.node_slot[m];
+    float hwf = 0.0f;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      res[q] = (double)(-kf * acc[q] - c.inv_bp1 * nonc[q]);
-      r[((size_t)e * NC + q) * NP + m] = res[q];
+      const float rv = -kf * acc[q] - c.inv_bp1 * nonc[q];
+      hwf = fmaf(nd.W[q], rv, hwf);
+      // the facet terms (written by the facet kernel, which ran first)
+      const float rt = sl >= 0 ? rv + __ldg(&satf[((size_t)e * NC + q) * NS + sl]) : rv;
+      r[((size_t)e * NC + q) * NP + m] = widen_f32(rt);
     }
-    if (prod) {
-      const double Hm = c_ref32.H[m] * __ldg(&J[(size_t)e * NP + m]);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) hw += (double)nd.W[q] * res[q];
-      hw *= Hm;
-    }
+    // entropy production of the volume part, H w . r (the facet kernel adds
+    // its part): per node in float32, summed in float64
+    if (prod) hw = widen_f32(__fdiv_rn(hwf, __ldg(&ihf[(size_t)e * NP + m])));
   }
   if (prod) {
     double v[1] = {hw};
@@ -172,11 +223,11 @@ __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kern
 }
 
 template <int D>
-__global__ void __launch_bounds__(128) face_f32_kernel(double* __restrict__ r, const double* __restrict__ u,
+__global__ void __launch_bounds__(128) face_f32_kernel(float* __restrict__ satf, const double* __restrict__ u,
                                                        const int2* __restrict__ fp, int n_pairs,
-                                                       const double* __restrict__ nu, const double* __restrict__ J,
-                                                       Phys<float> c, int dissipation, int* __restrict__ status,
-                                                       double* __restrict__ prod) {
+                                                       const double* __restrict__ nu, const float* __restrict__ ihf,
+                                                       Phys<float> c, Phys<double> c64, int dissipation,
+                                                       int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double hw = 0.0;
@@ -186,21 +237,21 @@ __global__ void __launch_bounds__(128) face_f32_kernel(double* __restrict__ r, c
     const int k = pr.x / NS, s = pr.x - k * NS;
     const int v = pr.y / NS, s2 = pr.y - v * NS;
     const int m = c_ref32.slot_node[s], n = c_ref32.slot_node[s2];
-    double uk[NC];
-    float du[NC];
+    float ukf[NC], du[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      uk[q] = __ldg(&u[((size_t)k * NC + q) * NP + m]);
-      du[q] = (float)(__ldg(&u[((size_t)v * NC + q) * NP + n]) - uk[q]);
+      const double a = __ldg(&u[((size_t)k * NC + q) * NP + m]);
+      ukf[q] = f32_trunc(a);
+      du[q] = f32_diff(__ldg(&u[((size_t)v * NC + q) * NP + n]), a);
     }
     Ref32<D> rk;
     Dev32<D> dv;
-    ref32_from_u<D>(uk, c, rk);
+    ref32_from_u<D>(ukf, c, rk);
     dev32<D>(rk, du, c, dv);
     if (!(rk.rho > 0.0f && rk.p > 0.0f && dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1))) atomicOr(status, 1);
     float nuv[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) nuv[i] = (float)__ldg(&nu[((size_t)k * NS + s) * D + i]);
+    for (int i = 0; i < D; ++i) nuv[i] = f32_trunc(__ldg(&nu[((size_t)k * NS + s) * D + i]));
     float G[NC], df[NC], Dw[NC];
     PairAvg<float, D> a;
     sy_flux_dev32<D>(rk, dv, c, nuv, G, a);
@@ -208,30 +259,23 @@ __global__ void __launch_bounds__(128) face_f32_kernel(double* __restrict__ r, c
 #pragma unroll
     for (int q = 0; q < NC; ++q) Dw[q] = 0.0f;
     if (dissipation) {
-      float b2 = 0.0f;
-#pragma unroll
-      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
-      const float b = sqrtf(b2);
-      const float ib = 1.0f / b;
-      float nh[D], mdw[NC], out[NC];
-#pragma unroll
-      for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
+      float mdw[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) mdw[q] = -dv.dW[q];  // w_k - w_v
-      diss_apply<float, D>(a, c, nh, mdw, out);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) Dw[q] = 0.5f * b * out[q];
+      diss32<D>(a, c, c64, nuv, mdw, Dw);
     }
-    const double ihk = 1.0 / (c_ref32.H[m] * __ldg(&J[(size_t)k * NP + m]));
-    const double ihv = 1.0 / (c_ref32.H[n] * __ldg(&J[(size_t)v * NP + n]));
+    const float ihk = __ldg(&ihf[(size_t)k * NP + m]);
+    const float ihv = __ldg(&ihf[(size_t)v * NP + n]);
+    float hwf = 0.0f;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      const double gk = (double)(-G[q] - Dw[q]);
-      const double gv = (double)(G[q] - df[q] + Dw[q]);
-      r[((size_t)k * NC + q) * NP + m] += gk * ihk;
-      r[((size_t)v * NC + q) * NP + n] += gv * ihv;
-      if (prod) hw += (double)rk.W[q] * gk + (double)(rk.W[q] + dv.dW[q]) * gv;
+      const float gk = -G[q] - Dw[q];
+      const float gv = G[q] - df[q] + Dw[q];
+      satf[((size_t)k * NC + q) * NS + s] = gk * ihk;
+      satf[((size_t)v * NC + q) * NS + s2] = gv * ihv;
+      hwf = fmaf(rk.W[q], gk, fmaf(rk.W[q] + dv.dW[q], gv, hwf));
     }
+    if (prod) hw = widen_f32(hwf);
   }
   if (prod) {
     double vv[1] = {hw};
@@ -240,16 +284,17 @@ __global__ void __launch_bounds__(128) face_f32_kernel(double* __restrict__ r, c
 }
 
 // boundary facet slots (pair (-1, -1)): the terms of face_f32_kernel for
-// side k alone, the exterior state u_b in place of the neighbour's:
-//   H_k r_k += -G - Dw,  G = nu . (F*(u_k, u_b) - F(u_k)), Dw = |nu|/2 X|L|SX^T (w_k - w_b)
+// side k alone, the exterior state u_b in place of the neighbour's, into the
+// facet scratch:  H_k sat_k = -G - Dw,  G = nu . (F*(u_k, u_b) - F(u_k)),
+// Dw = |nu|/2 X|L|SX^T (w_k - w_b)
 template <int D>
-__global__ void __launch_bounds__(128) face_bc_f32_kernel(double* __restrict__ r, const double* __restrict__ u,
+__global__ void __launch_bounds__(128) face_bc_f32_kernel(float* __restrict__ satf, const double* __restrict__ u,
                                                           const int* __restrict__ bslot,
                                                           const double* __restrict__ bstate, int n_b,
                                                           const double* __restrict__ nu,
-                                                          const double* __restrict__ J, Phys<float> c,
-                                                          int dissipation, int* __restrict__ status,
-                                                          double* __restrict__ prod) {
+                                                          const float* __restrict__ ihf, Phys<float> c,
+                                                          Phys<double> c64, int dissipation,
+                                                          int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double hw = 0.0;
@@ -258,48 +303,41 @@ __global__ void __launch_bounds__(128) face_bc_f32_kernel(double* __restrict__ r
     const int a = __ldg(&bslot[t]);
     const int k = a / NS, s = a - k * NS;
     const int m = c_ref32.slot_node[s];
-    double uk[NC];
-    float du[NC];
+    float ukf[NC], du[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      uk[q] = __ldg(&u[((size_t)k * NC + q) * NP + m]);
-      du[q] = (float)(__ldg(&bstate[(size_t)t * NC + q]) - uk[q]);
+      const double x = __ldg(&u[((size_t)k * NC + q) * NP + m]);
+      ukf[q] = f32_trunc(x);
+      du[q] = f32_diff(__ldg(&bstate[(size_t)t * NC + q]), x);
     }
     Ref32<D> rk;
     Dev32<D> dv;
-    ref32_from_u<D>(uk, c, rk);
+    ref32_from_u<D>(ukf, c, rk);
     dev32<D>(rk, du, c, dv);
     if (!(rk.rho > 0.0f && rk.p > 0.0f && dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1))) atomicOr(status, 1);
     float nuv[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) nuv[i] = (float)__ldg(&nu[((size_t)k * NS + s) * D + i]);
+    for (int i = 0; i < D; ++i) nuv[i] = f32_trunc(__ldg(&nu[((size_t)k * NS + s) * D + i]));
     float G[NC], Dw[NC];
     PairAvg<float, D> av;
     sy_flux_dev32<D>(rk, dv, c, nuv, G, av);
 #pragma unroll
     for (int q = 0; q < NC; ++q) Dw[q] = 0.0f;
     if (dissipation) {
-      float b2 = 0.0f;
-#pragma unroll
-      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
-      const float b = sqrtf(b2);
-      const float ib = 1.0f / b;
-      float nh[D], mdw[NC], o[NC];
-#pragma unroll
-      for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
+      float mdw[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) mdw[q] = -dv.dW[q];
-      diss_apply<float, D>(av, c, nh, mdw, o);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) Dw[q] = 0.5f * b * o[q];
+      diss32<D>(av, c, c64, nuv, mdw, Dw);
     }
-    const double ihk = 1.0 / (c_ref32.H[m] * __ldg(&J[(size_t)k * NP + m]));
+    const float ihk = __ldg(&ihf[(size_t)k * NP + m]);
+    float hwf = 0.0f;
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      const double gk = (double)(-G[q] - Dw[q]);
-      r[((size_t)k * NC + q) * NP + m] += gk * ihk;
-      if (prod) hw += (double)rk.W[q] * gk;
+      const float gk = -G[q] - Dw[q];
+      satf[((size_t)k * NC + q) * NS + s] = gk * ihk;
+      hwf = fmaf(rk.W[q], gk, hwf);
     }
+    if (prod) hw = widen_f32(hwf);
   }
   if (prod) {
     double vv[1] = {hw};
@@ -308,31 +346,35 @@ __global__ void __launch_bounds__(128) face_bc_f32_kernel(double* __restrict__ r
 }
 
 template <int D, int NP>
-static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial,
+                        float* satf) {
   constexpr int EB = (256 / NP) > 0 ? (256 / NP) : 1;
   const Phys<float> ph = make_phys<float>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
+  const Phys<double> ph64 = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   int np_used = 0;
   {
-    const int nb = (c->n_e + EB - 1) / EB;
-    ProfScope ps(c, PG_SPLIT, s);
-    split_volume_f32_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops32, c->b.J, c->n_e, ph, c->b.status,
-                                                              prod);
-    c->launches++;
-    if (prod) np_used += nb;
-  }
-  {
+    // facet terms first, into the float32 facet scratch the volume kernel adds
     const int bs = 128, nb = (c->n_pairs + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
-    face_f32_kernel<D><<<nb, bs, 0, s>>>(r, u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, ph,
-                                         c->prm.dissipation, c->b.status, prod ? prod + np_used : nullptr);
+    face_f32_kernel<D><<<nb, bs, 0, s>>>(satf, u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihf, ph, ph64,
+                                         c->prm.dissipation, c->b.status, prod);
     c->launches++;
     if (prod) np_used += nb;
   }
   if (c->n_bslot > 0) {
     const int bs = 128, nb = (c->n_bslot + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
-    face_bc_f32_kernel<D><<<nb, bs, 0, s>>>(r, u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.J, ph,
-                                            c->prm.dissipation, c->b.status, prod ? prod + np_used : nullptr);
+    face_bc_f32_kernel<D><<<nb, bs, 0, s>>>(satf, u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.ihf, ph,
+                                            ph64, c->prm.dissipation, c->b.status,
+                                            prod ? prod + np_used : nullptr);
+    c->launches++;
+    if (prod) np_used += nb;
+  }
+  {
+    const int nb = (c->n_e + EB - 1) / EB;
+    ProfScope ps(c, PG_SPLIT, s);
+    split_volume_f32_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops32, c->b.ihf, satf, c->n_e, ph,
+                                                              c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     if (prod) np_used += nb;
   }
@@ -340,27 +382,32 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
+int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial,
+                     double* scratch) {
+  // the float32 facet scratch [n_e][n_c][n_slot] lives in the first half of
+  // the float64 facet scratch (the context's, or the static one of the
+  // no-allocation entry point)
+  float* satf = reinterpret_cast<float*>(scratch);
   if (c->dim == 1) {
     switch (c->n_p) {
-      case 2: return split_f32_np<1, 2>(c, u, r, s, prod, n_partial);
-      case 3: return split_f32_np<1, 3>(c, u, r, s, prod, n_partial);
-      case 4: return split_f32_np<1, 4>(c, u, r, s, prod, n_partial);
-      case 5: return split_f32_np<1, 5>(c, u, r, s, prod, n_partial);
+      case 2: return split_f32_np<1, 2>(c, u, r, s, prod, n_partial, satf);
+      case 3: return split_f32_np<1, 3>(c, u, r, s, prod, n_partial, satf);
+      case 4: return split_f32_np<1, 4>(c, u, r, s, prod, n_partial, satf);
+      case 5: return split_f32_np<1, 5>(c, u, r, s, prod, n_partial, satf);
     }
   } else if (c->dim == 2) {
     switch (c->n_p) {
-      case 7: return split_f32_np<2, 7>(c, u, r, s, prod, n_partial);
-      case 12: return split_f32_np<2, 12>(c, u, r, s, prod, n_partial);
-      case 18: return split_f32_np<2, 18>(c, u, r, s, prod, n_partial);
-      case 27: return split_f32_np<2, 27>(c, u, r, s, prod, n_partial);
+      case 7: return split_f32_np<2, 7>(c, u, r, s, prod, n_partial, satf);
+      case 12: return split_f32_np<2, 12>(c, u, r, s, prod, n_partial, satf);
+      case 18: return split_f32_np<2, 18>(c, u, r, s, prod, n_partial, satf);
+      case 27: return split_f32_np<2, 27>(c, u, r, s, prod, n_partial, satf);
     }
   } else if (c->dim == 3) {
     switch (c->n_p) {
-      case 12: return split_f32_np<3, 12>(c, u, r, s, prod, n_partial);
-      case 25: return split_f32_np<3, 25>(c, u, r, s, prod, n_partial);
-      case 58: return split_f32_np<3, 58>(c, u, r, s, prod, n_partial);
-      case 78: return split_f32_np<3, 78>(c, u, r, s, prod, n_partial);
+      case 12: return split_f32_np<3, 12>(c, u, r, s, prod, n_partial, satf);
+      case 25: return split_f32_np<3, 25>(c, u, r, s, prod, n_partial, satf);
+      case 58: return split_f32_np<3, 58>(c, u, r, s, prod, n_partial, satf);
+      case 78: return split_f32_np<3, 78>(c, u, r, s, prod, n_partial, satf);
     }
   }
   return -2;

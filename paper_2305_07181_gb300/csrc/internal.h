@@ -46,6 +46,7 @@ struct Buffers {
   float* ops32 = nullptr;      // same, float (nearest)
   float* ops32lo = nullptr;    // same, float remainder ops64 - ops32 (compensated FP32-bulk contractions)
   double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
+  float* ihf = nullptr;        // [n_e][n_p] 1/(H_ref J), float32 (the float32 path's facet scaling)
   // element lists for the hybrid scheme (capacity n_e each), the flags they
   // come from, and the detector's scratch (unwidened flags, block counts + total)
   int* list_split = nullptr;
@@ -195,7 +196,8 @@ int set_ref_tables(const RefTables& t);
 // reference tables, and the launcher (volume kernel, then facet kernel adding
 // into r); -2 for an operator size not compiled in
 int set_ref_tables_f32(const RefTables& t);
-int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial);
+int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial,
+                     double* scratch);
 int launch_residual_vjp(esplit_ctx* c, const double* u, const double* cot, double* grad, cudaStream_t s);
 // static facet scratch of esplit_residual_noalloc: 2^21 doubles (16 MiB)
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(1) << 21;

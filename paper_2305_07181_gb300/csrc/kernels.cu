@@ -23,6 +23,7 @@
 #include "phys.cuh"
 #include "visc_flux.cuh"
 #include "reduce.cuh"
+#include "bits32.cuh"
 
 namespace esplit {
 
@@ -530,44 +531,6 @@ struct SplitSmem {
   T sfl[EB][D][D + 2][NP];
   T swl[EB][D + 2][NP];
 };
-
-// v = hi + lo with float hi (v's first 24 significant bits, truncated) and
-// float lo (the remaining 29 bits, rounded to 24), by integer operations on
-// the bit patterns: on GB300 a float64<->float32 conversion occupies the FP64
-// pipe, which the kernel's pointwise float64 work already saturates.  |v| below
-// 2^-126 gives hi = lo = 0; |v| below 2^-74 loses lo (both far below the
-// round-off of the float64 terms these variations are added to).
-__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((b >> 52) & 0x7ffULL);  // biased exponent
-  const unsigned sgn = (unsigned)(b >> 63) << 31;
-  if (e <= 1023 - 127) {
-    hi = 0.0f;
-    lo = 0.0f;
-    return;
-  }
-  const unsigned long long mant = b & 0xFFFFFFFFFFFFFULL;
-  hi = __uint_as_float(sgn | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(mant >> 29));
-  const int E = e - 1075;  // weight of the lowest mantissa bit
-  if (E < -126) {
-    lo = 0.0f;
-    return;
-  }
-  const float lf = __uint2float_rn((unsigned)(mant & 0x1FFFFFFFULL));
-  lo = __uint_as_float(sgn | __float_as_uint(__fmul_rn(lf, __uint_as_float((unsigned)(E + 127) << 23))));
-}
-
-// float -> double by the bit patterns (normal floats and zero; float
-// subnormals, far below the terms these sums are added to, give zero)
-__device__ __forceinline__ double widen_f32(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u) return 0.0;
-  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                               ((unsigned long long)(e - 127 + 1023) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)b);
-}
 
 // acc + cmp += (ah + al) (bh + bl), Dot2 step: exact product error by fmaf,
 // TwoSum for the addition; intrinsics keep the compiler from fusing them.
@@ -1256,7 +1219,7 @@ static bool use_f32_path(const esplit_ctx* c) {
 }
 
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
-  if (use_f32_path(c)) return launch_split_f32(c, u, r, s, prod, n_partial);
+  if (use_f32_path(c)) return launch_split_f32(c, u, r, s, prod, n_partial, c->b.sat);
   if (c->prm.precision != ESPLIT_FP64) return residual_t<float>(c, u, r, s, prod, n_partial, c->b.sat);
   return residual_t<double>(c, u, r, s, prod, n_partial, c->b.sat);
 }
@@ -1290,7 +1253,7 @@ int launch_residual_noalloc(esplit_ctx* c, const double* u, double* r, cudaStrea
   // kernel timing would create CUDA events: off for this thread's launches
   // (the context's setting, which other threads may be using, is untouched)
   t_no_events = true;
-  int rc = use_f32_path(c) ? launch_split_f32(c, u, r, s, nullptr, nullptr)  // needs no scratch
+  int rc = use_f32_path(c) ? launch_split_f32(c, u, r, s, nullptr, nullptr, scratch)
            : c->prm.precision != ESPLIT_FP64 ? residual_t<float>(c, u, r, s, nullptr, nullptr, scratch)
                                               : residual_t<double>(c, u, r, s, nullptr, nullptr, scratch);
   t_no_events = false;

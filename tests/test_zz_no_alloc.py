@@ -106,6 +106,25 @@ def test_noalloc_fp32_bulk_matches_residual(lib):
     s.close()
 
 
+def test_noalloc_fp32_matches_residual(lib):
+    """Float32 precision: the no-allocation call runs the same kernels in the
+    same order as esplit_residual, with its float32 facet scratch in the
+    static array: equal results, on two calls."""
+    op = tri_operator(3)
+    m = periodic_tri_mesh(op, 9, 10.0, 0.05)
+    s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32"))
+    ref = s.empty()
+    for call in range(2):
+        u = s.to_device(states.add_uniform_noise(states.isentropic_vortex(m), 1e-3, 130 + call))
+        s.residual(u, ref)
+        out = torch.full_like(ref, float("nan"))
+        rc = lib.capi.esplit_residual_noalloc(s.ctx, _ptr(u), _ptr(out), _stream())
+        assert rc == 0, lib.capi.esplit_last_error(s.ctx)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    s.close()
+
+
 def test_noalloc_allocates_nothing(lib):
     """After a first call (which looks up the static array and loads the
     kernels it launches), further calls leave the device's free memory and
