@@ -56,7 +56,10 @@ extern "C" {
                                differences, the residual's accumulation, the
                                entropy-production sums, the metric operators (formed
                                in float64, rounded once) and the relaxation step.
-                               Other schemes and the viscous terms: as
+                               Max-norm error <= 1e-5 relative per component.
+                               Other schemes, the viscous terms and the 58- and
+                               78-node tetrahedra (whose operator rows amplify
+                               float32 flux rounding beyond that bound): as
                                ESPLIT_FP32_BULK                                     */
 
 #define ESPLIT_SCHEME_SPLIT 0     /* entropy split, Eq. (100)                       */
@@ -312,7 +315,9 @@ int esplit_rrk_step_vjp(esplit_ctx* ctx, const double* u_dev, double dt, const d
                         double* ubar_dev, double* g_out, void* stream);
 
 /* Sticky status of asynchronous work (synchronises the context's last
- * stream): ESPLIT_OK or ESPLIT_ERR_NONPHYSICAL; reading clears it. */
+ * stream): ESPLIT_OK, ESPLIT_ERR_NONPHYSICAL, or ESPLIT_ERR_CUDA when a
+ * kernel's bounded wait for its shared-memory staging (bulk copy) ran out --
+ * its result was then computed from global memory; reading clears it. */
 int esplit_get_status(esplit_ctx* ctx);
 
 /* Message of the last failure on this context (static storage of ctx). */

@@ -35,13 +35,12 @@ __device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
 }
 
 // float -> double by the bit patterns (normal floats and zero; float
-// subnormals, far below the terms these sums are added to, give zero;
-// infinities and NaN take the conversion instruction)
+// subnormals, far below the terms these sums are added to, give zero; the
+// kernels report non-finite states through their own checks)
 __device__ __forceinline__ double widen_f32(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu;
   if (e == 0u) return 0.0;
-  if (e == 0xffu) return (double)f;
   const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
                                ((unsigned long long)(e - 127 + 1023) << 52) |
                                ((unsigned long long)(u & 0x7fffffu) << 29);

@@ -82,6 +82,7 @@ int read_status(esplit_ctx* c, cudaStream_t s, bool clear) {
   CK(cudaMemcpyAsync(&h, c->b.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (clear && h) CK(cudaMemsetAsync(c->b.status, 0, sizeof(int), s));
+  if (h & 4) return fail(c, ESPLIT_ERR_CUDA, "a kernel's wait for its shared-memory staging timed out");
   return h ? ESPLIT_ERR_NONPHYSICAL : ESPLIT_OK;
 }
 
@@ -162,7 +163,7 @@ void esplit_destroy(esplit_ctx* c) {
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.wslot, b.vfb, b.vfs, b.vus,
-                b.bslot, b.bstate, b.ihf};
+                b.bslot, b.bstate, b.ihf, b.opsD32};
   for (void* p : ps) dfree(p);
   if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
   if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
@@ -294,6 +295,13 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
   if ((rc = dalloc(c, &c->b.fcache, (size_t)(d + 9) * n_e * NS))) return rc;
   if ((rc = dalloc(c, &c->b.ihf, (size_t)n_e * NP))) return rc;
+  if (d <= 2) {
+    c->opsD_stride = (d * NP * NP + 3) / 4 * 4;
+    if ((rc = dalloc(c, &c->b.opsD32, (size_t)n_e * c->opsD_stride))) return rc;
+  } else {
+    dalloc(c, &c->b.opsD32, 0);
+    c->opsD_stride = 0;
+  }
   c->partial_cap = 0;
   if ((rc = ensure_partial(c))) return rc;
   CK(cudaMemcpy(c->b.J, J, sizeof(double) * n_e * NP, cudaMemcpyHostToDevice));

@@ -34,6 +34,7 @@
 #include "dev32.cuh"
 #include "internal.h"
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace esplit {
 
@@ -101,20 +102,78 @@ struct SplitSmem32 {
   float df[EB][D][D + 2][NP];  // flux variations
   float dw[EB][D + 2][NP];     // entropy-variable variations
   double u0[EB][D + 2];        // node-0 states
+  uint64_t bar;                // completion barrier of the operators' bulk copy
 };
 
-template <int D, int NP, int EB>
+// acc = sum_i D_i df_i, g_i = D_i dw at node m of element el, with the
+// element's D_i (layout [i][n][m]) at opb: in shared memory (SMEM) or global.
+// For operators above 20 nodes the sums are Kahan-compensated: the rounding
+// of partial sums much larger than the final, cancelling, result dominated
+// the error there.
+template <bool SMEM, int D, int NP, int EB>
+__device__ __forceinline__ void contract32(const float* __restrict__ opb, const SplitSmem32<D, NP, EB>& sm, int el,
+                                           int m, float (&acc)[D + 2], float (&g)[D][D + 2]) {
+  constexpr int NC = D + 2;
+  constexpr bool COMP = NP > 20;
+  float cacc[NC], cg[D][NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) acc[q] = cacc[q] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) g[i][q] = cg[i][q] = 0.0f;
+#pragma unroll 6
+    for (int n = 0; n < NP; ++n) {
+      const float dt = SMEM ? opb[(i * NP + n) * NP + m] : __ldg(&opb[(i * NP + n) * NP + m]);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        if constexpr (COMP) {
+          kahan_fma(dt, sm.df[el][i][q][n], acc[q], cacc[q]);
+          kahan_fma(dt, sm.dw[el][q][n], g[i][q], cg[i][q]);
+        } else {
+          acc[q] = fmaf(dt, sm.df[el][i][q][n], acc[q]);
+          g[i][q] = fmaf(dt, sm.dw[el][q][n], g[i][q]);
+        }
+      }
+    }
+  }
+  if constexpr (COMP) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      acc[q] = __fsub_rn(acc[q], cacc[q]);
+#pragma unroll
+      for (int i = 0; i < D; ++i) g[i][q] = __fsub_rn(g[i][q], cg[i][q]);
+    }
+  }
+}
+
+// STAGE: the block's operators (one contiguous range of opsD) are brought
+// into shared memory by one bulk copy at the start, overlapping the pointwise
+// phase; the contraction then reads them there.
+template <int D, int NP, int EB, bool STAGE>
 __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kernel(
     const double* __restrict__ u, double* __restrict__ r, const float* __restrict__ ops,
-    const float* __restrict__ ihf, const float* __restrict__ satf, int n_e, Phys<float> c, int* __restrict__ status,
-    double* __restrict__ prod) {
+    const float* __restrict__ opsD, int opsD_stride, const float* __restrict__ ihf, const float* __restrict__ satf,
+    int n_e, Phys<float> c, int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
   __shared__ SplitSmem32<D, NP, EB> sm;
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   const int NS = c_ref32.n_slot;
   const int el = threadIdx.x / NP;
   const int m = threadIdx.x - el * NP;
   const int e = blockIdx.x * EB + el;
   const bool active = (el < EB) && (e < n_e);
+  float* ops_sm = reinterpret_cast<float*>(dyn_smem);
+  if constexpr (STAGE) {
+    if (threadIdx.x == 0) mbar_init(&sm.bar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int e0 = blockIdx.x * EB;
+      const uint32_t bytes = (uint32_t)(min(EB, n_e - e0) * opsD_stride) * 4u;
+      mbar_expect_tx(&sm.bar, bytes);
+      bulk_load(ops_sm, opsD + (size_t)e0 * opsD_stride, bytes, &sm.bar);
+    }
+  }
   double uu[NC];
   if (active) {
 #pragma unroll
@@ -150,44 +209,23 @@ __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kern
     for (int q = 0; q < NC; ++q) sm.dw[el][q][m] = dv.dW[q];
   }
   __syncthreads();
+  bool staged = false;
+  if constexpr (STAGE) {
+    staged = mbar_wait(&sm.bar, 0);
+    if (!staged) {
+      // report, wait (bounded) for the copy still in flight into this block's
+      // shared memory, and contract from global memory instead
+      atomicOr(status, 4);
+      mbar_wait(&sm.bar, 0);
+    }
+  }
   double hw = 0.0;
   if (active) {
-    const float* op = ops + (size_t)e * (2 * D * NP * NP);
-    // float32 sums; for the larger operators (n_p > 20) compensated
-    // (Kahan: the rounding error of every addition is carried in a second
-    // accumulator), which removes the dominant error there -- the rounding
-    // of partial sums much larger than the final, cancelling, result
-    constexpr bool COMP = NP > 20;
-    float acc[NC], g[D][NC], cacc[NC], cg[D][NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) acc[q] = cacc[q] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-#pragma unroll
-      for (int q = 0; q < NC; ++q) g[i][q] = cg[i][q] = 0.0f;
-#pragma unroll 6
-      for (int n = 0; n < NP; ++n) {
-        const float dt = __ldg(&op[((D + i) * NP + n) * NP + m]);
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          if constexpr (COMP) {
-            kahan_fma(dt, sm.df[el][i][q][n], acc[q], cacc[q]);
-            kahan_fma(dt, sm.dw[el][q][n], g[i][q], cg[i][q]);
-          } else {
-            acc[q] = fmaf(dt, sm.df[el][i][q][n], acc[q]);
-            g[i][q] = fmaf(dt, sm.dw[el][q][n], g[i][q]);
-          }
-        }
-      }
-    }
-    if constexpr (COMP) {
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        acc[q] = __fsub_rn(acc[q], cacc[q]);
-#pragma unroll
-        for (int i = 0; i < D; ++i) g[i][q] = __fsub_rn(g[i][q], cg[i][q]);
-      }
-    }
+    float acc[NC], g[D][NC];
+    if (staged)
+      contract32<true, D, NP, EB>(ops_sm + (size_t)el * opsD_stride, sm, el, m, acc, g);
+    else
+      contract32<false, D, NP, EB>(ops + ((size_t)e * 2 + 1) * (D * NP * NP), sm, el, m, acc, g);
     Node<float, D> nd;
     node32<D>(rf, dv, nd);
     const JvpPrep<float> jp = jvp_prep<float, D>(nd, c);
@@ -373,8 +411,19 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
   {
     const int nb = (c->n_e + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    split_volume_f32_kernel<D, NP, EB><<<nb, EB * NP, 0, s>>>(u, r, c->b.ops32, c->b.ihf, satf, c->n_e, ph,
-                                                              c->b.status, prod ? prod + np_used : nullptr);
+    constexpr bool STAGE = D <= 2;
+    const size_t dyn = STAGE ? (size_t)EB * c->opsD_stride * sizeof(float) : 0;
+    if (STAGE && dyn > 48 * 1024) {
+      static bool attr_set = false;
+      if (!attr_set) {
+        cudaFuncSetAttribute(split_volume_f32_kernel<D, NP, EB, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn);
+        attr_set = true;
+      }
+    }
+    split_volume_f32_kernel<D, NP, EB, STAGE><<<nb, EB * NP, dyn, s>>>(
+        u, r, c->b.ops32, c->b.opsD32, c->opsD_stride, c->b.ihf, satf, c->n_e, ph, c->b.status,
+        prod ? prod + np_used : nullptr);
     c->launches++;
     if (prod) np_used += nb;
   }

@@ -47,6 +47,10 @@ struct Buffers {
   float* ops32lo = nullptr;    // same, float remainder ops64 - ops32 (compensated FP32-bulk contractions)
   double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
   float* ihf = nullptr;        // [n_e][n_p] 1/(H_ref J), float32 (the float32 path's facet scaling)
+  // the D_i half of ops32 alone, per element padded to a multiple of 4 floats
+  // (16 bytes), so that a block's elements are one contiguous, aligned range
+  // for a bulk copy into shared memory (float32 path, d <= 2)
+  float* opsD32 = nullptr;     // [n_e][opsD_stride]
   // element lists for the hybrid scheme (capacity n_e each), the flags they
   // come from, and the detector's scratch (unwidened flags, block counts + total)
   int* list_split = nullptr;
@@ -112,6 +116,7 @@ struct esplit_ctx {
   int n_e = 0, n_pairs = 0;
   int n_split = 0, n_had = 0;
   int n_bslot = 0;                 // boundary facet slots of the mesh
+  int opsD_stride = 0;             // floats per element in b.opsD32
   bool have_bstate = false;        // their exterior states are set
   std::vector<int> bslots;         // flat slot indices (element * n_slot + slot), ascending
   bool have_op = false, have_mesh = false, ops_beta_valid = false;

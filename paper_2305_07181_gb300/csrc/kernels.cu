@@ -91,6 +91,16 @@ __global__ void build_rows_kernel(const double* __restrict__ ops64, int n_e, int
   rows[idx] = s;
 }
 
+// opsD32[e][j] = D_i half of ops32[e] (j < d n_p^2), zero padding after it
+__global__ void build_opsD_kernel(const float* __restrict__ ops32, int n_e, int dnn, int stride,
+                                  float* __restrict__ opsD) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n_e * stride) return;
+  const size_t e = idx / stride;
+  const int j = (int)(idx - e * stride);
+  opsD[idx] = j < dnn ? ops32[(e * 2 + 1) * dnn + j] : 0.0f;
+}
+
 int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   size_t total = (size_t)c->n_e * 2 * c->dim * c->n_p * c->n_p;
   int bs = 256;
@@ -108,6 +118,13 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   size_t nr = (size_t)c->n_e * 2 * c->dim * c->n_p;
   build_rows_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(c->b.ops64, c->n_e, 2 * c->dim, c->b.rows);
   c->launches += 2;
+  if (c->b.opsD32) {
+    const int dnn = c->dim * c->n_p * c->n_p;
+    const size_t no = (size_t)c->n_e * c->opsD_stride;
+    build_opsD_kernel<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(c->b.ops32, c->n_e, dnn, c->opsD_stride,
+                                                                    c->b.opsD32);
+    c->launches++;
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1212,10 +1229,16 @@ static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s,
   return -2;
 }
 
-// the float32 deviation path (fp32.cu) covers the inviscid split scheme; the
-// other schemes and the viscous terms take the FP32-bulk kernels there
+// the float32 deviation path (fp32.cu) covers the inviscid split scheme on
+// lines, triangles and tetrahedra up to 25 nodes; the other schemes, the
+// viscous terms and the 58- and 78-node tetrahedra take the FP32-bulk kernels
+// there.  (Those two tetrahedron operators have rows with sum |D_mn| of 80 to
+// 170 at facet nodes of small volume weight: the float32 rounding of the flux
+// variations, amplified by that, is 1.4e-5 to 3.2e-5 of the residual, above
+// the 1e-5 bound of the float32 path.)
 static bool use_f32_path(const esplit_ctx* c) {
-  return c->prm.precision == ESPLIT_FP32 && c->prm.scheme == ESPLIT_SCHEME_SPLIT && !c->prm.viscous;
+  return c->prm.precision == ESPLIT_FP32 && c->prm.scheme == ESPLIT_SCHEME_SPLIT && !c->prm.viscous &&
+         !(c->dim == 3 && c->n_p > 25);
 }
 
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
