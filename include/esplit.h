@@ -47,7 +47,8 @@ extern "C" {
                                terms, entropy functionals and the relaxation root
                                solve in float64.  Hadamard forms: their two-point
                                fluxes in plain float32                              */
-#define ESPLIT_FP32 2       /* entropy-split scheme, inviscid: fluxes, entropy
+#define ESPLIT_FP32 2       /* entropy-split scheme, inviscid, lines and
+                               triangles: fluxes, entropy
                                variables, A~_i products, two-point fluxes,
                                dissipation and operator contractions in float32,
                                evaluated as deviations from float64 reference
@@ -57,10 +58,9 @@ extern "C" {
                                entropy-production sums, the metric operators (formed
                                in float64, rounded once) and the relaxation step.
                                Max-norm error <= 1e-5 relative per component.
-                               Other schemes, the viscous terms and the 58- and
-                               78-node tetrahedra (whose operator rows amplify
-                               float32 flux rounding beyond that bound): as
-                               ESPLIT_FP32_BULK                                     */
+                               Other schemes, the viscous terms and tetrahedra
+                               (whose operator rows amplify float32 flux rounding
+                               beyond that bound): as ESPLIT_FP32_BULK              */
 
 #define ESPLIT_SCHEME_SPLIT 0     /* entropy split, Eq. (100)                       */
 #define ESPLIT_SCHEME_HADAMARD 1  /* Sjogreen-Yee Hadamard form, Eq. (99)            */

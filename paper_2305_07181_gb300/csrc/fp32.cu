@@ -413,12 +413,13 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
     ProfScope ps(c, PG_SPLIT, s);
     constexpr bool STAGE = D <= 2;
     const size_t dyn = STAGE ? (size_t)EB * c->opsD_stride * sizeof(float) : 0;
-    if (STAGE && dyn > 48 * 1024) {
-      static bool attr_set = false;
-      if (!attr_set) {
+    if (STAGE) {
+      // static + dynamic shared memory above 48 KB needs the opt-in
+      static size_t attr_set = 0;
+      if (attr_set < dyn) {
         cudaFuncSetAttribute(split_volume_f32_kernel<D, NP, EB, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)dyn);
-        attr_set = true;
+        attr_set = dyn;
       }
     }
     split_volume_f32_kernel<D, NP, EB, STAGE><<<nb, EB * NP, dyn, s>>>(

@@ -1230,15 +1230,14 @@ static int residual_t(esplit_ctx* c, const double* u, double* r, cudaStream_t s,
 }
 
 // the float32 deviation path (fp32.cu) covers the inviscid split scheme on
-// lines, triangles and tetrahedra up to 25 nodes; the other schemes, the
-// viscous terms and the 58- and 78-node tetrahedra take the FP32-bulk kernels
-// there.  (Those two tetrahedron operators have rows with sum |D_mn| of 80 to
-// 170 at facet nodes of small volume weight: the float32 rounding of the flux
-// variations, amplified by that, is 1.4e-5 to 3.2e-5 of the residual, above
-// the 1e-5 bound of the float32 path.)
+// lines and triangles; the other schemes, the viscous terms and tetrahedra
+// take the FP32-bulk kernels there.  (The tetrahedron operators have rows with
+// sum |D_mn| of 40 to 170 at facet nodes of small volume weight, which
+// amplify the float32 rounding of the flux variations: 1.4e-5 at 25 nodes and
+// up to 3.2e-5 at 78 without dissipation, above the 1e-5 bound of the float32
+// path; triangles stay below 6e-6.)
 static bool use_f32_path(const esplit_ctx* c) {
-  return c->prm.precision == ESPLIT_FP32 && c->prm.scheme == ESPLIT_SCHEME_SPLIT && !c->prm.viscous &&
-         !(c->dim == 3 && c->n_p > 25);
+  return c->prm.precision == ESPLIT_FP32 && c->prm.scheme == ESPLIT_SCHEME_SPLIT && !c->prm.viscous && c->dim <= 2;
 }
 
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {

@@ -9,14 +9,22 @@
 // has the last entry 1/(R v_nc^2) only.
 #pragma once
 
+#include <type_traits>
+
 namespace esplit {
+
+// constants in the arithmetic of T: float for the float32 path, double for
+// double and the dual numbers of the reverse mode
+template <typename T>
+using vscal_t = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
 
 // dT/dW of Eq. (39) (the exact derivative; the printed Eq. (40) has a sign
 // typo in the momentum entries and drops alpha in the last entry).  T is
 // double or a dual number (the reverse mode differentiates these in u).
-template <typename T, int D, int ENT = 0>
-__device__ __forceinline__ void dT_dW(const Node<T, D>& n, const Phys<double>& c, T* TW) {
+template <typename T, int D, int ENT = 0, typename C = Phys<double>>
+__device__ __forceinline__ void dT_dW(const Node<T, D>& n, const C& c, T* TW) {
   constexpr int NC = D + 2;
+  using S = vscal_t<T>;
   if constexpr (ENT == 1) {
     const T pr = n.p * n.ir;  // p / rho = -1 / v_nc
 #pragma unroll
@@ -30,22 +38,23 @@ __device__ __forceinline__ void dT_dW(const Node<T, D>& n, const Phys<double>& c
   TW[0] = k;
 #pragma unroll
   for (int l = 0; l < D; ++l) TW[1 + l] = k * n.V[l];
-  TW[NC - 1] = -T_ / Wn + 0.5 * k * n.v2;
+  TW[NC - 1] = -T_ / Wn + S(0.5) * k * n.v2;
 }
 
 // F^V_i (i < D) from the entropy-variable gradients g[j] = dW/dx_j:
 //   dV_l/dx_j = -(g_j[1+l] + V_l g_j[nc]) / W_nc,  dT/dx_j = dT/dW . g_j,
 //   tau_ik = mu (dV_i/dx_k + dV_k/dx_i - 2/3 delta_ik div V),
 //   F_i = [0, tau_i., V . tau_i. + kappa dT/dx_i]
-template <typename T, int D, typename G, int ENT = 0>
-__device__ __forceinline__ void visc_flux(const Node<T, D>& n, const Phys<double>& c, int heat, const G (&g)[D][D + 2],
+template <typename T, int D, typename G, int ENT = 0, typename C = Phys<double>>
+__device__ __forceinline__ void visc_flux(const Node<T, D>& n, const C& c, int heat, const G (&g)[D][D + 2],
                                           T (&F)[D][D + 2]) {
   constexpr int NC = D + 2;
+  using S = vscal_t<T>;
   T iWn;  // 1 / w_nc
   if constexpr (ENT == 1)
     iWn = -(n.p * n.ir);
   else
-    iWn = -1.0 / n.q;
+    iWn = S(-1.0) / n.q;
   T Lg[D][D];  // Lg[j][l] = dV_l/dx_j
   T div = T(0.0);
 #pragma unroll
@@ -62,7 +71,7 @@ __device__ __forceinline__ void visc_flux(const Node<T, D>& n, const Phys<double
     F[i][0] = T(0.0);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      T tau = c.mu * (Lg[k][i] + Lg[i][k] - (k == i ? (2.0 / 3.0) * div : T(0.0)));
+      T tau = c.mu * (Lg[k][i] + Lg[i][k] - (k == i ? S(2.0 / 3.0) * div : T(0.0)));
       F[i][1 + k] = tau;
       e = e + n.V[k] * tau;
     }
@@ -78,15 +87,16 @@ __device__ __forceinline__ void visc_flux(const Node<T, D>& n, const Phys<double
 
 // a_j = sum_i K~_ij^T b_i: the gradient of sum_i b_i . F^V_i with respect to
 // g_j (F^V is linear in the gradients).
-template <typename T, int D, typename B, int ENT = 0>
-__device__ __forceinline__ void visc_flux_transpose(const Node<T, D>& n, const Phys<double>& c, int heat,
+template <typename T, int D, typename B, int ENT = 0, typename C = Phys<double>>
+__device__ __forceinline__ void visc_flux_transpose(const Node<T, D>& n, const C& c, int heat,
                                                     const B (&b)[D][D + 2], T (&a)[D][D + 2]) {
   constexpr int NC = D + 2;
+  using S = vscal_t<T>;
   T iWn;  // 1 / w_nc
   if constexpr (ENT == 1)
     iWn = -(n.p * n.ir);
   else
-    iWn = -1.0 / n.q;
+    iWn = S(-1.0) / n.q;
   T cc[D][D];
   T trc = T(0.0);
 #pragma unroll
@@ -104,7 +114,7 @@ __device__ __forceinline__ void visc_flux_transpose(const Node<T, D>& n, const P
     a[j][0] = hj * TW[0];
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-      T G = c.mu * (cc[j][l] + cc[l][j] - (j == l ? (2.0 / 3.0) * trc : T(0.0)));
+      T G = c.mu * (cc[j][l] + cc[l][j] - (j == l ? S(2.0 / 3.0) * trc : T(0.0)));
       a[j][1 + l] = -G * iWn + hj * TW[1 + l];
       sv = sv + G * n.V[l];
     }
