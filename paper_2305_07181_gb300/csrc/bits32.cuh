@@ -47,31 +47,23 @@ __device__ __forceinline__ double widen_f32(float f) {
   return __longlong_as_double((long long)b);
 }
 
-// (float)(a - b) for float64 a, b without float64 arithmetic: with a = ah + al
-// and b = bh + bl split as above, (ah - bh) is exact when a and b are within a
-// factor 2 of each other (Sterbenz) and the sum carries one float32 rounding
-// plus the remainders' rounding, ~2^-48 |a|.
-__device__ __forceinline__ float f32_diff(double a, double b) {
-  const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
-  const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
-  if (((ba >> 52) & 0x7ffULL) >= 1023 + 128 || ((bb >> 52) & 0x7ffULL) >= 1023 + 128)
-    return (float)(a - b);  // beyond the float32 range, infinities, NaN
-  float ah, al, bh, bl;
-  split_f64(a, ah, al);
-  split_f64(b, bh, bl);
-  return __fadd_rn(__fsub_rn(ah, bh), __fsub_rn(al, bl));
-}
-
-// float32 value of a float64 (its first 24 significant bits): the hi part of
-// split_f64; values beyond the float32 range take the conversion instruction
-// (overflow to infinity, NaN kept), so non-physical states stay detectable.
-__device__ __forceinline__ float f32_trunc(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+// float32 value of a float64, rounded to nearest (ties away from zero), by
+// integer operations: half a float32 unit in the last place is added to the
+// bit pattern (a carry out of the mantissa moves into the exponent) and the
+// low 29 bits dropped.  Values beyond the float32 range take the conversion
+// instruction (overflow to infinity, NaN kept), so non-physical states stay
+// detectable; |v| below 2^-126 gives 0.
+__device__ __forceinline__ float f32_round(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v) + (1ULL << 28);
   const int e = (int)((b >> 52) & 0x7ffULL);
   if (e >= 1023 + 128) return (float)v;
   if (e <= 1023 - 127) return 0.0f;
   return __uint_as_float(((unsigned)(b >> 63) << 31) | ((unsigned)(e - 1023 + 127) << 23) |
                          (unsigned)((b & 0xFFFFFFFFFFFFFULL) >> 29));
 }
+
+// (float)(a - b): one float64 subtraction (a single rounding at 2^-53), then
+// the bit-pattern rounding to float32
+__device__ __forceinline__ float f32_diff(double a, double b) { return f32_round(a - b); }
 
 }  // namespace esplit

@@ -59,6 +59,30 @@ int check_ready(esplit_ctx* c) {
   return ESPLIT_OK;
 }
 
+// floats per element of the padded D_i copy the float32 path stages in shared
+// memory: at least d n_p^2, a multiple of 4 (16 bytes, the bulk copy's unit),
+// and among those the one that spreads a warp's reads of one operator column
+// (lanes = consecutive nodes, in consecutive elements) over the most banks
+int opsD_stride_for(int d, int np) {
+  const int base = (d * np * np + 3) / 4 * 4;
+  int best = base, best_worst = 1 << 30;
+  for (int s = base; s < base + 32; s += 4) {
+    int worst = 0;
+    for (int w0 = 0; w0 < np; ++w0) {  // node of the warp's first lane
+      int cnt[32] = {0};
+      for (int l = 0; l < 32; ++l) {
+        const int e = (w0 + l) / np, m = (w0 + l) % np;
+        worst = std::max(worst, ++cnt[(e * s + m) % 32]);
+      }
+    }
+    if (worst < best_worst) {
+      best_worst = worst;
+      best = s;
+    }
+  }
+  return best;
+}
+
 int ensure_partial(esplit_ctx* c) {
   size_t need = 8 * ((size_t)c->n_e * c->n_p / 256 + 1) + 4 * ((size_t)c->n_e + 64);
   if (c->partial_cap >= need) return ESPLIT_OK;
@@ -296,7 +320,7 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.fcache, (size_t)(d + 9) * n_e * NS))) return rc;
   if ((rc = dalloc(c, &c->b.ihf, (size_t)n_e * NP))) return rc;
   if (d <= 2) {
-    c->opsD_stride = (d * NP * NP + 3) / 4 * 4;
+    c->opsD_stride = opsD_stride_for(d, NP);
     if ((rc = dalloc(c, &c->b.opsD32, (size_t)n_e * c->opsD_stride))) return rc;
   } else {
     dalloc(c, &c->b.opsD32, 0);

@@ -54,47 +54,21 @@ __device__ __forceinline__ void kahan_fma(float a, float b, float& s, float& c) 
 }
 
 // Dw = |nu|/2 X|L|SX^T (w_k - w_v) of Eq. (69) from the float32 pair averages
-// and entropy-variable jump.  In 3D the two small products with X (Eq. (80))
-// run in float64: at low Mach numbers the characteristic projections X^T dw
-// cancel strongly, and with the small facet weights of the larger
-// tetrahedron operators their float32 rounding reached ~1e-5 of the residual.
+// and entropy-variable jump
 template <int D>
-__device__ __forceinline__ void diss32(const PairAvg<float, D>& a, const Phys<float>& c, const Phys<double>& c64,
-                                       const float* nuv, const float* mdw, float* Dw) {
+__device__ __forceinline__ void diss32(const PairAvg<float, D>& a, const Phys<float>& c, const float* nuv,
+                                       const float* mdw, float* Dw) {
   float b2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
   const float b = sqrtf(b2);
   const float ib = 1.0f / b;
-  if constexpr (D == 3) {
-    PairAvg<double, D> a64;
-    a64.A1 = a.A1;
-    a64.E1 = a.E1;
-    a64.A2 = a.A2;
-    a64.E2 = a.E2;
-    a64.z1a = a.z1a;
-    a64.pa = a.pa;
-    a64.ke = a.ke;
-    double nh[D], dw[D + 2], o[D + 2];
+  float nh[D], o[D + 2];
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      a64.qV[i] = a.qV[i];
-      a64.Va[i] = a.Va[i];
-      nh[i] = (double)(nuv[i] * ib);
-    }
+  for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
+  diss_apply<float, D>(a, c, nh, mdw, o);
 #pragma unroll
-    for (int q = 0; q < D + 2; ++q) dw[q] = mdw[q];
-    diss_apply<double, D>(a64, c64, nh, dw, o);
-#pragma unroll
-    for (int q = 0; q < D + 2; ++q) Dw[q] = __double2float_rn(0.5 * (double)b * o[q]);
-  } else {
-    float nh[D], o[D + 2];
-#pragma unroll
-    for (int i = 0; i < D; ++i) nh[i] = nuv[i] * ib;
-    diss_apply<float, D>(a, c, nh, mdw, o);
-#pragma unroll
-    for (int q = 0; q < D + 2; ++q) Dw[q] = 0.5f * b * o[q];
-  }
+  for (int q = 0; q < D + 2; ++q) Dw[q] = 0.5f * b * o[q];
 }
 
 template <int D, int NP, int EB>
@@ -151,7 +125,7 @@ __device__ __forceinline__ void contract32(const float* __restrict__ opb, const 
 // into shared memory by one bulk copy at the start, overlapping the pointwise
 // phase; the contraction then reads them there.
 template <int D, int NP, int EB, bool STAGE>
-__global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kernel(
+__global__ void __launch_bounds__(EB * NP, 4) split_volume_f32_kernel(
     const double* __restrict__ u, double* __restrict__ r, const float* __restrict__ ops,
     const float* __restrict__ opsD, int opsD_stride, const float* __restrict__ ihf, const float* __restrict__ satf,
     int n_e, Phys<float> c, int* __restrict__ status, double* __restrict__ prod) {
@@ -192,7 +166,7 @@ __global__ void __launch_bounds__(EB * NP, D == 3 ? 2 : 3) split_volume_f32_kern
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       const double u0 = sm.u0[el][q];
-      u0f[q] = f32_trunc(u0);
+      u0f[q] = f32_round(u0);
       du[q] = f32_diff(uu[q], u0);
     }
     ref32_from_u<D>(u0f, c, rf);
@@ -264,8 +238,8 @@ template <int D>
 __global__ void __launch_bounds__(128) face_f32_kernel(float* __restrict__ satf, const double* __restrict__ u,
                                                        const int2* __restrict__ fp, int n_pairs,
                                                        const double* __restrict__ nu, const float* __restrict__ ihf,
-                                                       Phys<float> c, Phys<double> c64, int dissipation,
-                                                       int* __restrict__ status, double* __restrict__ prod) {
+                                                       Phys<float> c, int dissipation, int* __restrict__ status,
+                                                       double* __restrict__ prod) {
   constexpr int NC = D + 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double hw = 0.0;
@@ -279,7 +253,7 @@ __global__ void __launch_bounds__(128) face_f32_kernel(float* __restrict__ satf,
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       const double a = __ldg(&u[((size_t)k * NC + q) * NP + m]);
-      ukf[q] = f32_trunc(a);
+      ukf[q] = f32_round(a);
       du[q] = f32_diff(__ldg(&u[((size_t)v * NC + q) * NP + n]), a);
     }
     Ref32<D> rk;
@@ -289,7 +263,7 @@ __global__ void __launch_bounds__(128) face_f32_kernel(float* __restrict__ satf,
     if (!(rk.rho > 0.0f && rk.p > 0.0f && dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1))) atomicOr(status, 1);
     float nuv[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) nuv[i] = f32_trunc(__ldg(&nu[((size_t)k * NS + s) * D + i]));
+    for (int i = 0; i < D; ++i) nuv[i] = f32_round(__ldg(&nu[((size_t)k * NS + s) * D + i]));
     float G[NC], df[NC], Dw[NC];
     PairAvg<float, D> a;
     sy_flux_dev32<D>(rk, dv, c, nuv, G, a);
@@ -300,7 +274,7 @@ __global__ void __launch_bounds__(128) face_f32_kernel(float* __restrict__ satf,
       float mdw[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) mdw[q] = -dv.dW[q];  // w_k - w_v
-      diss32<D>(a, c, c64, nuv, mdw, Dw);
+      diss32<D>(a, c, nuv, mdw, Dw);
     }
     const float ihk = __ldg(&ihf[(size_t)k * NP + m]);
     const float ihv = __ldg(&ihf[(size_t)v * NP + n]);
@@ -331,8 +305,8 @@ __global__ void __launch_bounds__(128) face_bc_f32_kernel(float* __restrict__ sa
                                                           const double* __restrict__ bstate, int n_b,
                                                           const double* __restrict__ nu,
                                                           const float* __restrict__ ihf, Phys<float> c,
-                                                          Phys<double> c64, int dissipation,
-                                                          int* __restrict__ status, double* __restrict__ prod) {
+                                                          int dissipation, int* __restrict__ status,
+                                                          double* __restrict__ prod) {
   constexpr int NC = D + 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double hw = 0.0;
@@ -345,7 +319,7 @@ __global__ void __launch_bounds__(128) face_bc_f32_kernel(float* __restrict__ sa
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       const double x = __ldg(&u[((size_t)k * NC + q) * NP + m]);
-      ukf[q] = f32_trunc(x);
+      ukf[q] = f32_round(x);
       du[q] = f32_diff(__ldg(&bstate[(size_t)t * NC + q]), x);
     }
     Ref32<D> rk;
@@ -355,7 +329,7 @@ __global__ void __launch_bounds__(128) face_bc_f32_kernel(float* __restrict__ sa
     if (!(rk.rho > 0.0f && rk.p > 0.0f && dv.rho1 > 0.0f && dv.p1 > 0.0f && isfinite(dv.e1))) atomicOr(status, 1);
     float nuv[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) nuv[i] = f32_trunc(__ldg(&nu[((size_t)k * NS + s) * D + i]));
+    for (int i = 0; i < D; ++i) nuv[i] = f32_round(__ldg(&nu[((size_t)k * NS + s) * D + i]));
     float G[NC], Dw[NC];
     PairAvg<float, D> av;
     sy_flux_dev32<D>(rk, dv, c, nuv, G, av);
@@ -365,7 +339,7 @@ __global__ void __launch_bounds__(128) face_bc_f32_kernel(float* __restrict__ sa
       float mdw[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) mdw[q] = -dv.dW[q];
-      diss32<D>(av, c, c64, nuv, mdw, Dw);
+      diss32<D>(av, c, nuv, mdw, Dw);
     }
     const float ihk = __ldg(&ihf[(size_t)k * NP + m]);
     float hwf = 0.0f;
@@ -388,13 +362,12 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
                         float* satf) {
   constexpr int EB = (256 / NP) > 0 ? (256 / NP) : 1;
   const Phys<float> ph = make_phys<float>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
-  const Phys<double> ph64 = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
   int np_used = 0;
   {
     // facet terms first, into the float32 facet scratch the volume kernel adds
     const int bs = 128, nb = (c->n_pairs + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
-    face_f32_kernel<D><<<nb, bs, 0, s>>>(satf, u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihf, ph, ph64,
+    face_f32_kernel<D><<<nb, bs, 0, s>>>(satf, u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihf, ph,
                                          c->prm.dissipation, c->b.status, prod);
     c->launches++;
     if (prod) np_used += nb;
@@ -403,15 +376,14 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
     const int bs = 128, nb = (c->n_bslot + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
     face_bc_f32_kernel<D><<<nb, bs, 0, s>>>(satf, u, c->b.bslot, c->b.bstate, c->n_bslot, c->b.nu, c->b.ihf, ph,
-                                            ph64, c->prm.dissipation, c->b.status,
-                                            prod ? prod + np_used : nullptr);
+                                            c->prm.dissipation, c->b.status, prod ? prod + np_used : nullptr);
     c->launches++;
     if (prod) np_used += nb;
   }
   {
     const int nb = (c->n_e + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
-    constexpr bool STAGE = D <= 2;
+    constexpr bool STAGE = true;
     const size_t dyn = STAGE ? (size_t)EB * c->opsD_stride * sizeof(float) : 0;
     if (STAGE) {
       // static + dynamic shared memory above 48 KB needs the opt-in
@@ -452,15 +424,8 @@ int launch_split_f32(esplit_ctx* c, const double* u, double* r, cudaStream_t s, 
       case 18: return split_f32_np<2, 18>(c, u, r, s, prod, n_partial, satf);
       case 27: return split_f32_np<2, 27>(c, u, r, s, prod, n_partial, satf);
     }
-  } else if (c->dim == 3) {
-    switch (c->n_p) {
-      case 12: return split_f32_np<3, 12>(c, u, r, s, prod, n_partial, satf);
-      case 25: return split_f32_np<3, 25>(c, u, r, s, prod, n_partial, satf);
-      case 58: return split_f32_np<3, 58>(c, u, r, s, prod, n_partial, satf);
-      case 78: return split_f32_np<3, 78>(c, u, r, s, prod, n_partial, satf);
-    }
   }
-  return -2;
+  return -2;  // tetrahedra take the FP32-bulk kernels
 }
 
 }  // namespace esplit
