@@ -109,14 +109,18 @@ int esplit_version(void);
  * Asynchronous on `stream`; ESPLIT_ERR_ARG for fn outside 0..7. */
 int esplit_math_eval(int fn, const double* x_dev, double* y_dev, size_t n, void* stream);
 
-/* Measurement aid (no counterpart in the paper): the float64 FMA throughput
- * of CUDA device `device`, the peak that the float64 kernels' roofline
- * fractions are taken against (those kernels are bound by the float64 pipe).
- * Independent FMA chains, 8 per thread, 2048 threads per SM; the best of five
- * timed launches after one warm-up, on the legacy default stream.
- * *flops_per_s receives 2 x FMAs / second, *ms (may be NULL) the launch time.
- * Synchronises the device's default stream. */
-int esplit_measure_fp64_fma(int device, double* flops_per_s, double* ms);
+/* Measurement aid (no counterpart in the paper): float64 throughput of CUDA
+ * device `device`, the peak that the float64 kernels' roofline fractions are
+ * taken against (those kernels are bound by the float64 pipe).
+ *   mode 0: independent FMA chains, 8 per thread, 2048 threads per SM;
+ *   mode 1: independent chains of the float64 tensor-core MMA (mma.sync
+ *           m8n8k4, 256 FMAs per warp instruction), 8 per warp;
+ *   mode 2: both interleaved in every warp (4 MMA and 8 FMA chains).
+ * The best of five timed launches after one warm-up, on the legacy default
+ * stream.  *flops_per_s receives 2 x FMAs / second, *ms (may be NULL) the
+ * launch time.  ESPLIT_ERR_ARG for another mode.  Synchronises the device's
+ * default stream. */
+int esplit_measure_fp64(int device, int mode, double* flops_per_s, double* ms);
 
 /* Create a context on CUDA device `device` for dimension `dim` (1, 2 or 3;
  * 1: the inviscid problems of Secs. 7.1-7.2, no VJP).

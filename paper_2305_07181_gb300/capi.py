@@ -53,7 +53,7 @@ _I = ctypes.c_int
 _SIGNATURES = {
     "esplit_version": (_I, []),
     "esplit_math_eval": (_I, [_I, _P, _P, ctypes.c_size_t, _P]),
-    "esplit_measure_fp64_fma": (_I, [_I, _D, _D]),
+    "esplit_measure_fp64": (_I, [_I, _I, _D, _D]),
     "esplit_create": (_I, [ctypes.POINTER(_P), _I, _I]),
     "esplit_destroy": (None, [_P]),
     "esplit_upload_operator": (_I, [_P, _I, _I, _I, _P, _P, _P, _P, _P]),
@@ -247,10 +247,11 @@ def esplit_launch_count(ctx) -> int:
     return lib.esplit_launch_count(ctx)
 
 
-def esplit_measure_fp64_fma(device: int = 0):
-    """(rc, float64 FLOP/s, ms per timed launch)."""
+def esplit_measure_fp64(device: int = 0, mode: int = 0):
+    """(rc, float64 FLOP/s, ms per timed launch); mode 0 FMA chains, 1 float64
+    tensor-core MMA chains, 2 both interleaved."""
     f, ms = ctypes.c_double(), ctypes.c_double()
-    rc = lib.esplit_measure_fp64_fma(device, ctypes.byref(f), ctypes.byref(ms))
+    rc = lib.esplit_measure_fp64(device, mode, ctypes.byref(f), ctypes.byref(ms))
     return rc, f.value, ms.value
 
 

@@ -1,10 +1,15 @@
-// Measurement aid: the float64 FMA throughput of the current device, the
-// denominator of the roofline fraction the benchmark reports for the float64
-// kernels (they are bound by the float64 pipe, not by HBM).
+// Measurement aid: float64 throughput of the current device, the denominator
+// of the roofline fraction the benchmark reports for the float64 kernels (they
+// are bound by the float64 pipe, not by HBM), and the evidence for keeping the
+// float64 contractions off the tensor cores.
 //
-// Every thread runs CHAINS independent FMA chains (x <- x * a + b) for `iters`
-// steps; with 8 warps per SM scheduler and 8 chains a thread the pipe never
-// waits on a dependency.  Rate = 2 * threads * CHAINS * iters / time.
+// mode 0: every thread runs CHAINS independent FMA chains (x <- x * a + b);
+//         with 8 warps per SM scheduler and 8 chains a thread the pipe never
+//         waits on a dependency.  Rate = 2 * FMAs / time.
+// mode 1: every warp runs CHAINS independent chains of the float64 tensor-core
+//         MMA m8n8k4 (mma.sync, 256 FMAs per warp instruction).
+// mode 2: both at once in every warp: CHAINS/2 MMA chains and CHAINS FMA
+//         chains per thread, counted together.
 #include <cuda_runtime.h>
 
 #include "../../include/esplit.h"
@@ -16,41 +21,69 @@ constexpr int THREADS = 256;
 
 __device__ double g_calib_sink;
 
-__global__ void __launch_bounds__(THREADS) fma_chains_kernel(int iters, double a, double b) {
-  double x[CHAINS];
+__device__ __forceinline__ void dmma_step(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(THREADS) fp64_rate_kernel(int iters, double a, double b) {
+  double x[CHAINS], y0[CHAINS], y1[CHAINS];
 #pragma unroll
-  for (int j = 0; j < CHAINS; ++j) x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int j = 0; j < CHAINS; ++j) {
+    x[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+    y0[j] = 1e-3 * j;
+    y1[j] = 2e-3 * j;
+  }
   for (int it = 0; it < iters; ++it) {
+    if constexpr (MODE == 0 || MODE == 2) {
 #pragma unroll
-    for (int j = 0; j < CHAINS; ++j) x[j] = fma(x[j], a, b);
+      for (int j = 0; j < CHAINS; ++j) x[j] = fma(x[j], a, b);
+    }
+    if constexpr (MODE == 1) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) dmma_step(y0[j], y1[j], a * 1e-3, b);
+    }
+    if constexpr (MODE == 2) {
+#pragma unroll
+      for (int j = 0; j < CHAINS / 2; ++j) dmma_step(y0[j], y1[j], a * 1e-3, b);
+    }
   }
   double s = 0.0;
 #pragma unroll
-  for (int j = 0; j < CHAINS; ++j) s += x[j];
+  for (int j = 0; j < CHAINS; ++j) s += x[j] + y0[j] + y1[j];
   if (s == -1.0) g_calib_sink = s;  // keeps the chains live; never true for these inputs
 }
 
-}  // namespace
+template <int MODE>
+double fmas_per_launch(int blocks, int iters) {
+  const double threads = (double)blocks * THREADS;
+  const double warps = threads / 32.0;
+  double f = 0.0;
+  if (MODE == 0 || MODE == 2) f += threads * CHAINS * iters;
+  if (MODE == 1) f += warps * CHAINS * iters * 256.0;
+  if (MODE == 2) f += warps * (CHAINS / 2) * iters * 256.0;
+  return f;
+}
 
-extern "C" int esplit_measure_fp64_fma(int device, double* flops_per_s, double* ms_out) {
-  if (!flops_per_s) return ESPLIT_ERR_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return ESPLIT_ERR_CUDA;
-  int n_sm = 0;
-  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ESPLIT_ERR_CUDA;
+template <int MODE>
+int measure(int n_sm, double* flops_per_s, double* ms_out) {
   const int blocks = n_sm * 8;  // 2048 threads per SM
-  const int iters = 4096;
+  const int iters = MODE == 0 ? 4096 : 512;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return ESPLIT_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return ESPLIT_ERR_CUDA;
   }
-  // |a| < 1 keeps every chain bounded: x -> b / (1 - a)
+  // |a| < 1 keeps every FMA chain bounded (x -> b / (1 - a)); the MMA chains
+  // add 4 a b 1e-3 per step from small starting values
   const double a = 0.999999, b = 1e-7;
   float best = 1e30f;
   for (int rep = 0; rep < 6; ++rep) {
     cudaEventRecord(e0, 0);
-    fma_chains_kernel<<<blocks, THREADS>>>(iters, a, b);
+    fp64_rate_kernel<MODE><<<blocks, THREADS>>>(iters, a, b);
     cudaEventRecord(e1, 0);
     if (cudaEventSynchronize(e1) != cudaSuccess) break;
     float ms = 0.f;
@@ -60,8 +93,19 @@ extern "C" int esplit_measure_fp64_fma(int device, double* flops_per_s, double* 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess || best >= 1e30f) return ESPLIT_ERR_CUDA;
-  const double fmas = (double)blocks * THREADS * CHAINS * iters;
-  *flops_per_s = 2.0 * fmas / (best * 1e-3);
+  *flops_per_s = 2.0 * fmas_per_launch<MODE>(blocks, iters) / (best * 1e-3);
   if (ms_out) *ms_out = best;
   return ESPLIT_OK;
+}
+
+}  // namespace
+
+extern "C" int esplit_measure_fp64(int device, int mode, double* flops_per_s, double* ms_out) {
+  if (!flops_per_s || mode < 0 || mode > 2) return ESPLIT_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return ESPLIT_ERR_CUDA;
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ESPLIT_ERR_CUDA;
+  if (mode == 0) return measure<0>(n_sm, flops_per_s, ms_out);
+  if (mode == 1) return measure<1>(n_sm, flops_per_s, ms_out);
+  return measure<2>(n_sm, flops_per_s, ms_out);
 }
