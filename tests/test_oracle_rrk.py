@@ -86,3 +86,42 @@ def test_rk4_order():
     e1 = float((run(1) - ref).abs().max())
     e2 = float((run(2) - ref).abs().max())
     assert np.log2(e1 / e2) > 3.5
+
+
+def test_step_vjp_closed_form_for_ec():
+    """EC scheme: the relaxation step conserves the total entropy for every
+    u_n, so the gradient of S(u_{n+1}) with respect to u_n is H w(u_n); the
+    step reverse applied to H w(u_{n+1}) must give it (the implicit-function
+    term for g is needed: without it this fails)."""
+    from oracle.physics import entropy_variables
+    op, m, u = _vortex(p=2, N=3)
+    dt = states.cfl_timestep(m, u.numpy(), 0.1)
+    rhs = lambda x: R.residual(x, op, m, P)
+    u1, info = rrk.rrk4_step(u, dt, rhs, op, m, P)
+    Hn = rrk._H(op, m)
+    gS1 = Hn[:, None, :] * entropy_variables(u1.transpose(1, 2), P).transpose(1, 2)
+    gS0 = Hn[:, None, :] * entropy_variables(u.transpose(1, 2), P).transpose(1, 2)
+    ub0, g = rrk.rrk4_step_vjp(u, dt, rhs, gS1, op, m, P)
+    assert abs(g - info.g) == 0.0
+    err = float((ub0 - gS0).abs().max() / gS0.abs().max())
+    assert err <= 1e-11, err
+
+
+def test_step_vjp_central_differences():
+    """With dissipation: <ubar1, (step(u + h v) - step(u - h v)) / 2h> against
+    <ubar0, v> on random unit directions (h = 1e-6)."""
+    op, m, u = _vortex(p=2, N=3)
+    dt = states.cfl_timestep(m, u.numpy(), 0.1)
+    rhs = lambda x: R.residual(x, op, m, P, dissipation=True)
+    rng = np.random.default_rng(12)
+    ub1 = torch.as_tensor(rng.normal(size=tuple(u.shape)))
+    ub0, g = rrk.rrk4_step_vjp(u, dt, rhs, ub1, op, m, P)
+    h = 1e-6
+    for _ in range(4):
+        v = torch.as_tensor(rng.normal(size=tuple(u.shape)))
+        v /= v.norm()
+        up, _ = rrk.rrk4_step(u + h * v, dt, rhs, op, m, P)
+        um, _ = rrk.rrk4_step(u - h * v, dt, rhs, op, m, P)
+        fd = float(((up - um) / (2 * h) * ub1).sum())
+        ad = float((ub0 * v).sum())
+        assert abs(fd - ad) <= 1e-6 * max(1.0, abs(ad)), (fd, ad)
