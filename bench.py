@@ -174,6 +174,37 @@ def algorithmic_bytes(group, n_e, n_p, d, n_pairs):
     return None
 
 
+def algorithmic_bytes_f32_volume(n_e, n_p, d, n_pairs):
+    """Bytes the float32-path volume kernel must move per launch: the float32
+    D_i (unpadded), u in and r out (float64), the float32 1/(H J) and the
+    float32 facet contributions at the element's facet slots."""
+    nc = d + 2
+    n_slot = 2 * n_pairs // n_e
+    return n_e * (4 * d * n_p * n_p + 2 * 8 * n_p * nc + 4 * n_p + 4 * n_slot * nc)
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def f32_volume_roofline(prof, n_e, n_p, d, n_pairs):
+    """HBM roofline of the float32-path volume kernel from the profiled groups
+    of a timed region (the float32 path's volume launches are the split group)."""
+    if prof.get("split_volume", (0, 0))[1] == 0:
+        return None
+    ms = prof["split_volume"][0] / prof["split_volume"][1]
+    by = algorithmic_bytes_f32_volume(n_e, n_p, d, n_pairs)
+    peak, src = hbm_peak_gbs()
+    ach = by / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": None, "kernel": "split_volume_f32", "avg_launch_ms": ms,
+            "launches": prof["split_volume"][1], "algorithmic_bytes": by, "peak_source": src}
+
+
 # ---------------------------------------------------------------------------------------------
 def dist_setup(gpus, backend):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -201,12 +232,16 @@ def max_over_ranks(x, ws, device):
 
 
 def measure_fp64_peak(es, device):
-    """float64 throughput of this GPU (the library's calibration kernels), with
-    the SM clock sampled while they run: FMA chains (the roofline peak), the
-    float64 tensor-core MMA, and both interleaved."""
+    """Arithmetic throughput of this GPU (the library's calibration kernels),
+    with the SM clock sampled while they run: float64 FMA chains (the roofline
+    peak), the float64 tensor-core MMA, both interleaved, float32 FMA chains,
+    and the float64 divide and the library's log and exp, each as a cost in
+    float64 FMAs."""
+    names = ((0, "dfma"), (1, "dmma"), (2, "dfma_and_dmma"), (3, "ffma"), (4, "ddiv"), (5, "dlog"), (6, "dexp"),
+             (7, "dlog_cuda"), (8, "dexp_cuda"), (9, "cvt_round_trip"))
     out = {}
     with ClockSampler(device) as clk:
-        for mode, name in ((0, "dfma"), (1, "dmma"), (2, "dfma_and_dmma")):
+        for mode, name in names:
             best = 0.0
             t_end = time.perf_counter() + (1.0 if mode == 0 else 0.3)   # so that the sampler sees them
             while time.perf_counter() < t_end:
@@ -217,11 +252,17 @@ def measure_fp64_peak(es, device):
             out[name] = best
     c = clk.summary()
     mhz = c["sm_mhz"]
-    per_clk = {k: (v / 2.0 / (SM_COUNT * mhz * 1e6) if mhz else None) for k, v in out.items()}
+    dfma_per_s = out["dfma"] / 2.0
+    per_clk = {k: (v / 2.0 / (SM_COUNT * mhz * 1e6) if mhz else None) for k, v in out.items() if k in
+               ("dfma", "dmma", "dfma_and_dmma", "ffma")}
+    cost = {k: dfma_per_s / out[k] for k in ("ddiv", "dlog", "dexp", "dlog_cuda", "dexp_cuda", "cvt_round_trip")}
+    cost["ffma"] = dfma_per_s / (out["ffma"] / 2.0)
     return {"tflops": out["dfma"] / 1e12, "sm_mhz": mhz, "dfma_per_clk_per_sm": per_clk["dfma"],
-            "fma_per_clk_per_sm": per_clk, "reasons": c["reasons"],
-            "how": "esplit_measure_fp64: independent float64 FMA chains (8 per thread, 2048 threads per SM), "
-                   "float64 MMA m8n8k4 chains, and both interleaved; best launch each, SM clock sampled meanwhile"}
+            "fma_per_clk_per_sm": per_clk, "cost_in_dfma": cost, "rates": out, "reasons": c["reasons"],
+            "how": "esplit_measure_fp64: independent chains (8 per thread, 2048 threads per SM) of float64 FMA, "
+                   "float64 MMA m8n8k4, both interleaved, float32 FMA, float64 divide, the library's and CUDA's "
+                   "log and exp, a float64-float32-float64 round trip; best launch each, SM clock sampled "
+                   "meanwhile"}
 
 
 def vs_hadamard(es, device, flush, p, N):
@@ -267,10 +308,18 @@ def fp32_step_run(es, device, flush, p, N, steps=10):
         s.rrk_step(u, dt)
     stream = torch.cuda.current_stream(device)
     ts = _timed(lambda: s.rrk_step(u, dt), stream, flush, steps)
+    # kernel groups of as many steps again, with the library's per-group events
+    s.profile(True)
+    s.profile_read()
+    _timed(lambda: s.rrk_step(u, dt), stream, flush, steps)
+    prof = {g: v for g, v in s.profile_read().items() if v[1] > 0}
+    s.profile(False)
     s.close()
     ms = sum(ts) / len(ts)
     return {"value": 4 * mesh.n_e * op.n_p / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "residual_error_bound": 1e-5,
+            "volume_roofline": f32_volume_roofline(prof, mesh.n_e, op.n_p, op.d, solver_pairs(mesh, op)),
+            "kernel_ms_per_step": {g: v[0] / steps for g, v in prof.items()},
             "note": "precision fp32 on the headline workload; L2 flushed between steps"}
 
 
@@ -631,7 +680,9 @@ def main():
     fp64_peak = measure_fp64_peak(es, device)
     peak_tf = fp64_peak["tflops"] if fp64_peak else FP64_PEAK_NOMINAL / 1e12
     roofline = None
-    if fl is not None:
+    if args.precision == "fp32" and d <= 2:
+        roofline = f32_volume_roofline(groups, n_e, n_p, d, solver_pairs(mesh, op))
+    elif fl is not None:
         achieved = fl / (dom_ms * 1e-3) / 1e12
         peak = peak_tf if args.precision == "fp64" else None
         src = (f"measured: float64 FMA chains {fp64_peak['tflops']:.3f} TFLOP/s = "

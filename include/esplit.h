@@ -109,18 +109,26 @@ int esplit_version(void);
  * Asynchronous on `stream`; ESPLIT_ERR_ARG for fn outside 0..7. */
 int esplit_math_eval(int fn, const double* x_dev, double* y_dev, size_t n, void* stream);
 
-/* Measurement aid (no counterpart in the paper): float64 throughput of CUDA
- * device `device`, the peak that the float64 kernels' roofline fractions are
- * taken against (those kernels are bound by the float64 pipe).
- *   mode 0: independent FMA chains, 8 per thread, 2048 threads per SM;
+/* Measurement aid (no counterpart in the paper): arithmetic throughput of
+ * CUDA device `device`; mode 0 is the peak that the float64 kernels'
+ * roofline fractions are taken against (those kernels are bound by the
+ * float64 pipe), modes 1-6 the evidence for how they spend it.
+ *   mode 0: independent float64 FMA chains, 8 per thread, 2048 threads per SM;
  *   mode 1: independent chains of the float64 tensor-core MMA (mma.sync
  *           m8n8k4, 256 FMAs per warp instruction), 8 per warp;
- *   mode 2: both interleaved in every warp (4 MMA and 8 FMA chains).
+ *   mode 2: both interleaved in every warp (4 MMA and 8 FMA chains);
+ *   mode 3: float32 FMA chains (as mode 0);
+ *   mode 4: float64 divide chains x <- a / (x + 1);
+ *   mode 5: chains of the library's float64 log (x <- log x + 2.5);
+ *   mode 6: chains of the library's float64 exp (x <- exp(-x));
+ *   modes 7, 8: the same chains with the CUDA math library's log and exp;
+ *   mode 9: chains of a float64 -> float32 -> float64 round trip and an FMA.
  * The best of five timed launches after one warm-up, on the legacy default
- * stream.  *flops_per_s receives 2 x FMAs / second, *ms (may be NULL) the
- * launch time.  ESPLIT_ERR_ARG for another mode.  Synchronises the device's
- * default stream. */
-int esplit_measure_fp64(int device, int mode, double* flops_per_s, double* ms);
+ * stream.  *rate receives FLOP/s (2 per FMA) for modes 0-3 and operations
+ * per second for modes 4-9, *ms (may be NULL) the launch time.
+ * ESPLIT_ERR_ARG for another mode.  Synchronises the device's default
+ * stream. */
+int esplit_measure_fp64(int device, int mode, double* rate, double* ms);
 
 /* Create a context on CUDA device `device` for dimension `dim` (1, 2 or 3;
  * 1: the inviscid problems of Secs. 7.1-7.2, no VJP).

@@ -10,9 +10,21 @@
 //         MMA m8n8k4 (mma.sync, 256 FMAs per warp instruction).
 // mode 2: both at once in every warp: CHAINS/2 MMA chains and CHAINS FMA
 //         chains per thread, counted together.
+// modes 3-6: the costs the kernels' design weighs against a float64 FMA, as
+//         operations per second of CHAINS independent chains a thread:
+//         3 float32 FMA (x <- x * a + b); 4 float64 divide (x <- a / (x + 1));
+//         5 the library's float64 log (x <- log x + 2.5); 6 its float64 exp
+//         (x <- exp(-x)); 7 and 8 the CUDA library's float64 log and exp in
+//         the same chains; 9 a float64 -> float32 -> float64 round trip and an
+//         FMA (x <- (double)(float)(x * a) + b).  Every chain has a stable
+//         fixed point (0.62, 3.85, 0.57, 0.1) that its start values lead to,
+//         so no value leaves the range the functions are timed on.  The add
+//         of modes 4, 5, 7 and the FMA of mode 9 count as part of the
+//         operation.
 #include <cuda_runtime.h>
 
 #include "../../include/esplit.h"
+#include "fmath.cuh"
 
 namespace {
 
@@ -25,6 +37,22 @@ __device__ __forceinline__ void dmma_step(double& d0, double& d1, double a, doub
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
                : "+d"(d0), "+d"(d1)
                : "d"(a), "d"(b));
+}
+
+__device__ float g_calib_sink32;
+
+__global__ void __launch_bounds__(THREADS) fp32_rate_kernel(int iters, float a, float b) {
+  float x[CHAINS];
+#pragma unroll
+  for (int j = 0; j < CHAINS; ++j) x[j] = 1.0f + 1e-3f * (threadIdx.x + j);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < CHAINS; ++j) x[j] = fmaf(x[j], a, b);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < CHAINS; ++j) s += x[j];
+  if (s == -1.0f) g_calib_sink32 = s;
 }
 
 template <int MODE>
@@ -49,6 +77,30 @@ __global__ void __launch_bounds__(THREADS) fp64_rate_kernel(int iters, double a,
 #pragma unroll
       for (int j = 0; j < CHAINS / 2; ++j) dmma_step(y0[j], y1[j], a * 1e-3, b);
     }
+    if constexpr (MODE == 4) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) x[j] = a / (x[j] + 1.0);
+    }
+    if constexpr (MODE == 5) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) x[j] = esplit::fm::log(x[j]) + 2.5;
+    }
+    if constexpr (MODE == 6) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) x[j] = esplit::fm::exp(-x[j]);
+    }
+    if constexpr (MODE == 7) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) x[j] = ::log(x[j]) + 2.5;
+    }
+    if constexpr (MODE == 8) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) x[j] = ::exp(-x[j]);
+    }
+    if constexpr (MODE == 9) {
+#pragma unroll
+      for (int j = 0; j < CHAINS; ++j) x[j] = (double)__double2float_rn(x[j] * a) + b;
+    }
   }
   double s = 0.0;
 #pragma unroll
@@ -56,21 +108,30 @@ __global__ void __launch_bounds__(THREADS) fp64_rate_kernel(int iters, double a,
   if (s == -1.0) g_calib_sink = s;  // keeps the chains live; never true for these inputs
 }
 
+// FLOPs (modes 0-3: 2 per FMA) or operations (modes 4-6) per launch
 template <int MODE>
-double fmas_per_launch(int blocks, int iters) {
+double ops_per_launch(int blocks, int iters) {
   const double threads = (double)blocks * THREADS;
   const double warps = threads / 32.0;
   double f = 0.0;
-  if (MODE == 0 || MODE == 2) f += threads * CHAINS * iters;
-  if (MODE == 1) f += warps * CHAINS * iters * 256.0;
-  if (MODE == 2) f += warps * (CHAINS / 2) * iters * 256.0;
+  if (MODE == 0 || MODE == 2 || MODE == 3) f += 2.0 * threads * CHAINS * iters;
+  if (MODE == 1) f += 2.0 * warps * CHAINS * iters * 256.0;
+  if (MODE == 2) f += 2.0 * warps * (CHAINS / 2) * iters * 256.0;
+  if (MODE >= 4) f += threads * CHAINS * iters;
   return f;
 }
 
+// iterations a launch, for ~20 ms at the rates measured on GB300
 template <int MODE>
-int measure(int n_sm, double* flops_per_s, double* ms_out) {
+constexpr int iters_for() {
+  return MODE == 0 ? 4096 : MODE == 3 ? 65536 : MODE == 4 ? 512 : MODE == 5 ? 128 : MODE == 6 ? 256
+       : MODE == 7 ? 128 : MODE == 8 ? 256 : MODE == 9 ? 1024 : 512;
+}
+
+template <int MODE>
+int measure(int n_sm, double* rate, double* ms_out) {
   const int blocks = n_sm * 8;  // 2048 threads per SM
-  const int iters = MODE == 0 ? 4096 : 512;
+  const int iters = iters_for<MODE>();
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return ESPLIT_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -83,7 +144,10 @@ int measure(int n_sm, double* flops_per_s, double* ms_out) {
   float best = 1e30f;
   for (int rep = 0; rep < 6; ++rep) {
     cudaEventRecord(e0, 0);
-    fp64_rate_kernel<MODE><<<blocks, THREADS>>>(iters, a, b);
+    if constexpr (MODE == 3)
+      fp32_rate_kernel<<<blocks, THREADS>>>(iters, (float)a, (float)b);
+    else
+      fp64_rate_kernel<MODE><<<blocks, THREADS>>>(iters, a, b);
     cudaEventRecord(e1, 0);
     if (cudaEventSynchronize(e1) != cudaSuccess) break;
     float ms = 0.f;
@@ -93,19 +157,28 @@ int measure(int n_sm, double* flops_per_s, double* ms_out) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (cudaGetLastError() != cudaSuccess || best >= 1e30f) return ESPLIT_ERR_CUDA;
-  *flops_per_s = 2.0 * fmas_per_launch<MODE>(blocks, iters) / (best * 1e-3);
+  *rate = ops_per_launch<MODE>(blocks, iters) / (best * 1e-3);
   if (ms_out) *ms_out = best;
   return ESPLIT_OK;
 }
 
 }  // namespace
 
-extern "C" int esplit_measure_fp64(int device, int mode, double* flops_per_s, double* ms_out) {
-  if (!flops_per_s || mode < 0 || mode > 2) return ESPLIT_ERR_ARG;
+extern "C" int esplit_measure_fp64(int device, int mode, double* rate, double* ms_out) {
+  if (!rate || mode < 0 || mode > 9) return ESPLIT_ERR_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return ESPLIT_ERR_CUDA;
   int n_sm = 0;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ESPLIT_ERR_CUDA;
-  if (mode == 0) return measure<0>(n_sm, flops_per_s, ms_out);
-  if (mode == 1) return measure<1>(n_sm, flops_per_s, ms_out);
-  return measure<2>(n_sm, flops_per_s, ms_out);
+  switch (mode) {
+    case 0: return measure<0>(n_sm, rate, ms_out);
+    case 1: return measure<1>(n_sm, rate, ms_out);
+    case 2: return measure<2>(n_sm, rate, ms_out);
+    case 3: return measure<3>(n_sm, rate, ms_out);
+    case 4: return measure<4>(n_sm, rate, ms_out);
+    case 5: return measure<5>(n_sm, rate, ms_out);
+    case 6: return measure<6>(n_sm, rate, ms_out);
+    case 7: return measure<7>(n_sm, rate, ms_out);
+    case 8: return measure<8>(n_sm, rate, ms_out);
+    default: return measure<9>(n_sm, rate, ms_out);
+  }
 }

@@ -59,20 +59,24 @@ int check_ready(esplit_ctx* c) {
   return ESPLIT_OK;
 }
 
-// floats per element of the padded D_i copy the float32 path stages in shared
-// memory: at least d n_p^2, a multiple of 4 (16 bytes, the bulk copy's unit),
-// and among those the one that spreads a warp's reads of one operator column
-// (lanes = consecutive nodes, in consecutive elements) over the most banks
+// floats per element of the D_i rows the float32 path stages in shared memory:
+// at least d n_p npp, a multiple of 4 (16 bytes, the bulk copy's unit), and
+// among those the one that spreads a warp's 16-byte row reads (lanes =
+// consecutive nodes, in consecutive elements; 8 lanes per shared-memory
+// phase) over the most bank groups
 int opsD_stride_for(int d, int np) {
-  const int base = (d * np * np + 3) / 4 * 4;
+  const int npp = esplit::npp_for(np);
+  const int base = d * np * npp;
   int best = base, best_worst = 1 << 30;
   for (int s = base; s < base + 32; s += 4) {
     int worst = 0;
     for (int w0 = 0; w0 < np; ++w0) {  // node of the warp's first lane
-      int cnt[32] = {0};
-      for (int l = 0; l < 32; ++l) {
-        const int e = (w0 + l) / np, m = (w0 + l) % np;
-        worst = std::max(worst, ++cnt[(e * s + m) % 32]);
+      for (int ph = 0; ph < 4; ++ph) {
+        int cnt[8] = {0};
+        for (int l = 8 * ph; l < 8 * ph + 8; ++l) {
+          const int e = (w0 + l) / np, m = (w0 + l) % np;
+          worst = std::max(worst, ++cnt[((e * s) / 4 + m * (npp / 4)) % 8]);
+        }
       }
     }
     if (worst < best_worst) {
@@ -622,7 +626,7 @@ static int rrk_prepare(esplit_ctx* c, const double* u, double dt) {
     if ((rc = dalloc(c, &c->b.stage_u, n))) return rc;
     if ((rc = dalloc(c, &c->b.stage_r, n))) return rc;
     if ((rc = dalloc(c, &c->b.dacc, n))) return rc;
-    if ((rc = dalloc(c, &c->b.node_cache, 4 * (size_t)c->n_e * c->n_p))) return rc;
+    if ((rc = dalloc(c, &c->b.node_cache, 3 * (size_t)c->n_e * c->n_p))) return rc;
   }
   return ESPLIT_OK;
 }
@@ -970,7 +974,7 @@ int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double*
     if ((rc = dalloc(c, &c->b.vjp_work, 12 * n))) return rc;
   }
   if (!c->b.node_cache) {
-    if ((rc = dalloc(c, &c->b.node_cache, 4 * (size_t)c->n_e * c->n_p))) return rc;
+    if ((rc = dalloc(c, &c->b.node_cache, 3 * (size_t)c->n_e * c->n_p))) return rc;
   }
   double* W = c->b.vjp_work;
   double* Us[3] = {W, W + n, W + 2 * n};                  // U_2, U_3, U_4

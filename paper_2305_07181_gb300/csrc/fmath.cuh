@@ -12,13 +12,16 @@
 //         exp(r) - 1 by its Taylor series through r^6 (truncation < 2^-58);
 //         2^(j/32) tabulated as a float64 pair.
 //   log1p(x) = log(u + c) with u = 1 + x rounded and c = x - (u - 1) the
-//   rounding error, carried into r; expm1 from the exp reduction as
+//   rounding error, carried into r; for |x| < 2^-5 directly by its Taylor
+//   series through x^12 (truncation < 2^-63 |x|); expm1 from the exp reduction as
 //   (2^k T_hi - 1) + 2^k (T_hi p + T_lo) (the first difference is exact where
 //   it cancels), and for |x| < 1/16 by its Taylor series through x^10.
 //   Tables: fmath_tables.h (gen_fmath_tables.py).
 // Domain: finite normal positive arguments for log (log1p: 1 + x normal
 // positive), |x| < 708 for exp/expm1; anything else goes to the CUDA library
-// function.  Error: a few ulp (tests/test_gpu_fmath.py compares against
+// function.  The range tests and the grid point c are formed from the bit
+// patterns by integer operations: on GB300 a float64 compare or an
+// integer-to-float64 conversion occupies the float64 pipe like an FMA.  Error: a few ulp (tests/test_gpu_fmath.py compares against
 // the host's correctly rounded-to-1-ulp libm over random arguments).
 #pragma once
 
@@ -51,7 +54,12 @@ __device__ __forceinline__ double log_core(double x, double corr) {
     j = 128 + (int)((f + (1LL << 44)) >> 45);
   }
   const int t = j - LOG_J0;
-  const double c = (double)j * 0.0078125;  // j/128, exact
+  // c = j/128 built from its bits: j in [91, 128] is (j - 64)/64 above 2^-1
+  // (j = 128 carries into the exponent: 1.0), j in [128, 181] is (j - 128)/128
+  // above 1
+  const long long cb = (f >= F_SQRT2) ? (1022LL << 52) + ((long long)(j - 64) << 46)
+                                      : (1023LL << 52) + ((long long)(j - 128) << 45);
+  const double c = __longlong_as_double(cb);
   const double inv = __ldg(&LOG_INV_C[t]);
   double r = (m - c) * inv;
   if (CORR) r = fma(corr * pow2i(-k), inv, r);
@@ -70,13 +78,37 @@ __device__ __forceinline__ double log_core(double x, double corr) {
   return hi + (lo + p);
 }
 
+// normal, positive, below 2^1022: sign 0 and biased exponent field 1..2044
 __device__ __forceinline__ bool log_domain(double x) {
-  return x >= 2.2250738585072014e-308 && x < 4.49423283715579e+307;  // normal, positive, below 2^1022
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return b - (1ULL << 52) < (2044ULL << 52);
 }
+
+// |x| < y for a positive finite y given by its bit pattern (the patterns of
+// non-negative floats order as the values; NaN: false)
+__device__ __forceinline__ bool abs_below(double x, unsigned long long y_bits) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL) < y_bits;
+}
+constexpr unsigned long long BITS_2M5 = 0x3FA0000000000000ULL;  // 2^-5
+constexpr unsigned long long BITS_2M4 = 0x3FB0000000000000ULL;  // 2^-4
+constexpr unsigned long long BITS_708 = 0x4086200000000000ULL;  // 708.0
 
 __device__ __forceinline__ double log(double x) { return log_domain(x) ? log_core<false>(x, 0.0) : ::log(x); }
 
 __device__ __forceinline__ double log1p(double x) {
+  if (abs_below(x, BITS_2M5)) {
+    double q = fma(x, LOG_C12, LOG_C11);
+    q = fma(x, q, LOG_C10);
+    q = fma(x, q, LOG_C9);
+    q = fma(x, q, LOG_C8);
+    q = fma(x, q, LOG_C7);
+    q = fma(x, q, LOG_C6);
+    q = fma(x, q, LOG_C5);
+    q = fma(x, q, LOG_C4);
+    q = fma(x, q, LOG_C3);
+    q = fma(x, q, LOG_C2);
+    return fma(x * x, q, x);
+  }
   const double u = 1.0 + x;
   if (!log_domain(u)) return ::log1p(x);
   const double corr = x - (u - 1.0);
@@ -101,7 +133,7 @@ __device__ __forceinline__ double exp_reduce(double x, int& j, int& k) {
 }
 
 __device__ __forceinline__ double exp(double x) {
-  if (!(fabs(x) < 708.0)) return ::exp(x);
+  if (!abs_below(x, BITS_708)) return ::exp(x);
   int j, k;
   const double p = exp_reduce(x, j, k);
   const double th = __ldg(&EXP_T_HI[j]);
@@ -110,7 +142,7 @@ __device__ __forceinline__ double exp(double x) {
 }
 
 __device__ __forceinline__ double expm1(double x) {
-  if (fabs(x) < 0.0625) {  // Taylor series through x^10 (truncation < 2^-64 |x|)
+  if (abs_below(x, BITS_2M4)) {  // Taylor series through x^10 (truncation < 2^-64 |x|)
     double q = fma(x, EXP_E10, EXP_E9);
     q = fma(x, q, EXP_E8);
     q = fma(x, q, EXP_E7);
@@ -121,7 +153,7 @@ __device__ __forceinline__ double expm1(double x) {
     q = fma(x, q, EXP_E2);
     return fma(x * x, q, x);
   }
-  if (!(fabs(x) < 708.0)) return ::expm1(x);
+  if (!abs_below(x, BITS_708)) return ::expm1(x);
   int j, k;
   const double p = exp_reduce(x, j, k);
   const double th = __ldg(&EXP_T_HI[j]);

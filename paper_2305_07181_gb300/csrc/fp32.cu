@@ -71,52 +71,81 @@ __device__ __forceinline__ void diss32(const PairAvg<float, D>& a, const Phys<fl
   for (int q = 0; q < D + 2; ++q) Dw[q] = 0.5f * b * o[q];
 }
 
+// Variations of the element's nodes, one float4 per node and direction (the
+// n_c <= 4 components of lines and triangles; unused lanes zero), rows padded
+// to NPP with zeros and each element by one float4, so that the lanes of two
+// elements in a warp read different bank groups.
 template <int D, int NP, int EB>
 struct SplitSmem32 {
-  float df[EB][D][D + 2][NP];  // flux variations
-  float dw[EB][D + 2][NP];     // entropy-variable variations
+  static constexpr int NPP = npp_for(NP);
+  float4 df[EB][D * NPP + 1];  // flux variations: df[el][i * NPP + n]
+  float4 dw[EB][NPP + 1];      // entropy-variable variations
   double u0[EB][D + 2];        // node-0 states
   uint64_t bar;                // completion barrier of the operators' bulk copy
 };
 
-// acc = sum_i D_i df_i, g_i = D_i dw at node m of element el, with the
-// element's D_i (layout [i][n][m]) at opb: in shared memory (SMEM) or global.
-// For operators above 20 nodes the sums are Kahan-compensated: the rounding
-// of partial sums much larger than the final, cancelling, result dominated
-// the error there.
+__device__ __forceinline__ float4 f4(const float* v, int nc) {
+  return make_float4(v[0], v[1], v[2], nc > 3 ? v[3] : 0.0f);
+}
+
+// acc += a f (four components), plain or Kahan-compensated
+template <bool COMP>
+__device__ __forceinline__ void fma4(float a, const float4& f, float4& acc, float4& cmp) {
+  if constexpr (COMP) {
+    kahan_fma(a, f.x, acc.x, cmp.x);
+    kahan_fma(a, f.y, acc.y, cmp.y);
+    kahan_fma(a, f.z, acc.z, cmp.z);
+    kahan_fma(a, f.w, acc.w, cmp.w);
+  } else {
+    acc.x = fmaf(a, f.x, acc.x);
+    acc.y = fmaf(a, f.y, acc.y);
+    acc.z = fmaf(a, f.z, acc.z);
+    acc.w = fmaf(a, f.w, acc.w);
+  }
+}
+
+// acc = sum_i D_i df_i, g_i = D_i dw at node m of element el, from the
+// element's D_i rows opr[(i NP + m) NPP + n] (shared memory, or global memory
+// when SMEM is false): per 16-byte load of four row entries, eight 16-byte
+// broadcast loads of the variations and 32 FMAs.  For operators above 20
+// nodes the sums are Kahan-compensated: the rounding of partial sums much
+// larger than the final, cancelling, result dominated the error there.
 template <bool SMEM, int D, int NP, int EB>
-__device__ __forceinline__ void contract32(const float* __restrict__ opb, const SplitSmem32<D, NP, EB>& sm, int el,
-                                           int m, float (&acc)[D + 2], float (&g)[D][D + 2]) {
-  constexpr int NC = D + 2;
+__device__ __forceinline__ void contract32(const float* __restrict__ opr, const SplitSmem32<D, NP, EB>& sm, int el,
+                                           int m, float4& acc, float4 (&g)[D]) {
+  constexpr int NPP = SplitSmem32<D, NP, EB>::NPP;
   constexpr bool COMP = NP > 20;
-  float cacc[NC], cg[D][NC];
-#pragma unroll
-  for (int q = 0; q < NC; ++q) acc[q] = cacc[q] = 0.0f;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 cacc = z, cg[D];
+  acc = z;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
+    g[i] = z;
+    cg[i] = z;
+    const float4* row = reinterpret_cast<const float4*>(opr + (i * NP + m) * NPP);
+#pragma unroll 1
+    for (int nb = 0; nb < NPP / 4; ++nb) {
+      const float4 a = SMEM ? row[nb] : __ldg(&row[nb]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-    for (int q = 0; q < NC; ++q) g[i][q] = cg[i][q] = 0.0f;
-#pragma unroll 6
-    for (int n = 0; n < NP; ++n) {
-      const float dt = SMEM ? opb[(i * NP + n) * NP + m] : __ldg(&opb[(i * NP + n) * NP + m]);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        if constexpr (COMP) {
-          kahan_fma(dt, sm.df[el][i][q][n], acc[q], cacc[q]);
-          kahan_fma(dt, sm.dw[el][q][n], g[i][q], cg[i][q]);
-        } else {
-          acc[q] = fmaf(dt, sm.df[el][i][q][n], acc[q]);
-          g[i][q] = fmaf(dt, sm.dw[el][q][n], g[i][q]);
-        }
+      for (int t = 0; t < 4; ++t) {
+        const int n = 4 * nb + t;
+        fma4<COMP>(av[t], sm.df[el][i * NPP + n], acc, cacc);
+        fma4<COMP>(av[t], sm.dw[el][n], g[i], cg[i]);
       }
     }
   }
   if constexpr (COMP) {
+    acc.x = __fsub_rn(acc.x, cacc.x);
+    acc.y = __fsub_rn(acc.y, cacc.y);
+    acc.z = __fsub_rn(acc.z, cacc.z);
+    acc.w = __fsub_rn(acc.w, cacc.w);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      acc[q] = __fsub_rn(acc[q], cacc[q]);
-#pragma unroll
-      for (int i = 0; i < D; ++i) g[i][q] = __fsub_rn(g[i][q], cg[i][q]);
+    for (int i = 0; i < D; ++i) {
+      g[i].x = __fsub_rn(g[i].x, cg[i].x);
+      g[i].y = __fsub_rn(g[i].y, cg[i].y);
+      g[i].z = __fsub_rn(g[i].z, cg[i].z);
+      g[i].w = __fsub_rn(g[i].w, cg[i].w);
     }
   }
 }
@@ -126,10 +155,11 @@ __device__ __forceinline__ void contract32(const float* __restrict__ opb, const 
 // phase; the contraction then reads them there.
 template <int D, int NP, int EB, bool STAGE>
 __global__ void __launch_bounds__(EB * NP, 4) split_volume_f32_kernel(
-    const double* __restrict__ u, double* __restrict__ r, const float* __restrict__ ops,
-    const float* __restrict__ opsD, int opsD_stride, const float* __restrict__ ihf, const float* __restrict__ satf,
+    const double* __restrict__ u, double* __restrict__ r, const float* __restrict__ opsD, int opsD_stride, const float* __restrict__ ihf, const float* __restrict__ satf,
     int n_e, Phys<float> c, int* __restrict__ status, double* __restrict__ prod) {
   constexpr int NC = D + 2;
+  constexpr int NPP = SplitSmem32<D, NP, EB>::NPP;
+  static_assert(NC <= 4, "one float4 per node and direction");
   __shared__ SplitSmem32<D, NP, EB> sm;
   extern __shared__ __align__(128) unsigned char dyn_smem[];
   const int NS = c_ref32.n_slot;
@@ -176,11 +206,16 @@ __global__ void __launch_bounds__(EB * NP, 4) split_volume_f32_kernel(
     for (int i = 0; i < D; ++i) {
       float F[NC];
       dflux32<D>(rf, du, dv, i, F);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) sm.df[el][i][q][m] = F[q];
+      sm.df[el][i * NPP + m] = f4(F, NC);
     }
+    sm.dw[el][m] = f4(dv.dW, NC);
+    // zero rows for the padding nodes NP..NPP-1 (their operator entries are 0)
+    for (int pz = m; pz < NPP - NP; pz += NP) {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) sm.dw[el][q][m] = dv.dW[q];
+      for (int i = 0; i < D; ++i) sm.df[el][i * NPP + NP + pz] = z;
+      sm.dw[el][NP + pz] = z;
+    }
   }
   __syncthreads();
   bool staged = false;
@@ -195,11 +230,23 @@ __global__ void __launch_bounds__(EB * NP, 4) split_volume_f32_kernel(
   }
   double hw = 0.0;
   if (active) {
-    float acc[NC], g[D][NC];
+    float4 acc4, g4[D];
     if (staged)
-      contract32<true, D, NP, EB>(ops_sm + (size_t)el * opsD_stride, sm, el, m, acc, g);
+      contract32<true, D, NP, EB>(ops_sm + (size_t)el * opsD_stride, sm, el, m, acc4, g4);
     else
-      contract32<false, D, NP, EB>(ops + ((size_t)e * 2 + 1) * (D * NP * NP), sm, el, m, acc, g);
+      contract32<false, D, NP, EB>(opsD + (size_t)e * opsD_stride, sm, el, m, acc4, g4);
+    float acc[NC], g[D][NC];
+    {
+      const float a4[4] = {acc4.x, acc4.y, acc4.z, acc4.w};
+#pragma unroll
+      for (int q = 0; q < NC; ++q) acc[q] = a4[q];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const float b4[4] = {g4[i].x, g4[i].y, g4[i].z, g4[i].w};
+#pragma unroll
+        for (int q = 0; q < NC; ++q) g[i][q] = b4[q];
+      }
+    }
     Node<float, D> nd;
     node32<D>(rf, dv, nd);
     const JvpPrep<float> jp = jvp_prep<float, D>(nd, c);
@@ -395,7 +442,7 @@ static int split_f32_np(esplit_ctx* c, const double* u, double* r, cudaStream_t 
       }
     }
     split_volume_f32_kernel<D, NP, EB, STAGE><<<nb, EB * NP, dyn, s>>>(
-        u, r, c->b.ops32, c->b.opsD32, c->opsD_stride, c->b.ihf, satf, c->n_e, ph, c->b.status,
+        u, r, c->b.opsD32, c->opsD_stride, c->b.ihf, satf, c->n_e, ph, c->b.status,
         prod ? prod + np_used : nullptr);
     c->launches++;
     if (prod) np_used += nb;

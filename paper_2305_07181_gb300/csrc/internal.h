@@ -11,6 +11,13 @@
 namespace esplit {
 
 constexpr int MAX_NP = 80;
+
+// row length of the float32 path's staged operators: the smallest multiple of
+// 4 (one 16-byte load) not below n_p whose number of 16-byte chunks is odd, so
+// that 8 consecutive rows fall in 8 different bank groups
+__host__ __device__ constexpr int npp_for(int np) {
+  return ((np + 3) / 4 % 2 == 1) ? (np + 3) / 4 * 4 : (np + 3) / 4 * 4 + 4;
+}
 constexpr int MAX_SLOT = 64;
 
 // Reference-operator tables every kernel reads (constant memory).
@@ -47,9 +54,11 @@ struct Buffers {
   float* ops32lo = nullptr;    // same, float remainder ops64 - ops32 (compensated FP32-bulk contractions)
   double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
   float* ihf = nullptr;        // [n_e][n_p] 1/(H_ref J), float32 (the float32 path's facet scaling)
-  // the D_i half of ops32 alone, per element padded to a multiple of 4 floats
-  // (16 bytes), so that a block's elements are one contiguous, aligned range
-  // for a bulk copy into shared memory (float32 path, d <= 2)
+  // the D_i of ops32 again, as rows: [e][i][m][n] with n padded to
+  // npp_for(n_p) (zeros), each element padded to opsD_stride floats (a
+  // multiple of 4), so that a block's elements are one contiguous, aligned
+  // range for a bulk copy into shared memory and a thread reads its row 4
+  // entries at a time (float32 path, d <= 2)
   float* opsD32 = nullptr;     // [n_e][opsD_stride]
   // element lists for the hybrid scheme (capacity n_e each), the flags they
   // come from, and the detector's scratch (unwidened flags, block counts + total)
@@ -69,7 +78,7 @@ struct Buffers {
   double* stage_u = nullptr;
   double* stage_r = nullptr;
   double* dacc = nullptr;
-  double* node_cache = nullptr;  // [4][n_e n_p]: s, 1/rho, 1/p, log q of u_n
+  double* node_cache = nullptr;  // [3][n_e n_p]: s, 1/rho, 1/p of u_n
   // viscous scratch: nodal F^V [n_e][d][n_c][n_p], facet jump terms
   // [n_e][n_c][n_slot] and lift vectors a_j [n_e][d][n_c][n_slot]
   double* fv = nullptr;

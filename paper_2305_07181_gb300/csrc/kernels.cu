@@ -91,14 +91,21 @@ __global__ void build_rows_kernel(const double* __restrict__ ops64, int n_e, int
   rows[idx] = s;
 }
 
-// opsD32[e][j] = D_i half of ops32[e] (j < d n_p^2), zero padding after it
-__global__ void build_opsD_kernel(const float* __restrict__ ops32, int n_e, int dnn, int stride,
+// opsD32[e][i][m][n] = D_i[m][n] (ops32 holds it at [e][d + i][n][m]) for
+// n < n_p, zero in the row padding up to npp and after the d n_p npp entries
+__global__ void build_opsD_kernel(const float* __restrict__ ops32, int n_e, int d, int np, int npp, int stride,
                                   float* __restrict__ opsD) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n_e * stride) return;
   const size_t e = idx / stride;
   const int j = (int)(idx - e * stride);
-  opsD[idx] = j < dnn ? ops32[(e * 2 + 1) * dnn + j] : 0.0f;
+  float v = 0.0f;
+  if (j < d * np * npp) {
+    const int i = j / (np * npp), rem = j - i * np * npp;
+    const int m = rem / npp, n = rem - m * npp;
+    if (n < np) v = ops32[(((e * 2 * d) + d + i) * np + n) * np + m];
+  }
+  opsD[idx] = v;
 }
 
 int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
@@ -119,10 +126,9 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   build_rows_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(c->b.ops64, c->n_e, 2 * c->dim, c->b.rows);
   c->launches += 2;
   if (c->b.opsD32) {
-    const int dnn = c->dim * c->n_p * c->n_p;
     const size_t no = (size_t)c->n_e * c->opsD_stride;
-    build_opsD_kernel<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(c->b.ops32, c->n_e, dnn, c->opsD_stride,
-                                                                    c->b.opsD32);
+    build_opsD_kernel<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(c->b.ops32, c->n_e, c->dim, c->n_p,
+                                                                    npp_for(c->n_p), c->opsD_stride, c->b.opsD32);
     c->launches++;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
   }
   if (prod) {
     double vv[1] = {hw};
-    block_sum<1>(vv, prod + blockIdx.x);
+    block_sum_t<1, 128>(vv, prod + blockIdx.x);
   }
 }
 
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(128) face_bc_kernel(const double* __restrict__
   }
   if (ADD && prod) {
     double vv[1] = {hw};
-    block_sum<1>(vv, prod + blockIdx.x);
+    block_sum_t<1, 128>(vv, prod + blockIdx.x);
   }
 }
 
@@ -704,7 +710,6 @@ __global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ?
       ncache[g] = sH;
       ncache[nn + g] = nd.ir;
       ncache[2 * nn + g] = jp.itheta * nd.ir;  // 1/p
-      ncache[3 * nn + g] = nd.lnq;
       const double Hm0 = c_ref.H[m] * __ldg(&J[(size_t)e * NP + m]);
       ent_s = Hm0 * sH;
       ent_a = Hm0 * fabs(sH);
@@ -818,12 +823,12 @@ __global__ void __launch_bounds__(EB * NP, (sizeof(T) == 4 && !VISC && D == 2) ?
   }
   if (prod) {
     double v[1] = {hw};
-    block_sum<1>(v, prod + blockIdx.x);
+    block_sum_t<1, round32(EB * NP)>(v, prod + blockIdx.x);
   }
   if constexpr (ENT) {
     __syncthreads();  // the block sum's shared scratch is reused
     double v2[2] = {ent_s, ent_a};
-    block_sum<2>(v2, ent_part + 2 * blockIdx.x);
+    block_sum_t<2, round32(EB * NP)>(v2, ent_part + 2 * blockIdx.x);
   }
 }
 
@@ -1301,20 +1306,28 @@ __global__ void __launch_bounds__(256) entropy_kernel(const double* __restrict__
     double uu[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) uu[q] = __ldg(&u[(e * NC + q) * NP + m]);
-    Node<double, D> nd;
-    node_from_u<double, D>(uu, c, nd);
+    // one division for 1/rho and 1/p: P = rho p = (gam-1)(rho E - |m|^2/2),
+    // y = 1/(rho P), 1/rho = P y, 1/p = rho^2 y, p = P/rho
+    const double rho = uu[0];
+    double mm = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) mm += uu[1 + i] * uu[1 + i];
+    const double P = c.gm1 * (rho * uu[NC - 1] - 0.5 * mm);
+    const double y = 1.0 / (rho * P);
+    const double ir = P * y, ip = (rho * rho) * y, p = P * ir;
+    // S_H = beta rho (p rho^-gam)^(1/(alpha+gam)) = beta q p, log q = a_q log rho + b_q log p
+    const double lnq = c.a_q * fm::log(rho) + c.b_q * fm::log(p);
+    const double sH = c.beta * fm::exp(lnq) * p;
     double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
-    double sH = c.beta * nd.q * nd.p;  // S_H = beta rho (p rho^-gam)^(1/(alpha+gam)) = beta q p
     v[0] = H * sH;
     v[1] = H * fabs(sH);
-    if (cache) {  // per-node values the relaxation passes reuse: s, 1/rho, 1/p, log q
+    if (cache) {  // per-node values the relaxation passes reuse: s, 1/rho, 1/p
       cache[g] = sH;
-      cache[n_nodes + g] = 1.0 / nd.rho;
-      cache[2 * n_nodes + g] = 1.0 / nd.p;
-      cache[3 * n_nodes + g] = nd.lnq;
+      cache[n_nodes + g] = ir;
+      cache[2 * n_nodes + g] = ip;
     }
   }
-  block_sum<2>(v, part + 2 * blockIdx.x);
+  block_sum_t<2, 256>(v, part + 2 * blockIdx.x);
 }
 
 template <int D, int W>
@@ -1348,9 +1361,9 @@ __global__ void __launch_bounds__(256) entropy_rate_kernel(const double* __restr
   }
   if constexpr (W == 1) {
     double v1[1] = {v[0]};
-    block_sum<1>(v1, part + blockIdx.x);
+    block_sum_t<1, 256>(v1, part + blockIdx.x);
   } else {
-    block_sum<2>(v, part + 2 * blockIdx.x);
+    block_sum_t<2, 256>(v, part + 2 * blockIdx.x);
   }
 }
 
@@ -1520,12 +1533,12 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
 }
 
 // Entropy change s(u + g d) - s(u), slope w(u + g d) . d and (SECOND)
-// curvature d . (dw/dg) at one node, from the cached s(u), 1/rho, 1/p, log q
-// of u.  Along u' = u + g d: drho' = d_0, dV' = (d_m - V' d_0)/rho',
+// curvature d . (dw/dg) at one node, from the cached s(u), 1/rho and 1/p of
+// u.  Along u' = u + g d: drho' = d_0, dV' = (d_m - V' d_0)/rho',
 // dp' = (gam-1)(d_E - V'.d_m + |V'|^2 d_0/2), dq'/q' = a_q d_0/rho' + b_q dp'/p'.
 template <int D, bool SECOND = false>
 __device__ __forceinline__ void entropy_change_and_slope(const double* u, const double* dd, double g, double s0,
-                                                         double ir, double ip, double lnq, const Phys<double>& c,
+                                                         double ir, double ip, const Phys<double>& c,
                                                          double& ds, double& wd, double* d2 = nullptr) {
   constexpr int NC = D + 2;
   double rho = u[0];
@@ -1543,9 +1556,11 @@ __device__ __forceinline__ void entropy_change_and_slope(const double* u, const 
   double dp = c.gm1 * (dE - dke);
   double l1 = fm::log1p(drho * ir), l2 = fm::log1p(dp * ip);
   ds = s0 * fm::expm1(c.a_q * l1 + (c.b_q + 1.0) * l2);
-  // entropy variables at u' = u + g d (Eq. (25)) from log q' = log q + a_q l1 + b_q l2
-  double q1 = fm::exp(lnq + c.a_q * l1 + c.b_q * l2);
+  // entropy variables at u' = u + g d (Eq. (25)); q' = s'/(beta p') with
+  // s' = s + ds (S_H = beta q p), one division that also gives 1/p'
   double p1 = c.gm1 * (u[NC - 1] - 0.5 * mm * ir) + dp;
+  double ibp1 = 1.0 / (c.beta * p1);
+  double q1 = (s0 + ds) * ibp1;
   double v2 = 0.0, vd = 0.0;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -1569,7 +1584,7 @@ __device__ __forceinline__ void entropy_change_and_slope(const double* u, const 
       dvd += dV[i] * dd[1 + i];
     }
     double dp1 = c.gm1 * (dd[NC - 1] - vdm + 0.5 * v2 * dd[0]);
-    double dq1 = q1 * (c.a_q * dd[0] * ir1 + c.b_q * dp1 / p1);
+    double dq1 = q1 * (c.a_q * dd[0] * ir1 + c.b_q * dp1 * (c.beta * ibp1));
     double dW0 = dq1 * (c.w1c * p1 * ir1 - 0.5 * v2) + q1 * (c.w1c * (dp1 - p1 * dd[0] * ir1) * ir1 - vdv);
     *d2 = dW0 * dd[0] + dq1 * vd + q1 * dvd - dq1 * dd[NC - 1];
   }
@@ -1598,23 +1613,23 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
       uu[q] = __ldg(&un[ix]);
     }
     double s0 = __ldg(&cache[t]), ir = __ldg(&cache[n_nodes + t]);
-    double ip = __ldg(&cache[2 * n_nodes + t]), lnq = __ldg(&cache[3 * n_nodes + t]);
+    double ip = __ldg(&cache[2 * n_nodes + t]);
     double H = c_ref.H[m] * __ldg(&J[e * NP + m]);
     double ds, wd;
     double d2 = 0.0;
-    entropy_change_and_slope<D, true>(uu, dd, ga, s0, ir, ip, lnq, c, ds, wd, &d2);
+    entropy_change_and_slope<D, true>(uu, dd, ga, s0, ir, ip, c, ds, wd, &d2);
     v[0] = H * ds;
     v[1] = H * wd;
     v[2] = H * fabs(ds);
     v[3] = H * d2;  // curvature; replaced below when a second point is evaluated
     if (gb > 0.0) {
-      entropy_change_and_slope<D>(uu, dd, gb, s0, ir, ip, lnq, c, ds, wd);
+      entropy_change_and_slope<D>(uu, dd, gb, s0, ir, ip, c, ds, wd);
       v[3] = H * ds;
       v[4] = H * wd;
       v[5] = H * fabs(ds);
     }
   }
-  block_sum<6>(v, part + 6 * blockIdx.x);
+  block_sum_t<6, 256>(v, part + 6 * blockIdx.x);
 }
 
 __device__ void root_update_body(const double* tot, RootState* st);
@@ -1633,12 +1648,14 @@ __global__ void __launch_bounds__(1024) root_update_kernel(const double* __restr
     return;
   }
   __shared__ double tot[6];
-  for (int k = 0; k < 6; ++k) {
-    double v[1] = {0.0};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[0] += part[(size_t)i * 6 + k];
-    block_sum<1>(v, tot + k);
-    __syncthreads();
+  // the six sums in one pass over the partials (each thread's order, and the
+  // shuffle tree per value, as six separate block sums would take them)
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] += part[(size_t)i * 6 + k];
   }
+  block_sum<6>(v, tot);
   if (threadIdx.x != 0) return;
   root_update_body(tot, st);
   if constexpr (COND) {

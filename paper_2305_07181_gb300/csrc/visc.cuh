@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) visc_jump_kernel(double* __restrict__ r, 
   }
   if (prod) {
     double vv[1] = {hw};
-    block_sum<1>(vv, prod + blockIdx.x);
+    block_sum_t<1, 128>(vv, prod + blockIdx.x);
   }
 }
 
