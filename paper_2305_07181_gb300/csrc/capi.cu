@@ -191,7 +191,7 @@ void esplit_destroy(esplit_ctx* c) {
   void* ps[] = {b.Qref, b.J,       b.nu,      b.pair,   b.Lam,     b.face_pairs, b.ops64,   b.ops32,   b.ops32lo,
                 b.list_split, b.list_had, b.hflags, b.hflag0, b.hcount, b.sat, b.fcache, b.rows, b.partial, b.scal, b.root, b.status, b.stage_u,
                 b.stage_r, b.dacc, b.node_cache, b.vjp_work, b.host_u, b.host_r, b.fv, b.vsat, b.va, b.wslot, b.vfb, b.vfs, b.vus,
-                b.bslot, b.bstate, b.ihf, b.opsD32};
+                b.bslot, b.bstate, b.ihf, b.opsD32, b.ihd, b.nscale};
   for (void* p : ps) dfree(p);
   if (c->sg.exec) cudaGraphExecDestroy(c->sg.exec);
   if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
@@ -323,6 +323,8 @@ int esplit_upload_mesh(esplit_ctx* c, int n_e, const double* J, const double* La
   if ((rc = dalloc(c, &c->b.sat, (size_t)n_e * c->n_c * NS))) return rc;
   if ((rc = dalloc(c, &c->b.fcache, (size_t)(d + 9) * n_e * NS))) return rc;
   if ((rc = dalloc(c, &c->b.ihf, (size_t)n_e * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.ihd, (size_t)n_e * NP))) return rc;
+  if ((rc = dalloc(c, &c->b.nscale, (size_t)n_e * NS * (d + 1)))) return rc;
   if (d <= 2) {
     c->opsD_stride = opsD_stride_for(d, NP);
     if ((rc = dalloc(c, &c->b.opsD32, (size_t)n_e * c->opsD_stride))) return rc;

@@ -54,6 +54,8 @@ struct Buffers {
   float* ops32lo = nullptr;    // same, float remainder ops64 - ops32 (compensated FP32-bulk contractions)
   double* rows = nullptr;      // [n_e][2d][n_p] row sums of the ops64 matrices
   float* ihf = nullptr;        // [n_e][n_p] 1/(H_ref J), float32 (the float32 path's facet scaling)
+  double* ihd = nullptr;       // [n_e][n_p] 1/(H_ref J) (the float64 facet kernels' scaling)
+  double* nscale = nullptr;    // [n_e][n_slot][d + 1] |nu|, nu/|nu| of every facet slot
   // the D_i of ops32 again, as rows: [e][i][m][n] with n padded to
   // npp_for(n_p) (zeros), each element padded to opsD_stride floats (a
   // multiple of 4), so that a block's elements are one contiguous, aligned

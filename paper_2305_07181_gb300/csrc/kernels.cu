@@ -108,6 +108,29 @@ __global__ void build_opsD_kernel(const float* __restrict__ ops32, int n_e, int 
   opsD[idx] = v;
 }
 
+// per-node 1/(H_m J_km) and per-slot |nu| and nu/|nu|, formed once here with
+// the expressions the facet kernels used to evaluate per node pair (two
+// divisions, a square root and d more divisions a pair on the float64 pipe)
+template <int D>
+__global__ void facet_tables_kernel(const double* __restrict__ J, const double* __restrict__ nu, int n_e,
+                                    double* __restrict__ ihd, double* __restrict__ nscale) {
+  const int NP = c_ref.n_p, NS = c_ref.n_slot;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (size_t)n_e * NP) ihd[idx] = 1.0 / (c_ref.H[idx % NP] * J[idx]);
+  if (idx < (size_t)n_e * NS) {
+    double nuv[D], b2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      nuv[i] = nu[idx * D + i];
+      b2 += nuv[i] * nuv[i];
+    }
+    const double b = sqrt(b2);
+    nscale[idx * (D + 1)] = b;
+#pragma unroll
+    for (int i = 0; i < D; ++i) nscale[idx * (D + 1) + 1 + i] = nuv[i] / b;
+  }
+}
+
 int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   size_t total = (size_t)c->n_e * 2 * c->dim * c->n_p * c->n_p;
   int bs = 256;
@@ -125,6 +148,17 @@ int launch_build_ops(esplit_ctx* c, cudaStream_t s) {
   size_t nr = (size_t)c->n_e * 2 * c->dim * c->n_p;
   build_rows_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(c->b.ops64, c->n_e, 2 * c->dim, c->b.rows);
   c->launches += 2;
+  {
+    const size_t nn = (size_t)c->n_e * c->n_p, ns = (size_t)c->n_e * c->n_slot, nt = nn > ns ? nn : ns;
+    const unsigned nbt = (unsigned)((nt + 255) / 256);
+    if (c->dim == 1)
+      facet_tables_kernel<1><<<nbt, 256, 0, s>>>(c->b.J, c->b.nu, c->n_e, c->b.ihd, c->b.nscale);
+    else if (c->dim == 2)
+      facet_tables_kernel<2><<<nbt, 256, 0, s>>>(c->b.J, c->b.nu, c->n_e, c->b.ihd, c->b.nscale);
+    else
+      facet_tables_kernel<3><<<nbt, 256, 0, s>>>(c->b.J, c->b.nu, c->n_e, c->b.ihd, c->b.nscale);
+    c->launches++;
+  }
   if (c->b.opsD32) {
     const size_t no = (size_t)c->n_e * c->opsD_stride;
     build_opsD_kernel<<<(unsigned)((no + 255) / 256), 256, 0, s>>>(c->b.ops32, c->n_e, c->dim, c->n_p,
@@ -161,7 +195,8 @@ __device__ __forceinline__ void normal_flux(const Node<double, D>& n, const TN* 
 template <typename T, int D, bool VISC, int FLUX = 0>
 __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u, const int2* __restrict__ fp,
                                                    int n_pairs, const double* __restrict__ nu,
-                                                   const double* __restrict__ J, double* __restrict__ sat,
+                                                   const double* __restrict__ ihd,
+                                                   const double* __restrict__ nscale, double* __restrict__ sat,
                                                    Phys<T> c, int dissipation, int* __restrict__ status,
                                                    int ef_mode, const unsigned char* __restrict__ hflags,
                                                    int visc_heat, double* __restrict__ ah) {
@@ -195,13 +230,11 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
     ir_avg<T, D>(ik, iv, c, a);
     ir_flux_dir<T, D>(a, c, nuv, G);
     if (dissipation) {
-      T b2 = T(0);
-#pragma unroll
-      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
-      T b = t_sqrt(b2);
+      const double* ns = nscale + (size_t)pr.x * (D + 1);  // |nu|, nu/|nu| of slot (k, s)
+      const T b = (T)__ldg(&ns[0]);
       T nh[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+      for (int i = 0; i < D; ++i) nh[i] = (T)__ldg(&ns[1 + i]);
       T wk[NC], wv[NC], dw[NC], out[NC];
       std_entropy_vars<T, D>(nk, ik, c, wk);
       std_entropy_vars<T, D>(nv, iv, c, wv);
@@ -220,13 +253,11 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
     pair_avg<T, D>(zk, zv, c, a);
     sy_flux_dir<T, D>(a, c, nuv, G);
     if (dissipation) {
-      T b2 = T(0);
-#pragma unroll
-      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
-      T b = t_sqrt(b2);
+      const double* ns = nscale + (size_t)pr.x * (D + 1);  // |nu|, nu/|nu| of slot (k, s)
+      const T b = (T)__ldg(&ns[0]);
       T nh[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+      for (int i = 0; i < D; ++i) nh[i] = (T)__ldg(&ns[1 + i]);
       T dw[NC], out[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
@@ -235,8 +266,7 @@ __global__ void __launch_bounds__(128) face_kernel(const double* __restrict__ u,
       for (int q = 0; q < NC; ++q) G[q] += T(0.5) * b * out[q];
     }
   }
-  double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
-  double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+  const double ihk = __ldg(&ihd[(size_t)k * NP + m]), ihv = __ldg(&ihd[(size_t)v * NP + n]);
   double ek[NC], ev[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) ek[q] = ev[q] = 0.0;
@@ -320,7 +350,8 @@ __device__ __forceinline__ void node_from_cache(const double* __restrict__ fc, s
 template <int D>
 __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r, const int2* __restrict__ fp,
                                                           int n_pairs, const double* __restrict__ nu,
-                                                          const double* __restrict__ J,
+                                                          const double* __restrict__ ihd,
+                                                          const double* __restrict__ nscale,
                                                           const double* __restrict__ fc, int n_slot_total,
                                                           Phys<double> c, int dissipation,
                                                           double* __restrict__ prod, int ef_mode,
@@ -352,13 +383,11 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
     double G[NC];
     sy_flux_dir<double, D>(a, c, nuv, G);
     if (dissipation) {
-      double b2 = 0.0;
-#pragma unroll
-      for (int i = 0; i < D; ++i) b2 += nuv[i] * nuv[i];
-      double b = sqrt(b2);
+      const double* ns = nscale + (size_t)pr.x * (D + 1);  // |nu|, nu/|nu| of slot (k, s)
+      const double b = __ldg(&ns[0]);
       double nh[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) nh[i] = nuv[i] / b;
+      for (int i = 0; i < D; ++i) nh[i] = __ldg(&ns[1 + i]);
       double dw[NC], out[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) dw[q] = nk.W[q] - nv.W[q];
@@ -373,8 +402,7 @@ __global__ void __launch_bounds__(128) face_cached_kernel(double* __restrict__ r
     for (int q = 0; q < NC; ++q) ek[q] = ev[q] = 0.0;
     if (ef_mode == 1 || (ef_mode == 2 && __ldg(&hflags[k]) == 0)) normal_flux<D>(nk, nuv, ek);
     if (ef_mode == 1 || (ef_mode == 2 && __ldg(&hflags[v]) == 0)) normal_flux<D>(nv, nuv, ev);
-    double ihk = 1.0 / (c_ref.H[m] * __ldg(&J[(size_t)k * NP + m]));
-    double ihv = 1.0 / (c_ref.H[n] * __ldg(&J[(size_t)v * NP + n]));
+    const double ihk = __ldg(&ihd[(size_t)k * NP + m]), ihv = __ldg(&ihd[(size_t)v * NP + n]);
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       double gk = ek[q] - G[q], gv = G[q] - ev[q];
@@ -1071,19 +1099,19 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     const int ef_mode = c->prm.scheme == ESPLIT_SCHEME_SPLIT ? 1 : (c->prm.scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0);
     const int visc_heat = c->prm.viscous ? c->prm.heat_flux : -1;
     if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR && visc_heat >= 0)
-      face_kernel<double, D, true, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat,
+      face_kernel<double, D, true, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihd, c->b.nscale, sat,
                                                         ph64, c->prm.dissipation, c->b.status, 0, c->b.hflags,
                                                         visc_heat, c->b.va);
     else if (c->prm.scheme == ESPLIT_SCHEME_HADAMARD_IR)
-      face_kernel<double, D, false, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat,
+      face_kernel<double, D, false, 1><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihd, c->b.nscale, sat,
                                                          ph64, c->prm.dissipation, c->b.status, 0, c->b.hflags, 0,
                                                          nullptr);
     else if (visc_heat >= 0)
-      face_kernel<double, D, true><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
+      face_kernel<double, D, true><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihd, c->b.nscale, sat, ph64,
                                                      c->prm.dissipation, c->b.status, ef_mode, c->b.hflags,
                                                      visc_heat, c->b.va);
     else
-      face_kernel<double, D, false><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, sat, ph64,
+      face_kernel<double, D, false><<<nb, bs, 0, s>>>(u, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihd, c->b.nscale, sat, ph64,
                                                       c->prm.dissipation, c->b.status, ef_mode, c->b.hflags, 0,
                                                       nullptr);
     c->launches++;
@@ -1185,7 +1213,8 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
     int bs = 128;
     int nb = (c->n_pairs + bs - 1) / bs;
     ProfScope ps(c, PG_FACE, s);
-    face_cached_kernel<D><<<nb, bs, 0, s>>>(r, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.J, c->b.fcache,
+    face_cached_kernel<D><<<nb, bs, 0, s>>>(r, c->b.face_pairs, c->n_pairs, c->b.nu, c->b.ihd, c->b.nscale,
+                                            c->b.fcache,
                                             c->n_e * c->n_slot, ph64, c->prm.dissipation,
                                             prod ? prod + np_used : nullptr,
                                             scheme == ESPLIT_SCHEME_SPLIT ? 1 : (scheme == ESPLIT_SCHEME_HYBRID ? 2 : 0),
