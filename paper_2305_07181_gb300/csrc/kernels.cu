@@ -1065,6 +1065,15 @@ namespace esplit {
 template <int NP>
 struct VolCfg {
   static constexpr int EB_SPLIT = (256 / NP) > 0 ? (256 / NP) : 1;
+  // float64 on triangles: the float64-pipe-bound split kernel keeps 2 blocks
+  // of ~250 threads per SM, and a grid of n_e / EB_SPLIT blocks leaves the
+  // SMs unevenly loaded by up to one block in ~15 (config 2, p 3); blocks of
+  // about 128 threads (4-5 per SM) halve that granularity.  Taken where such
+  // a block fills at least 95 % of its warps' lanes (n_p = 7, 18; measured at
+  // n_p = 18: 0.506 -> 0.490 ms per launch).
+  static constexpr int EB_HALF = (128 / NP) > 0 ? (128 / NP) : 1;
+  static constexpr bool HALF_FILLS = EB_HALF * NP * 100 >= 95 * 32 * ((EB_HALF * NP + 31) / 32);
+  static constexpr int EB_SPLIT64_2D = HALF_FILLS ? EB_HALF : EB_SPLIT;
   // larger operators (tetrahedra of degree 3 and 4): the pair contributions
   // pass through shared memory in chunks of HAD_KC pair offsets, which leaves
   // room for more elements per block
@@ -1126,7 +1135,7 @@ static int residual_np(esplit_ctx* c, const double* u, double* r, cudaStream_t s
   const int* lsplit = scheme == ESPLIT_SCHEME_HYBRID ? c->b.list_split : nullptr;
   const int* lhad = scheme == ESPLIT_SCHEME_HYBRID ? c->b.list_had : nullptr;
   if (n_split > 0) {
-    constexpr int EB = VolCfg<NP>::EB_SPLIT;
+    constexpr int EB = (std::is_same<T, double>::value && D == 2) ? VolCfg<NP>::EB_SPLIT64_2D : VolCfg<NP>::EB_SPLIT;
     int nb = (n_split + EB - 1) / EB;
     ProfScope ps(c, PG_SPLIT, s);
     // the split kernel also forms the viscous volume terms (it has D_i w)

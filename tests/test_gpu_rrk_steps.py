@@ -171,3 +171,52 @@ def test_launch_count_and_timing_small_mesh(lib):
     per_step = (s.launch_count() - n0) / 10
     assert 10 <= per_step <= 40
     s.close()
+
+
+def _assembled_step(s, u, dt, g):
+    """u_n + g d with d = dt sum_i b_i r_i from four separate residual calls
+    and torch arithmetic (the relaxation parameter g taken from the library's
+    own step)."""
+    A, B = (0.0, 0.5, 0.5, 1.0), (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
+    d = torch.zeros_like(u)
+    r = None
+    for i in range(4):
+        Ui = u if i == 0 else u + (A[i] * dt) * r
+        r = s.residual(Ui)
+        d += (B[i] * dt) * r
+    return u + g * d
+
+
+@pytest.mark.parametrize("case", ["split_fp64", "split_fp32_bulk", "split_fp32", "hybrid_fp64", "split_tet_fp32"])
+def test_step_stage_updates_match_separate_residuals(lib, case):
+    """The relaxation step (its stage states, the combination d of the four
+    stage residuals and the update u_n + g d, all on the device) equals
+    u_n + g d assembled from four esplit_residual calls and torch arithmetic, to the
+    rounding of the stage sums: 1e-13 of the state's scale, component-wise.
+    The float32 path takes 1e-9: torch forms the stage states U_i with a
+    rounding of its own, and a last-bit change of U_i can flip the float32
+    rounding of a deviation (one float32 ulp, 6e-8, of dU/dt there), which a
+    step (dt |dU/dt| ~ 6e-3 of |u| here) carries to ~4e-10 of the state."""
+    if case == "split_tet_fp32":
+        op = tet_operator(1)
+        m = periodic_tet_mesh(op, 3)
+        u0 = states.add_uniform_noise(states.taylor_green(m), 1e-3, 5)
+        dt = states.cfl_timestep(m, u0, 0.1)
+    else:
+        op, m, u0, dt = _tri(p=3, N=6)
+    prec = {"split_fp64": "fp64", "split_fp32_bulk": "fp32_bulk", "split_fp32": "fp32", "hybrid_fp64": "fp64",
+            "split_tet_fp32": "fp32"}[case]
+    scheme = "hybrid" if case.startswith("hybrid") else "split"
+    s = lib.Solver(op, m, lib.Params(scheme=scheme, dissipation=True, precision=prec))
+    if scheme == "hybrid":
+        s.set_hybrid_flags(np.random.default_rng(3).integers(0, 2, m.n_e).astype(np.uint8))
+    u = s.to_device(u0)
+    ref_in = u.clone()
+    g, info = s.rrk_step(u, dt)
+    assert info.status == 0
+    ref = _assembled_step(s, ref_in, dt, g)
+    scale = ref.abs().amax(dim=(0, 2))
+    err = ((u - ref).abs().amax(dim=(0, 2)) / scale).max().item()
+    print(f"{case}: step vs assembled stages, rel err {err:.2e}")
+    assert err <= (1e-9 if prec == "fp32" and op.d == 2 else 1e-13)
+    s.close()
