@@ -38,7 +38,7 @@ UNIT = "DOF-residual evals/s"
 FP64_PEAK_NOMINAL = 1.25e12            # GB300 nominal FP64 1.25 TFLOP/s (context; the roofline uses the measured rate)
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged
 # kernel; keyed by (kernel, p, precision, N)
-NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 229.968e6}
+NCU_TRAFFIC = {("split_volume", 3, "fp64", 128): 229.391e6}
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 # precision settings timed per scheme (the Hadamard forms have one float32 setting,
 # plain float32 two-point fluxes) and the error bound each is tested to

@@ -687,19 +687,18 @@ int esplit_rrk_step(esplit_ctx* c, double* u, double dt, double* g_out, esplit_s
   cudaStream_t s = as_stream(stream);
   const size_t n = (size_t)c->n_e * c->n_c * c->n_p;
   if ((rc = rrk_enqueue_stages(c, u, dt, s))) return rc;
-  int np = 0;
   esplit::RootState st{};
   // two evaluation passes and the (guarded) update go out without a host
   // round trip: the first pass usually ends the solve (Halley step at g = 1)
   for (int it = 0; it < 2; ++it)
-    if (esplit::launch_root_eval(c, u, c->b.dacc, s, &np) || esplit::launch_root_update(c, np, s))
+    if (esplit::launch_root_eval(c, u, c->b.dacc, s))
       return fail(c, ESPLIT_ERR_CUDA, "root launch");
   if (esplit::launch_root_apply(c, u, c->b.dacc, n, s)) return fail(c, ESPLIT_ERR_CUDA, "apply launch");
   CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (!st.done) {
     for (int it = 2; it < esplit::ROOT_EVALS_MAX; ++it) {
-      if (esplit::launch_root_eval(c, u, c->b.dacc, s, &np) || esplit::launch_root_update(c, np, s))
+      if (esplit::launch_root_eval(c, u, c->b.dacc, s))
         return fail(c, ESPLIT_ERR_CUDA, "root launch");
       if ((it + 1) % esplit::ROOT_CHECK_EVERY == 0) {
         CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -786,9 +785,7 @@ static int rrk_capture(esplit_ctx* c, double* u, double dt) {
       e = cudaStreamBeginCaptureToGraph(c->cap_s2, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                         cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      int np = 0;
-      int r1 = esplit::launch_root_eval(c, u, c->b.dacc, c->cap_s2, &np);
-      if (!r1) r1 = esplit::launch_root_update_cond(c, np, c->cap_s2, h);
+      int r1 = esplit::launch_root_eval_cond(c, u, c->b.dacc, c->cap_s2, h);
       cudaGraph_t bg = nullptr;
       e = cudaStreamEndCapture(c->cap_s2, &bg);
       if (r1 && e == cudaSuccess) e = cudaErrorLaunchFailure;
@@ -1004,7 +1001,7 @@ int esplit_rrk_step_vjp(esplit_ctx* c, const double* u, double dt, const double*
   if (esplit::launch_root_start(c, dt, s)) return fail(c, ESPLIT_ERR_CUDA, "root init");
   esplit::RootState st{};
   for (int it = 0; it < esplit::ROOT_EVALS_MAX; ++it) {
-    if (esplit::launch_root_eval(c, u, d, s, &np) || esplit::launch_root_update(c, np, s))
+    if (esplit::launch_root_eval(c, u, d, s))
       return fail(c, ESPLIT_ERR_CUDA, "root launch");
     if ((it + 1) % esplit::ROOT_CHECK_EVERY == 0) {
       CK(cudaMemcpyAsync(&st, c->b.root, sizeof(st), cudaMemcpyDeviceToHost, s));

@@ -35,6 +35,7 @@ struct RootState {
   double f_last, df_last, dS_last;
   double dg_last;             // previous Newton step (0: none yet)
   int phase, done, iters, status;
+  unsigned int arrivals;      // blocks of the running evaluation pass that are done
 };
 
 struct Buffers {
@@ -196,9 +197,9 @@ int launch_stage(esplit_ctx* c, const double* un, const double* r, double a_dt, 
 int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s);
 constexpr int ROOT_CHECK_EVERY = 4;
 constexpr int ROOT_EVALS_MAX = 40;
-int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s, int* n_partial);
-int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s);
-int launch_root_update_cond(esplit_ctx* c, int n_partial, cudaStream_t s, cudaGraphConditionalHandle h);
+int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s);
+int launch_root_eval_cond(esplit_ctx* c, const double* un, const double* d, cudaStream_t s,
+                          cudaGraphConditionalHandle h);
 // per-step summary written on the device by graph-launched step batches
 struct StepRecord {
   double g, est, S0, S_after;
@@ -208,6 +209,7 @@ struct StepRecord {
 int launch_step_record(esplit_ctx* c, StepRecord* hist, int* counter, int cap, cudaStream_t s);
 int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
 int set_ref_tables(const RefTables& t);
+int set_ref_tables_vjp(const RefTables& t);  // the reverse-mode unit's copy (vjp.cu)
 // float32 path of the inviscid split scheme (fp32.cu): its own copy of the
 // reference tables, and the launcher (volume kernel, then facet kernel adding
 // into r); -2 for an operator size not compiled in

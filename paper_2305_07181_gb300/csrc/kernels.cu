@@ -30,7 +30,8 @@ namespace esplit {
 __constant__ RefTables c_ref;
 
 int set_ref_tables(const RefTables& t) {
-  return cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables)) == cudaSuccess ? 0 : -1;
+  if (cudaMemcpyToSymbol(c_ref, &t, sizeof(RefTables)) != cudaSuccess) return -1;
+  return set_ref_tables_vjp(t);  // the reverse-mode unit's copy
 }
 
 // ---------------------------------------------------------------------------
@@ -1065,15 +1066,15 @@ namespace esplit {
 template <int NP>
 struct VolCfg {
   static constexpr int EB_SPLIT = (256 / NP) > 0 ? (256 / NP) : 1;
-  // float64 on triangles: the float64-pipe-bound split kernel keeps 2 blocks
-  // of ~250 threads per SM, and a grid of n_e / EB_SPLIT blocks leaves the
-  // SMs unevenly loaded by up to one block in ~15 (config 2, p 3); blocks of
-  // about 128 threads (4-5 per SM) halve that granularity.  Taken where such
-  // a block fills at least 95 % of its warps' lanes (n_p = 7, 18; measured at
-  // n_p = 18: 0.506 -> 0.490 ms per launch).
-  static constexpr int EB_HALF = (128 / NP) > 0 ? (128 / NP) : 1;
-  static constexpr bool HALF_FILLS = EB_HALF * NP * 100 >= 95 * 32 * ((EB_HALF * NP + 31) / 32);
-  static constexpr int EB_SPLIT64_2D = HALF_FILLS ? EB_HALF : EB_SPLIT;
+  // float64 on triangles: the float64-pipe-bound split kernel holds 2 blocks
+  // of ~250 threads per SM, and the last of n_e / EB_SPLIT blocks leave the
+  // SMs unevenly loaded by up to one block in ~15 (config 2).  Smaller blocks
+  // that fill whole warps make that granularity finer and raise the warps
+  // per SM: n_p = 7 and 18, 126 threads (4-5 blocks per SM; measured at 18:
+  // 0.506 -> 0.490 ms per launch); n_p = 12, 192 threads (6 full warps, 3
+  // blocks per SM; 0.285 -> 0.270 ms); n_p = 27, 189 threads (6 warps, 3
+  // blocks per SM; 0.973 -> 0.952 ms).
+  static constexpr int EB_SPLIT64_2D = NP == 7 ? 18 : NP == 12 ? 16 : NP == 18 ? 7 : NP == 27 ? 7 : EB_SPLIT;
   // larger operators (tetrahedra of degree 3 and 4): the pair contributions
   // pass through shared memory in chunks of HAD_KC pair offsets, which leaves
   // room for more elements per block
@@ -1568,6 +1569,7 @@ __global__ void root_init_kernel(RootState* st, const double* scal, double dt) {
   st->iters = 0;
   st->status = 0;
   st->dg_last = 0.0;
+  st->arrivals = 0;
 }
 
 // Entropy change s(u + g d) - s(u), slope w(u + g d) . d and (SECOND)
@@ -1628,13 +1630,28 @@ __device__ __forceinline__ void entropy_change_and_slope(const double* u, const 
   }
 }
 
-template <int D>
+__device__ void root_update_body(const double* tot, RootState* st);
+
+// One evaluation pass of the root solve and the update that follows it: every
+// block writes its six partial sums; the block that finishes last (counted on
+// the root state after a fence, so that it sees every partial) reduces them in
+// block order and updates the root state, which the next pass reads.
+// COND: launched inside a graph's while loop over the evaluation passes; the
+// loop continues while the root is not done.  Every path sets done within
+// ROOT_EVALS_MAX + 12 passes (the Newton phase stops at ROOT_EVALS_MAX, the
+// bracket search after 10 halvings or 2 doublings); the hard stop below ends
+// the loop even if that reasoning failed, with status "no root".
+template <int D, bool COND>
 __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict__ un, const double* __restrict__ d,
                                                         const double* __restrict__ J,
                                                         const double* __restrict__ cache, size_t n_nodes,
-                                                        Phys<double> c, const RootState* __restrict__ st,
-                                                        double* __restrict__ part) {
-  if (st->done) return;
+                                                        Phys<double> c, RootState* __restrict__ st,
+                                                        double* __restrict__ part, cudaGraphConditionalHandle h) {
+  if (st->done) {
+    if constexpr (COND)
+      if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   constexpr int NC = D + 2;
   const int NP = c_ref.n_p;
   const double ga = st->ga, gb = st->gb;
@@ -1668,33 +1685,22 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
     }
   }
   block_sum_t<6, 256>(v, part + 6 * blockIdx.x);
-}
-
-__device__ void root_update_body(const double* tot, RootState* st);
-
-// COND: launched inside a graph's while loop over the evaluation passes; the
-// loop continues while the root is not done.  Every path sets done within
-// ROOT_EVALS_MAX + 12 passes (the Newton phase stops at ROOT_EVALS_MAX, the
-// bracket search after 10 halvings or 2 doublings); the hard stop below ends
-// the loop even if that reasoning failed, with status "no root".
-template <bool COND>
-__global__ void __launch_bounds__(1024) root_update_kernel(const double* __restrict__ part, int n,
-                                                           RootState* st, cudaGraphConditionalHandle h) {
-  if (st->done) {
-    if constexpr (COND)
-      if (threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
-    return;
-  }
+  __threadfence();  // this block's partials, before it is counted
+  __syncthreads();
+  __shared__ int last;
+  if (threadIdx.x == 0) last = atomicAdd(&st->arrivals, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   __shared__ double tot[6];
-  // the six sums in one pass over the partials (each thread's order, and the
-  // shuffle tree per value, as six separate block sums would take them)
-  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v[k] += part[(size_t)i * 6 + k];
+    for (int k = 0; k < 6; ++k) w[k] += __ldcg(&part[(size_t)i * 6 + k]);
   }
-  block_sum<6>(v, tot);
+  block_sum<6>(w, tot);
   if (threadIdx.x != 0) return;
+  st->arrivals = 0;
   root_update_body(tot, st);
   if constexpr (COND) {
     if (!st->done && st->iters >= ROOT_EVALS_MAX + 16) {
@@ -1862,33 +1868,30 @@ __device__ void root_update_body(const double* tot, RootState* st) {
   st->ga = gn;
 }
 
-int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s, int* n_partial) {
+template <bool COND>
+static int root_eval_launch(esplit_ctx* c, const double* un, const double* d, cudaStream_t s,
+                            cudaGraphConditionalHandle h) {
   size_t n = (size_t)c->n_e * c->n_p;
   int nb = (int)((n + 255) / 256);
   Phys<double> ph = make_phys<double>(c->prm.gam, c->prm.beta, c->prm.R, c->prm.mu, c->prm.Pr);
-  ProfScope ps(c, PG_ROOT, s);
   if (c->dim == 1)
-    root_eval_kernel<1><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
+    root_eval_kernel<1, COND><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial, h);
   else if (c->dim == 2)
-    root_eval_kernel<2><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
+    root_eval_kernel<2, COND><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial, h);
   else
-    root_eval_kernel<3><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial);
+    root_eval_kernel<3, COND><<<nb, 256, 0, s>>>(un, d, c->b.J, c->b.node_cache, n, ph, c->b.root, c->b.partial, h);
   c->launches++;
-  *n_partial = nb;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_root_update(esplit_ctx* c, int n_partial, cudaStream_t s) {
+int launch_root_eval(esplit_ctx* c, const double* un, const double* d, cudaStream_t s) {
   ProfScope ps(c, PG_ROOT, s);
-  root_update_kernel<false><<<1, 1024, 0, s>>>(c->b.partial, n_partial, c->b.root, 0);
-  c->launches++;
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  return root_eval_launch<false>(c, un, d, s, 0);
 }
 
-int launch_root_update_cond(esplit_ctx* c, int n_partial, cudaStream_t s, cudaGraphConditionalHandle h) {
-  root_update_kernel<true><<<1, 1024, 0, s>>>(c->b.partial, n_partial, c->b.root, h);
-  c->launches++;
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+int launch_root_eval_cond(esplit_ctx* c, const double* un, const double* d, cudaStream_t s,
+                          cudaGraphConditionalHandle h) {
+  return root_eval_launch<true>(c, un, d, s, h);
 }
 
 // one record per completed step of a graph-launched batch, at the slot the
@@ -1942,9 +1945,6 @@ int launch_root_start(esplit_ctx* c, double dt, cudaStream_t s) {
 
 }  // namespace esplit
 
-#include "vjp.cuh"
-#include "visc_vjp.cuh"
-#include "rrk_vjp.cuh"
 #include "hybrid.cuh"
 
 namespace esplit {

@@ -326,3 +326,46 @@ def test_full_size_against_extended_precision(lib):
         print(f"GPU vs 50 digits, {scheme}: max err/(eps scale) {float((err / (eps * sc)).max()):.2f}, "
               f"plain max-norm rel {rel_err(r, gold[scheme]):.2e}")
         assert np.all(err <= 4.0 * eps * sc)
+
+
+def test_rrk_multi_pass_root_parity(lib):
+    """Steps large enough that Halley's step from g = 1 is not accepted, so
+    the device root solve takes further evaluation passes (each pass's last
+    block updates the root state that the next pass reads): g and the new
+    state against the oracle's bisection (g 1e-10, state 1e-12), and the same
+    step as a CUDA graph (esplit_rrk_steps, the passes in a conditional while
+    node) equal to the single step."""
+    R, Dg, rrk, OP = _oracle()
+    op, m = _mesh(2, N=6)
+    u0 = states.add_uniform_noise(states.isentropic_vortex(m), 2e-2, 9)
+    rhs = lambda x: R.residual(x, op, m, OP(), dissipation=True)
+    chosen = None
+    for cfl in (0.5, 1.0, 1.5, 2.0, 3.0):
+        dt = states.cfl_timestep(m, u0, cfl)
+        s = lib.Solver(op, m, lib.Params(dissipation=True))
+        ud = s.to_device(u0)
+        try:
+            g, info = s.rrk_step(ud, dt)
+        except lib.EsplitError:
+            s.close()
+            continue
+        if info.iterations >= 2:
+            chosen = (cfl, dt, g, info, ud.cpu().numpy())
+            s.close()
+            break
+        s.close()
+    if chosen is None:
+        pytest.skip("every step size tried was accepted after one pass or failed")
+    cfl, dt, g, info, u1 = chosen
+    uo, io = rrk.rrk4_step(torch.as_tensor(u0), dt, rhs, op, m, OP())
+    print(f"CFL {cfl}: {info.iterations} evaluation passes, g {g:.15f} (oracle {io.g:.15f})")
+    assert abs(g - io.g) <= 1e-10
+    assert rel_err(u1, uo.numpy()) <= 1e-12
+    a = lib.Solver(op, m, lib.Params(dissipation=True))
+    b = lib.Solver(op, m, lib.Params(dissipation=True))
+    ua, ub = a.to_device(u0), b.to_device(u0)
+    gs = [a.rrk_step(ua, dt)[0]]
+    gb, _ = b.rrk_steps(ub, dt, 1)
+    assert gb == gs and torch.equal(ua, ub)
+    a.close()
+    b.close()
