@@ -197,6 +197,9 @@ void esplit_destroy(esplit_ctx* c) {
   if (c->sg.graph) cudaGraphDestroy(c->sg.graph);
   if (c->cap_s) cudaStreamDestroy(c->cap_s);
   if (c->cap_s2) cudaStreamDestroy(c->cap_s2);
+  if (c->side_s) cudaStreamDestroy(c->side_s);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   dfree(c->hist);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
@@ -630,6 +633,11 @@ static int rrk_prepare(esplit_ctx* c, const double* u, double dt) {
     if ((rc = dalloc(c, &c->b.dacc, n))) return rc;
     if ((rc = dalloc(c, &c->b.node_cache, 3 * (size_t)c->n_e * c->n_p))) return rc;
   }
+  if (esplit::uses_f32_path(c) && !c->side_s) {
+    CK(cudaStreamCreateWithFlags(&c->side_s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
   return ESPLIT_OK;
 }
 
@@ -647,8 +655,19 @@ static int rrk_enqueue_stages(esplit_ctx* c, const double* u, double dt, cudaStr
   const int ent_cap = (int)std::max<size_t>((size_t)c->n_e * c->n_p / 256 + 1, (size_t)c->n_e);
   int off = 2 * ent_cap;
   // stage 0: the split volume kernel computes the entropy of u_n on the way
-  // (entropy-split scheme); otherwise the entropy kernel does
-  c->ent_part = c->b.partial;
+  // (entropy-split scheme); otherwise the entropy kernel does.  On the
+  // float32 path (whose kernels leave the float64 pipe mostly idle) it runs on
+  // the side stream from the start of the step, joined before the reduction
+  const bool side = esplit::uses_f32_path(c) && c->side_s;
+  int ne_side = 0;
+  if (side) {
+    CK(cudaEventRecord(c->ev_fork, s));
+    CK(cudaStreamWaitEvent(c->side_s, c->ev_fork, 0));
+    if (esplit::launch_entropy(c, u, c->side_s, &ne_side, c->b.node_cache, c->b.partial))
+      return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
+    CK(cudaEventRecord(c->ev_join, c->side_s));
+  }
+  c->ent_part = side ? nullptr : c->b.partial;
   c->ent_n = 0;
   for (int i = 0; i < 4; ++i) {
     const double* Ui = (i == 0) ? u : c->b.stage_u;
@@ -656,7 +675,7 @@ static int rrk_enqueue_stages(esplit_ctx* c, const double* u, double dt, cudaStr
     if (i == 0) {
       c->ent_part = nullptr;
       if (rc) return rc;
-      int ne = c->ent_n;
+      int ne = side ? ne_side : c->ent_n;
       if (ne == 0 && esplit::launch_entropy(c, u, s, &ne, c->b.node_cache, c->b.partial))
         return fail(c, ESPLIT_ERR_CUDA, "entropy launch");
       R.off[0] = 0;
@@ -676,6 +695,7 @@ static int rrk_enqueue_stages(esplit_ctx* c, const double* u, double dt, cudaStr
       return fail(c, ESPLIT_ERR_CUDA, "stage launch");
   }
   R.n = 5;
+  if (side) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
   if (esplit::launch_reduce_regions(c, c->b.partial, R, s)) return fail(c, ESPLIT_ERR_CUDA, "reduce");
   if (esplit::launch_root_start(c, dt, s)) return fail(c, ESPLIT_ERR_CUDA, "root init");
   return ESPLIT_OK;

@@ -151,6 +151,10 @@ struct esplit_ctx {
   unsigned long long version = 1;
   StepGraph sg;
   cudaStream_t cap_s = nullptr, cap_s2 = nullptr;  // capture streams (non-blocking)
+  // side stream of the relaxation step on the float32 path: the float64
+  // entropy of u_n runs there beside the stages (fork and join events)
+  cudaStream_t side_s = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void* hist = nullptr;                            // StepRecord[HIST_CAP] + int counter
   bool prof = false;
   std::vector<esplit::ProfRec> recs;
@@ -209,6 +213,7 @@ struct StepRecord {
 int launch_step_record(esplit_ctx* c, StepRecord* hist, int* counter, int cap, cudaStream_t s);
 int launch_root_apply(esplit_ctx* c, double* un, const double* d, size_t n, cudaStream_t s);
 int set_ref_tables(const RefTables& t);
+bool uses_f32_path(const esplit_ctx* c);  // the residual takes the float32 path (fp32.cu)
 int set_ref_tables_vjp(const RefTables& t);  // the reverse-mode unit's copy (vjp.cu)
 // float32 path of the inviscid split scheme (fp32.cu): its own copy of the
 // reference tables, and the launcher (volume kernel, then facet kernel adding

@@ -1284,6 +1284,8 @@ static bool use_f32_path(const esplit_ctx* c) {
   return c->prm.precision == ESPLIT_FP32 && c->prm.scheme == ESPLIT_SCHEME_SPLIT && !c->prm.viscous && c->dim <= 2;
 }
 
+bool uses_f32_path(const esplit_ctx* c) { return use_f32_path(c); }
+
 int launch_residual(esplit_ctx* c, const double* u, double* r, cudaStream_t s, double* prod, int* n_partial) {
   if (use_f32_path(c)) return launch_split_f32(c, u, r, s, prod, n_partial, c->b.sat);
   if (c->prm.precision != ESPLIT_FP64) return residual_t<float>(c, u, r, s, prod, n_partial, c->b.sat);
@@ -1694,6 +1696,9 @@ __global__ void __launch_bounds__(256) root_eval_kernel(const double* __restrict
   __threadfence();
   __shared__ double tot[6];
   double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  // unrolled so that the loads of several rounds are in flight together (the
+  // partials come from L2; the sums keep each thread's round order)
+#pragma unroll 4
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] += __ldcg(&part[(size_t)i * 6 + k]);
