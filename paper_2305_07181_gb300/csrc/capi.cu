@@ -764,8 +764,9 @@ void drop_step_graph(esplit_ctx* c) {
 
 // Records one relaxation step for state u and dt as a CUDA graph: the stages,
 // reductions and root start as captured from rrk_enqueue_stages, the root
-// solve as a conditional while node whose body is one evaluation pass and one
-// update (the update clears the loop condition once the root is done), then
+// solve as a conditional while node whose body is one evaluation pass with its
+// root update (the pass's last block clears the loop condition once the root
+// is done), then
 // the guarded update of u and the step record.  The launches are the ones
 // esplit_rrk_step makes, in the same order, so the results are identical.
 static int rrk_capture(esplit_ctx* c, double* u, double dt) {
