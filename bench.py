@@ -238,7 +238,7 @@ def measure_fp64_peak(es, device):
     and the float64 divide and the library's log and exp, each as a cost in
     float64 FMAs."""
     names = ((0, "dfma"), (1, "dmma"), (2, "dfma_and_dmma"), (3, "ffma"), (4, "ddiv"), (5, "dlog"), (6, "dexp"),
-             (7, "dlog_cuda"), (8, "dexp_cuda"), (9, "cvt_round_trip"))
+             (7, "dlog_cuda"), (8, "dexp_cuda"), (9, "cvt_round_trip"), (10, "bf16_mma_sync"))
     out = {}
     with ClockSampler(device) as clk:
         for mode, name in names:
@@ -258,11 +258,12 @@ def measure_fp64_peak(es, device):
     cost = {k: dfma_per_s / out[k] for k in ("ddiv", "dlog", "dexp", "dlog_cuda", "dexp_cuda", "cvt_round_trip")}
     cost["ffma"] = dfma_per_s / (out["ffma"] / 2.0)
     return {"tflops": out["dfma"] / 1e12, "sm_mhz": mhz, "dfma_per_clk_per_sm": per_clk["dfma"],
+            "bf16_mma_sync_tflops": out["bf16_mma_sync"] / 1e12,
             "fma_per_clk_per_sm": per_clk, "cost_in_dfma": cost, "rates": out, "reasons": c["reasons"],
             "how": "esplit_measure_fp64: independent chains (8 per thread, 2048 threads per SM) of float64 FMA, "
                    "float64 MMA m8n8k4, both interleaved, float32 FMA, float64 divide, the library's and CUDA's "
-                   "log and exp, a float64-float32-float64 round trip; best launch each, SM clock sampled "
-                   "meanwhile"}
+                   "log and exp, a float64-float32-float64 round trip, the warp-level bf16 MMA; best launch "
+                   "each, SM clock sampled meanwhile"}
 
 
 def vs_hadamard(es, device, flush, p, N):

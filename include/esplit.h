@@ -122,10 +122,12 @@ int esplit_math_eval(int fn, const double* x_dev, double* y_dev, size_t n, void*
  *   mode 5: chains of the library's float64 log (x <- log x + 2.5);
  *   mode 6: chains of the library's float64 exp (x <- exp(-x));
  *   modes 7, 8: the same chains with the CUDA math library's log and exp;
- *   mode 9: chains of a float64 -> float32 -> float64 round trip and an FMA.
+ *   mode 9: chains of a float64 -> float32 -> float64 round trip and an FMA;
+ *   mode 10: chains of the warp-level bf16 tensor-core MMA (mma.sync
+ *           m16n8k16, float32 accumulation), 8 per warp.
  * The best of five timed launches after one warm-up, on the legacy default
- * stream.  *rate receives FLOP/s (2 per FMA) for modes 0-3 and operations
- * per second for modes 4-9, *ms (may be NULL) the launch time.
+ * stream.  *rate receives FLOP/s (2 per FMA) for modes 0-3 and 10 and
+ * operations per second for modes 4-9, *ms (may be NULL) the launch time.
  * ESPLIT_ERR_ARG for another mode.  Synchronises the device's default
  * stream. */
 int esplit_measure_fp64(int device, int mode, double* rate, double* ms);

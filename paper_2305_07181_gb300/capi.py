@@ -251,8 +251,9 @@ def esplit_measure_fp64(device: int = 0, mode: int = 0):
     """(rc, rate, ms per timed launch): FLOP/s of float64 FMA chains (mode 0),
     float64 tensor-core MMA chains (1), both interleaved (2), float32 FMA
     chains (3); operations per second of float64 divide (4), the library's
-    log (5) and exp (6), the CUDA library's log (7) and exp (8), and a
-    float64 -> float32 -> float64 round trip with an FMA (9)."""
+    log (5) and exp (6), the CUDA library's log (7) and exp (8), a
+    float64 -> float32 -> float64 round trip with an FMA (9); FLOP/s of the
+    warp-level bf16 tensor-core MMA (10)."""
     f, ms = ctypes.c_double(), ctypes.c_double()
     rc = lib.esplit_measure_fp64(device, mode, ctypes.byref(f), ctypes.byref(ms))
     return rc, f.value, ms.value

@@ -21,6 +21,8 @@
 //         so no value leaves the range the functions are timed on.  The add
 //         of modes 4, 5, 7 and the FMA of mode 9 count as part of the
 //         operation.
+// mode 10: the warp-level bf16 tensor-core MMA (see bf16_mma_rate_kernel),
+//         FLOP/s.
 #include <cuda_runtime.h>
 
 #include "../../include/esplit.h"
@@ -40,6 +42,30 @@ __device__ __forceinline__ void dmma_step(double& d0, double& d1, double a, doub
 }
 
 __device__ float g_calib_sink32;
+
+// mode 10: the warp-level bf16 tensor-core MMA (mma.sync m16n8k16, float32
+// accumulation, 4,096 FLOP per warp instruction), CHAINS independent
+// accumulator tiles per warp; the bf16 operands are small constants, so the
+// accumulators grow by at most 16 * 2^-14 a step
+__global__ void __launch_bounds__(THREADS) bf16_mma_rate_kernel(int iters) {
+  float d[CHAINS][4];
+#pragma unroll
+  for (int j = 0; j < CHAINS; ++j) d[j][0] = d[j][1] = d[j][2] = d[j][3] = 0.0f;
+  const unsigned a = 0x3C003C00u;  // two bf16 2^-7
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < CHAINS; ++j)
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+          "{%0, %1, %2, %3};"
+          : "+f"(d[j][0]), "+f"(d[j][1]), "+f"(d[j][2]), "+f"(d[j][3])
+          : "r"(a), "r"(a), "r"(a), "r"(a), "r"(a), "r"(a));
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < CHAINS; ++j) s += d[j][0] + d[j][1] + d[j][2] + d[j][3];
+  if (s == -1.0f) g_calib_sink32 = s;
+}
 
 __global__ void __launch_bounds__(THREADS) fp32_rate_kernel(int iters, float a, float b) {
   float x[CHAINS];
@@ -117,7 +143,8 @@ double ops_per_launch(int blocks, int iters) {
   if (MODE == 0 || MODE == 2 || MODE == 3) f += 2.0 * threads * CHAINS * iters;
   if (MODE == 1) f += 2.0 * warps * CHAINS * iters * 256.0;
   if (MODE == 2) f += 2.0 * warps * (CHAINS / 2) * iters * 256.0;
-  if (MODE >= 4) f += threads * CHAINS * iters;
+  if (MODE >= 4 && MODE <= 9) f += threads * CHAINS * iters;
+  if (MODE == 10) f += warps * CHAINS * iters * 4096.0;
   return f;
 }
 
@@ -125,7 +152,7 @@ double ops_per_launch(int blocks, int iters) {
 template <int MODE>
 constexpr int iters_for() {
   return MODE == 0 ? 4096 : MODE == 3 ? 65536 : MODE == 4 ? 512 : MODE == 5 ? 128 : MODE == 6 ? 256
-       : MODE == 7 ? 128 : MODE == 8 ? 256 : MODE == 9 ? 1024 : 512;
+       : MODE == 7 ? 128 : MODE == 8 ? 256 : MODE == 9 ? 1024 : MODE == 10 ? 16384 : 512;
 }
 
 template <int MODE>
@@ -146,6 +173,8 @@ int measure(int n_sm, double* rate, double* ms_out) {
     cudaEventRecord(e0, 0);
     if constexpr (MODE == 3)
       fp32_rate_kernel<<<blocks, THREADS>>>(iters, (float)a, (float)b);
+    else if constexpr (MODE == 10)
+      bf16_mma_rate_kernel<<<blocks, THREADS>>>(iters);
     else
       fp64_rate_kernel<MODE><<<blocks, THREADS>>>(iters, a, b);
     cudaEventRecord(e1, 0);
@@ -165,7 +194,7 @@ int measure(int n_sm, double* rate, double* ms_out) {
 }  // namespace
 
 extern "C" int esplit_measure_fp64(int device, int mode, double* rate, double* ms_out) {
-  if (!rate || mode < 0 || mode > 9) return ESPLIT_ERR_ARG;
+  if (!rate || mode < 0 || mode > 10) return ESPLIT_ERR_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return ESPLIT_ERR_CUDA;
   int n_sm = 0;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return ESPLIT_ERR_CUDA;
@@ -179,6 +208,7 @@ extern "C" int esplit_measure_fp64(int device, int mode, double* rate, double* m
     case 6: return measure<6>(n_sm, rate, ms_out);
     case 7: return measure<7>(n_sm, rate, ms_out);
     case 8: return measure<8>(n_sm, rate, ms_out);
-    default: return measure<9>(n_sm, rate, ms_out);
+    case 9: return measure<9>(n_sm, rate, ms_out);
+    default: return measure<10>(n_sm, rate, ms_out);
   }
 }
