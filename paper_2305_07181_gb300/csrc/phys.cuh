@@ -398,8 +398,15 @@ __device__ __forceinline__ void sy_flux_dir(const PairAvg<T, D>& a, const C& c, 
 template <typename T, int D, typename C>
 __device__ __forceinline__ void diss_apply(const PairAvg<T, D>& a, const C& c, const T* n, const T* dw,
                                            T* out) {
-  T rho_h = a.z1a / (a.A1 * a.E1);
-  T iz = T(1) / a.z1a;
+  // the reciprocals of z1a, A1 E1 and p_h, and eta, from one division:
+  // D0 = 1/(z1a A1 E1 E2 p_h)
+  const T ae = a.A1 * a.E1;
+  T p_h = a.pa;
+  const T D0 = T(1) / (a.z1a * ae * a.E2 * p_h);
+  const T iz = ae * a.E2 * p_h * D0;        // 1/z1a
+  const T iae = a.z1a * a.E2 * p_h * D0;    // 1/(A1 E1)
+  const T ip_h = a.z1a * ae * a.E2 * D0;    // 1/p_h
+  T rho_h = a.z1a * iae;
   T Vh[D];
   T vh2 = T(0), vn = T(0);
 #pragma unroll
@@ -408,10 +415,9 @@ __device__ __forceinline__ void diss_apply(const PairAvg<T, D>& a, const C& c, c
     vh2 += Vh[i] * Vh[i];
     vn += Vh[i] * n[i];
   }
-  T p_h = a.pa;
-  T theta = rho_h / (p_h * a.A1 * a.E1);
-  T eta = T(1) / (a.z1a * a.E2 * a.E1);
-  T ah = t_sqrt(c.gam * p_h / rho_h);
+  T theta = rho_h * iae * ip_h;             // rho_h / (p_h A1 E1)
+  T eta = a.A1 * p_h * D0;                  // 1/(z1a E2 E1)
+  T ah = t_sqrt(c.gam * p_h * ae * iz);     // sqrt(gam p_h / rho_h)
   T Hh = ah * ah * c.inv_gm1 + T(0.5) * vh2;
   constexpr int NC = D + 2;
   // columns of X^
