@@ -68,7 +68,7 @@ def test_1d_fp64_parity(lib, p, scheme, diss):
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_1d_fp32_and_entropy(lib, p):
+def test_1d_fp32_bulk_and_entropy(lib, p):
     R, Dg, rrk, Hy, OP = _oracle()
     op = line_operator(p)
     m = periodic_line_mesh(op, 64, 2.0, amp=0.1)
@@ -76,7 +76,7 @@ def test_1d_fp32_and_entropy(lib, p):
     s = lib.Solver(op, m, lib.Params(dissipation=True, precision="fp32_bulk"))
     ud = s.to_device(u)
     err = rel_err(s.residual(ud).cpu().numpy(), R.residual(u, op, m, OP(), dissipation=True).numpy())
-    print(f"1D p={p} fp32 split rel err {err:.2e}")
+    print(f"1D p={p} fp32_bulk split rel err {err:.2e}")
     assert err <= 1e-11
     ur = states.random_positive_state(m.n_e, 1, op.n_p, seed=40 + p)
     udr = s.to_device(ur)
