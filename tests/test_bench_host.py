@@ -64,3 +64,26 @@ def test_reference_arm_two_ranks():
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1 and json.loads(lines[0])["n_gpus"] == 2
+
+
+def test_roofline_byte_and_flop_counts():
+    """The algorithmic counts the bench divides by the live kernel times,
+    against hand counts at config 2 (32,768 triangles, p = 3: 18 nodes, 12
+    facet slots, 196,608 node pairs)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n_e, n_p, d, n_pairs = 32768, 18, 2, 196608
+    nc = d + 2
+    # float64 split kernel: 2d contractions of n_p x n_p with n_p x nc, plus the pointwise count
+    assert bench.algorithmic_flops("split_volume", n_e, n_p, d, n_pairs) == n_e * (4 * d * n_p * n_p * nc
+                                                                                  + n_p * (30 + 43 * d))
+    assert bench.algorithmic_flops("split_volume", n_e, n_p, d, n_pairs) == 408158208
+    # float32 volume kernel: float32 D_i, float64 u in and r out, float32 1/(H J) and facet scratch
+    per_el = 4 * d * n_p * n_p + 16 * n_p * nc + 4 * n_p + 4 * 12 * nc
+    assert bench.algorithmic_bytes_f32_volume(n_e, n_p, d, n_pairs) == n_e * per_el == 131334144
+    prof = {"split_volume": (0.4, 10)}  # 10 launches, 0.4 ms in total
+    rl = bench.f32_volume_roofline(prof, n_e, n_p, d, n_pairs)
+    assert rl["bound"] == "hbm" and rl["unit"] == "GB/s"
+    assert abs(rl["achieved"] - 131334144 / 0.04e-3 / 1e9) < 1e-6
+    assert abs(rl["frac"] - rl["achieved"] / rl["peak"]) < 1e-12
+    assert bench.f32_volume_roofline({}, n_e, n_p, d, n_pairs) is None
